@@ -1,0 +1,416 @@
+"""Benchmark of the three-table plan on GB300 through the C ABI.
+
+Default workload (one GPU): x100 -- D 1.5M, M 15M, F 60M rows resident in
+HBM; D.seg == 1, M.date < 1200, F.date2 > 1200; join F-M-D; group by M key
+SUM(price * (100 - disc)); top-10.  A step is one pq_run_plan over the whole
+workload.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload x100|small|skew] [--mode plan|serve|stream]
+
+--impl reference times the CPU oracle (the plain relational definition,
+single-threaded) on the same workload, metric and unit.
+--mode serve: batched / served execution of a query stream against the plain
+one-query-at-a-time path (queries/s, p50/p99 latency).
+--mode stream: the storage-resident plan (x2000 by default) streamed from
+pinned host memory, against the measured host-to-device link.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "plan rows/s and GB/s vs HBM/host-link roofline; p50/p99 latency batched vs plain"
+L2_BYTES = 129 * 2**20
+WORKLOAD_TEXT = {
+    "small": "small: D 15k, M 150k, F 600k rows",
+    "x100": "x100: D 1.5M, M 15M, F 60M rows, all columns resident in HBM",
+    "x2000": "x2000: D 30M, M 300M, F 1.2B rows in pinned host memory, 128 MiB chunks, "
+             "16 GB device budget",
+    "skew": "skew: D 4M, M 40M, F 200M rows, Zipf(1.0) foreign keys, pass-all predicates",
+}
+QUERY_TEXT = ("D.seg == 1, M.date < 1200, F.date2 > 1200; join F-M-D; group by M.key "
+              "SUM(price*(100-disc)) int64; top-10")
+
+
+def table_bytes(n_d, n_m, n_f):
+    """Algorithmic bytes of a plan: every referenced column read once."""
+    return 5 * n_d + 16 * n_m + 21 * n_f
+
+
+def query(name):
+    import datagen
+    q = dict(datagen.QUERY)
+    if name == "skew":
+        return dict(seg=0, m_date_lt=0, f_date_gt=0, k=10, d_op="all", m_op="all", f_op="all")
+    return dict(seg=q["seg"], m_date_lt=q["m_date_lt"], f_date_gt=q["f_date_gt"], k=q["k"],
+                d_op="==", m_op="<", f_op=">")
+
+
+# ------------------------------------------------------------------ clocks ----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers ----
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pq_plan_kernels.cuh", "pq_dev.cuh", "pq_topk.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_02862_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        t = json.load(fh)
+    e = t.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- CPU side ----
+def cpu_oracle_rate(D, M, F, q, budget_s=20.0, max_runs=3):
+    """Oracle (single-threaded) on the workload: F rows per second."""
+    import oracle
+    oracle.build()
+    runs, t_total = 0, 0.0
+    n_f = len(F["mkey"])
+    while runs < max_runs and t_total < budget_s:
+        t0 = time.perf_counter()
+        oracle.run_plan(D, M, F, **q)
+        t_total += time.perf_counter() - t0
+        runs += 1
+    return n_f * runs / t_total, runs, t_total
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import datagen
+    import oracle
+    oracle.build()
+    D, M, F = datagen.workload(args.workload)
+    q = query(args.workload)
+    # Each step runs the oracle on a bounded F prefix (D and M whole) so that
+    # warm-up plus timed steps end within a few minutes.
+    f_sample = min(len(F["mkey"]), args.ref_f_rows)
+    Fs = {k: v[:f_sample] for k, v in F.items()}
+    for _ in range(args.warmup):
+        oracle.run_plan(D, M, Fs, **q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run_plan(D, M, Fs, **q)
+    t = time.perf_counter() - t0
+    value = f_sample * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "query": QUERY_TEXT},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"F rows [0, {f_sample}) with D and M whole, per step"},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side ----
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    import datagen
+    rank, world, local = dist_setup(args.gpus)
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+
+    w = datagen.WORKLOADS[args.workload]
+    n_d, n_m, n_f = w["n_d"], w["n_m"], w["n_f"]
+    q = query(args.workload)
+    # Pinned host copies of the tables (for the end-to-end leg), device copies
+    # (resident leg).
+    host = {}
+    for name, cols, n in (("D", datagen.D_COLS, n_d), ("M", datagen.M_COLS, n_m),
+                          ("F", datagen.F_COLS, n_f)):
+        host[name] = {c: torch.empty(n, dtype=getattr(torch, np.dtype(dt).name), pin_memory=True)
+                      for c, dt in cols}
+    out = {k: {c: t.numpy() for c, t in v.items()} for k, v in host.items()}
+    D, M, F = datagen.workload(args.workload, out=out)
+    dev = {k: {c: t.cuda() for c, t in v.items()} for k, v in host.items()}
+    torch.cuda.synchronize()
+
+    s = torch.cuda.Stream()
+    ctx = pq.Context(arena_bytes=args.arena_gb << 30, profile=1)
+    with torch.cuda.stream(s):
+        TD = pq.pq_load_columns(ctx, [dev["D"]["key"], dev["D"]["seg"]], stream=s)
+        TM = pq.pq_load_columns(ctx, [dev["M"]["key"], dev["M"]["dref"], dev["M"]["date"]],
+                                stream=s)
+        TF = pq.pq_load_columns(ctx, [dev["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                                stream=s)
+    plan = pq.make_plan(TD, TM, TF, **q)
+    res = pq.pinned_results(1)
+
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pq.pq_run_plan(ctx, plan, res[0], stream=s)
+        ctx.sync(s)
+    check = res[0].as_dict()
+    ctx.profile_reset()
+    launches0 = ctx.stats()["kernel_launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(s):
+            ev0.record(s)
+            evs = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                pq.pq_run_plan(ctx, plan, res[0], stream=s)
+                evs.append(a)
+            ev1.record(s)
+        torch.cuda.synchronize()
+        barrier(world)
+    ctx.sync(s)
+    t_ms = ev0.elapsed_time(ev1)
+    evs.append(ev1)
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(evs) - 1)]
+    t_ms = max_over_ranks(t_ms, world)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    fprobe_ms, fprobe_n = ctx.profile("plan_fprobe")
+    per_stage = {}
+    for nm in ("plan_dscan", "plan_dfill", "plan_dbuild", "plan_mscan", "plan_mfill",
+               "plan_mbuild", "plan_fprobe", "plan_topk"):
+        try:
+            ms, n = ctx.profile(nm)
+            per_stage[nm] = round(ms / max(n, 1), 5)
+        except pq.PQError:
+            pass
+    assert res[0].as_dict() == check, "results changed between steps"
+
+    value = world * n_f * args.steps / (t_ms / 1e3)
+    plan_bytes = table_bytes(n_d, n_m, n_f)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    # Dominant kernel: the F probe.  Algorithmic bytes per launch: date2 and
+    # mkey of every F row (12 B/row); price and disc of the ~0.5 % matching
+    # rows are not counted.
+    fprobe_bytes = 12 * n_f
+    fprobe_avg_s = fprobe_ms / max(fprobe_n, 1) / 1e3
+    achieved = fprobe_bytes / fprobe_avg_s / 1e9
+    roofline = {"kernel": "k_plan_fprobe", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": ncu_traffic("k_plan_fprobe", args.workload),
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src ==
+                "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": fprobe_bytes,
+                "avg_launch_ms": round(fprobe_avg_s * 1e3, 5), "launches": fprobe_n}
+
+    # End to end through the public API with host buffers: the tables stream
+    # from pinned host memory each step (host-to-device copies inside the timed
+    # region) and the result is read back to pinned host memory.
+    e2e = None
+    if not args.no_e2e:
+        ctx2 = pq.Context(arena_bytes=args.arena_gb << 30)
+        with torch.cuda.stream(s):
+            HD = pq.pq_load_columns(ctx2, [host["D"]["key"], host["D"]["seg"]],
+                                    mode=pq.PQ_STREAMING)
+            HM = pq.pq_load_columns(ctx2, [host["M"][c] for c in ("key", "dref", "date")],
+                                    mode=pq.PQ_STREAMING)
+            HF = pq.pq_load_columns(ctx2, [host["F"][c] for c in ("mkey", "price", "disc",
+                                                                 "date2")],
+                                    mode=pq.PQ_STREAMING)
+            hplan = pq.make_plan(HD, HM, HF, **q)
+            hres = pq.pinned_results(1)
+            pq.pq_run_plan(ctx2, hplan, hres[0], stream=s)
+            ctx2.sync(s)
+            st0 = ctx2.stats()
+            k_e2e = max(1, min(args.steps, args.e2e_steps))
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                pq.pq_run_plan(ctx2, hplan, hres[0], stream=s)
+                ctx2.sync(s)
+            t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+            st1 = ctx2.stats()
+        assert hres[0].as_dict() == check, "end-to-end result differs from resident result"
+        e2e = {"value": world * n_f * k_e2e / t_e2e, "unit": "rows/s",
+               "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // k_e2e,
+               "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // k_e2e,
+               "steps": k_e2e, "ms_per_step": 1e3 * t_e2e / k_e2e,
+               "path": "pq_run_plan on PQ_STREAMING tables in pinned host memory"}
+        ctx2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, runs, secs = cpu_oracle_rate(D, M, F, q)
+        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": f"{runs} full run(s) of the plan on the same workload "
+                         f"({secs:.1f} s, single thread)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "query": QUERY_TEXT,
+                   "l2": f"inputs ({plan_bytes / 1e9:.2f} GB) larger than L2 (129 MB); "
+                         "no flush between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "gb_per_s": round(world * plan_bytes * args.steps / (t_ms / 1e3) / 1e9, 1),
+        "plan_frac_of_hbm": round(plan_bytes * args.steps / (t_ms / 1e3) / 1e9 / hbm, 4),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "stage_ms": per_stage,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "result": {"ngroups": check["ngroups"], "top_key": check["keys"][:1]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="x100", choices=["small", "x100", "skew"])
+    ap.add_argument("--arena-gb", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-f-rows", type=int, default=20_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+// pq_dev.cuh -- device helpers shared by the kernels of libpq.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pqk {
+
+typedef long long i64;
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr i64 kEmpty = (i64)0x8000000000000000ULL;  // INT64_MIN marks a free slot
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxK = 64;
+
+// Device status word: first error wins; `detail` carries a count or index.
+struct DevStatus {
+  int code;
+  int pad;
+  i64 detail;
+};
+
+__device__ __forceinline__ void latch(DevStatus* st, int code, i64 detail) {
+  if (atomicCAS(&st->code, 0, code) == 0) atomicExch((u64*)&st->detail, (u64)detail);
+}
+
+// Predicate "v op c" lowered on the host to a closed range with a negation:
+// pass = (lo <= v <= hi) xor neg.  '<' c -> [MIN, c-1], '==' c -> [c, c],
+// '!=' c -> [c, c] negated, always-true -> [MIN, MAX].
+struct Pred {
+  i64 lo, hi;
+  int neg, pad;
+};
+__device__ __forceinline__ bool pass(const Pred& p, i64 v) {
+  return ((v >= p.lo) & (v <= p.hi)) ^ (p.neg != 0);
+}
+
+// Hash-table slot hash: the MurmurHash3 64-bit finaliser (Appleby), so that
+// dense or strided keys spread over a power-of-two table.
+__device__ __forceinline__ u64 slot_hash(i64 k) {
+  u64 x = (u64)k;
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return x;
+}
+
+// Radix bucket: Fibonacci hashing (Knuth), top log2P bits of k * 2^64/phi.
+__device__ __forceinline__ u32 fib_bucket(i64 k, int log2P) {
+  return log2P == 0 ? 0u : (u32)(((u64)k * 0x9E3779B97F4A7C15ULL) >> (64 - log2P));
+}
+
+// Smallest power-of-two exponent with 2^e > count / lf (and e >= 6).  The
+// host sizes every table region with this same function from an upper bound
+// of the count, so the device's choice always fits the region.
+__host__ __device__ __forceinline__ int cap_log2(i64 count, int lf1024) {
+  i64 need = (count * 1024 + lf1024 - 1) / lf1024 + 1;
+  int e = 6;
+  while (((i64)1 << e) < need) ++e;
+  return e;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+
+__device__ __forceinline__ u32 lanemask_lt() {
+  u32 m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Reserve `cnt` consecutive output positions per lane from a global counter
+// with one atomic per warp.  Every lane of the warp must call it.
+__device__ __forceinline__ u64 warp_reserve(u64* counter, u32 cnt) {
+  const int lane = threadIdx.x & 31;
+  u32 incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u32 y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  u32 total = __shfl_sync(kFull, incl, 31);
+  u64 base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, (u64)total);
+  base = __shfl_sync(kFull, base, 31);
+  return base + (incl - cnt);
+}
+
+// Bounded spin: returns false once `limit` polls have been spent.
+struct Spin {
+  i64 left;
+  __device__ explicit Spin(i64 limit) : left(limit) {}
+  __device__ __forceinline__ bool again() {
+    if (--left <= 0) return false;
+    __nanosleep(64);
+    return true;
+  }
+};
+
+__device__ __forceinline__ u64 ld_volatile_u64(const u64* p) {
+  return *(const volatile u64*)p;
+}
+__device__ __forceinline__ void st_volatile_u64(u64* p, u64 v) { *(volatile u64*)p = v; }
+
+// A counter that other blocks of this kernel updated with atomics (read by
+// the block that finishes last, after its fence).
+__device__ __forceinline__ i64 ld_count(const u64* p) { return (i64)ld_volatile_u64(p); }
+
+// Single-pass tile prefix by decoupled look-back (Merrill & Garland, "Single-
+// pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA TR 2016).  Each
+// status word packs a 2-bit flag (0 not ready, 1 aggregate, 2 inclusive
+// prefix) and a 62-bit non-negative value.  Called by one full warp of the
+// block that owns `tile`; returns the exclusive prefix of `tile` in every
+// lane and publishes tile's inclusive prefix.  Tiles must be claimed in
+// increasing order by running blocks (an atomic ticket), so every awaited
+// predecessor belongs to a resident block and the wait ends; it is still
+// bounded by `limit`, after which the status latches PQ_ERR_TIMEOUT (6) and
+// the missing part counts as zero.
+__device__ __forceinline__ i64 lookback_prefix(u64* state, i64 tile, i64 aggregate,
+                                               i64 limit, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  constexpr u64 kA = 1ULL << 62, kP = 2ULL << 62, kMask = (1ULL << 62) - 1;
+  if (tile == 0) {
+    if (lane == 0) st_volatile_u64(&state[0], kP | (u64)aggregate);
+    return 0;
+  }
+  if (lane == 0) st_volatile_u64(&state[tile], kA | (u64)aggregate);
+  i64 prefix = 0;
+  i64 idx = tile - 1 - lane;
+  Spin spin(limit);
+  bool timed_out = false;
+  while (true) {
+    u64 s = idx >= 0 ? ld_volatile_u64(&state[idx]) : kP;
+    while (__any_sync(kFull, (s >> 62) == 0)) {
+      if (!spin.again()) {
+        timed_out = true;
+        if ((s >> 62) == 0) s = kP;  // give up: count the missing tile as 0
+        break;
+      }
+      if ((s >> 62) == 0) s = ld_volatile_u64(&state[idx]);
+    }
+    const u32 pmask = __ballot_sync(kFull, (s >> 62) == 2);
+    i64 v = (i64)(s & kMask);
+    if (pmask) {
+      const int first = __ffs(pmask) - 1;  // nearest predecessor with a prefix
+      if (lane > first) v = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    prefix += v;
+    if (pmask) break;
+    idx -= 32;
+  }
+  if (timed_out && lane == 0) latch(st, 6, tile);
+  if (lane == 0) st_volatile_u64(&state[tile], kP | (u64)(prefix + aggregate));
+  return prefix;
+}
+
+}  // namespace pqk

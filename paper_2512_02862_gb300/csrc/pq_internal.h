@@ -1,0 +1,216 @@
+// pq_internal.h -- host-side internals shared by the translation units of libpq.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/pq.h"
+#include "pq_dev.cuh"
+
+namespace pqh {
+
+using pqk::i64;
+
+// ---------------------------------------------------------------------------
+// Arena: first-fit pool allocator over the caller's device buffer (the pool
+// allocator of Sec. 3.1).  Frees are stream-ordered: a block released on a
+// stream becomes reusable once an event recorded on that stream completes.
+class Arena {
+ public:
+  void init(char* base, size_t bytes);
+  void shutdown();
+  // nullptr when the request cannot be met even after waiting for pending frees.
+  void* alloc(size_t bytes, size_t align = 256);
+  void release(void* p, cudaStream_t s);  // reusable once `s` reaches this point
+  void release_now(void* p);
+  size_t in_use() const { return in_use_; }
+  size_t high_water() const { return high_; }
+  size_t capacity() const { return cap_; }
+  size_t largest_free();
+
+ private:
+  void reclaim(bool wait_one);
+  void insert_free(size_t off, size_t size);
+  char* base_ = nullptr;
+  size_t cap_ = 0, in_use_ = 0, high_ = 0;
+  std::map<size_t, size_t> free_;             // offset -> size, coalesced
+  std::unordered_map<size_t, size_t> live_;   // offset -> size
+  struct Pending { size_t off, size; cudaEvent_t ev; };
+  std::deque<Pending> pending_;
+  std::vector<cudaEvent_t> events_;
+  std::mutex mu_;
+};
+
+// Pinned host staging ring for small uploads (descriptors) and result
+// read-back: no pageable copies ever reach a stream (Sec. 4.2, "mis-sync").
+class PinnedRing {
+ public:
+  bool init(size_t slot_bytes, int slots);
+  void shutdown();
+  // Copies `bytes` (<= slot size) from `src` into a free pinned slot and
+  // enqueues the upload to `dst` on `s`.
+  cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s);
+  size_t slot_bytes() const { return slot_; }
+
+ private:
+  char* host_ = nullptr;
+  size_t slot_ = 0;
+  int n_ = 0, next_ = 0;
+  std::vector<cudaEvent_t> ev_;
+  std::mutex mu_;
+};
+
+struct Column {
+  int type = 0;           // pq_dtype
+  const void* dev = nullptr;   // device pointer (resident) or nullptr
+  pq_source src{};        // original source (streaming)
+  bool pinned = false;    // host source is page-locked
+  void* owned = nullptr;  // arena block owned by the table
+  std::string path;
+};
+
+}  // namespace pqh
+
+struct pq_table {
+  uint64_t id = 0;
+  int64_t nrows = 0;
+  int mode = 0;
+  std::vector<pqh::Column> cols;
+};
+
+struct pq_ht {
+  pqk::i64* keys = nullptr;
+  pqk::i64* vals = nullptr;
+  pqk::i64* meta = nullptr;   // [0] duplicate-key flag, [1] inserted count
+  int log2cap = 0;
+  int64_t n = 0;
+  void* block = nullptr;
+};
+
+namespace pqh {
+
+struct Profile {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+  size_t used = 0;
+  double total_ms = 0;
+  int64_t launches = 0;
+};
+
+struct PlanCache;   // pq_plan.cu
+struct Server;      // pq_serve.cu
+
+struct DsetEntry {
+  uint64_t table_id;
+  int64_t row0, rows;
+  pqk::Pred pred;
+  int lf1024;
+  void* block;        // arena block: header word (log2 of the slot count), slots
+  pqk::i64* keys;
+  int log2max;
+  cudaEvent_t ready;  // recorded after the set is built
+  uint64_t last_use;
+};
+
+}  // namespace pqh
+
+struct pq_ctx {
+  pq_options opt{};
+  int device = 0;
+  int num_sms = 0;
+  pqh::Arena arena;
+  pqh::PinnedRing ring;
+  pqk::DevStatus* d_status = nullptr;
+  pqk::DevStatus* h_status = nullptr;   // pinned mirror
+  int64_t* h_small = nullptr;            // pinned scratch for count read-backs
+  std::mutex small_mu;
+  std::mutex mu;                         // serialises API calls that touch state
+  std::string last_error;
+  std::atomic<int64_t> launches{0}, h2d{0}, d2h{0}, chunks{0}, plans{0}, replays{0};
+  std::atomic<uint64_t> next_table_id{1};
+  std::map<std::string, pqh::Profile> prof;
+  std::vector<cudaStream_t> copy_streams;
+  std::list<pqh::DsetEntry> dsets;   // stable addresses
+  uint64_t dset_tick = 0;
+  pqh::PlanCache* plan_cache = nullptr;   // owned; freed by plan_cache_destroy
+  pqh::Server* server = nullptr;          // owned; freed by server_stop
+  double last_latency_us = 0;
+  // tuning (kernel launch shapes chosen by pq_autotune or the options)
+  int tune_threads = 256;
+  int tune_bps = 2;
+};
+
+namespace pqh {
+
+pq_status fail(pq_ctx* ctx, pq_status st, const char* fmt, ...);
+pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what);
+
+#define PQ_CUDA(ctx, call)                                      \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return pqh::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// After a kernel launch: count it and turn a launch error into PQ_ERR_CUDA.
+#define PQ_LAUNCHED(ctx)                                                  \
+  do {                                                                    \
+    (ctx)->launches.fetch_add(1, std::memory_order_relaxed);              \
+    cudaError_t e_ = cudaGetLastError();                                  \
+    if (e_ != cudaSuccess) return pqh::cuda_fail(ctx, e_, "kernel launch"); \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+pqk::Pred make_pred(int op, int64_t c, bool* ok);
+size_t dtype_size(int type);
+bool valid_dtype(int type);
+int grid_persistent(pq_ctx* ctx, int threads);
+
+// Profiling: start/stop events around a kernel when ctx->opt.profile is set.
+void prof_begin(pq_ctx* ctx, const char* name, cudaStream_t s, cudaEvent_t* stop_out);
+void prof_end(cudaEvent_t stop, cudaStream_t s);
+void prof_collect(pq_ctx* ctx);
+
+// Scoped arena scratch released on a stream at scope exit.
+struct Scratch {
+  pq_ctx* ctx;
+  cudaStream_t s;
+  std::vector<void*> blocks;
+  Scratch(pq_ctx* c, cudaStream_t st) : ctx(c), s(st) {}
+  void* get(size_t bytes) {
+    void* p = ctx->arena.alloc(bytes ? bytes : 256);
+    if (p) blocks.push_back(p);
+    return p;
+  }
+  ~Scratch() {
+    for (void* p : blocks) ctx->arena.release(p, s);
+  }
+};
+
+// Launchers implemented in pq_ops.cu, used by the plan paths.
+pq_status fill_i64(pq_ctx* ctx, pqk::i64* p, int64_t n, pqk::i64 v, cudaStream_t s);
+
+// Plan internals (pq_plan.cu) used by pq_serve.cu and pq_tune.cu.
+pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
+                             cudaStream_t s, bool allow_graph);
+// Upper bound of the arena bytes a batch of these plans needs (0 if invalid).
+size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n);
+pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result,
+                             cudaStream_t s);
+bool is_pinned(const void* p);
+void plan_cache_destroy(pq_ctx* ctx);
+// Drop cached graphs that reference table `id`.
+void forget_table(pq_ctx* ctx, uint64_t id, cudaStream_t s);
+void server_stop(pq_ctx* ctx);
+
+}  // namespace pqh

@@ -1,0 +1,524 @@
+// pq_plan.cu -- resident plan driver: batches, D-set cache, CUDA-graph cache.
+#include <algorithm>
+#include <cstring>
+
+#define PQ_DEFINE_PLAN_KERNELS
+#include "pq_plan_host.h"
+
+using namespace pqk;
+
+namespace pqh {
+
+static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+bool is_pinned(const void* p) {
+  cudaPointerAttributes at{};
+  bool pinned = cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  cudaGetLastError();
+  return pinned;
+}
+
+static bool range(const pq_table* t, int64_t row0, int64_t rows, i64* r0, i64* n) {
+  if (!t || row0 < 0 || row0 > t->nrows) return false;
+  if (rows < 0) rows = t->nrows - row0;
+  if (row0 + rows > t->nrows) return false;
+  *r0 = row0;
+  *n = rows;
+  return true;
+}
+
+static bool check_types(const pq_table* t, std::initializer_list<int> types) {
+  if ((int)t->cols.size() < (int)types.size()) return false;
+  int i = 0;
+  for (int ty : types)
+    if (t->cols[i++].type != ty) return false;
+  return true;
+}
+
+pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need_resident) {
+  r = ResolvedPlan();
+  if (!p.D || !p.M || !p.F) return fail(ctx, PQ_ERR_INVALID_ARG, "plan: missing table");
+  if (!check_types(p.D, {PQ_INT32, PQ_INT8}) || !check_types(p.M, {PQ_INT64, PQ_INT32, PQ_INT32}) ||
+      !check_types(p.F, {PQ_INT64, PQ_INT64, PQ_INT8, PQ_INT32}))
+    return fail(ctx, PQ_ERR_INVALID_ARG, "plan: column types do not match D/M/F");
+  if (!range(p.D, p.d_row0, p.d_rows, &r.d_row0, &r.n_d) ||
+      !range(p.M, p.m_row0, p.m_rows, &r.m_row0, &r.n_m) ||
+      !range(p.F, p.f_row0, p.f_rows, &r.f_row0, &r.n_f))
+    return fail(ctx, PQ_ERR_INVALID_ARG, "plan: row range outside a table");
+  if (p.k < 1 || p.k > PQ_MAX_K) return fail(ctx, PQ_ERR_INVALID_ARG, "plan: k out of range");
+  float lf = p.load_factor > 0 ? p.load_factor : ctx->opt.load_factor;
+  if (lf < 0.05f || lf > 0.9f) return fail(ctx, PQ_ERR_INVALID_ARG, "plan: load factor");
+  bool ok1, ok2, ok3;
+  PlanDev& d = r.dev;
+  d.pd = make_pred(p.d_op, p.d_c, &ok1);
+  d.pm = make_pred(p.m_op, p.m_c, &ok2);
+  d.pf = make_pred(p.f_op, p.f_c, &ok3);
+  if (!ok1 || !ok2 || !ok3) return fail(ctx, PQ_ERR_INVALID_ARG, "plan: bad predicate");
+  d.k = p.k;
+  d.lf1024 = (int)(lf * 1024 + 0.5f);
+  d.n_d = r.n_d;
+  d.n_m = r.n_m;
+  d.n_f = r.n_f;
+  r.e_d = cap_log2(r.n_d, d.lf1024);
+  r.e_m = cap_log2(r.n_m, d.lf1024);
+  r.parts = std::max<i64>(1, (r.n_m + kTK - 1) / kTK);
+  const pq_table* T[3] = {p.D, p.M, p.F};
+  for (int t = 0; t < 3; ++t) {
+    r.resident[t] = true;
+    for (auto& c : T[t]->cols) r.resident[t] = r.resident[t] && c.dev != nullptr;
+    if (need_resident && !r.resident[t])
+      return fail(ctx, PQ_ERR_INVALID_ARG, "plan: table %d is not resident", t);
+  }
+  auto col = [](const pq_table* t, int c, i64 row0) -> const char* {
+    const char* base = (const char*)t->cols[c].dev;
+    return base ? base + row0 * dtype_size(t->cols[c].type) : nullptr;
+  };
+  d.d_key = (const int*)col(p.D, 0, r.d_row0);
+  d.d_seg = (const signed char*)col(p.D, 1, r.d_row0);
+  d.m_key = (const i64*)col(p.M, 0, r.m_row0);
+  d.m_dref = (const int*)col(p.M, 1, r.m_row0);
+  d.m_date = (const int*)col(p.M, 2, r.m_row0);
+  d.f_mkey = (const i64*)col(p.F, 0, r.f_row0);
+  d.f_price = (const i64*)col(p.F, 1, r.f_row0);
+  d.f_disc = (const signed char*)col(p.F, 2, r.f_row0);
+  d.f_date = (const int*)col(p.F, 3, r.f_row0);
+  const void* ptrs[9] = {d.d_key, d.d_seg, d.m_key, d.m_dref, d.m_date,
+                         d.f_mkey, d.f_price, d.f_disc, d.f_date};
+  d.vec = 1;
+  for (auto q : ptrs) d.vec &= (((uintptr_t)q) & 15) == 0;
+  return PQ_OK;
+}
+
+size_t plan_bytes(const ResolvedPlan& r) {
+  size_t b = 0;
+  if (r.builds) b += al(r.n_d * 8);                                // D list
+  if (r.builds && r.dset_from == -1) b += 256 + al(((size_t)8) << r.e_d);  // own D-set
+  const size_t slots = (size_t)1 << r.e_m;
+  b += al(r.n_m * 8);                    // M list
+  b += al(slots * 8) * 2 + al(slots * 4);  // table keys, sums, first-hit flags
+  b += al(r.n_m * 4);                    // group list
+  b += al(r.parts * r.dev.k * 8) * 2 + al(r.parts * 4);  // top-k partials
+  return b;
+}
+
+void plan_assign(ResolvedPlan& r, char* base) {
+  PlanDev& d = r.dev;
+  char* p = base;
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += al(bytes);
+    return q;
+  };
+  d.build_dset = r.builds ? 1 : 0;
+  d.dlist = r.builds ? (i64*)take(r.n_d * 8) : nullptr;
+  if (r.builds && r.dset_from == -1) {
+    char* blk = take(256 + (((size_t)8) << r.e_d));
+    d.dset_log2 = (int*)blk;
+    d.dset = (i64*)(blk + 256);
+  }
+  const size_t slots = (size_t)1 << r.e_m;
+  d.mlist = (i64*)take(r.n_m * 8);
+  d.ht_keys = (i64*)take(slots * 8);
+  d.ht_sums = (i64*)take(slots * 8);
+  d.ht_cnt = (u32*)take(slots * 4);
+  d.glist = (u32*)take(r.n_m * 4);
+  d.tk_k = (i64*)take(r.parts * d.k * 8);
+  d.tk_s = (i64*)take(r.parts * d.k * 8);
+  d.tk_c = (int*)take(r.parts * 4);
+}
+
+BatchLayout batch_layout(int nq) {
+  BatchLayout L;
+  size_t o = 0;
+  L.desc = o;
+  o += sizeof(PlanDev) * nq;
+  o = (o + 15) / 16 * 16;
+  L.tD = o;
+  o += 8 * (nq + 1);
+  L.tM = o;
+  o += 8 * (nq + 1);
+  L.tF = o;
+  o += 8 * (nq + 1);
+  L.dyn = al(o);
+  o = L.dyn + 8 * 5 * (nq + 1);
+  L.work = al(o);
+  o = L.work + 256;
+  L.ctr = o;
+  o += sizeof(QCtr) * nq;
+  L.out = al(o);
+  o = L.out + sizeof(pq_result) * nq;
+  L.end = al(o);
+  return L;
+}
+
+Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
+  Batch b{};
+  b.q = (PlanDev*)(ws + L.desc);
+  b.nq = nq;
+  b.tD = (const i64*)(ws + L.tD);
+  b.tM = (const i64*)(ws + L.tM);
+  b.tF = (const i64*)(ws + L.tF);
+  b.dyn = (i64*)(ws + L.dyn);
+  b.work = (u32*)(ws + L.work);
+  b.st = ctx->d_status;
+  b.spin_limit = ctx->opt.spin_limit;
+  b.ov.table = 0;
+  return b;
+}
+
+static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill", "plan_dbuild", "plan_mscan",
+                                   "plan_mfill",  "plan_mbuild", "plan_fprobe", "plan_topk"};
+
+pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s) {
+  const int grid = grid_persistent(ctx, 256);
+  cudaEvent_t stop;
+  prof_begin(ctx, kPhaseName[phase], s, &stop);
+  switch (phase) {
+    case kPhaseD:
+      if (vec) k_plan_dscan<true><<<grid, 256, 0, s>>>(b);
+      else k_plan_dscan<false><<<grid, 256, 0, s>>>(b);
+      break;
+    case kPhaseDfill: k_plan_fill<<<grid, 256, 0, s>>>(b, 0); break;
+    case kPhaseDbuild: k_plan_dbuild<<<grid, 256, 0, s>>>(b); break;
+    case kPhaseM:
+      if (vec) k_plan_mscan<true><<<grid, 256, 0, s>>>(b);
+      else k_plan_mscan<false><<<grid, 256, 0, s>>>(b);
+      break;
+    case kPhaseMfill: k_plan_fill<<<grid, 256, 0, s>>>(b, 1); break;
+    case kPhaseMbuild: k_plan_mbuild<<<grid, 256, 0, s>>>(b); break;
+    case kPhaseF:
+      if (vec) k_plan_fprobe<true><<<grid, 256, 0, s>>>(b);
+      else k_plan_fprobe<false><<<grid, 256, 0, s>>>(b);
+      break;
+    case kPhaseTopk: k_plan_topk<<<grid, 256, 0, s>>>(b); break;
+  }
+  prof_end(stop, s);
+  PQ_LAUNCHED(ctx);
+  return PQ_OK;
+}
+
+// ------------------------------------------------------------ graph cache ----
+struct GraphEntry {
+  std::string key;
+  uint64_t tids[3];
+  void* ws = nullptr;
+  pq_result* out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  uint64_t last_use = 0;
+};
+
+struct PlanCache {
+  std::vector<GraphEntry> entries;
+  uint64_t tick = 0;
+};
+
+void plan_cache_destroy(pq_ctx* ctx) {
+  if (ctx->plan_cache) {
+    for (auto& e : ctx->plan_cache->entries) {
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+      if (e.done) cudaEventDestroy(e.done);
+      ctx->arena.release_now(e.ws);
+    }
+    delete ctx->plan_cache;
+    ctx->plan_cache = nullptr;
+  }
+  for (auto& d : ctx->dsets) {
+    if (d.ready) cudaEventDestroy(d.ready);
+    ctx->arena.release_now(d.block);
+  }
+  ctx->dsets.clear();
+}
+
+static std::string plan_key(pq_ctx* ctx, const pq_plan& p) {
+  pq_plan q = p;
+  uint64_t ids[3] = {p.D->id, p.M->id, p.F->id};
+  q.D = q.M = q.F = nullptr;
+  std::string k((const char*)&q, sizeof q);
+  k.append((const char*)ids, sizeof ids);
+  k.append((const char*)&ctx->tune_bps, sizeof ctx->tune_bps);
+  return k;
+}
+
+// Drop cached graphs and D-sets that reference table `id` (called on free).
+void forget_table(pq_ctx* ctx, uint64_t id, cudaStream_t s) {
+  if (!ctx->plan_cache) return;
+  auto& v = ctx->plan_cache->entries;
+  for (auto it = v.begin(); it != v.end();) {
+    if (it->tids[0] == id || it->tids[1] == id || it->tids[2] == id) {
+      if (it->done) cudaEventSynchronize(it->done), cudaEventDestroy(it->done);
+      if (it->exec) cudaGraphExecDestroy(it->exec);
+      ctx->arena.release(it->ws, s);
+      it = v.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ batch ----
+static pq_status read_back(pq_ctx* ctx, pq_result* results, const pq_result* dev, int n,
+                           cudaStream_t s) {
+  const size_t bytes = sizeof(pq_result) * n;
+  ctx->d2h += (int64_t)bytes;
+  if (is_pinned(results)) {
+    PQ_CUDA(ctx, cudaMemcpyAsync(results, dev, bytes, cudaMemcpyDeviceToHost, s));
+    return PQ_OK;
+  }
+  pq_result* tmp = nullptr;
+  PQ_CUDA(ctx, cudaHostAlloc((void**)&tmp, bytes, 0));
+  cudaError_t e = cudaMemcpyAsync(tmp, dev, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) memcpy(results, tmp, bytes);
+  cudaFreeHost(tmp);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "result read-back");
+  return PQ_OK;
+}
+
+static bool same_dset(const ResolvedPlan& a, const pq_plan& pa, const ResolvedPlan& b,
+                      const pq_plan& pb) {
+  return pa.D->id == pb.D->id && a.d_row0 == b.d_row0 && a.n_d == b.n_d &&
+         a.dev.pd.lo == b.dev.pd.lo && a.dev.pd.hi == b.dev.pd.hi &&
+         a.dev.pd.neg == b.dev.pd.neg && a.dev.lf1024 == b.dev.lf1024;
+}
+
+size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n) {
+  size_t total = batch_layout(n).end;
+  for (int i = 0; i < n; ++i) {
+    ResolvedPlan r;
+    if (resolve_plan(ctx, plans[i], r, true) != PQ_OK) return 0;
+    total += plan_bytes(r);
+  }
+  return total;
+}
+
+pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
+                             cudaStream_t s, bool allow_graph) {
+  if (n <= 0 || !plans || !results) return fail(ctx, PQ_ERR_INVALID_ARG, "batch: bad arguments");
+  std::vector<ResolvedPlan> R(n);
+  for (int i = 0; i < n; ++i) {
+    pq_status st = resolve_plan(ctx, plans[i], R[i], true);
+    if (st != PQ_OK) return st;
+  }
+  // Graph replay for a repeated single plan.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool graphable = allow_graph && n == 1 && s != nullptr && !ctx->opt.profile &&
+                         cap == cudaStreamCaptureStatusNone &&
+                         !(plans[0].flags & (PQ_PLAN_NO_GRAPH | PQ_PLAN_CACHE_DSET));
+  std::string gkey;
+  if (graphable) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->plan_cache) ctx->plan_cache = new PlanCache();
+    gkey = plan_key(ctx, plans[0]);
+    for (auto& e : ctx->plan_cache->entries) {
+      if (e.key != gkey) continue;
+      e.last_use = ++ctx->plan_cache->tick;
+      PQ_CUDA(ctx, cudaStreamWaitEvent(s, e.done, 0));
+      PQ_CUDA(ctx, cudaGraphLaunch(e.exec, s));
+      PQ_CUDA(ctx, cudaEventRecord(e.done, s));
+      ctx->replays++;
+      ctx->plans++;
+      ctx->launches += 8;
+      return read_back(ctx, results, e.out, 1, s);
+    }
+  }
+
+  // D-set sharing inside the batch and across batches (cache).
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  std::vector<cudaEvent_t> waits;
+  for (int i = 0; i < n; ++i) {
+    ResolvedPlan& r = R[i];
+    for (int j = 0; j < i; ++j)
+      if (R[j].builds && same_dset(R[j], plans[j], r, plans[i])) {
+        r.builds = false;
+        r.dset_from = j;
+        break;
+      }
+    if (!r.builds || !(plans[i].flags & PQ_PLAN_CACHE_DSET)) continue;
+    for (auto& e : ctx->dsets) {
+      if (e.table_id == plans[i].D->id && e.row0 == r.d_row0 && e.rows == r.n_d &&
+          e.pred.lo == r.dev.pd.lo && e.pred.hi == r.dev.pd.hi && e.pred.neg == r.dev.pd.neg &&
+          e.lf1024 == r.dev.lf1024) {
+        r.builds = false;
+        r.dset_from = -2;
+        r.cache = &e;
+        e.last_use = ++ctx->dset_tick;
+        waits.push_back(e.ready);
+        break;
+      }
+    }
+    if (r.builds) {
+      DsetEntry e{};
+      e.table_id = plans[i].D->id;
+      e.row0 = r.d_row0;
+      e.rows = r.n_d;
+      e.pred = r.dev.pd;
+      e.lf1024 = r.dev.lf1024;
+      e.log2max = r.e_d;
+      e.block = ctx->arena.alloc(256 + (((size_t)8) << r.e_d));
+      if (!e.block) continue;  // no room to cache: build in the workspace
+      if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+        ctx->arena.release_now(e.block);
+        continue;
+      }
+      e.keys = (i64*)((char*)e.block + 256);
+      if (ctx->dsets.size() >= 64) {
+        // Evict the least recently used set that this batch does not use.
+        auto old = ctx->dsets.end();
+        for (auto it = ctx->dsets.begin(); it != ctx->dsets.end(); ++it) {
+          bool used = false;
+          for (int j = 0; j < i; ++j) used = used || R[j].cache == &*it;
+          if (!used && (old == ctx->dsets.end() || it->last_use < old->last_use)) old = it;
+        }
+        if (old != ctx->dsets.end()) {
+          cudaEventSynchronize(old->ready);
+          cudaEventDestroy(old->ready);
+          ctx->arena.release(old->block, s);
+          ctx->dsets.erase(old);
+        }
+      }
+      e.last_use = ++ctx->dset_tick;
+      ctx->dsets.push_back(e);
+      r.cache = &ctx->dsets.back();
+      r.cache_new = true;
+      r.dset_from = -3;  // builds into a new cache block
+    }
+  }
+
+  const BatchLayout L = batch_layout(n);
+  size_t total = L.end;
+  std::vector<size_t> off(n);
+  for (int i = 0; i < n; ++i) {
+    off[i] = total;
+    total += plan_bytes(R[i]);
+  }
+  char* ws = (char*)ctx->arena.alloc(total);
+  if (!ws) {
+    return fail(ctx, PQ_ERR_BUDGET, "batch of %d plans needs %zu bytes (largest free %zu)", n,
+                total, ctx->arena.largest_free());
+  }
+  bool any_build = false, vec = true;
+  std::vector<char> host(L.upload_bytes());
+  PlanDev* descs = (PlanDev*)host.data();
+  i64* tD = (i64*)(host.data() + (L.tD - L.desc));
+  i64* tM = (i64*)(host.data() + (L.tM - L.desc));
+  i64* tF = (i64*)(host.data() + (L.tF - L.desc));
+  tD[0] = tM[0] = tF[0] = 0;
+  QCtr* ctr = (QCtr*)(ws + L.ctr);
+  pq_result* out = (pq_result*)(ws + L.out);
+  for (int i = 0; i < n; ++i) {
+    ResolvedPlan& r = R[i];
+    plan_assign(r, ws + off[i]);
+    PlanDev& d = r.dev;
+    if (r.dset_from >= 0) {
+      d.dset_log2 = R[r.dset_from].dev.dset_log2;
+      d.dset = R[r.dset_from].dev.dset;
+    } else if (r.cache) {
+      d.dset_log2 = (int*)r.cache->block;
+      d.dset = r.cache->keys;
+    }
+    d.ctr = ctr + i;
+    d.out = out + i;
+    any_build = any_build || r.builds;
+    vec = vec && d.vec;
+    descs[i] = d;
+    tD[i + 1] = tD[i] + (r.builds ? (r.n_d + kTD - 1) / kTD : 0);
+    tM[i + 1] = tM[i] + (r.n_m + kTM - 1) / kTM;
+    tF[i + 1] = tF[i] + (r.n_f + kTF - 1) / kTF;
+  }
+  lk.unlock();
+
+  for (auto ev : waits) PQ_CUDA(ctx, cudaStreamWaitEvent(s, ev, 0));
+  PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
+  const Batch b = make_batch(ctx, ws, n, L);
+
+  auto chain = [&]() -> pq_status {
+    PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
+    for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk; ++ph) {
+      pq_status st = launch_phase(ctx, ph, b, vec, s);
+      if (st != PQ_OK) return st;
+    }
+    return PQ_OK;
+  };
+
+  pq_status st = PQ_OK;
+  if (graphable) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (captured) {
+      st = chain();
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      captured = st == PQ_OK && e == cudaSuccess &&
+                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    if (captured) {
+      GraphEntry e;
+      e.key = gkey;
+      e.tids[0] = plans[0].D->id;
+      e.tids[1] = plans[0].M->id;
+      e.tids[2] = plans[0].F->id;
+      e.ws = ws;
+      e.out = out;
+      e.exec = exec;
+      cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming);
+      PQ_CUDA(ctx, cudaGraphLaunch(exec, s));
+      PQ_CUDA(ctx, cudaEventRecord(e.done, s));
+      ctx->plans++;
+      std::lock_guard<std::mutex> g(ctx->mu);
+      auto& v = ctx->plan_cache->entries;
+      if (v.size() >= 16) {
+        auto old = std::min_element(v.begin(), v.end(), [](const GraphEntry& a,
+                                                            const GraphEntry& c) {
+          return a.last_use < c.last_use;
+        });
+        cudaEventSynchronize(old->done);
+        cudaEventDestroy(old->done);
+        cudaGraphExecDestroy(old->exec);
+        ctx->arena.release(old->ws, s);
+        v.erase(old);
+      }
+      e.last_use = ++ctx->plan_cache->tick;
+      v.push_back(e);
+      return read_back(ctx, results, out, 1, s);
+    }
+    if (st != PQ_OK) {
+      ctx->arena.release(ws, s);
+      return st;
+    }
+  }
+  st = chain();
+  if (st == PQ_OK) {
+    for (int i = 0; i < n; ++i)
+      if (R[i].cache_new && R[i].cache) cudaEventRecord(R[i].cache->ready, s);
+    st = read_back(ctx, results, out, n, s);
+    ctx->plans += n;
+  }
+  ctx->arena.release(ws, s);
+  return st;
+}
+
+}  // namespace pqh
+
+extern "C" {
+
+pq_status pq_run_plan(pq_ctx* ctx, const pq_plan* plan, pq_result* result, void* stream) {
+  if (!ctx || !plan || !result) return PQ_ERR_INVALID_ARG;
+  pqh::ResolvedPlan r;
+  pq_status st = pqh::resolve_plan(ctx, *plan, r, false);
+  if (st != PQ_OK) return st;
+  if (!r.resident[0] || !r.resident[1] || !r.resident[2])
+    return pqh::run_plan_streaming(ctx, plan, result, pqh::S(stream));
+  return pqh::run_batch_internal(ctx, plan, 1, result, pqh::S(stream), true);
+}
+
+pq_status pq_run_batch(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
+                       void* stream) {
+  if (!ctx) return PQ_ERR_INVALID_ARG;
+  return pqh::run_batch_internal(ctx, plans, n, results, pqh::S(stream), false);
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// pq_plan_host.h -- host-side plan resolution and workspace layout shared by
+// the resident (pq_plan.cu) and streaming (pq_stream.cu) plan drivers.
+#pragma once
+#include "pq_internal.h"
+#include "pq_plan_kernels.cuh"
+
+namespace pqh {
+
+// A plan resolved against its tables: row ranges, predicates, sizes.
+struct ResolvedPlan {
+  pqk::PlanDev dev{};
+  i64 n_d = 0, n_m = 0, n_f = 0;
+  i64 d_row0 = 0, m_row0 = 0, f_row0 = 0;
+  int e_d = 6, e_m = 6;   // log2 of the largest D-set / M-table slot counts
+  i64 parts = 1;          // top-k tiles at most
+  bool builds = true;     // fills its D-set in this batch
+  int dset_from = -1;     // -1 own block, >= 0 builder index in the batch, -2 cache
+  DsetEntry* cache = nullptr;
+  bool cache_new = false;
+  bool resident[3] = {false, false, false};
+};
+
+// Validate `p`; fill predicates, sizes and (for resident tables) the column
+// pointers of r.dev.  need_resident: every table must be resident.
+pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need_resident);
+
+// Per-plan workspace bytes (excluding a cached D-set block).
+size_t plan_bytes(const ResolvedPlan& r);
+
+// Carve the plan's workspace pointers out of `base` (as sized by plan_bytes).
+void plan_assign(ResolvedPlan& r, char* base);
+
+// Batch header layout inside the workspace.
+struct BatchLayout {
+  size_t desc = 0, tD = 0, tM = 0, tF = 0, dyn = 0, work = 0, ctr = 0, out = 0, end = 0;
+  size_t upload_bytes() const { return work - desc; }  // descriptors + tile prefixes
+  size_t zero_bytes() const { return out - work; }     // tickets + per-plan counters
+};
+BatchLayout batch_layout(int nq);
+
+// The batch argument of every plan kernel for a workspace at `ws`.
+pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
+
+// Launch the chain of plan kernels for the whole batch (phases D, M, F and
+// top-k).  any_build: at least one plan fills a D-set.  vec: every column
+// pointer 16-byte aligned.
+pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s);
+
+enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseF,
+       kPhaseTopk };
+
+}  // namespace pqh

@@ -1,0 +1,315 @@
+// pq_serve.cu -- continuous-batching serving loop and the autotuner.
+//
+// Requests (plans over resident tables) queue in submission order.  A server
+// thread owns `serve_slots` streams; whenever a stream is free it admits the
+// queued requests that fit the arena (up to kMaxBatch), runs them as one batch
+// (pq_run_batch's persistent kernels) and goes back to admitting, so requests
+// that arrive while earlier batches are on the GPU start as soon as a slot and
+// memory are free and overlap with them on the device.  D-sets are cached
+// across requests (hash tables kept resident).  Completion is signalled by a
+// host callback enqueued after each batch, so no thread polls the GPU.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "pq_plan_host.h"
+
+using namespace pqk;
+
+namespace pqh {
+
+namespace {
+constexpr int kMaxBatch = 512;
+using Clock = std::chrono::steady_clock;
+}  // namespace
+
+struct Request {
+  uint64_t ticket;
+  pq_plan plan;
+  size_t bytes;
+  Clock::time_point t0;
+};
+
+struct Finished {
+  pq_result res;
+  double latency_us;
+};
+
+struct ServeSlot {
+  cudaStream_t s = nullptr;
+  pq_result* results = nullptr;  // pinned, kMaxBatch entries
+  std::vector<Request> reqs;
+  bool busy = false;
+  bool completed = false;
+  pq_status st = PQ_OK;
+  struct Server* srv = nullptr;
+};
+
+struct Server {
+  pq_ctx* ctx = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;       // wakes the server thread
+  std::condition_variable cv_done;  // wakes pq_poll callers
+  std::deque<Request> pending;
+  std::unordered_map<uint64_t, Finished> done;
+  std::vector<ServeSlot> slots;
+  std::thread th;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  double last_latency_us = 0;
+
+  void loop();
+};
+
+static void CUDART_CB on_batch_done(void* arg) {
+  ServeSlot* sl = (ServeSlot*)arg;
+  {
+    std::lock_guard<std::mutex> g(sl->srv->mu);
+    sl->completed = true;
+  }
+  sl->srv->cv.notify_all();
+}
+
+void Server::loop() {
+  std::unique_lock<std::mutex> lk(mu);
+  while (true) {
+    // Deliver finished batches.
+    for (auto& sl : slots) {
+      if (!sl.busy || !sl.completed) continue;
+      const auto now = Clock::now();
+      for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        Finished f;
+        f.res = sl.results[i];
+        if (sl.st != PQ_OK) f.res.status = sl.st;
+        f.latency_us = std::chrono::duration<double, std::micro>(now - sl.reqs[i].t0).count();
+        done[sl.reqs[i].ticket] = f;
+      }
+      sl.reqs.clear();
+      sl.busy = sl.completed = false;
+      cv_done.notify_all();
+    }
+    if (stop) {
+      bool any = false;
+      for (auto& sl : slots) any = any || sl.busy;
+      if (!any) return;
+    }
+    // Admit queued requests into free slots.
+    bool progressed = false;
+    for (auto& sl : slots) {
+      if (sl.busy || pending.empty() || stop) continue;
+      size_t budget = ctx->arena.largest_free();
+      size_t used = batch_layout(kMaxBatch).end;
+      std::vector<Request> take;
+      while (!pending.empty() && (int)take.size() < kMaxBatch &&
+             (take.empty() || used + pending.front().bytes <= budget)) {
+        used += pending.front().bytes;
+        take.push_back(pending.front());
+        pending.pop_front();
+      }
+      std::vector<pq_plan> plans;
+      for (auto& r : take) plans.push_back(r.plan);
+      lk.unlock();
+      pq_status st = run_batch_internal(ctx, plans.data(), (int)plans.size(), sl.results, sl.s,
+                                        false);
+      if (st == PQ_OK) st = cudaLaunchHostFunc(sl.s, on_batch_done, &sl) == cudaSuccess
+                                ? PQ_OK
+                                : PQ_ERR_CUDA;
+      lk.lock();
+      bool others_busy = false;
+      for (auto& o : slots) others_busy = others_busy || o.busy;
+      if (st == PQ_ERR_BUDGET && others_busy) {
+        // Not enough memory while other batches hold it: requeue and wait.
+        for (auto it = take.rbegin(); it != take.rend(); ++it) pending.push_front(*it);
+        break;
+      }
+      if (st != PQ_OK) {
+        for (auto& r : take) {
+          Finished f;
+          memset(&f.res, 0, sizeof f.res);
+          f.res.status = st;
+          f.latency_us = 0;
+          done[r.ticket] = f;
+        }
+        cv_done.notify_all();
+        continue;
+      }
+      sl.reqs = std::move(take);
+      sl.busy = true;
+      sl.completed = false;
+      sl.st = PQ_OK;
+      progressed = true;
+    }
+    if (progressed) continue;
+    cv.wait(lk, [&] {
+      if (stop) return true;
+      bool free_slot = false;
+      for (auto& sl : slots) {
+        if (sl.busy && sl.completed) return true;
+        free_slot = free_slot || !sl.busy;
+      }
+      return free_slot && !pending.empty();
+    });
+  }
+}
+
+void server_stop(pq_ctx* ctx) {
+  Server* srv = ctx->server;
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  if (srv->th.joinable()) srv->th.join();
+  for (auto& sl : srv->slots) {
+    if (sl.s) cudaStreamSynchronize(sl.s), cudaStreamDestroy(sl.s);
+    if (sl.results) cudaFreeHost(sl.results);
+  }
+  delete srv;
+  ctx->server = nullptr;
+}
+
+static pq_status server_start(pq_ctx* ctx) {
+  if (ctx->server) return PQ_OK;
+  std::unique_ptr<Server> srv(new Server());
+  srv->ctx = ctx;
+  srv->slots.resize(std::max(1, ctx->opt.serve_slots));
+  for (auto& sl : srv->slots) {
+    sl.srv = srv.get();
+    if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaHostAlloc((void**)&sl.results, sizeof(pq_result) * kMaxBatch, 0) != cudaSuccess) {
+      for (auto& o : srv->slots) {
+        if (o.s) cudaStreamDestroy(o.s);
+        if (o.results) cudaFreeHost(o.results);
+      }
+      return fail(ctx, PQ_ERR_CUDA, "serving loop: stream or pinned buffer");
+    }
+  }
+  Server* raw = srv.release();
+  ctx->server = raw;
+  raw->th = std::thread([raw] {
+    cudaSetDevice(raw->ctx->device);
+    raw->loop();
+  });
+  return PQ_OK;
+}
+
+}  // namespace pqh
+
+using namespace pqh;
+
+extern "C" {
+
+pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket) {
+  if (!ctx || !plan || !ticket) return PQ_ERR_INVALID_ARG;
+  ResolvedPlan r;
+  pq_status st = resolve_plan(ctx, *plan, r, true);
+  if (st != PQ_OK) return st;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    st = server_start(ctx);
+  }
+  if (st != PQ_OK) return st;
+  Server* srv = ctx->server;
+  Request q;
+  q.plan = *plan;
+  q.plan.flags |= PQ_PLAN_CACHE_DSET;
+  q.bytes = plan_bytes(r) + 256;
+  q.t0 = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    if ((int)srv->pending.size() >= ctx->opt.serve_queue)
+      return fail(ctx, PQ_ERR_BUSY, "serving queue holds %d requests", ctx->opt.serve_queue);
+    q.ticket = srv->next_ticket++;
+    srv->pending.push_back(q);
+  }
+  srv->cv.notify_all();
+  *ticket = q.ticket;
+  return PQ_OK;
+}
+
+pq_status pq_poll(pq_ctx* ctx, uint64_t ticket, pq_result* result, int timeout_ms) {
+  if (!ctx || !result) return PQ_ERR_INVALID_ARG;
+  Server* srv = ctx->server;
+  if (!srv) return fail(ctx, PQ_ERR_INVALID_ARG, "no request was submitted");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto ready = [&] { return srv->done.count(ticket) > 0; };
+  if (timeout_ms < 0) srv->cv_done.wait(lk, ready);
+  else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    return PQ_ERR_TIMEOUT;
+  Finished f = srv->done[ticket];
+  srv->done.erase(ticket);
+  lk.unlock();
+  *result = f.res;
+  ctx->last_latency_us = f.latency_us;
+  return (pq_status)(f.res.status == PQ_OK ? PQ_OK : f.res.status);
+}
+
+double pq_last_latency_us(pq_ctx* ctx) { return ctx ? ctx->last_latency_us : 0.0; }
+
+pq_status pq_autotune(pq_ctx* ctx, const pq_plan* sample, pq_tuning* out) {
+  if (!ctx || !sample || !out) return PQ_ERR_INVALID_ARG;
+  ResolvedPlan r;
+  pq_status st = resolve_plan(ctx, *sample, r, true);
+  if (st != PQ_OK) return st;
+  cudaStream_t s;
+  PQ_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  pq_result* res = nullptr;
+  cudaEvent_t a, b;
+  if (cudaHostAlloc((void**)&res, sizeof(pq_result), 0) != cudaSuccess ||
+      cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return fail(ctx, PQ_ERR_CUDA, "autotune setup");
+  }
+  const int saved_bps = ctx->tune_bps;
+  const float saved_lf = ctx->opt.load_factor;
+  memset(out, 0, sizeof *out);
+  out->best_ms = 1e30f;
+  const int bps_set[] = {1, 2, 3, 4, 6};
+  const float lf_set[] = {0.25f, 0.4f, 0.5f, 0.7f};
+  pq_plan p = *sample;
+  p.flags |= PQ_PLAN_NO_GRAPH;
+  for (int bps : bps_set) {
+    for (float lf : lf_set) {
+      ctx->tune_bps = bps;
+      p.load_factor = lf;
+      float t[5];
+      int ok = 0;
+      for (int rep = 0; rep < 6 && st == PQ_OK; ++rep) {
+        cudaEventRecord(a, s);
+        st = run_batch_internal(ctx, &p, 1, res, s, false);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = PQ_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) t[ok++] = ms;  // first run warms caches and code
+      }
+      if (st != PQ_OK) break;
+      std::sort(t, t + ok);
+      out->tried++;
+      if (t[ok / 2] < out->best_ms) {
+        out->best_ms = t[ok / 2];
+        out->blocks_per_sm = bps;
+        out->load_factor = lf;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFreeHost(res);
+  cudaStreamDestroy(s);
+  if (st != PQ_OK) {
+    ctx->tune_bps = saved_bps;
+    ctx->opt.load_factor = saved_lf;
+    return st;
+  }
+  out->block_threads = 256;
+  out->log2P = ctx->opt.log2P;
+  out->partitioned = 0;
+  ctx->tune_bps = out->blocks_per_sm;
+  ctx->opt.blocks_per_sm = out->blocks_per_sm;
+  ctx->opt.load_factor = out->load_factor;
+  return PQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,450 @@
+// pq_stream.cu -- streaming plan driver: host-resident (pinned, pageable or
+// file) tables are fed to the plan kernels chunk by chunk.
+//
+// Pipeline (chunked execution on several streams, Sec. 3.2; overlapped scan,
+// Sec. 4.2; queue-based scheduling with a bounded queue, Sec. 5.4):
+//   * the chunks of D, M and F form one sequence ("reader combining",
+//     Sec. 5.2: one ingest pool serves every scan of the plan);
+//   * pinned host columns are copied straight from their rows; pageable
+//     memory and files are first filled into pinned staging buffers by
+//     reader threads (multiple producers), in chunk order, and consumed by
+//     the plan thread (single consumer);
+//   * copies run on the context's copy streams into a ring of device slots,
+//     each copy waits (on the GPU) for the kernel that last used its slot, and
+//     each scan kernel waits for its copy -- the host never blocks on the GPU
+//     except once after the D and M scans to size the tables exactly;
+//   * the staging buffers and device slots bound the memory in flight
+//     (adaptive regulation, Sec. 5.4).
+#include <fcntl.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <thread>
+
+#include "pq_plan_host.h"
+
+using namespace pqk;
+
+namespace pqh {
+
+namespace {
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Chunk {
+  int table;   // 0 D, 1 M, 2 F
+  i64 row0;    // first row inside the plan's row range
+  i64 rows;
+};
+
+struct TableIn {
+  const pq_table* t = nullptr;
+  i64 row0 = 0;    // plan row offset inside the table
+  int ncols = 0;
+  size_t esize[4] = {0, 0, 0, 0};
+  size_t row_bytes = 0;
+};
+
+// Column j of chunk c laid out in a slot: columns one after another, each
+// starting on a 256-byte boundary.
+size_t col_offset(const TableIn& T, i64 rows, int j) {
+  size_t o = 0;
+  for (int i = 0; i < j; ++i) o += al(T.esize[i] * rows);
+  return o;
+}
+
+// Multi-producer single-consumer staging queue.  Producers claim chunks in
+// order after taking a free staging buffer, so the chunk the consumer waits
+// for always owns a buffer and the queue cannot deadlock.
+class Stager {
+ public:
+  Stager(pq_ctx* ctx, const TableIn* tabs, const std::vector<Chunk>& chunks, size_t buf_bytes,
+         int nbuf, int nthreads)
+      : ctx_(ctx), tabs_(tabs), chunks_(chunks), buf_bytes_(buf_bytes) {
+    bufs_.resize(nbuf, nullptr);
+    evs_.resize(nbuf, nullptr);
+    for (int i = 0; i < nbuf; ++i) {
+      if (cudaHostAlloc((void**)&bufs_[i], buf_bytes, 0) != cudaSuccess ||
+          cudaEventCreateWithFlags(&evs_[i], cudaEventDisableTiming) != cudaSuccess) {
+        ok_ = false;
+        return;
+      }
+      free_.push_back(i);
+    }
+    ready_.assign(chunks.size(), -1);
+    for (int i = 0; i < nthreads; ++i) th_.emplace_back([this] { run(); });
+  }
+
+  ~Stager() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+    for (size_t i = 0; i < bufs_.size(); ++i) {
+      if (evs_[i]) cudaEventSynchronize(evs_[i]), cudaEventDestroy(evs_[i]);
+      if (bufs_[i]) cudaFreeHost(bufs_[i]);
+    }
+  }
+
+  bool ok() const { return ok_; }
+
+  // Wait until chunk c is staged; returns its buffer index or -1 (I/O error).
+  int wait(size_t c) {
+    std::unique_lock<std::mutex> g(mu_);
+    cv_.wait(g, [&] { return ready_[c] != -1 || err_; });
+    return err_ ? -1 : ready_[c];
+  }
+
+  char* buf(int i) const { return bufs_[i]; }
+
+  // The consumer enqueued the copies out of buffer i; it is free again once
+  // event `after` (recorded after those copies) completes.
+  void release(int i, cudaStream_t s) {
+    cudaEventRecord(evs_[i], s);
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      free_.push_back(i);
+    }
+    cv_.notify_all();
+  }
+
+  std::string error() const { return msg_; }
+
+ private:
+  void run() {
+    while (true) {
+      int b;
+      size_t c;
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return stop_ || err_ || (!free_.empty() && next_ < chunks_.size()); });
+        if (stop_ || err_ || next_ >= chunks_.size()) return;
+        b = free_.front();
+        free_.pop_front();
+        c = next_++;
+      }
+      cudaEventSynchronize(evs_[b]);  // previous copies out of this buffer are done
+      std::string m;
+      bool good = fill(chunks_[c], bufs_[b], &m);
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        if (good) ready_[c] = b;
+        else err_ = true, msg_ = m;
+      }
+      cv_.notify_all();
+    }
+  }
+
+  bool fill(const Chunk& ch, char* dst, std::string* msg) {
+    const TableIn& T = tabs_[ch.table];
+    for (int j = 0; j < T.ncols; ++j) {
+      const Column& col = T.t->cols[j];
+      const size_t es = T.esize[j];
+      const size_t bytes = es * ch.rows;
+      const size_t src_off = es * (T.row0 + ch.row0);
+      char* d = dst + col_offset(T, ch.rows, j);
+      if (col.src.kind == PQ_SRC_FILE) {
+        int fd = open(col.path.c_str(), O_RDONLY);
+        if (fd < 0) {
+          *msg = "open " + col.path;
+          return false;
+        }
+        size_t got = 0;
+        while (got < bytes) {
+          ssize_t r = pread(fd, d + got, bytes - got, (off_t)(col.src.offset + src_off + got));
+          if (r <= 0) break;
+          got += (size_t)r;
+        }
+        close(fd);
+        if (got != bytes) {
+          *msg = "short read from " + col.path;
+          return false;
+        }
+      } else {
+        memcpy(d, (const char*)col.src.ptr + src_off, bytes);
+      }
+    }
+    return true;
+  }
+
+  pq_ctx* ctx_;
+  const TableIn* tabs_;
+  const std::vector<Chunk>& chunks_;
+  size_t buf_bytes_;
+  std::vector<char*> bufs_;
+  std::vector<cudaEvent_t> evs_;
+  std::deque<int> free_;
+  std::vector<int> ready_;
+  size_t next_ = 0;
+  bool stop_ = false, err_ = false, ok_ = true;
+  std::string msg_;
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::vector<std::thread> th_;
+};
+
+}  // namespace
+
+pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result,
+                             cudaStream_t s) {
+  ResolvedPlan r;
+  pq_status st = resolve_plan(ctx, *plan, r, false);
+  if (st != PQ_OK) return st;
+  const pq_table* T3[3] = {plan->D, plan->M, plan->F};
+  const i64 row0[3] = {r.d_row0, r.m_row0, r.f_row0};
+  const i64 nrows[3] = {r.n_d, r.n_m, r.n_f};
+  TableIn tabs[3];
+  const size_t chunk_bytes = (size_t)ctx->opt.chunk_bytes;
+  std::vector<Chunk> chunks;
+  bool need_stage = false;
+  for (int t = 0; t < 3; ++t) {
+    TableIn& T = tabs[t];
+    T.t = T3[t];
+    T.row0 = row0[t];
+    T.ncols = t == 0 ? 2 : t == 1 ? 3 : 4;
+    for (int j = 0; j < T.ncols; ++j) {
+      T.esize[j] = dtype_size(T.t->cols[j].type);
+      T.row_bytes += T.esize[j];
+    }
+    if (r.resident[t]) continue;
+    for (int j = 0; j < T.ncols; ++j) {
+      const Column& c = T.t->cols[j];
+      if (c.dev) return fail(ctx, PQ_ERR_INVALID_ARG, "streaming table mixes device columns");
+      if (!(c.src.kind == PQ_SRC_HOST && c.pinned)) need_stage = true;
+    }
+    i64 rows_per = (i64)((chunk_bytes - 4 * 256) / T.row_bytes) / 64 * 64;
+    rows_per = std::max<i64>(rows_per, 64);
+    for (i64 a = 0; a < nrows[t]; a += rows_per)
+      chunks.push_back({t, a, std::min(rows_per, nrows[t] - a)});
+  }
+
+  // Workspace part 1: header, D list, M list (sized by row counts); the D-set,
+  // M table and group list are sized after the scans.
+  const BatchLayout L = batch_layout(1);
+  const int nslots = std::max(2, ctx->opt.ring_slots);
+  Scratch scr(ctx, s);
+  char* ws = (char*)scr.get(L.end + al(r.n_d * 8) + al(r.n_m * 8));
+  char* ring = chunks.empty() ? nullptr : (char*)scr.get((chunk_bytes + 1024) * nslots);
+  if (!ws || (!chunks.empty() && !ring))
+    return fail(ctx, PQ_ERR_BUDGET, "streaming plan: workspace and %d chunk slots of %zu bytes",
+                nslots, chunk_bytes);
+  PlanDev& d = r.dev;
+  d.build_dset = 1;
+  d.dlist = (i64*)(ws + L.end);
+  d.mlist = (i64*)(ws + L.end + al(r.n_d * 8));
+  QCtr* ctr = (QCtr*)(ws + L.ctr);
+  d.ctr = ctr;
+  d.out = (pq_result*)(ws + L.out);
+  // Streamed columns live in ring slots: the kernels get them through the
+  // chunk override, so only resident tables' pointers matter in `d`.
+  bool vec = true;
+  for (int t = 0; t < 3; ++t)
+    if (r.resident[t]) {
+      const void* ptrs[4] = {t == 0 ? (const void*)d.d_key : t == 1 ? (const void*)d.m_key
+                                                                     : (const void*)d.f_mkey,
+                             t == 0 ? (const void*)d.d_seg : t == 1 ? (const void*)d.m_dref
+                                                                    : (const void*)d.f_price,
+                             t == 1 ? (const void*)d.m_date : (const void*)d.f_disc,
+                             (const void*)d.f_date};
+      for (int j = 0; j < tabs[t].ncols; ++j) vec = vec && (((uintptr_t)ptrs[j]) & 15) == 0;
+    }
+
+  std::vector<char> host(L.upload_bytes());
+  auto upload_desc = [&](i64 tiles_d, i64 tiles_m, i64 tiles_f) -> cudaError_t {
+    memcpy(host.data(), &d, sizeof d);
+    i64* tD = (i64*)(host.data() + (L.tD - L.desc));
+    i64* tM = (i64*)(host.data() + (L.tM - L.desc));
+    i64* tF = (i64*)(host.data() + (L.tF - L.desc));
+    tD[0] = tM[0] = tF[0] = 0;
+    tD[1] = tiles_d;
+    tM[1] = tiles_m;
+    tF[1] = tiles_f;
+    return ctx->ring.upload(ws + L.desc, host.data(), host.size(), s);
+  };
+  // D-set region placeholder until the D scan is done: a 64-slot block.
+  char* dset_blk = (char*)scr.get(256 + 64 * 8);
+  if (!dset_blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set");
+  d.dset_log2 = (int*)dset_blk;
+  d.dset = (i64*)(dset_blk + 256);
+  PQ_CUDA(ctx, upload_desc(r.resident[0] ? (r.n_d + kTD - 1) / kTD : 0,
+                           r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
+                           r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+  PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
+  Batch b = make_batch(ctx, ws, 1, L);
+
+  std::unique_ptr<Stager> stager;
+  if (need_stage) {
+    stager.reset(new Stager(ctx, tabs, chunks, chunk_bytes + 1024,
+                            std::max(2, ctx->opt.ring_slots), std::max(1, ctx->opt.ingest_threads)));
+    if (!stager->ok()) return fail(ctx, PQ_ERR_CUDA, "streaming plan: pinned staging");
+  }
+  std::vector<cudaEvent_t> slot_free(nslots), copy_done(nslots);
+  for (int i = 0; i < nslots; ++i) {
+    cudaEventCreateWithFlags(&slot_free[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&copy_done[i], cudaEventDisableTiming);
+  }
+  struct EvGuard {
+    std::vector<cudaEvent_t>& a;
+    std::vector<cudaEvent_t>& b;
+    ~EvGuard() {
+      for (auto e : a) cudaEventSynchronize(e), cudaEventDestroy(e);
+      for (auto e : b) cudaEventSynchronize(e), cudaEventDestroy(e);
+    }
+  } guard{slot_free, copy_done};
+
+  const int ncs = (int)ctx->copy_streams.size();
+  size_t issued = 0;  // chunks whose copies are enqueued
+  // Enqueue the copies of chunk c into slot c % nslots.
+  auto issue = [&](size_t c) -> pq_status {
+    const Chunk& ch = chunks[c];
+    const TableIn& T = tabs[ch.table];
+    const int slot = (int)(c % nslots);
+    cudaStream_t cs = ctx->copy_streams[c % ncs];
+    char* dst = ring + slot * (chunk_bytes + 1024);
+    PQ_CUDA(ctx, cudaStreamWaitEvent(cs, slot_free[slot], 0));
+    int sb = -1;
+    if (stager) {
+      sb = stager->wait(c);
+      if (sb < 0) return fail(ctx, PQ_ERR_IO, "streaming plan: %s", stager->error().c_str());
+    }
+    size_t total = 0;
+    for (int j = 0; j < T.ncols; ++j) {
+      const size_t bytes = T.esize[j] * ch.rows;
+      const size_t off = col_offset(T, ch.rows, j);
+      const void* src = stager ? (const void*)(stager->buf(sb) + off)
+                               : (const void*)((const char*)T.t->cols[j].src.ptr +
+                                               T.esize[j] * (T.row0 + ch.row0));
+      PQ_CUDA(ctx, cudaMemcpyAsync(dst + off, src, bytes, cudaMemcpyHostToDevice, cs));
+      total += bytes;
+    }
+    PQ_CUDA(ctx, cudaEventRecord(copy_done[slot], cs));
+    if (stager) stager->release(sb, cs);
+    ctx->h2d += (int64_t)total;
+    ctx->chunks++;
+    return PQ_OK;
+  };
+  auto prefetch = [&](size_t upto) -> pq_status {
+    while (issued < chunks.size() && issued < upto) {
+      pq_status e = issue(issued);
+      if (e != PQ_OK) return e;
+      ++issued;
+    }
+    return PQ_OK;
+  };
+  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseF};
+  size_t c = 0;
+  for (int t = 0; t < 3; ++t) {
+    if (r.resident[t]) {
+      st = launch_phase(ctx, phase_of[t], b, vec && d.vec, s);
+      if (st != PQ_OK) return st;
+    } else if (nrows[t] == 0) {
+      // An empty streamed table: one launch with no tiles still lets the
+      // kernel's last block size the following phases.
+      Batch bc = b;
+      bc.ov.table = t + 1;
+      bc.ov.n = 0;
+      bc.ov.tiles = 0;
+      st = launch_phase(ctx, phase_of[t], bc, true, s);
+      if (st != PQ_OK) return st;
+    } else {
+      for (; c < chunks.size() && chunks[c].table == t; ++c) {
+        st = prefetch(c + nslots);
+        if (st != PQ_OK) return st;
+        const Chunk& ch = chunks[c];
+        const TableIn& T = tabs[t];
+        const int slot = (int)(c % nslots);
+        char* src = ring + slot * (chunk_bytes + 1024);
+        PQ_CUDA(ctx, cudaStreamWaitEvent(s, copy_done[slot], 0));
+        Batch bc = b;
+        bc.ov.table = t + 1;
+        bc.ov.n = ch.rows;
+        const int tile = t == 0 ? kTD : t == 1 ? kTM : kTF;
+        bc.ov.tiles = (ch.rows + tile - 1) / tile;
+        for (int j = 0; j < T.ncols; ++j) bc.ov.p[j] = src + col_offset(T, ch.rows, j);
+        st = launch_phase(ctx, phase_of[t], bc, true, s);
+        if (st != PQ_OK) return st;
+        PQ_CUDA(ctx, cudaEventRecord(slot_free[slot], s));
+      }
+    }
+    if (t == 2) break;
+    // Size the next table exactly from the device count (one host wait per
+    // phase; the copies already enqueued keep streaming meanwhile).
+    st = prefetch(c + nslots);
+    if (st != PQ_OK) return st;
+    i64 count = 0;
+    {
+      std::lock_guard<std::mutex> g(ctx->small_mu);
+      cudaError_t e = cudaMemcpyAsync(ctx->h_small, t == 0 ? (void*)&ctr->dcount
+                                                           : (void*)&ctr->mcount,
+                                      8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming plan: count read-back");
+      count = ctx->h_small[0];
+    }
+    const int e = cap_log2(count, d.lf1024);
+    if (t == 0) {
+      char* blk = (char*)scr.get(256 + (((size_t)8) << e));
+      if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set of 2^%d slots", e);
+      d.dset_log2 = (int*)blk;
+      d.dset = (i64*)(blk + 256);
+      PQ_CUDA(ctx, upload_desc(0, r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
+                               r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+      // The dscan kernel sized the fill/build phases; it wrote the log2 into
+      // the placeholder, which is copied to the real block.
+      PQ_CUDA(ctx, cudaMemcpyAsync(d.dset_log2, dset_blk, 4, cudaMemcpyDeviceToDevice, s));
+      for (int ph : {kPhaseDfill, kPhaseDbuild}) {
+        st = launch_phase(ctx, ph, b, true, s);
+        if (st != PQ_OK) return st;
+      }
+    } else {
+      const size_t slots = (size_t)1 << e;
+      const i64 parts = std::max<i64>(1, (count + kTK - 1) / kTK);
+      char* blk = (char*)scr.get(al(slots * 8) * 2 + al(slots * 4) + al(count * 4 + 4) +
+                                 al(parts * d.k * 8) * 2 + al(parts * 4));
+      if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: M table of 2^%d slots", e);
+      char* p = blk;
+      d.ht_keys = (i64*)p;
+      p += al(slots * 8);
+      d.ht_sums = (i64*)p;
+      p += al(slots * 8);
+      d.ht_cnt = (u32*)p;
+      p += al(slots * 4);
+      d.glist = (u32*)p;
+      p += al(count * 4 + 4);
+      d.tk_k = (i64*)p;
+      p += al(parts * d.k * 8);
+      d.tk_s = (i64*)p;
+      p += al(parts * d.k * 8);
+      d.tk_c = (int*)p;
+      PQ_CUDA(ctx, upload_desc(0, 0, r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+      for (int ph : {kPhaseMfill, kPhaseMbuild}) {
+        st = launch_phase(ctx, ph, b, true, s);
+        if (st != PQ_OK) return st;
+      }
+    }
+  }
+  st = launch_phase(ctx, kPhaseTopk, b, true, s);
+  if (st != PQ_OK) return st;
+  ctx->plans++;
+  const size_t bytes = sizeof(pq_result);
+  ctx->d2h += (int64_t)bytes;
+  if (is_pinned(result)) {
+    PQ_CUDA(ctx, cudaMemcpyAsync(result, d.out, bytes, cudaMemcpyDeviceToHost, s));
+    return PQ_OK;
+  }
+  pq_result* tmp = nullptr;
+  PQ_CUDA(ctx, cudaHostAlloc((void**)&tmp, bytes, 0));
+  cudaError_t e = cudaMemcpyAsync(tmp, d.out, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) memcpy(result, tmp, bytes);
+  cudaFreeHost(tmp);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "result read-back");
+  return PQ_OK;
+}
+
+}  // namespace pqh

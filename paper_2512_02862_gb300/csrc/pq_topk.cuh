@@ -1,0 +1,111 @@
+// pq_topk.cuh -- warp-register top-k list used by pq_topk and the plan.
+//
+// Order: larger sum first, ties by smaller key (ORDER BY sum DESC, key ASC).
+// A warp keeps its best K <= 64 entries sorted in registers: lane j holds
+// entries j and 32 + j.  Candidates are tested 32 at a time against the
+// current K-th entry, and the few that beat it are inserted one by one with
+// a warp-wide shift, so after the list fills most candidates cost one
+// comparison.
+#pragma once
+#include "pq_dev.cuh"
+
+namespace pqk {
+
+__device__ __forceinline__ bool tk_before(i64 ka, i64 sa, i64 kb, i64 sb) {
+  return sa > sb || (sa == sb && ka < kb);
+}
+
+struct TopList {
+  i64 k0, s0, k1, s1;  // entries lane and 32 + lane
+  int cnt;             // warp-uniform number of valid entries
+
+  __device__ void clear() {
+    k0 = k1 = 0;
+    s0 = s1 = 0;
+    cnt = 0;
+  }
+
+  // Entry K-1 (the admission threshold), valid when cnt == K.
+  __device__ __forceinline__ void last(int K, i64& k, i64& s) const {
+    const int idx = K - 1;
+    i64 a = idx < 32 ? k0 : k1, b = idx < 32 ? s0 : s1;
+    k = __shfl_sync(kFull, a, idx & 31);
+    s = __shfl_sync(kFull, b, idx & 31);
+  }
+
+  // Warp-uniform insert of the broadcast candidate (ck, cs).
+  __device__ __forceinline__ void insert(int K, i64 ck, i64 cs) {
+    const int lane = threadIdx.x & 31;
+    const bool b0 = lane < cnt && tk_before(k0, s0, ck, cs);
+    const bool b1 = 32 + lane < cnt && tk_before(k1, s1, ck, cs);
+    const int pos = __popc(__ballot_sync(kFull, b0)) + __popc(__ballot_sync(kFull, b1));
+    if (pos >= K) return;
+    const i64 upk0 = __shfl_up_sync(kFull, k0, 1), ups0 = __shfl_up_sync(kFull, s0, 1);
+    const i64 upk1 = __shfl_up_sync(kFull, k1, 1), ups1 = __shfl_up_sync(kFull, s1, 1);
+    const i64 lk0 = __shfl_sync(kFull, k0, 31), ls0 = __shfl_sync(kFull, s0, 31);
+    const int i1 = 32 + lane;
+    if (i1 > pos) {
+      k1 = lane == 0 ? lk0 : upk1;
+      s1 = lane == 0 ? ls0 : ups1;
+    } else if (i1 == pos) {
+      k1 = ck;
+      s1 = cs;
+    }
+    if (lane > pos) {
+      k0 = upk0;
+      s0 = ups0;
+    } else if (lane == pos) {
+      k0 = ck;
+      s0 = cs;
+    }
+    cnt = cnt + 1 < K ? cnt + 1 : K;
+  }
+
+  // Offer one candidate per lane (valid lanes only); warp-uniform call.
+  __device__ __forceinline__ void offer(int K, bool valid, i64 ck, i64 cs) {
+    bool want = valid;
+    if (cnt == K) {
+      i64 tk, ts;
+      last(K, tk, ts);
+      want = valid && tk_before(ck, cs, tk, ts);
+    }
+    u32 m = __ballot_sync(kFull, want);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const i64 k = __shfl_sync(kFull, ck, src), s = __shfl_sync(kFull, cs, src);
+      insert(K, k, s);
+    }
+  }
+
+  // Write entries [0, cnt) to keys/sums (one warp).
+  __device__ __forceinline__ void store(i64* keys, i64* sums) const {
+    const int lane = threadIdx.x & 31;
+    if (lane < cnt) keys[lane] = k0, sums[lane] = s0;
+    if (32 + lane < cnt) keys[32 + lane] = k1, sums[32 + lane] = s1;
+  }
+};
+
+// Merge the per-warp lists of one block into warp 0's list through shared
+// memory (`sk`, `ss`: nwarps * K entries, `sc`: nwarps counts).
+__device__ __forceinline__ void tk_block_merge(TopList& L, int K, i64* sk, i64* ss, int* sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp > 0) {
+    L.store(sk + warp * K, ss + warp * K);
+    if (lane == 0) sc[warp] = L.cnt;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < nw; ++w) {
+      const int c = sc[w];
+      for (int j = 0; j < c; j += 32) {
+        const bool v = j + lane < c;
+        const i64 k = v ? sk[w * K + j + lane] : 0, s = v ? ss[w * K + j + lane] : 0;
+        L.offer(K, v, k, s);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace pqk

@@ -1,0 +1,296 @@
+"""Parity of the whole plan (CUDA through the C ABI) with the CPU oracle,
+bit-exact: the hand-worked example, the small workload under many
+predicates, the full x100 workload in the benchmark's launch configuration,
+duplicate build keys, row ranges, unaligned views, CUDA-graph replay,
+batches, streaming (pinned, pageable, file sources), serving and errors."""
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from gpu_util import assert_same, load_tables, oracle_plan, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2512_02862_gb300 as pq  # noqa: E402
+import pins  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = pq.Context(arena_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.Stream()
+
+
+@pytest.fixture(scope="module")
+def small():
+    return datagen.workload("small")
+
+
+@pytest.fixture(scope="module")
+def small_tables(ctx, stream, small):
+    with torch.cuda.stream(stream):
+        return load_tables(pq, ctx, *small, stream=stream)
+
+
+def run(ctx, stream, plan):
+    with torch.cuda.stream(stream):
+        res = pq.pq_run_plan(ctx, plan, stream=stream)
+        ctx.sync(stream)
+    return res.as_dict()
+
+
+def test_hand_worked_example(ctx, stream):
+    g = pins.read_golden("tiny_plan.txt")
+    D = dict(key=np.array(g["D.key"][0], np.int32), seg=np.array(g["D.seg"][0], np.int8))
+    M = dict(key=np.array(g["M.key"][0], np.int64), dref=np.array(g["M.dref"][0], np.int32),
+             date=np.array(g["M.date"][0], np.int32))
+    F = dict(mkey=np.array(g["F.mkey"][0], np.int64), price=np.array(g["F.price"][0], np.int64),
+             disc=np.array(g["F.disc"][0], np.int8), date2=np.array(g["F.date2"][0], np.int32))
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF))
+    assert got["ngroups"] == g["expect.ngroups"][0][0]
+    assert got["keys"] == g["expect.keys"][0] and got["sums"] == g["expect.sums"][0]
+
+
+PREDS = [dict(seg=1, mc=1200, fc=1200), dict(seg=0, mc=2000, fc=300), dict(seg=4, mc=100, fc=2300),
+         dict(seg=1, mc=1200, fc=1200, d_op="!=", m_op=">=", f_op="<="),
+         dict(seg=9, mc=1200, fc=1200),                            # no D row passes
+         dict(seg=0, mc=0, fc=0, d_op="all", m_op="all", f_op="all")]
+
+
+@pytest.mark.parametrize("p", PREDS, ids=lambda p: "-".join(f"{k}{v}" for k, v in p.items()))
+@pytest.mark.parametrize("k", [1, 10, 64])
+def test_small_workload_matches_oracle(ctx, stream, small, small_tables, p, k):
+    TD, TM, TF, _ = small_tables
+    plan = pq.make_plan(TD, TM, TF, seg=p["seg"], m_date_lt=p["mc"], f_date_gt=p["fc"], k=k,
+                        d_op=p.get("d_op", "=="), m_op=p.get("m_op", "<"),
+                        f_op=p.get("f_op", ">"), flags=pq.PQ_PLAN_NO_GRAPH)
+    want = oracle_plan(*small, seg=p["seg"], mc=p["mc"], fc=p["fc"], k=k,
+                       d_op=p.get("d_op", "=="), m_op=p.get("m_op", "<"), f_op=p.get("f_op", ">"))
+    assert_same(run(ctx, stream, plan), want, str(p))
+
+
+def test_pass_all_closed_form(ctx, stream, small, small_tables):
+    """Every foreign key exists: groups = distinct F.mkey, and the top group
+    sum is the largest per-key sum of price * (100 - disc)."""
+    D, M, F = small
+    TD, TM, TF, _ = small_tables
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, d_op="all", m_op="all", f_op="all", k=64))
+    assert got["ngroups"] == len(np.unique(F["mkey"]))
+    rev = F["price"].astype(np.int64) * (100 - F["disc"].astype(np.int64))
+    keys, inv = np.unique(F["mkey"], return_inverse=True)
+    sums = np.bincount(inv, weights=rev.astype(np.float64))
+    assert got["sums"][0] == int(np.max(sums))
+
+
+def test_x100_workload_full_size(ctx, stream):
+    """The benchmark's workload (D 1.5M, M 15M, F 60M rows) and launch shape."""
+    D, M, F = datagen.workload("x100")
+    want = oracle.run_plan(D, M, F, k=10)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    plan = pq.make_plan(TD, TM, TF, k=10)
+    for rep in range(3):   # first run captures a graph, later runs replay it
+        assert_same(run(ctx, stream, plan), want, f"rep {rep}")
+    assert ctx.stats()["graph_replays"] >= 2
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
+def test_duplicate_build_keys(ctx, stream):
+    rng = np.random.default_rng(8)
+    D, M, F = datagen.make(3000, 40_000, 160_000, seed=8)
+    M = dict(M)
+    dup = rng.integers(0, 40_000, size=5000)
+    M["key"] = M["key"].copy()
+    M["key"][dup] = M["key"][(dup + 1) % 40_000]       # some keys now appear twice
+    want = oracle_plan(D, M, F, seg=2, mc=1800, fc=600, k=64)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=2, m_date_lt=1800, f_date_gt=600, k=64))
+    assert_same(got, want)
+
+
+@pytest.mark.parametrize("rows", [dict(m=(16, 30_000), f=(4096, 200_000)),
+                                  dict(d=(1, 5000), m=(3, 77_777), f=(5, 123_457)),
+                                  dict(f=(599_999, 1)), dict(m=(0, 0))])
+def test_row_ranges_and_unaligned_views(ctx, stream, small, small_tables, rows):
+    TD, TM, TF, _ = small_tables
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, rows=rows, k=10))
+    assert_same(got, oracle_plan(*small, rows=rows, k=10), str(rows))
+
+
+def random_plans(rng, tables, n, n_m, n_f, starts):
+    TD, TM, TF = tables
+    plans, specs = [], []
+    for _ in range(n):
+        a = int(rng.integers(0, n_m - 1)) // 16 * 16
+        b = min(n_m, a + int(rng.integers(1, n_m // 4)))
+        f0 = int(starts[a]) // 16 * 16
+        f1 = max(f0, int(starts[b]) // 16 * 16)
+        seg, c, k = int(rng.integers(0, 5)), int(rng.integers(0, 2406)), int(rng.integers(1, 65))
+        rows = dict(m=(a, b - a), f=(f0, f1 - f0))
+        plans.append(pq.make_plan(TD, TM, TF, seg=seg, m_date_lt=c, f_date_gt=c, k=k, rows=rows))
+        specs.append(dict(seg=seg, mc=c, fc=c, k=k, rows=rows))
+    return plans, specs
+
+
+def test_batch_of_uneven_plans(ctx, stream, small, small_tables):
+    D, M, F = small
+    starts = datagen.f_starts(1, len(M["key"]), len(F["mkey"]))
+    rng = np.random.default_rng(21)
+    plans, specs = random_plans(rng, small_tables[:3], 64, len(M["key"]), len(F["mkey"]), starts)
+    with torch.cuda.stream(stream):
+        res = pq.pq_run_batch(ctx, plans, stream=stream)
+        ctx.sync(stream)
+    for i, sp in enumerate(specs):
+        assert_same(res[i].as_dict(), oracle_plan(D, M, F, **sp), f"plan {i}")
+    # the same plans one at a time give the same results
+    for i in (0, 17, 63):
+        assert run(ctx, stream, plans[i]) == res[i].as_dict()
+
+
+def test_batch_with_cached_dimension_sets(ctx, stream, small, small_tables):
+    D, M, F = small
+    TD, TM, TF, _ = small_tables
+    plans = [pq.make_plan(TD, TM, TF, seg=s % 5, m_date_lt=300 + 97 * s, f_date_gt=2000 - 50 * s,
+                          k=10, flags=pq.PQ_PLAN_CACHE_DSET) for s in range(20)]
+    for rep in range(2):     # second pass hits the resident D-sets
+        with torch.cuda.stream(stream):
+            res = pq.pq_run_batch(ctx, plans, stream=stream)
+            ctx.sync(stream)
+        for s in range(20):
+            assert_same(res[s].as_dict(), oracle_plan(D, M, F, seg=s % 5, mc=300 + 97 * s,
+                                                      fc=2000 - 50 * s), f"rep {rep} plan {s}")
+
+
+@pytest.fixture(scope="module")
+def stream_ctx():
+    c = pq.Context(arena_bytes=2 << 30, chunk_bytes=1 << 20, ring_slots=3, copy_streams=2,
+                   ingest_threads=3)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("source", ["pinned", "pageable", "file"])
+def test_streaming_plan_matches_oracle(stream_ctx, stream, small, tmp_path, source):
+    D, M, F = small
+    ctx = stream_ctx
+
+    def cols(tab, names):
+        out = []
+        for nm in names:
+            a = np.ascontiguousarray(tab[nm])
+            if source == "pinned":
+                out.append(torch.from_numpy(a).pin_memory())
+            elif source == "pageable":
+                out.append(a)
+            else:
+                p = tmp_path / f"{id(tab)}_{nm}.bin"
+                a.tofile(p)
+                code = {1: pq.PQ_INT8, 4: pq.PQ_INT32, 8: pq.PQ_INT64}[a.itemsize]
+                out.append((str(p), code, 0, len(a)))
+        return out
+
+    with torch.cuda.stream(stream):
+        TD = pq.pq_load_columns(ctx, cols(D, ["key", "seg"]), mode=pq.PQ_STREAMING)
+        TM = pq.pq_load_columns(ctx, cols(M, ["key", "dref", "date"]), mode=pq.PQ_STREAMING)
+        TF = pq.pq_load_columns(ctx, cols(F, ["mkey", "price", "disc", "date2"]),
+                                mode=pq.PQ_STREAMING)
+        for p in (dict(seg=1, mc=1200, fc=1200), dict(seg=3, mc=2200, fc=100)):
+            got = pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF, seg=p["seg"], m_date_lt=p["mc"],
+                                                   f_date_gt=p["fc"], k=32), stream=stream)
+            ctx.sync(stream)
+            assert_same(got.as_dict(), oracle_plan(D, M, F, k=32, **p), source)
+        assert ctx.stats()["chunks_ingested"] > 20
+
+
+def test_streaming_fact_table_with_resident_dimensions(stream_ctx, stream, small):
+    D, M, F = small
+    ctx = stream_ctx
+    with torch.cuda.stream(stream):
+        d, m = to_dev(D), to_dev(M)
+        TD = pq.pq_load_columns(ctx, [d["key"], d["seg"]])
+        TM = pq.pq_load_columns(ctx, [m["key"], m["dref"], m["date"]])
+        TF = pq.pq_load_columns(ctx, [torch.from_numpy(F[c]).pin_memory()
+                                      for c in ("mkey", "price", "disc", "date2")],
+                                mode=pq.PQ_STREAMING)
+        got = pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF, rows=dict(f=(1000, 500_000))),
+                             stream=stream)
+        ctx.sync(stream)
+    assert_same(got.as_dict(), oracle_plan(D, M, F, rows=dict(f=(1000, 500_000))))
+
+
+def test_serving_results_same_alone_and_in_the_mix(ctx, stream, small, small_tables):
+    D, M, F = small
+    starts = datagen.f_starts(1, len(M["key"]), len(F["mkey"]))
+    rng = np.random.default_rng(33)
+    plans, specs = random_plans(rng, small_tables[:3], 150, len(M["key"]), len(F["mkey"]),
+                                starts)
+    tickets = [pq.pq_submit(ctx, p) for p in plans]
+    for i, t in enumerate(tickets):
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=60_000)
+        assert st == pq.PQ_OK and lat > 0
+        want = oracle_plan(D, M, F, **specs[i])
+        assert_same(res.as_dict(), want, f"served {i}")
+        if i % 37 == 0:
+            assert run(ctx, stream, plans[i]) == res.as_dict()   # alone
+
+
+def test_autotune_keeps_results(ctx, stream, small, small_tables):
+    TD, TM, TF, _ = small_tables
+    plan = pq.make_plan(TD, TM, TF)
+    t = pq.pq_autotune(ctx, plan)
+    assert t["tried"] >= 4 and t["best_ms"] > 0
+    assert_same(run(ctx, stream, plan), oracle_plan(*small))
+
+
+@pytest.mark.parametrize("price", [2**56, 2**60], ids=["sum-overflows", "product-overflows"])
+def test_overflow_is_reported(ctx, stream, price):
+    D = dict(key=np.array([1], np.int32), seg=np.array([1], np.int8))
+    M = dict(key=np.array([5], np.int64), dref=np.array([1], np.int32),
+             date=np.array([0], np.int32))
+    n = 4
+    F = dict(mkey=np.full(n, 5, np.int64), price=np.full(n, price, np.int64),
+             disc=np.zeros(n, np.int8), date2=np.full(n, 2000, np.int32))
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+        res = pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF, flags=pq.PQ_PLAN_NO_GRAPH),
+                             stream=stream)
+        with pytest.raises(pq.PQError) as e:
+            ctx.sync(stream)
+    assert e.value.status == pq.PQ_ERR_OVERFLOW and res.status == pq.PQ_ERR_OVERFLOW
+    assert oracle.run_plan(D, M, F)["status"] == 7
+
+
+def test_budget_and_argument_errors(stream, small):
+    c = pq.Context(arena_bytes=8 << 20)
+    D, M, F = small
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, c, D, M, F, stream=stream)
+        with pytest.raises(pq.PQError) as e:
+            pq.pq_run_plan(c, pq.make_plan(TD, TM, TF), stream=stream)
+        assert e.value.status == pq.PQ_ERR_BUDGET
+        with pytest.raises(pq.PQError) as e:
+            pq.pq_run_plan(c, pq.make_plan(TD, TM, TF, k=0), stream=stream)
+        assert e.value.status == pq.PQ_ERR_INVALID_ARG
+        with pytest.raises(pq.PQError) as e:
+            pq.pq_run_plan(c, pq.make_plan(TD, TM, TF, rows=dict(f=(0, 10**9))), stream=stream)
+        assert e.value.status == pq.PQ_ERR_INVALID_ARG
+    c.close()
