@@ -392,16 +392,254 @@ def run_ours(args):
     return 0
 
 
+def resident_tables(pq, ctx, host_or_np, stream):
+    import torch
+    dev = {k: {c: (torch.from_numpy(v) if isinstance(v, np.ndarray) else v).cuda()
+               for c, v in t.items()} for k, t in host_or_np.items()}
+    TD = pq.pq_load_columns(ctx, [dev["D"]["key"], dev["D"]["seg"]], stream=stream)
+    TM = pq.pq_load_columns(ctx, [dev["M"][c] for c in ("key", "dref", "date")], stream=stream)
+    TF = pq.pq_load_columns(ctx, [dev["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                            stream=stream)
+    return TD, TM, TF, dev
+
+
+def run_serve(args):
+    """Batched and served execution of a query stream (serving workload:
+    lognormal F sizes, randomised predicates, Poisson arrivals, 32 GB budget)
+    against the plain one-query-at-a-time path on the same GPU."""
+    import torch
+
+    import __graft_entry__
+    import datagen
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+    torch.cuda.set_device(0)
+    w = datagen.WORKLOADS["x100"]
+    D, M, F = datagen.workload("x100")
+    starts = datagen.f_starts(w["seed"], w["n_m"], w["n_f"])
+    qs = datagen.query_stream(5, args.queries, w["n_m"], starts, rate_qps=args.rate)
+    s = torch.cuda.Stream()
+    ctx = pq.Context(arena_bytes=32 << 30)
+    with torch.cuda.stream(s):
+        TD, TM, TF, keep = resident_tables(pq, ctx, {"D": D, "M": M, "F": F}, s)
+
+    def plan(q, flags):
+        return pq.make_plan(TD, TM, TF, seg=q["seg"], m_date_lt=q["c"], f_date_gt=q["c"], k=10,
+                            rows=dict(m=(q["m_row0"], q["m_rows"]),
+                                      f=(q["f_row0"], q["f_rows"])), flags=flags)
+
+    plain_plans = [plan(q, pq.PQ_PLAN_NO_GRAPH) for q in qs]
+    serve_plans = [plan(q, 0) for q in qs]
+    n = len(qs)
+    f_rows = sum(q["f_rows"] for q in qs)
+    res_plain = pq.pinned_results(n)
+    res_batch = pq.pinned_results(n)
+
+    def plain_closed():
+        with torch.cuda.stream(s):
+            for i, p in enumerate(plain_plans):
+                pq.pq_run_plan(ctx, p, res_plain[i], stream=s)
+                ctx.sync(s)      # the plain path waits for every query
+
+    def batched_closed(bs=512):
+        with torch.cuda.stream(s):
+            for a in range(0, n, bs):
+                sub = serve_plans[a:a + bs]
+                arr = (pq.pq_plan * len(sub))(*sub)
+                ctx.check(pq.library().pq_run_batch(
+                    ctx.h, arr, len(sub), pq.ctypes.byref(res_batch, a * pq.ctypes.sizeof(
+                        pq.pq_result)), pq._stream(s)))
+            ctx.sync(s)
+
+    def served_closed():
+        tickets = [pq.pq_submit(ctx, p) for p in serve_plans]
+        out = []
+        for t in tickets:
+            st, r, lat = pq.pq_poll(ctx, t, timeout_ms=600_000)
+            assert st == pq.PQ_OK, st
+            out.append(r.as_dict())
+        return out
+
+    with torch.cuda.stream(s):          # warm-up: code, caches, resident D-sets
+        for p in plain_plans[:args.warmup]:
+            pq.pq_run_plan(ctx, p, res_plain[0], stream=s)
+            ctx.sync(s)
+    batched_closed()
+    served_closed()
+    t0 = time.perf_counter(); plain_closed(); t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter(); batched_closed(); t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter(); served = served_closed(); t_serve = time.perf_counter() - t0
+    plain = [res_plain[i].as_dict() for i in range(n)]
+    batch = [res_batch[i].as_dict() for i in range(n)]
+    assert plain == batch == served, "batched / served results differ from the plain path"
+
+    # Open loop: queries arrive on their Poisson schedule.
+    arrive = np.array([q["arrive_s"] for q in qs])
+    lat_plain = []
+    t_start = time.perf_counter()
+    with torch.cuda.stream(s):
+        for i, p in enumerate(plain_plans):
+            now = time.perf_counter() - t_start
+            if now < arrive[i]:
+                time.sleep(arrive[i] - now)
+            pq.pq_run_plan(ctx, p, res_plain[i], stream=s)
+            ctx.sync(s)
+            lat_plain.append(time.perf_counter() - t_start - arrive[i])
+    tickets = [None] * n
+
+    def feeder():
+        t_s = time.perf_counter()
+        for i, p in enumerate(serve_plans):
+            now = time.perf_counter() - t_s
+            if now < arrive[i]:
+                time.sleep(arrive[i] - now)
+            tickets[i] = pq.pq_submit(ctx, p)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    lat_serve = []
+    for i in range(n):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        st, r, lat = pq.pq_poll(ctx, tickets[i], timeout_ms=600_000)
+        assert st == pq.PQ_OK and r.as_dict() == plain[i]
+        lat_serve.append(lat / 1e6)
+    th.join()
+    pct = lambda a, p: round(1e3 * float(np.percentile(a, p)), 3)
+    line = {
+        "metric": METRIC, "mode": "serve", "value": n / t_serve, "unit": "queries/s",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"serving: {n} queries on slices of x100 (F sizes lognormal "
+                               "median 500k, sigma 1.5, 10k..30M), randomised seg and date "
+                               f"constants, Poisson {args.rate} q/s, 32 GB budget",
+                   "f_rows_total": int(f_rows)},
+        "closed_loop_qps": {"plain": n / t_plain, "batched": n / t_batch, "served": n / t_serve},
+        "speedup_vs_plain": {"batched": t_plain / t_batch, "served": t_plain / t_serve},
+        "open_loop_latency_ms": {"rate_qps": args.rate,
+                                 "plain": {"p50": pct(lat_plain, 50), "p99": pct(lat_plain, 99)},
+                                 "served": {"p50": pct(lat_serve, 50),
+                                            "p99": pct(lat_serve, 99)}},
+        "results_identical": True,
+        "rows_per_s_served": f_rows / t_serve,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def measure_h2d(nbytes=1 << 30, reps=5):
+    """Host-to-device copy bandwidth from pinned memory (GB/s, best of reps)."""
+    import torch
+    src = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dst.copy_(src, non_blocking=True)
+        b.record()
+        b.synchronize()
+        best = max(best, nbytes / (a.elapsed_time(b) / 1e3) / 1e9)
+    del src, dst
+    return best
+
+
+def run_stream(args):
+    """Storage-resident plan: the x2000 tables live in pinned host memory and
+    stream through the 128 MiB chunk ring under a 16 GB device budget."""
+    import torch
+
+    import __graft_entry__
+    import datagen
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+    torch.cuda.set_device(0)
+    name = args.workload if args.workload != "x100" else "x2000"
+    w = datagen.WORKLOADS[name]
+    n_d, n_m, n_f = w["n_d"], w["n_m"], w["n_f"]
+    link = measure_h2d()
+    host = {}
+    for tn, cols, n in (("D", datagen.D_COLS, n_d), ("M", datagen.M_COLS, n_m),
+                        ("F", datagen.F_COLS, n_f)):
+        host[tn] = {c: torch.empty(n, dtype=getattr(torch, np.dtype(dt).name), pin_memory=True)
+                    for c, dt in cols}
+    out = {k: {c: t.numpy() for c, t in v.items()} for k, v in host.items()}
+    t0 = time.perf_counter()
+    D, M, F = datagen.workload(name, out=out)
+    t_gen = time.perf_counter() - t0
+    q = query(name)
+    s = torch.cuda.Stream()
+    ctx = pq.Context(arena_bytes=16 << 30, chunk_bytes=128 << 20, ring_slots=6, copy_streams=2)
+    HD = pq.pq_load_columns(ctx, [host["D"]["key"], host["D"]["seg"]], mode=pq.PQ_STREAMING)
+    HM = pq.pq_load_columns(ctx, [host["M"][c] for c in ("key", "dref", "date")],
+                            mode=pq.PQ_STREAMING)
+    HF = pq.pq_load_columns(ctx, [host["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                            mode=pq.PQ_STREAMING)
+    plan = pq.make_plan(HD, HM, HF, **q)
+    res = pq.pinned_results(1)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pq.pq_run_plan(ctx, plan, res[0], stream=s)
+            ctx.sync(s)
+        st0 = ctx.stats()
+        times = []
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                pq.pq_run_plan(ctx, plan, res[0], stream=s)
+                ctx.sync(s)
+                times.append(time.perf_counter() - t0)
+        st1 = ctx.stats()
+    got = res[0].as_dict()
+    # Sampled check: each reported group's sum recomputed from the rows of F
+    # that carry its key (with M's and D's predicates), independently of the GPU.
+    keys = np.array(got["keys"], dtype=np.int64)
+    sel = np.isin(F["mkey"], keys) & (F["date2"] > q["f_date_gt"]) if name != "skew" else \
+        np.isin(F["mkey"], keys)
+    rev = F["price"][sel].astype(np.int64) * (100 - F["disc"][sel].astype(np.int64))
+    sums = {int(k): 0 for k in keys}
+    for k, v in zip(F["mkey"][sel].tolist(), rev.tolist()):
+        sums[k] += v
+    checked = all(sums[int(k)] == int(sv) for k, sv in zip(got["keys"], got["sums"]))
+    t = float(np.median(times))
+    bytes_ = (st1["h2d_bytes"] - st0["h2d_bytes"]) / args.steps
+    gbps = bytes_ / t / 1e9
+    line = {
+        "metric": METRIC, "mode": "stream", "value": n_f / t, "unit": "rows/s",
+        "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT.get(name, name), "query": QUERY_TEXT,
+                   "source": "pinned host memory (stands in for NVMe)",
+                   "chunk_bytes": 128 << 20, "ring_slots": 6, "copy_streams": 2,
+                   "arena_gb": 16},
+        "h2d_gb_per_step": round(bytes_ / 1e9, 3), "gb_per_s": round(gbps, 1),
+        "roofline": {"bound": "host-link", "achieved": round(gbps, 1), "peak": round(link, 1),
+                     "unit": "GB/s", "frac": round(gbps / link, 4),
+                     "peak_source": "measured here: pinned cudaMemcpyAsync H2D, 1 GiB, best of 5"},
+        "arena_high_water_gb": round(st1["arena_high_water"] / 1e9, 2),
+        "chunks_per_step": (st1["chunks_ingested"] - st0["chunks_ingested"]) // args.steps,
+        "clocks": clk.summary(), "generate_s": round(t_gen, 1),
+        "result": {"ngroups": got["ngroups"], "top_keys": got["keys"][:3]},
+        "sampled_check": {"groups_checked": len(keys), "sums_match": checked},
+    }
+    print(json.dumps(line))
+    ctx.close()
+    return 0 if checked else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="x100", choices=["small", "x100", "skew"])
+    ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream"])
+    ap.add_argument("--workload", default="x100", choices=["small", "x100", "x2000", "skew"])
     ap.add_argument("--arena-gb", type=int, default=6)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-f-rows", type=int, default=20_000_000)
+    ap.add_argument("--queries", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=500.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args(argv)
@@ -409,6 +647,10 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serve":
+        return run_serve(args)
+    if args.mode == "stream":
+        return run_stream(args)
     return run_ours(args)
 
 

@@ -301,7 +301,7 @@ pq_status pq_default_options(pq_options* o) {
   if (!o) return PQ_ERR_INVALID_ARG;
   memset(o, 0, sizeof *o);
   o->block_threads = 256;
-  o->blocks_per_sm = 2;
+  o->blocks_per_sm = 4;
   o->load_factor = 0.5f;
   o->log2P = 6;
   o->chunk_bytes = 128ll << 20;

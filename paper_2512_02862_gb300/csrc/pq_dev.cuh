@@ -52,6 +52,72 @@ __device__ __forceinline__ u32 fib_bucket(i64 k, int log2P) {
   return log2P == 0 ? 0u : (u32)(((u64)k * 0x9E3779B97F4A7C15ULL) >> (64 - log2P));
 }
 
+// Slot of key k in a plan hash table of 2^(64 - shift) slots: the top bits of
+// the Fibonacci product (one 64-bit multiply).  Multiplicative hashing spreads
+// arithmetic key sequences (dense ids, strided keys) evenly, which keeps
+// linear-probing runs short.
+__device__ __forceinline__ u64 fib_slot(i64 k, int shift) {
+  return ((u64)k * 0x9E3779B97F4A7C15ULL) >> shift;
+}
+
+// A predicate on an int32 column as one unsigned range test:
+// pass = ((u32)(v - lo) <= span) xor neg.
+struct Pred32 {
+  int lo;
+  unsigned span;
+  unsigned neg;
+};
+__device__ __forceinline__ Pred32 to32(const Pred& p) {
+  const i64 lo = p.lo < (i64)INT32_MIN ? (i64)INT32_MIN : p.lo;
+  const i64 hi = p.hi > (i64)INT32_MAX ? (i64)INT32_MAX : p.hi;
+  Pred32 r;
+  if (lo > hi) {  // no int32 value is in range: all-range test, inverted
+    r.lo = INT32_MIN;
+    r.span = 0xFFFFFFFFu;
+    r.neg = p.neg ? 0u : 1u;
+  } else {
+    r.lo = (int)lo;
+    r.span = (unsigned)(hi - lo);
+    r.neg = p.neg ? 1u : 0u;
+  }
+  return r;
+}
+__device__ __forceinline__ unsigned pass32(const Pred32& p, int v) {
+  return (unsigned)((unsigned)(v - p.lo) <= p.span) ^ p.neg;
+}
+
+// L2 cache policies: hash tables are probed many times and should stay in L2
+// (evict_last); scanned columns are read once (evict_first, no L1 allocation).
+__device__ __forceinline__ u64 policy_keep() {
+  u64 p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ u64 policy_stream() {
+  u64 p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ i64 ld_keep(const i64* ptr, u64 pol) {
+  i64 v;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int4 ld_stream_v4(const void* ptr, u64 pol) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ longlong2 ld_stream_v2(const void* ptr, u64 pol) {
+  longlong2 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s64 {%0, %1}, [%2], %3;"
+               : "=l"(v.x), "=l"(v.y)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
+
 // Smallest power-of-two exponent with 2^e > count / lf (and e >= 6).  The
 // host sizes every table region with this same function from an upper bound
 // of the count, so the device's choice always fits the region.

@@ -33,7 +33,9 @@ void plan_assign(ResolvedPlan& r, char* base);
 // Batch header layout inside the workspace.
 struct BatchLayout {
   size_t desc = 0, tD = 0, tM = 0, tF = 0, dyn = 0, work = 0, ctr = 0, out = 0, end = 0;
-  size_t upload_bytes() const { return work - desc; }  // descriptors + tile prefixes
+  // Descriptors + static tile prefixes.  The dynamic prefixes that follow are
+  // written by the kernels and must never be overwritten by a re-upload.
+  size_t upload_bytes() const { return dyn - desc; }
   size_t zero_bytes() const { return out - work; }     // tickets + per-plan counters
 };
 BatchLayout batch_layout(int nq);

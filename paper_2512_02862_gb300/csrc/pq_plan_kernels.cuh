@@ -1,7 +1,7 @@
 // pq_plan_kernels.cuh -- the kernels of the three-table plan, batched.
 //
 // One launch of each kernel serves every plan of a batch: persistent blocks
-// claim tiles of a flattened work list (atomic ticket, work stealing) and map
+// claim tiles of a flattened work list (atomic tickets, work stealing) and map
 // a tile to its plan by binary search in a tile prefix array.  A single plan
 // is a batch of one.  Phases (each one kernel):
 //   dscan   D rows: seg predicate -> append key to the plan's D list
@@ -16,6 +16,15 @@
 // The last block of dscan / mscan / fprobe sizes the next phases from the
 // device counts (no host synchronisation: deferred synchronisation taken to
 // its end, Sec. 3.3).
+//
+// The scans are warp-centric: a warp claims its own tile (no block barrier on
+// the streaming path), reads 4 consecutive rows per lane with 128-bit loads
+// software-pipelined two iterations ahead, and reads the wide columns (keys,
+// references) only for 4-row groups whose predicate holds.  Passing rows are
+// compacted into per-warp shared-memory rings so that every hash probe runs
+// with all 32 lanes busy.  Scanned columns are loaded with an L2 evict-first
+// policy and hash-table probes with evict-last, so the tables stay in L2
+// while the columns stream past.
 #pragma once
 #include "../../include/pq.h"
 #include "pq_dev.cuh"
@@ -23,12 +32,13 @@
 
 namespace pqk {
 
-constexpr int kTD = 8192;   // D rows per tile
-constexpr int kTM = 4096;   // M rows per tile
-constexpr int kTF = 8192;   // F rows per tile
-constexpr int kTC = 8192;   // slots cleared per tile
-constexpr int kTB = 4096;   // list entries inserted per tile
-constexpr int kTK = 4096;   // groups per top-k tile
+constexpr int kTD = 4096;    // D rows per warp tile
+constexpr int kTM = 2048;    // M rows per warp tile
+constexpr int kTF = 4096;    // F rows per warp tile
+constexpr int kTC = 16384;   // slots cleared per block tile
+constexpr int kTB = 1024;    // list entries inserted per block tile
+constexpr int kTK = 1024;    // groups per top-k block tile
+constexpr int kQ = 256;      // entries of a warp's shared-memory ring
 
 struct QCtr {
   u64 dcount, mcount, gcount;
@@ -113,13 +123,20 @@ __device__ __forceinline__ int find_q(const i64* pre, int nq, i64 t) {
   return lo;
 }
 
-// Claim the next tile of phase `ph` (block-wide).
+// Claim the next tile of phase `ph` for the whole block.
 __device__ __forceinline__ i64 claim(u32* work, int ph) {
   __shared__ i64 s_t;
   __syncthreads();
   if (threadIdx.x == 0) s_t = atomicAdd(&work[ph], 1u);
   __syncthreads();
   return s_t;
+}
+
+// Claim the next tile of phase `ph` for one warp (no block barrier).
+__device__ __forceinline__ i64 warp_claim(u32* work, int ph) {
+  u32 t = 0;
+  if ((threadIdx.x & 31) == 0) t = atomicAdd(&work[ph], 1u);
+  return (i64)__shfl_sync(kFull, t, 0);
 }
 
 // Returns true in the block that finishes last; that block also resets the
@@ -141,7 +158,7 @@ __device__ __forceinline__ bool finish(u32* work, int ph) {
   return s_last;
 }
 
-// Block-wide exclusive scan helper over nq values produced by `f(q)`; writes
+// Block-wide exclusive scan over nq values produced by `f(q)`; writes
 // pre[0..nq] (pre[nq] = total).  Run by one whole block.
 template <typename F>
 __device__ void block_prefix(i64* pre, int nq, F f) {
@@ -186,10 +203,12 @@ __device__ __forceinline__ void q_latch(QCtr* c, DevStatus* st, int code, i64 de
   latch(st, code, detail);
 }
 
-__device__ __forceinline__ bool set_contains(const i64* set, u64 mask, i64 k) {
-  u64 s = slot_hash(k) & mask;
+// Membership of k in a key set of 2^(64 - shift) slots (linear probing).
+__device__ __forceinline__ bool set_contains(const i64* set, int shift, u64 mask, i64 k,
+                                             u64 keep) {
+  u64 s = fib_slot(k, shift);
   for (u64 p = 0; p <= mask; ++p) {
-    const i64 kk = __ldg(set + s);
+    const i64 kk = ld_keep(set + s, keep);
     if (kk == k) return true;
     if (kk == kEmpty) return false;
     s = (s + 1) & mask;
@@ -197,27 +216,80 @@ __device__ __forceinline__ bool set_contains(const i64* set, u64 mask, i64 k) {
   return false;
 }
 
+// Four consecutive int32 values starting at row e0; `rem` rows remain in the
+// column from e0 (rows beyond read as 0).
+template <bool VEC>
+__device__ __forceinline__ int4 load_i32x4(const int* p, i64 e0, i64 rem, u64 pol) {
+  if (VEC && rem >= 4) return ld_stream_v4(p + e0, pol);
+  int4 v;
+  v.x = rem > 0 ? ld_stream(p + e0) : 0;
+  v.y = rem > 1 ? ld_stream(p + e0 + 1) : 0;
+  v.z = rem > 2 ? ld_stream(p + e0 + 2) : 0;
+  v.w = rem > 3 ? ld_stream(p + e0 + 3) : 0;
+  return v;
+}
+
+// The int64 values of rows e0..e0+3 selected by `bits` (others unspecified).
+template <bool VEC>
+__device__ __forceinline__ void load_i64x4(const i64* p, i64 e0, i64 rem, u32 bits, u64 pol,
+                                           i64 v[4]) {
+  if (VEC && rem >= 4) {
+    const longlong2 a = ld_stream_v2(p + e0, pol);
+    const longlong2 c = ld_stream_v2(p + e0 + 2, pol);
+    v[0] = a.x, v[1] = a.y, v[2] = c.x, v[3] = c.y;
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) v[s] = (bits >> s) & 1 ? ld_stream(p + e0 + s) : 0;
+  }
+}
+
+// Predicate bits of 4 rows; rows at or beyond `rem` never pass.
+__device__ __forceinline__ u32 pass4(const Pred32& p, int4 d, i64 rem) {
+  const u32 live = rem >= 4 ? 0xFu : rem <= 0 ? 0u : (1u << rem) - 1u;
+  return (pass32(p, d.x) | pass32(p, d.y) << 1 | pass32(p, d.z) << 2 | pass32(p, d.w) << 3) &
+         live;
+}
+
+// Append the rows selected by `bits` (4 per lane) to a warp ring at `tail`:
+// slot order is (row-in-lane, lane), fixed by four ballots.  Returns the
+// number appended (warp-uniform).
+template <typename W>
+__device__ __forceinline__ u32 ring_append(u32 bits, u32 tail, W write) {
+  const u32 lt = lanemask_lt();
+  u32 base = tail;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const u32 m = __ballot_sync(kFull, (bits >> s) & 1u);
+    if ((bits >> s) & 1u) write(s, base + __popc(m & lt));
+    base += __popc(m);
+  }
+  return base - tail;
+}
+
 // ------------------------------------------------------------------ dscan ----
-// Tile of 8192 D rows; thread t handles rows 16t .. 16t+15 of each half (one
-// 128-bit load of seg = 16 int8 rows), keys are loaded only where seg passes.
+// Warp tile of 4096 D rows, 512 per iteration: lane l reads seg of rows
+// 16l .. 16l+15 with one 128-bit load; keys only where seg passes.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
   const bool ov = b.ov.table == 1;
   const i64 total = ov ? b.ov.tiles : b.tD[b.nq];
+  const int lane = threadIdx.x & 31;
+  const u64 strm = policy_stream();
   while (true) {
-    const i64 t = claim(b.work, kPhDscan);
+    const i64 t = warp_claim(b.work, kPhDscan);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tD, b.nq, t);
     const PlanDev& q = b.q[qi];
     const int* d_key = ov ? (const int*)b.ov.p[0] : q.d_key;
     const signed char* d_seg = ov ? (const signed char*)b.ov.p[1] : q.d_seg;
     const i64 n = ov ? b.ov.n : q.n_d;
-    const i64 r0 = (t - (ov ? 0 : b.tD[qi])) * kTD;
-    for (int half = 0; half < kTD / 4096; ++half) {
-      const i64 e0 = r0 + half * 4096 + threadIdx.x * 16;
+    const i64 base = (t - (ov ? 0 : b.tD[qi])) * kTD;
+    for (int it = 0; it < kTD / 512; ++it) {
+      if (base + it * 512 >= n) break;
+      const i64 e0 = base + it * 512 + lane * 16;
       u32 bits = 0;
       if (VEC && e0 + 16 <= n) {
-        int4 v = ld_stream(reinterpret_cast<const int4*>(d_seg + e0));
+        int4 v = ld_stream_v4(d_seg + e0, strm);
         const signed char* c = reinterpret_cast<const signed char*>(&v);
 #pragma unroll
         for (int s = 0; s < 16; ++s) bits |= (u32)pass(q.pd, c[s]) << s;
@@ -279,12 +351,13 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const u64 mask = (1ULL << *q.dset_log2) - 1;
+    const int e = *q.dset_log2;
+    const u64 mask = (1ULL << e) - 1;
     const i64 n = (i64)q.ctr->dcount;
     const i64 i0 = (t - pre[qi]) * kTB;
     for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x) {
       const i64 k = q.dlist[i];
-      u64 s = slot_hash(k) & mask;
+      u64 s = fib_slot(k, 64 - e);
       for (u64 p = 0; p <= mask; ++p) {
         const i64 old = (i64)atomicCAS((u64*)&q.dset[s], (u64)kEmpty, (u64)k);
         if (old == kEmpty || old == k) break;
@@ -296,73 +369,98 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
 }
 
 // ------------------------------------------------------------------ mscan ----
-// Tile of 4096 M rows laid out like the filter: warp w, group g, lane l reads
-// rows w*512 + g*128 + 4l .. +3.  dref is read only for groups with a date
-// hit, the key only for groups with a D-set member.
+// Warp tile of 2048 M rows, 128 per iteration (lane l: rows 4l .. 4l+3).
+// date is read two iterations ahead and dref one ahead, only for 4-row groups
+// with a date hit.  Date-passing (dref, row) pairs enter ring A and are
+// probed against the D-set 32 at a time; the keys of the members (read only
+// for them) enter ring B and leave for the M list in runs of 128 (one atomic
+// reservation per run).
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_plan_mscan(Batch b) {
+__global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
+  __shared__ int s_ad[8][kQ];
+  __shared__ u32 s_ar[8][kQ];
+  __shared__ i64 s_rb[8][kQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* ad = s_ad[warp];
+  u32* ar = s_ar[warp];
+  i64* rb = s_rb[warp];
+  const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 2;
   const i64 total = ov ? b.ov.tiles : b.tM[b.nq];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
-    const i64 t = claim(b.work, kPhMscan);
+    const i64 t = warp_claim(b.work, kPhMscan);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tM, b.nq, t);
     const PlanDev& q = b.q[qi];
     const i64* m_key = ov ? (const i64*)b.ov.p[0] : q.m_key;
     const int* m_dref = ov ? (const int*)b.ov.p[1] : q.m_dref;
     const int* m_date = ov ? (const int*)b.ov.p[2] : q.m_date;
-    const u64 dmask = (1ULL << *q.dset_log2) - 1;
-    const i64 r0 = (t - (ov ? 0 : b.tM[qi])) * kTM + warp * 512 + lane * 4;
+    const int de = *q.dset_log2;
+    const u64 dmask = (1ULL << de) - 1;
+    const Pred32 pm = to32(q.pm);
     const i64 n = ov ? b.ov.n : q.n_m;
-    u32 member = 0;
-    i64 keys[16];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const i64 e0 = r0 + g * 128;
-      int dt[4];
-      if (VEC && e0 + 4 <= n) {
-        int4 v = ld_stream(reinterpret_cast<const int4*>(m_date + e0));
-        dt[0] = v.x, dt[1] = v.y, dt[2] = v.z, dt[3] = v.w;
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dt[s] = e0 + s < n ? ld_stream(m_date + e0 + s) : 0;
+    const i64 base = (t - (ov ? 0 : b.tM[qi])) * kTM;
+    const i64 lim = min(n - base, (i64)kTM);
+    const int iters = (int)((lim + 127) / 128);
+    u32 ah = 0, at = 0, bh = 0, bt = 0;
+    auto flush_b = [&](u32 cnt) {
+      u64 o = 0;
+      if (lane == 0) o = atomicAdd(&q.ctr->mcount, (u64)cnt);
+      o = __shfl_sync(kFull, o, 0);
+      for (u32 j = lane; j < cnt; j += 32) q.mlist[o + j] = rb[(bh + j) & (kQ - 1)];
+      bh += cnt;
+    };
+    auto probe_a = [&](u32 cnt) {
+      bool mem = false;
+      i64 key = 0;
+      if ((u32)lane < cnt) {
+        const u32 j = (ah + lane) & (kQ - 1);
+        mem = set_contains(q.dset, 64 - de, dmask, ad[j], keep);
+        if (mem) key = __ldg(m_key + base + ar[j]);
       }
-      u32 hit = 0;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) hit |= (u32)(e0 + s < n && pass(q.pm, dt[s])) << s;
-      if (hit) {
-        int dr[4];
-        if (VEC && e0 + 4 <= n) {
-          int4 v = ld_stream(reinterpret_cast<const int4*>(m_dref + e0));
-          dr[0] = v.x, dr[1] = v.y, dr[2] = v.z, dr[3] = v.w;
-        } else {
-#pragma unroll
-          for (int s = 0; s < 4; ++s) dr[s] = (hit >> s) & 1 ? ld_stream(m_dref + e0 + s) : 0;
-        }
-        u32 mem = 0;
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-          if ((hit >> s) & 1) mem |= (u32)set_contains(q.dset, dmask, dr[s]) << s;
-        if (mem) {
-          if (VEC && e0 + 4 <= n) {
-            longlong2 a = ld_stream(reinterpret_cast<const longlong2*>(m_key + e0));
-            longlong2 c = ld_stream(reinterpret_cast<const longlong2*>(m_key + e0 + 2));
-            keys[g * 4 + 0] = a.x, keys[g * 4 + 1] = a.y, keys[g * 4 + 2] = c.x,
-                         keys[g * 4 + 3] = c.y;
-          } else {
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-              keys[g * 4 + s] = (mem >> s) & 1 ? ld_stream(m_key + e0 + s) : 0;
-          }
-        }
-        member |= mem << (4 * g);
+      const u32 m = __ballot_sync(kFull, mem);
+      if (mem) rb[(bt + __popc(m & lanemask_lt())) & (kQ - 1)] = key;
+      bt += __popc(m);
+      ah += cnt;
+      __syncwarp();
+      if (bt - bh >= 128) flush_b(128);
+    };
+    const i64 r0 = lane * 4;
+    int4 dB = load_i32x4<VEC>(m_date, base + r0, lim - r0, strm);
+    int4 dC = iters > 1 ? load_i32x4<VEC>(m_date, base + 128 + r0, lim - 128 - r0, strm)
+                        : make_int4(0, 0, 0, 0);
+    u32 hA = pass4(pm, dB, lim - r0);
+    int4 rA = hA ? load_i32x4<VEC>(m_dref, base + r0, lim - r0, strm) : make_int4(0, 0, 0, 0);
+    dB = dC;
+    if (iters > 2) dC = load_i32x4<VEC>(m_date, base + 256 + r0, lim - 256 - r0, strm);
+    for (int it = 0; it < iters; ++it) {
+      const i64 rel1 = (it + 1) * 128 + r0;
+      u32 hB = 0;
+      int4 rB = make_int4(0, 0, 0, 0);
+      if (it + 1 < iters) {
+        hB = pass4(pm, dB, lim - rel1);
+        if (hB) rB = load_i32x4<VEC>(m_dref, base + rel1, lim - rel1, strm);
       }
+      dB = dC;
+      if (it + 3 < iters) {
+        const i64 rel3 = (it + 3) * 128 + r0;
+        dC = load_i32x4<VEC>(m_date, base + rel3, lim - rel3, strm);
+      }
+      const int dr[4] = {rA.x, rA.y, rA.z, rA.w};
+      __syncwarp();
+      at += ring_append(hA, at, [&](int s, u32 pos) {
+        ad[pos & (kQ - 1)] = dr[s];
+        ar[pos & (kQ - 1)] = (u32)(it * 128 + r0 + s);
+      });
+      __syncwarp();
+      while (at - ah >= 32) probe_a(32);
+      hA = hB;
+      rA = rB;
     }
-    u64 at = warp_reserve(&q.ctr->mcount, (u32)__popc(member));
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if ((member >> j) & 1) q.mlist[at++] = keys[j];
+    __syncwarp();
+    if (at - ah) probe_a(at - ah);
+    if (bt - bh) flush_b(bt - bh);
+    __syncwarp();
   }
   if (finish(b.work, kPhMscan)) {
     block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
@@ -386,7 +484,8 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const u64 mask = (1ULL << q.ctr->mlog2) - 1;
+    const int e = q.ctr->mlog2;
+    const u64 mask = (1ULL << e) - 1;
     const i64 n = (i64)q.ctr->mcount;
     const i64 i0 = (t - pre[qi]) * kTB;
     for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x) {
@@ -395,7 +494,7 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
         q_latch(q.ctr, b.st, PQ_ERR_RESERVED_KEY, i);
         continue;
       }
-      u64 s = slot_hash(k) & mask;
+      u64 s = fib_slot(k, 64 - e);
       for (u64 p = 0; p <= mask; ++p) {
         const i64 old = (i64)atomicCAS((u64*)&q.ht_keys[s], (u64)kEmpty, (u64)k);
         if (old == kEmpty) {
@@ -412,96 +511,158 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
 }
 
 // ----------------------------------------------------------------- fprobe ----
-// Tile of 8192 F rows in 8 groups of 1024 (thread t: rows 4t .. 4t+3 of each
-// group).  All date2 loads of the tile are issued before any is used; mkey is
-// read only for groups with a passing row; price and disc only on a hit.
+struct ProbeCtx {
+  const i64* keys;
+  i64* sums;
+  u32* cnt;
+  u32* glist;
+  QCtr* ctr;
+  const i64* price;
+  const signed char* disc;
+  DevStatus* st;
+  i64 base;
+  u64 mask;
+  u64 keep;
+  int shift;
+  bool dup;
+};
+
+// Finish the probe of key k (F row base + r) whose first slot `slot` held kk:
+// on a match add the row's exact revenue (times the key's multiplicity) into
+// the first matching slot and record the slot as a group on its first hit.
+__device__ __forceinline__ void probe_finish(const ProbeCtx& c, i64 k, u32 r, u64 slot, i64 kk) {
+  i64 first = -1, mult = 0;
+  for (u64 p = 0; p <= c.mask; ++p) {
+    if (kk == kEmpty) break;
+    if (kk == k) {
+      if (first < 0) first = (i64)slot;
+      ++mult;
+      if (!c.dup) break;
+    }
+    slot = (slot + 1) & c.mask;
+    kk = ld_keep(c.keys + slot, c.keep);
+  }
+  if (first < 0) return;
+  const i64 row = c.base + r;
+  // Exact revenue: the product is formed in 128 bits so that a value outside
+  // int64 is reported instead of wrapping.
+  const __int128 v128 =
+      (__int128)mult * ((__int128)__ldg(c.price + row) * (100 - (i64)__ldg(c.disc + row)));
+  const i64 v = (i64)v128;
+  if (v128 != (__int128)v) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
+  const i64 old = (i64)atomicAdd((u64*)&c.sums[first], (u64)v);
+  if ((v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v))
+    q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
+  if (*(volatile u32*)&c.cnt[first] == 0 && atomicExch(&c.cnt[first], 1u) == 0u) {
+    const u64 gi = atomicAdd(&c.ctr->gcount, 1ULL);
+    c.glist[gi] = (u32)first;
+  }
+}
+
+__device__ __forceinline__ void probe1(const ProbeCtx& c, i64 k, u32 r) {
+  const u64 s = fib_slot(k, c.shift);
+  probe_finish(c, k, r, s, ld_keep(c.keys + s, c.keep));
+}
+
+// Two probes per lane with both first loads in flight together.
+__device__ __forceinline__ void probe2(const ProbeCtx& c, i64 k0, u32 r0, i64 k1, u32 r1) {
+  const u64 s0 = fib_slot(k0, c.shift), s1 = fib_slot(k1, c.shift);
+  const i64 kk0 = ld_keep(c.keys + s0, c.keep);
+  const i64 kk1 = ld_keep(c.keys + s1, c.keep);
+  probe_finish(c, k0, r0, s0, kk0);
+  probe_finish(c, k1, r1, s1, kk1);
+}
+
+// Warp tile of 4096 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
+// date2 is read two iterations ahead and mkey one ahead, only for 4-row groups
+// (one 32-byte sector) with a passing row.  Passing (key, row) pairs enter the
+// warp's ring and are probed 64 at a time, two per lane.
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
+__global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
+  __shared__ i64 s_qk[8][kQ];
+  __shared__ u32 s_qr[8][kQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  i64* qk = s_qk[warp];
+  u32* qr = s_qr[warp];
+  const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
   while (true) {
-    const i64 t = claim(b.work, kPhFprobe);
+    const i64 t = warp_claim(b.work, kPhFprobe);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tF, b.nq, t);
     const PlanDev& q = b.q[qi];
     const i64* f_mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
-    const i64* f_price = ov ? (const i64*)b.ov.p[1] : q.f_price;
-    const signed char* f_disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
     const int* f_date = ov ? (const int*)b.ov.p[3] : q.f_date;
-    const int e = q.ctr->mlog2;
-    const u64 mask = (1ULL << e) - 1;
-    const bool dup = q.ctr->dup != 0;
     const i64 n = ov ? b.ov.n : q.n_f;
-    const i64 r0 = (t - (ov ? 0 : b.tF[qi])) * kTF + threadIdx.x * 4;
-    int dt[8][4];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const i64 e0 = r0 + g * 1024;
-      if (VEC && e0 + 4 <= n) {
-        int4 v = ld_stream(reinterpret_cast<const int4*>(f_date + e0));
-        dt[g][0] = v.x, dt[g][1] = v.y, dt[g][2] = v.z, dt[g][3] = v.w;
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) dt[g][s] = e0 + s < n ? ld_stream(f_date + e0 + s) : 0;
+    const i64 base = (t - (ov ? 0 : b.tF[qi])) * kTF;
+    ProbeCtx pc;
+    pc.keys = q.ht_keys;
+    pc.sums = q.ht_sums;
+    pc.cnt = q.ht_cnt;
+    pc.glist = q.glist;
+    pc.ctr = q.ctr;
+    pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
+    pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+    pc.st = b.st;
+    pc.base = base;
+    const int e = q.ctr->mlog2;
+    pc.mask = (1ULL << e) - 1;
+    pc.shift = 64 - e;
+    pc.keep = keep;
+    pc.dup = q.ctr->dup != 0;
+    const Pred32 pf = to32(q.pf);
+    const i64 lim = min(n - base, (i64)kTF);
+    const int iters = (int)((lim + 127) / 128);
+    const i64 r0 = lane * 4;
+    u32 head = 0, tail = 0;
+    int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
+    int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, base + 128 + r0, lim - 128 - r0, strm)
+                        : make_int4(0, 0, 0, 0);
+    u32 bA = pass4(pf, dB, lim - r0);
+    i64 mA[4] = {0, 0, 0, 0};
+    if (bA) load_i64x4<VEC>(f_mkey, base + r0, lim - r0, bA, strm, mA);
+    dB = dC;
+    if (iters > 2) dC = load_i32x4<VEC>(f_date, base + 256 + r0, lim - 256 - r0, strm);
+    for (int it = 0; it < iters; ++it) {
+      const i64 rel1 = (it + 1) * 128 + r0;
+      u32 bB = 0;
+      i64 mB[4] = {0, 0, 0, 0};
+      if (it + 1 < iters) {
+        bB = pass4(pf, dB, lim - rel1);
+        if (bB) load_i64x4<VEC>(f_mkey, base + rel1, lim - rel1, bB, strm, mB);
       }
-    }
-    u32 hit = 0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g)
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        hit |= (u32)(r0 + g * 1024 + s < n && pass(q.pf, dt[g][s])) << (g * 4 + s);
-    if (!hit) continue;
-    i64 mk[8][4];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const i64 e0 = r0 + g * 1024;
-      const u32 hg = (hit >> (4 * g)) & 0xFu;
-      if (!hg) continue;
-      if (VEC && e0 + 4 <= n) {
-        longlong2 a = ld_stream(reinterpret_cast<const longlong2*>(f_mkey + e0));
-        longlong2 c = ld_stream(reinterpret_cast<const longlong2*>(f_mkey + e0 + 2));
-        mk[g][0] = a.x, mk[g][1] = a.y, mk[g][2] = c.x, mk[g][3] = c.y;
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) mk[g][s] = (hg >> s) & 1 ? ld_stream(f_mkey + e0 + s) : 0;
+      dB = dC;
+      if (it + 3 < iters) {
+        const i64 rel3 = (it + 3) * 128 + r0;
+        dC = load_i32x4<VEC>(f_date, base + rel3, lim - rel3, strm);
       }
-    }
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (!((hit >> (g * 4 + s)) & 1)) continue;
-        const i64 row = r0 + g * 1024 + s;
-        const i64 k = mk[g][s];
-        u64 slot = slot_hash(k) & mask;
-        i64 first = -1, mult = 0;
-        for (u64 p = 0; p <= mask; ++p) {
-          const i64 kk = __ldg(q.ht_keys + slot);
-          if (kk == kEmpty) break;
-          if (kk == k) {
-            if (first < 0) first = (i64)slot;
-            ++mult;
-            if (!dup) break;
-          }
-          slot = (slot + 1) & mask;
-        }
-        if (first < 0) continue;
-        // Exact revenue: the product is formed in 128 bits so that a value
-        // outside int64 is reported instead of wrapping.
-        const __int128 v128 =
-            (__int128)mult * ((__int128)__ldg(f_price + row) * (100 - (i64)__ldg(f_disc + row)));
-        const i64 v = (i64)v128;
-        if (v128 != (__int128)v) q_latch(q.ctr, b.st, PQ_ERR_OVERFLOW, k);
-        const i64 old = (i64)atomicAdd((u64*)&q.ht_sums[first], (u64)v);
-        if ((v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v))
-          q_latch(q.ctr, b.st, PQ_ERR_OVERFLOW, k);
-        if (*(volatile u32*)&q.ht_cnt[first] == 0 && atomicExch(&q.ht_cnt[first], 1u) == 0u) {
-          const u64 gi = atomicAdd(&q.ctr->gcount, 1ULL);
-          q.glist[gi] = (u32)first;
-        }
+      __syncwarp();
+      tail += ring_append(bA, tail, [&](int s, u32 pos) {
+        qk[pos & (kQ - 1)] = mA[s];
+        qr[pos & (kQ - 1)] = (u32)(it * 128 + r0 + s);
+      });
+      __syncwarp();
+      while (tail - head >= 64) {
+        const u32 j0 = (head + lane) & (kQ - 1), j1 = (head + 32 + lane) & (kQ - 1);
+        probe2(pc, qk[j0], qr[j0], qk[j1], qr[j1]);
+        head += 64;
       }
+      bA = bB;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) mA[s] = mB[s];
     }
+    __syncwarp();
+    if (tail - head >= 32) {
+      const u32 j = (head + lane) & (kQ - 1);
+      probe1(pc, qk[j], qr[j]);
+      head += 32;
+    }
+    if ((u32)lane < tail - head) {
+      const u32 j = (head + lane) & (kQ - 1);
+      probe1(pc, qk[j], qr[j]);
+    }
+    __syncwarp();
   }
   if (finish(b.work, kPhFprobe)) {
     block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
@@ -517,13 +678,15 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
 }
 
 // ------------------------------------------------------------------- topk ----
+// Per (plan, 1024 groups) block top-k; the block that finishes a plan's last
+// chunk merges the partial lists with all its warps, then warp 0 merges those.
 __global__ void __launch_bounds__(256) k_plan_topk(Batch b) {
   __shared__ i64 sk[8 * kMaxK], ss[8 * kMaxK];
   __shared__ int sc[8];
   __shared__ bool s_last;
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
     const i64 t = claim(b.work, kPhTopk);
     if (t >= total) break;
@@ -553,17 +716,20 @@ __global__ void __launch_bounds__(256) k_plan_topk(Batch b) {
       if (lane == 0) s_last = ((i64)tk == parts - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x < 32) {
+    if (s_last) {
       __threadfence();
-      const i64 parts = pre[qi + 1] - pre[qi];
+      const i64 cand = (pre[qi + 1] - pre[qi]) * K;
       L.clear();
-      for (i64 j = 0; j < parts * K; j += 32) {
+      for (i64 j = (i64)warp * 32; j < cand; j += blockDim.x) {
         const i64 e = j + lane;
-        const bool v = e < parts * K && (int)(e % K) < *(volatile int*)&q.tk_c[e / K];
+        const bool v = e < cand && (int)(e % K) < *(volatile int*)&q.tk_c[e / K];
         L.offer(K, v, v ? *(volatile i64*)&q.tk_k[e] : 0, v ? *(volatile i64*)&q.tk_s[e] : 0);
       }
-      L.store((i64*)q.out->keys, (i64*)q.out->sums);
-      if (lane == 0) q.out->n = L.cnt;
+      tk_block_merge(L, K, sk, ss, sc);
+      if (threadIdx.x < 32) {
+        L.store((i64*)q.out->keys, (i64*)q.out->sums);
+        if (lane == 0) q.out->n = L.cnt;
+      }
     }
   }
   finish(b.work, kPhTopk);
