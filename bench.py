@@ -166,13 +166,20 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the job's time is its slowest replica)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank: int, steps: int, t_max_s: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas: all units over the slowest time."""
+    return world * units_per_rank * steps / t_max_s
 
 
 # -------------------------------------------------------------- CPU side ----
@@ -301,7 +308,7 @@ def run_ours(args):
             pass
     assert res[0].as_dict() == check, "results changed between steps"
 
-    value = world * n_f * args.steps / (t_ms / 1e3)
+    value = job_rate(n_f, args.steps, t_ms / 1e3, world)
     plan_bytes = table_bytes(n_d, n_m, n_f)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -446,9 +453,10 @@ def run_serve(args):
             for a in range(0, n, bs):
                 sub = serve_plans[a:a + bs]
                 arr = (pq.pq_plan * len(sub))(*sub)
-                ctx.check(pq.library().pq_run_batch(
-                    ctx.h, arr, len(sub), pq.ctypes.byref(res_batch, a * pq.ctypes.sizeof(
-                        pq.pq_result)), pq._stream(s)))
+                dst = pq.ctypes.cast(pq.ctypes.addressof(res_batch) +
+                                     a * pq.ctypes.sizeof(pq.pq_result),
+                                     pq.ctypes.POINTER(pq.pq_result))
+                ctx.check(pq.library().pq_run_batch(ctx.h, arr, len(sub), dst, pq._stream(s)))
             ctx.sync(s)
 
     def served_closed():
@@ -522,6 +530,84 @@ def run_serve(args):
         "results_identical": True,
         "rows_per_s_served": f_rows / t_serve,
     }
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def run_ops(args):
+    """Each standalone operator on x100-sized columns, timed with CUDA events
+    on its stream (median of args.steps launches after args.warmup), against
+    the HBM roofline.  Algorithmic bytes: every input read once and every
+    output written once."""
+    import torch
+
+    import __graft_entry__
+    import datagen
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+    torch.cuda.set_device(0)
+    D, M, F = datagen.workload("x100")
+    s = torch.cuda.Stream()
+    ctx = pq.Context(arena_bytes=16 << 30)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    date2, mkey, price = dev(F["date2"]), dev(F["mkey"]), dev(F["price"])
+    m_key = dev(M["key"])
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+
+    def timed(fn):
+        with torch.cuda.stream(s):
+            for _ in range(args.warmup):
+                out = fn()
+            ctx.sync(s)
+            ts = []
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                out = fn()
+                b.record(s)
+                ts.append((a, b))
+            ctx.sync(s)
+        return float(np.median([a.elapsed_time(b) for a, b in ts])), out
+
+    rows = []
+
+    def add(name, ms, nbytes, units, note):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        rows.append({"op": name, "ms": round(ms, 4), "gb_per_s": round(gbs, 1),
+                     "frac_hbm": round(gbs / hbm, 3), "units_per_s": units / (ms / 1e3),
+                     "bytes": nbytes, "note": note})
+
+    n_f, n_m = len(F["mkey"]), len(M["key"])
+    ms, (sel, cnt) = timed(lambda: pq.pq_filter(ctx, date2, ">", 1200, stream=s))
+    k = int(cnt.item())
+    add("pq_filter", ms, 4 * n_f + 8 * k, n_f, f"F.date2 > 1200 over {n_f} int32 rows, {k} ids out")
+    for lp in (6, 10):
+        ms, _ = timed(lambda: pq.pq_partition(ctx, mkey, [price], log2P=lp, stream=s))
+        add(f"pq_partition P={1 << lp}", ms, 2 * 16 * n_f, n_f,
+            f"F.mkey + price ({n_f} rows), read twice-free definition: 16 B in + 16 B out per row")
+    ht_holder = {}
+
+    def build():
+        if "ht" in ht_holder:
+            ht_holder["ht"].free(s)
+        ht_holder["ht"] = pq.pq_join_build(ctx, m_key, None, stream=s)
+        return ht_holder["ht"]
+    ms, ht = timed(build)
+    add("pq_join_build", ms, 8 * n_m, n_m, f"{n_m} int64 M keys, value = row id")
+    ms, (r, v, c) = timed(lambda: pq.pq_join_probe(ctx, ht_holder["ht"], mkey, cap=n_f, stream=s))
+    hits = int(c.item())
+    add("pq_join_probe", ms, 8 * n_f + 16 * hits, n_f, f"{n_f} F.mkey probes, {hits} pairs out")
+    ms, (gk, gs, gn) = timed(lambda: pq.pq_groupby_sum(ctx, mkey, price, cap=n_m, stream=s))
+    g = int(gn.item())
+    add("pq_groupby_sum", ms, 16 * n_f + 16 * g, n_f, f"group {n_f} rows by F.mkey, {g} groups")
+    ms, _ = timed(lambda: pq.pq_topk(ctx, gk[:g], gs[:g], 10, stream=s))
+    add("pq_topk", ms, 16 * g, g, f"k=10 over {g} groups")
+    line = {"metric": METRIC, "mode": "ops", "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["x100"], "peak_hbm_gbs": hbm},
+            "ops": rows}
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -633,7 +719,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream"])
+    ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream", "ops"])
     ap.add_argument("--workload", default="x100", choices=["small", "x100", "x2000", "skew"])
     ap.add_argument("--arena-gb", type=int, default=6)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -651,6 +737,8 @@ def main(argv=None):
         return run_serve(args)
     if args.mode == "stream":
         return run_stream(args)
+    if args.mode == "ops":
+        return run_ops(args)
     return run_ours(args)
 
 

@@ -103,6 +103,61 @@ __device__ __forceinline__ i64 ld_keep(const i64* ptr, u64 pol) {
   asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
   return v;
 }
+__device__ __forceinline__ unsigned short ld_keep_u16(const unsigned short* ptr, u64 pol) {
+  unsigned short v;
+  asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
+// Bucketized, tagged open addressing for the plan's tables.  A table of 2^e
+// slots is 2^(e-3) buckets of 8 slots; a bucket's eight 16-bit tags fill one
+// 16-byte word.  Key k goes to bucket = top bits of the Fibonacci product
+// h = k * 2^64/phi and carries tag = the 16 bits below them (forced odd, so
+// 0 marks an empty slot).  A lookup reads one 16-byte tag word, compares all
+// eight tags at once (SIMD halfword compares), reads an 8-byte key only on a
+// tag match, and moves to the next bucket only while buckets are full; an
+// insert claims the first free tag of the first non-full bucket with a 16-bit
+// CAS, so a bucket with a free slot ends every lookup.
+struct BucketTag {
+  u64 bucket;
+  unsigned tag;
+};
+__device__ __forceinline__ BucketTag bucket_tag(i64 k, int shiftb) {
+  const u64 h = (u64)k * 0x9E3779B97F4A7C15ULL;
+  BucketTag r;
+  r.bucket = h >> shiftb;
+  r.tag = (unsigned)((h >> (shiftb - 16)) & 0xFFFFu) | 1u;
+  return r;
+}
+
+// Byte masks of the slots of a bucket whose tag equals v (v replicated in both
+// halves of v2): byte j of lo (slots 0..3) / hi (slots 4..7) is 0xFF on a match.
+struct Mask8 {
+  u32 lo, hi;
+};
+__device__ __forceinline__ Mask8 match8(uint4 w, unsigned v2) {
+  Mask8 m;
+  m.lo = __byte_perm(__vcmpeq2(w.x, v2), __vcmpeq2(w.y, v2), 0x7531);
+  m.hi = __byte_perm(__vcmpeq2(w.z, v2), __vcmpeq2(w.w, v2), 0x7531);
+  return m;
+}
+__device__ __forceinline__ bool any8(Mask8 m) { return (m.lo | m.hi) != 0; }
+// Index of the first set slot (mask must be non-empty) and its removal.
+__device__ __forceinline__ int first8(Mask8 m) {
+  return m.lo ? (__ffs(m.lo) - 1) >> 3 : 4 + ((__ffs(m.hi) - 1) >> 3);
+}
+__device__ __forceinline__ void drop8(Mask8& m, int j) {
+  if (j < 4) m.lo &= ~(0xFFu << (8 * j));
+  else m.hi &= ~(0xFFu << (8 * (j - 4)));
+}
+
+__device__ __forceinline__ uint4 ld_keep_v4u(const void* ptr, u64 pol) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(ptr), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ int4 ld_stream_v4(const void* ptr, u64 pol) {
   int4 v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"

@@ -92,10 +92,9 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
 size_t plan_bytes(const ResolvedPlan& r) {
   size_t b = 0;
   if (r.builds) b += al(r.n_d * 8);                                // D list
-  if (r.builds && r.dset_from == -1) b += 256 + al(((size_t)8) << r.e_d);  // own D-set
-  const size_t slots = (size_t)1 << r.e_m;
+  if (r.builds && r.dset_from == -1) b += dset_block_bytes(r.e_d);  // own D-set
   b += al(r.n_m * 8);                    // M list
-  b += al(slots * 8) * 2 + al(slots * 4);  // table keys, sums, first-hit flags
+  b += mtable_bytes(r.e_m);              // table tags, keys, sums, first-hit flags
   b += al(r.n_m * 4);                    // group list
   b += al(r.parts * r.dev.k * 8) * 2 + al(r.parts * 4);  // top-k partials
   return b;
@@ -111,16 +110,9 @@ void plan_assign(ResolvedPlan& r, char* base) {
   };
   d.build_dset = r.builds ? 1 : 0;
   d.dlist = r.builds ? (i64*)take(r.n_d * 8) : nullptr;
-  if (r.builds && r.dset_from == -1) {
-    char* blk = take(256 + (((size_t)8) << r.e_d));
-    d.dset_log2 = (int*)blk;
-    d.dset = (i64*)(blk + 256);
-  }
-  const size_t slots = (size_t)1 << r.e_m;
+  if (r.builds && r.dset_from == -1) dset_block_assign(take(dset_block_bytes(r.e_d)), r.e_d, d);
   d.mlist = (i64*)take(r.n_m * 8);
-  d.ht_keys = (i64*)take(slots * 8);
-  d.ht_sums = (i64*)take(slots * 8);
-  d.ht_cnt = (u32*)take(slots * 4);
+  p = mtable_assign(p, r.e_m, d);
   d.glist = (u32*)take(r.n_m * 4);
   d.tk_k = (i64*)take(r.parts * d.k * 8);
   d.tk_s = (i64*)take(r.parts * d.k * 8);
@@ -356,13 +348,13 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       e.pred = r.dev.pd;
       e.lf1024 = r.dev.lf1024;
       e.log2max = r.e_d;
-      e.block = ctx->arena.alloc(256 + (((size_t)8) << r.e_d));
+      e.block = ctx->arena.alloc(dset_block_bytes(r.e_d));
       if (!e.block) continue;  // no room to cache: build in the workspace
       if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
         ctx->arena.release_now(e.block);
         continue;
       }
-      e.keys = (i64*)((char*)e.block + 256);
+      e.keys = nullptr;  // laid out by dset_block_assign
       if (ctx->dsets.size() >= 64) {
         // Evict the least recently used set that this batch does not use.
         auto old = ctx->dsets.end();
@@ -413,10 +405,10 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     PlanDev& d = r.dev;
     if (r.dset_from >= 0) {
       d.dset_log2 = R[r.dset_from].dev.dset_log2;
+      d.dset_tag = R[r.dset_from].dev.dset_tag;
       d.dset = R[r.dset_from].dev.dset;
     } else if (r.cache) {
-      d.dset_log2 = (int*)r.cache->block;
-      d.dset = r.cache->keys;
+      dset_block_assign((char*)r.cache->block, r.cache->log2max, d);
     }
     d.ctr = ctr + i;
     d.out = out + i;

@@ -68,8 +68,10 @@ struct PlanDev {
   int vec;          // every column pointer is 16-byte aligned
   i64* dlist;
   int* dset_log2;   // header word of the D-set block
-  i64* dset;        // D-set slots
+  i64* dset;        // D-set keys
+  unsigned short* dset_tag;  // D-set tags (0 = empty)
   i64* mlist;
+  unsigned short* ht_tag;    // M table tags (0 = empty)
   i64* ht_keys;
   i64* ht_sums;
   u32* ht_cnt;
@@ -203,17 +205,62 @@ __device__ __forceinline__ void q_latch(QCtr* c, DevStatus* st, int code, i64 de
   latch(st, code, detail);
 }
 
-// Membership of k in a key set of 2^(64 - shift) slots (linear probing).
-__device__ __forceinline__ bool set_contains(const i64* set, int shift, u64 mask, i64 k,
-                                             u64 keep) {
-  u64 s = fib_slot(k, shift);
-  for (u64 p = 0; p <= mask; ++p) {
-    const i64 kk = ld_keep(set + s, keep);
-    if (kk == k) return true;
-    if (kk == kEmpty) return false;
-    s = (s + 1) & mask;
+// Geometry of a bucketized table of 2^e slots: bucket mask and the shift that
+// takes a bucket index from the top of the Fibonacci product.
+struct Geo {
+  u64 bmask;
+  int shiftb;
+};
+__device__ __forceinline__ Geo geo(int e) {
+  Geo g;
+  g.bmask = (1ULL << (e - 3)) - 1;
+  g.shiftb = 64 - (e - 3);
+  return g;
+}
+
+// Membership of k in a bucketized key set.
+__device__ __forceinline__ bool set_contains(const unsigned short* tags, const i64* keys, Geo g,
+                                             i64 k, u64 keep) {
+  const BucketTag bt = bucket_tag(k, g.shiftb);
+  const unsigned v2 = bt.tag * 0x10001u;
+  u64 b = bt.bucket;
+  for (u64 p = 0; p <= g.bmask; ++p) {
+    const uint4 w = ld_keep_v4u(tags + b * 8, keep);
+    Mask8 m = match8(w, v2);
+    while (any8(m)) {
+      const int j = first8(m);
+      if (ld_keep(keys + b * 8 + j, keep) == k) return true;
+      drop8(m, j);
+    }
+    if (any8(match8(w, 0u))) return false;
+    b = (b + 1) & g.bmask;
   }
   return false;
+}
+
+// Insert k (one slot per insert, so duplicate keys take one slot each):
+// claim the first free tag of the first non-full bucket with a 16-bit CAS,
+// then write the key.  Returns the slot.
+__device__ __forceinline__ u64 tagged_insert(unsigned short* tags, i64* keys, Geo g, i64 k) {
+  const BucketTag bt = bucket_tag(k, g.shiftb);
+  u64 b = bt.bucket;
+  for (u64 p = 0; p <= g.bmask; ++p) {
+    uint4 w;
+    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                 : "l"(tags + b * 8));
+    Mask8 e = match8(w, 0u);
+    while (any8(e)) {
+      const int j = first8(e);
+      if (atomicCAS(tags + b * 8 + j, (unsigned short)0, (unsigned short)bt.tag) == 0) {
+        keys[b * 8 + j] = k;
+        return b * 8 + j;
+      }
+      drop8(e, j);
+    }
+    b = (b + 1) & g.bmask;
+  }
+  return ~0ULL;  // unreachable: a table is never filled beyond its load factor
 }
 
 // Four consecutive int32 values starting at row e0; `rem` rows remain in the
@@ -322,7 +369,8 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
 }
 
 // ------------------------------------------------------------------- fill ----
-// which = 0: D-set slots, 1: M table keys.
+// Clear the tags (2 bytes per slot) of the D-set (which = 0) or the M table
+// (which = 1); keys and sums are written by the inserting thread.
 __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
   const i64* pre = b.dyn + (which == 0 ? 0 : 2) * (b.nq + 1);
   const int ph = which == 0 ? kPhDfill : kPhMfill;
@@ -333,11 +381,11 @@ __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
     const int e = which == 0 ? *q.dset_log2 : q.ctr->mlog2;
-    i64* dst = which == 0 ? q.dset : q.ht_keys;
+    unsigned short* dst = which == 0 ? q.dset_tag : q.ht_tag;
     const i64 n = (i64)1 << e;
     const i64 s0 = (t - pre[qi]) * kTC;
-    for (i64 i = s0 + threadIdx.x * 2; i < s0 + kTC && i < n; i += 512)
-      *reinterpret_cast<longlong2*>(dst + i) = make_longlong2(kEmpty, kEmpty);
+    for (i64 i = s0 + threadIdx.x * 8; i < s0 + kTC && i < n; i += 256 * 8)
+      *reinterpret_cast<int4*>(dst + i) = make_int4(0, 0, 0, 0);
   }
   finish(b.work, ph);
 }
@@ -351,19 +399,11 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int e = *q.dset_log2;
-    const u64 mask = (1ULL << e) - 1;
+    const Geo g = geo(*q.dset_log2);
     const i64 n = (i64)q.ctr->dcount;
     const i64 i0 = (t - pre[qi]) * kTB;
-    for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x) {
-      const i64 k = q.dlist[i];
-      u64 s = fib_slot(k, 64 - e);
-      for (u64 p = 0; p <= mask; ++p) {
-        const i64 old = (i64)atomicCAS((u64*)&q.dset[s], (u64)kEmpty, (u64)k);
-        if (old == kEmpty || old == k) break;
-        s = (s + 1) & mask;
-      }
-    }
+    for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x)
+      tagged_insert(q.dset_tag, q.dset, g, q.dlist[i]);
   }
   finish(b.work, kPhDbuild);
 }
@@ -395,8 +435,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
     const i64* m_key = ov ? (const i64*)b.ov.p[0] : q.m_key;
     const int* m_dref = ov ? (const int*)b.ov.p[1] : q.m_dref;
     const int* m_date = ov ? (const int*)b.ov.p[2] : q.m_date;
-    const int de = *q.dset_log2;
-    const u64 dmask = (1ULL << de) - 1;
+    const Geo dg = geo(*q.dset_log2);
     const Pred32 pm = to32(q.pm);
     const i64 n = ov ? b.ov.n : q.n_m;
     const i64 base = (t - (ov ? 0 : b.tM[qi])) * kTM;
@@ -415,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
       i64 key = 0;
       if ((u32)lane < cnt) {
         const u32 j = (ah + lane) & (kQ - 1);
-        mem = set_contains(q.dset, 64 - de, dmask, ad[j], keep);
+        mem = set_contains(q.dset_tag, q.dset, dg, ad[j], keep);
         if (mem) key = __ldg(m_key + base + ar[j]);
       }
       const u32 m = __ballot_sync(kFull, mem);
@@ -484,8 +523,7 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int e = q.ctr->mlog2;
-    const u64 mask = (1ULL << e) - 1;
+    const Geo g = geo(q.ctr->mlog2);
     const i64 n = (i64)q.ctr->mcount;
     const i64 i0 = (t - pre[qi]) * kTB;
     for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x) {
@@ -494,17 +532,9 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
         q_latch(q.ctr, b.st, PQ_ERR_RESERVED_KEY, i);
         continue;
       }
-      u64 s = fib_slot(k, 64 - e);
-      for (u64 p = 0; p <= mask; ++p) {
-        const i64 old = (i64)atomicCAS((u64*)&q.ht_keys[s], (u64)kEmpty, (u64)k);
-        if (old == kEmpty) {
-          q.ht_sums[s] = 0;
-          q.ht_cnt[s] = 0;
-          break;
-        }
-        if (old == k) q.ctr->dup = 1;
-        s = (s + 1) & mask;
-      }
+      const u64 s = tagged_insert(q.ht_tag, q.ht_keys, g, k);
+      q.ht_sums[s] = 0;
+      q.ht_cnt[s] = 0;
     }
   }
   finish(b.work, kPhMbuild);
@@ -512,6 +542,7 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
 
 // ----------------------------------------------------------------- fprobe ----
 struct ProbeCtx {
+  const unsigned short* tags;
   const i64* keys;
   i64* sums;
   u32* cnt;
@@ -521,26 +552,34 @@ struct ProbeCtx {
   const signed char* disc;
   DevStatus* st;
   i64 base;
-  u64 mask;
   u64 keep;
-  int shift;
-  bool dup;
+  Geo g;
 };
 
-// Finish the probe of key k (F row base + r) whose first slot `slot` held kk:
-// on a match add the row's exact revenue (times the key's multiplicity) into
-// the first matching slot and record the slot as a group on its first hit.
-__device__ __forceinline__ void probe_finish(const ProbeCtx& c, i64 k, u32 r, u64 slot, i64 kk) {
+// Finish the probe of key k (F row base + r) whose home bucket's tag word w
+// has been read: count the slots holding k (its multiplicity in M', found in
+// the home bucket and, while buckets are full, the next ones) and add the
+// row's exact revenue times that count into the first of them, recording
+// that slot as a group on its first hit.
+__device__ __forceinline__ void probe_finish(const ProbeCtx& c, i64 k, u32 r, BucketTag bt,
+                                             uint4 w) {
   i64 first = -1, mult = 0;
-  for (u64 p = 0; p <= c.mask; ++p) {
-    if (kk == kEmpty) break;
-    if (kk == k) {
-      if (first < 0) first = (i64)slot;
-      ++mult;
-      if (!c.dup) break;
+  const unsigned v2 = bt.tag * 0x10001u;
+  u64 b = bt.bucket;
+  for (u64 p = 0; p <= c.g.bmask; ++p) {
+    Mask8 m = match8(w, v2);
+    while (any8(m)) {
+      const int j = first8(m);
+      const u64 slot = b * 8 + j;
+      if (ld_keep(c.keys + slot, c.keep) == k) {
+        if (first < 0) first = (i64)slot;
+        ++mult;
+      }
+      drop8(m, j);
     }
-    slot = (slot + 1) & c.mask;
-    kk = ld_keep(c.keys + slot, c.keep);
+    if (any8(match8(w, 0u))) break;
+    b = (b + 1) & c.g.bmask;
+    w = ld_keep_v4u(c.tags + b * 8, c.keep);
   }
   if (first < 0) return;
   const i64 row = c.base + r;
@@ -560,17 +599,17 @@ __device__ __forceinline__ void probe_finish(const ProbeCtx& c, i64 k, u32 r, u6
 }
 
 __device__ __forceinline__ void probe1(const ProbeCtx& c, i64 k, u32 r) {
-  const u64 s = fib_slot(k, c.shift);
-  probe_finish(c, k, r, s, ld_keep(c.keys + s, c.keep));
+  const BucketTag bt = bucket_tag(k, c.g.shiftb);
+  probe_finish(c, k, r, bt, ld_keep_v4u(c.tags + bt.bucket * 8, c.keep));
 }
 
-// Two probes per lane with both first loads in flight together.
+// Two probes per lane with both home-bucket loads in flight together.
 __device__ __forceinline__ void probe2(const ProbeCtx& c, i64 k0, u32 r0, i64 k1, u32 r1) {
-  const u64 s0 = fib_slot(k0, c.shift), s1 = fib_slot(k1, c.shift);
-  const i64 kk0 = ld_keep(c.keys + s0, c.keep);
-  const i64 kk1 = ld_keep(c.keys + s1, c.keep);
-  probe_finish(c, k0, r0, s0, kk0);
-  probe_finish(c, k1, r1, s1, kk1);
+  const BucketTag b0 = bucket_tag(k0, c.g.shiftb), b1 = bucket_tag(k1, c.g.shiftb);
+  const uint4 w0 = ld_keep_v4u(c.tags + b0.bucket * 8, c.keep);
+  const uint4 w1 = ld_keep_v4u(c.tags + b1.bucket * 8, c.keep);
+  probe_finish(c, k0, r0, b0, w0);
+  probe_finish(c, k1, r1, b1, w1);
 }
 
 // Warp tile of 4096 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
@@ -597,6 +636,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
     const i64 n = ov ? b.ov.n : q.n_f;
     const i64 base = (t - (ov ? 0 : b.tF[qi])) * kTF;
     ProbeCtx pc;
+    pc.tags = q.ht_tag;
     pc.keys = q.ht_keys;
     pc.sums = q.ht_sums;
     pc.cnt = q.ht_cnt;
@@ -607,10 +647,8 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
     pc.st = b.st;
     pc.base = base;
     const int e = q.ctr->mlog2;
-    pc.mask = (1ULL << e) - 1;
-    pc.shift = 64 - e;
+    pc.g = geo(e);
     pc.keep = keep;
-    pc.dup = q.ctr->dup != 0;
     const Pred32 pf = to32(q.pf);
     const i64 lim = min(n - base, (i64)kTF);
     const int iters = (int)((lim + 127) / 128);

@@ -267,10 +267,9 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     return ctx->ring.upload(ws + L.desc, host.data(), host.size(), s);
   };
   // D-set region placeholder until the D scan is done: a 64-slot block.
-  char* dset_blk = (char*)scr.get(256 + 64 * 8);
+  char* dset_blk = (char*)scr.get(dset_block_bytes(6));
   if (!dset_blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set");
-  d.dset_log2 = (int*)dset_blk;
-  d.dset = (i64*)(dset_blk + 256);
+  dset_block_assign(dset_blk, 6, d);
   PQ_CUDA(ctx, upload_desc(r.resident[0] ? (r.n_d + kTD - 1) / kTD : 0,
                            r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
                            r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
@@ -388,10 +387,9 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     }
     const int e = cap_log2(count, d.lf1024);
     if (t == 0) {
-      char* blk = (char*)scr.get(256 + (((size_t)8) << e));
+      char* blk = (char*)scr.get(dset_block_bytes(e));
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set of 2^%d slots", e);
-      d.dset_log2 = (int*)blk;
-      d.dset = (i64*)(blk + 256);
+      dset_block_assign(blk, e, d);
       PQ_CUDA(ctx, upload_desc(0, r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
                                r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
       // The dscan kernel sized the fill/build phases; it wrote the log2 into
@@ -402,18 +400,11 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         if (st != PQ_OK) return st;
       }
     } else {
-      const size_t slots = (size_t)1 << e;
       const i64 parts = std::max<i64>(1, (count + kTK - 1) / kTK);
-      char* blk = (char*)scr.get(al(slots * 8) * 2 + al(slots * 4) + al(count * 4 + 4) +
-                                 al(parts * d.k * 8) * 2 + al(parts * 4));
+      char* blk = (char*)scr.get(mtable_bytes(e) + al(count * 4 + 4) + al(parts * d.k * 8) * 2 +
+                                 al(parts * 4));
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: M table of 2^%d slots", e);
-      char* p = blk;
-      d.ht_keys = (i64*)p;
-      p += al(slots * 8);
-      d.ht_sums = (i64*)p;
-      p += al(slots * 8);
-      d.ht_cnt = (u32*)p;
-      p += al(slots * 4);
+      char* p = mtable_assign(blk, e, d);
       d.glist = (u32*)p;
       p += al(count * 4 + 4);
       d.tk_k = (i64*)p;
