@@ -250,6 +250,26 @@ pq_status pq_topk(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t
                   const int64_t* d_n, int k, int64_t* out_keys, int64_t* out_sums,
                   int64_t* d_nout, void* stream);
 
+/* Allocation-free selection (no counterpart in the paper): the same result
+ * as pq_filter, for callers that cannot allocate device memory -- code that
+ * runs while a CUDA graph is being captured, or inside a runtime that owns
+ * every allocation -- and that may have no context.  Its scratch is a fixed
+ * static device array inside libpq (about 1 MiB, held by every GPU that loads
+ * the library until the process exits), so it needs neither an arena nor any
+ * allocation; the caller passes the inputs and outputs as for pq_filter.
+ * Limits: at most 536,870,912 rows tested per call (col.n, or n_in with a
+ * selection vector); larger inputs return PQ_ERR_CAPACITY before any GPU
+ * work.  The first call on a device looks up the array's device address
+ * (once per device, with that device current), so make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller; each call clears what it uses first.  If
+ * `d_error` (device int32) is non-NULL it receives 0, or PQ_ERR_TIMEOUT if a
+ * bounded wait gave up.  Returns PQ_ERR_INVALID_ARG for bad arguments and
+ * PQ_ERR_CUDA if the set-up or a launch fails. */
+pq_status pq_filter_noalloc(pq_col col, int op, int64_t c, const int64_t* sel_in, int64_t n_in,
+                            int64_t* sel_out, int64_t* d_count, int32_t* d_error, void* stream);
+
 /* ---- the plan ------------------------------------------------------------- */
 
 enum pq_plan_flags {

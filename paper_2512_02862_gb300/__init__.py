@@ -123,6 +123,7 @@ def library():
         "pq_submit": [vp, POINTER(pq_plan), POINTER(c_uint64)],
         "pq_poll": [vp, c_uint64, POINTER(pq_result), i32],
         "pq_autotune": [vp, POINTER(pq_plan), POINTER(pq_tuning)],
+        "pq_filter_noalloc": [pq_col, i32, i64, vp, i64, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

@@ -1,6 +1,7 @@
 // pq_ops.cu -- standalone operators: filter, radix partition, hash-join
 // build/probe, group-by SUM, top-k.
 #include <algorithm>
+#include <mutex>
 
 #include "pq_internal.h"
 #include "pq_topk.cuh"
@@ -728,3 +729,105 @@ pq_status pq_topk(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free filter ====
+// pq_filter needs scratch for its single-pass tile prefixes, normally carved
+// from the context's arena.  Some callers cannot allocate device memory at all
+// (for example code that runs while a CUDA graph is being captured, or inside
+// a runtime that owns every allocation and forbids others), and they may not
+// have a context either.  For them the same kernel runs with its scratch in
+// this file-scope device array: a fixed 1 MiB of tile states plus a small
+// header, which every GPU that loads the library keeps until the process
+// exits.  All calls share the array, so calls that overlap on the GPU race;
+// each call clears the part it uses before its kernel runs.
+namespace {
+
+constexpr i64 kNoAllocTiles = 1 << 17;                  // 131072 tiles
+constexpr i64 kNoAllocRows = kNoAllocTiles * kFilterTile;  // 536,870,912 rows
+constexpr int kNoAllocHeader = 32;                      // words: ticket, status
+
+__device__ __align__(256) u64 g_noalloc_scratch[kNoAllocHeader + kNoAllocTiles];
+
+struct NoAllocDevice {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+  u64* scratch = nullptr;  // device address of g_noalloc_scratch
+  int sms = 0;
+};
+NoAllocDevice g_noalloc_dev[256];
+
+// Per-device set-up, run once with that device current: the host cannot use
+// the array's name as a device address, so it asks the runtime for it.
+cudaError_t noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  std::call_once(d.once, [&d, dev] {
+    d.err = cudaGetSymbolAddress((void**)&d.scratch, g_noalloc_scratch);
+    if (d.err == cudaSuccess)
+      d.err = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  *out = &d;
+  return d.err;
+}
+
+}  // namespace
+
+extern "C" pq_status pq_filter_noalloc(pq_col col, int op, int64_t c, const int64_t* sel_in,
+                                       int64_t n_in, int64_t* sel_out, int64_t* d_count,
+                                       int32_t* d_error, void* stream) {
+  bool ok;
+  Pred p = pqh::make_pred(op, c, &ok);
+  if (!ok || !pqh::valid_dtype(col.type) || col.n < 0 || !d_count || col.reserved != 0)
+    return PQ_ERR_INVALID_ARG;
+  const bool sel = sel_in != nullptr;
+  const i64 n_cap = sel ? n_in : col.n;
+  if (n_cap < 0 || (n_cap > 0 && (!sel_out || (!col.data && col.n > 0))))
+    return PQ_ERR_INVALID_ARG;
+  if (n_cap > kNoAllocRows) return PQ_ERR_CAPACITY;  // beyond the static scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PQ_ERR_CUDA;
+  NoAllocDevice* d = nullptr;
+  if (noalloc_setup(dev, &d) != cudaSuccess) return PQ_ERR_CUDA;
+  cudaStream_t s = S(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(int64_t), s) != cudaSuccess) return PQ_ERR_CUDA;
+  if (d_error && cudaMemsetAsync(d_error, 0, sizeof(int32_t), s) != cudaSuccess)
+    return PQ_ERR_CUDA;
+  if (n_cap == 0) return PQ_OK;
+  const i64 ntiles = (n_cap + kFilterTile - 1) / kFilterTile;
+  u64* hdr = d->scratch;
+  if (cudaMemsetAsync(hdr, 0, (kNoAllocHeader + ntiles) * sizeof(u64), s) != cudaSuccess)
+    return PQ_ERR_CUDA;
+  u32* ticket = (u32*)hdr;
+  DevStatus* status = (DevStatus*)(hdr + 2);
+  u64* state = hdr + kNoAllocHeader;
+  const bool vec = sel ? aligned16(sel_in) : aligned16(col.data);
+  const int grid = (int)std::max<i64>(1, std::min<i64>(ntiles, (i64)d->sms * 4));
+  const i64 spin = 1ll << 22;
+  PQ_DISPATCH_T(col.type, T, {
+    if (sel) {
+      if (vec)
+        k_filter<T, true, true><<<grid, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in,
+                                                     n_cap, nullptr, p, (i64*)sel_out,
+                                                     (i64*)d_count, state, ticket, spin, status);
+      else
+        k_filter<T, true, false><<<grid, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in,
+                                                      n_cap, nullptr, p, (i64*)sel_out,
+                                                      (i64*)d_count, state, ticket, spin, status);
+    } else {
+      if (vec)
+        k_filter<T, false, true><<<grid, 256, 0, s>>>((const T*)col.data, nullptr, n_cap,
+                                                      nullptr, p, (i64*)sel_out, (i64*)d_count,
+                                                      state, ticket, spin, status);
+      else
+        k_filter<T, false, false><<<grid, 256, 0, s>>>((const T*)col.data, nullptr, n_cap,
+                                                       nullptr, p, (i64*)sel_out, (i64*)d_count,
+                                                       state, ticket, spin, status);
+    }
+  });
+  if (cudaGetLastError() != cudaSuccess) return PQ_ERR_CUDA;
+  if (d_error &&
+      cudaMemcpyAsync(d_error, &status->code, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+    return PQ_ERR_CUDA;
+  return PQ_OK;
+}
