@@ -404,9 +404,9 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     plan_assign(r, ws + off[i]);
     PlanDev& d = r.dev;
     if (r.dset_from >= 0) {
-      d.dset_log2 = R[r.dset_from].dev.dset_log2;
-      d.dset_tag = R[r.dset_from].dev.dset_tag;
-      d.dset = R[r.dset_from].dev.dset;
+      const PlanDev& src = R[r.dset_from].dev;
+      d.dset_log2 = src.dset_log2;
+      d.dset_tag = src.dset_tag;
     } else if (r.cache) {
       dset_block_assign((char*)r.cache->block, r.cache->log2max, d);
     }

@@ -26,30 +26,20 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
 
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-// A D-set block of 2^e slots: a 256-byte header whose first word is the
-// log2 of the slot count in use, the 2-byte tags, then the 8-byte keys.
-inline size_t dset_block_bytes(int e) { return 256 + al256((size_t)2 << e) + ((size_t)8 << e); }
-inline void dset_block_assign(char* blk, int e, pqk::PlanDev& d) {
+// A D-set block of 2^e slots: a 256-byte header (the log2 of the slot count
+// in use, then the key-range bitmap's base and bit count) followed by a key
+// set laid out by pqk::table_layout.
+inline size_t dset_block_bytes(int e) { return 256 + pqk::table_layout(e, false).total; }
+inline void dset_block_assign(char* blk, int, pqk::PlanDev& d) {
   d.dset_log2 = (int*)blk;
   d.dset_tag = (unsigned short*)(blk + 256);
-  d.dset = (i64*)(blk + 256 + al256((size_t)2 << e));
 }
 
-// An M table of 2^e slots: tags, keys, sums, first-hit flags.
-inline size_t mtable_bytes(int e) {
-  const size_t n = (size_t)1 << e;
-  return al256(n * 2) + al256(n * 8) * 2 + al256(n * 4);
-}
+// An M table of 2^e slots with {key, sum} records (pqk::table_layout).
+inline size_t mtable_bytes(int e) { return al256(pqk::table_layout(e, true).total); }
 inline char* mtable_assign(char* p, int e, pqk::PlanDev& d) {
-  const size_t n = (size_t)1 << e;
   d.ht_tag = (unsigned short*)p;
-  p += al256(n * 2);
-  d.ht_keys = (i64*)p;
-  p += al256(n * 8);
-  d.ht_sums = (i64*)p;
-  p += al256(n * 8);
-  d.ht_cnt = (pqk::u32*)p;
-  return p + al256(n * 4);
+  return p + mtable_bytes(e);
 }
 
 // Per-plan workspace bytes (excluding a cached D-set block).

@@ -32,12 +32,11 @@
 
 namespace pqk {
 
-constexpr int kTD = 4096;    // D rows per warp tile
-constexpr int kTM = 2048;    // M rows per warp tile
-constexpr int kTF = 4096;    // F rows per warp tile
-constexpr int kTC = 16384;   // slots cleared per block tile
-constexpr int kTB = 1024;    // list entries inserted per block tile
-constexpr int kTK = 1024;    // groups per top-k block tile
+constexpr int kTD = 1024;    // D rows per warp tile
+constexpr int kTM = 1024;    // M rows per warp tile
+constexpr int kTF = 2048;    // F rows per warp tile
+constexpr int kTB = 128;     // list entries inserted per warp tile (4 per lane)
+constexpr int kTK = 1024;    // groups per top-k warp tile
 constexpr int kQ = 256;      // entries of a warp's shared-memory ring
 
 struct QCtr {
@@ -46,8 +45,125 @@ struct QCtr {
   u32 tk_ticket;
   int status;
   int mlog2;
+  // Order-preserving key ranges (ukey = key xor 2^63), zero-initialised:
+  // n* holds ~min, u* holds max, both grown with atomicMax.
+  u64 d_nmin, d_umax, m_nmin, m_umax;
+  u64 m_umin;  // M bitmap: ukey of bit 0
+  u64 m_bits;  // M bitmap: bit count (0 = no bitmap)
   u64 pad[2];
 };
+
+// Key-range semi-join filter.  When the keys of a filtered build side span
+// at most 32 bits per table slot, an exact bitmap over that range sits beside
+// the table: a probe key outside the range, or whose bit is clear, cannot
+// match, so only the few keys whose bit is set probe the table.
+__device__ __forceinline__ u64 ukey(i64 k) { return (u64)k ^ 0x8000000000000000ULL; }
+
+struct RangeBits {
+  u64 umin, bits;
+};
+// Choose a bitmap for `count` keys spanning [~nmin, umax] (ukeys) in a table
+// of 2^e slots: used when the span is below 32 * 2^e bits.
+__device__ __forceinline__ RangeBits range_bits(i64 count, u64 nmin, u64 umax, int e) {
+  RangeBits r{0, 0};
+  if (count <= 0) return r;
+  const u64 umin = ~nmin;
+  const u64 span = umax - umin;  // bits - 1
+  if (umax >= umin && span < (32ULL << e)) {
+    r.umin = umin;
+    r.bits = span + 1;
+  }
+  return r;
+}
+// Layout of a plan table of 2^e slots (byte offsets from its tag array; the
+// host carves workspaces and the device clears tables with this one
+// function).  tags: 2 B per slot (0 = free); bcnt: one u32 fill counter per
+// 8-slot bucket; hit: first-hit bits (tables with sums only); keybm: the
+// key-range bitmap (up to 32 bits per slot); rec: 8-byte keys, or 16-byte
+// {key, sum} records.  Everything before `rec` starts at zero.
+struct TableLayout {
+  u64 bcnt, hit, keybm, rec, total;
+};
+__host__ __device__ __forceinline__ TableLayout table_layout(int e, bool with_sums) {
+  const u64 n = 1ULL << e;
+  auto a = [](u64 x) { return (x + 255) & ~255ULL; };
+  TableLayout L;
+  L.bcnt = a(2 * n);
+  L.hit = L.bcnt + a(n / 2);
+  L.keybm = L.hit + (with_sums ? a(n / 8) : 0);
+  L.rec = L.keybm + a(4 * n);
+  L.total = L.rec + (with_sums ? 16 : 8) * n;
+  return L;
+}
+
+// Clearing a table: its tags, bucket counters, hit bits and the used part of
+// its key bitmap, in 16-byte units, kTCU units per fill tile.
+constexpr int kTCU = 2048;
+__host__ __device__ __forceinline__ i64 clear_units(int e, bool with_sums, u64 bits) {
+  return (i64)((table_layout(e, with_sums).keybm + ((bits + 31) / 32) * 4 + 15) / 16);
+}
+__host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bits) {
+  return (clear_units(e, with_sums, bits) + kTCU - 1) / kTCU;
+}
+
+__device__ __forceinline__ bool bit_test(const u32* bm, u64 idx, u64 keep) {
+  u32 w;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(w) : "l"(bm + (idx >> 5)), "l"(keep));
+  return (w >> (idx & 31)) & 1u;
+}
+__device__ __forceinline__ void bit_set(u32* bm, u64 idx) {
+  atomicOr(bm + (idx >> 5), 1u << (idx & 31));
+}
+
+// Key-range bitmap test of a lane's 4 keys, split in two so that the word
+// loads issued in one scan iteration are consumed in the next.  Keys outside
+// `valid` never pass; with no bitmap (bits == 0) every valid key passes, and
+// the caller resolves it against the table.
+struct BmStage {
+  u32 w[4];  // loaded words (0: key invalid or out of range)
+  u32 sh;    // bit positions within the words, 5 bits per key
+};
+template <typename K>
+__device__ __forceinline__ void bm_issue(BmStage& st, const u32* bm, u64 umin, u64 bits, u32 valid,
+                                         const K k[4], u64 keep) {
+  st.sh = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const u64 idx = ukey((i64)k[s]) - umin;
+    const bool in = ((valid >> s) & 1u) && (bits == 0 || idx < bits);
+    u32 w = 0;
+    if (in) {
+      if (bits == 0) {
+        w = ~0u;
+      } else {
+        asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;"
+            : "=r"(w) : "l"(bm + (idx >> 5)), "l"(keep));
+      }
+    }
+    st.w[s] = w;
+    st.sh |= (u32)(idx & 31) << (5 * s);
+  }
+}
+__device__ __forceinline__ u32 bm_hits(const BmStage& st) {
+  u32 h = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) h |= ((st.w[s] >> ((st.sh >> (5 * s)) & 31)) & 1u) << s;
+  return h;
+}
+
+// Warp-wide fold of per-lane key ranges into the (zero-initialised) counters.
+__device__ __forceinline__ void range_commit(u64 lane_nmin, u64 lane_umax, u64* nmin, u64* umax) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 a = __shfl_xor_sync(kFull, lane_nmin, o), c = __shfl_xor_sync(kFull, lane_umax, o);
+    lane_nmin = a > lane_nmin ? a : lane_nmin;
+    lane_umax = c > lane_umax ? c : lane_umax;
+  }
+  if ((threadIdx.x & 31) == 0 && (lane_nmin | lane_umax)) {
+    atomicMax(nmin, lane_nmin);
+    atomicMax(umax, lane_umax);
+  }
+}
 
 struct PlanDev {
   const int* d_key;
@@ -67,14 +183,11 @@ struct PlanDev {
   int build_dset;   // this plan fills its D-set in this batch
   int vec;          // every column pointer is 16-byte aligned
   i64* dlist;
-  int* dset_log2;   // header word of the D-set block
-  i64* dset;        // D-set keys
-  unsigned short* dset_tag;  // D-set tags (0 = empty)
+  int* dset_log2;   // header of the D-set block: log2 slots, then (u64) bitmap
+                    // base ukey at byte 8 and bit count at byte 16
+  unsigned short* dset_tag;  // D-set table (keys only), laid out by table_layout
   i64* mlist;
-  unsigned short* ht_tag;    // M table tags (0 = empty)
-  i64* ht_keys;
-  i64* ht_sums;
-  u32* ht_cnt;
+  unsigned short* ht_tag;    // M table ({key, sum} records), laid out by table_layout
   u32* glist;
   i64* tk_k;
   i64* tk_s;
@@ -218,49 +331,87 @@ __device__ __forceinline__ Geo geo(int e) {
   return g;
 }
 
-// Membership of k in a bucketized key set.
-__device__ __forceinline__ bool set_contains(const unsigned short* tags, const i64* keys, Geo g,
-                                             i64 k, u64 keep) {
-  const BucketTag bt = bucket_tag(k, g.shiftb);
+// Device view of a table laid out by table_layout.
+struct TableView {
+  unsigned short* tags;
+  u32* bcnt;
+  u32* hit;
+  u32* keybm;
+  i64* rec;
+  Geo g;
+};
+__device__ __forceinline__ TableView table_view(unsigned short* tags, int e, bool with_sums) {
+  const TableLayout L = table_layout(e, with_sums);
+  char* base = reinterpret_cast<char*>(tags);
+  TableView t;
+  t.tags = tags;
+  t.bcnt = reinterpret_cast<u32*>(base + L.bcnt);
+  t.hit = reinterpret_cast<u32*>(base + L.hit);
+  t.keybm = reinterpret_cast<u32*>(base + L.keybm);
+  t.rec = reinterpret_cast<i64*>(base + L.rec);
+  t.g = geo(e);
+  return t;
+}
+
+// Membership of k in a bucketized key set (8-byte key records).
+__device__ __forceinline__ bool set_contains(const TableView& t, i64 k, u64 keep) {
+  const BucketTag bt = bucket_tag(k, t.g.shiftb);
   const unsigned v2 = bt.tag * 0x10001u;
   u64 b = bt.bucket;
-  for (u64 p = 0; p <= g.bmask; ++p) {
-    const uint4 w = ld_keep_v4u(tags + b * 8, keep);
+  for (u64 p = 0; p <= t.g.bmask; ++p) {
+    const uint4 w = ld_keep_v4u(t.tags + b * 8, keep);
     Mask8 m = match8(w, v2);
     while (any8(m)) {
       const int j = first8(m);
-      if (ld_keep(keys + b * 8 + j, keep) == k) return true;
+      if (ld_keep(t.rec + b * 8 + j, keep) == k) return true;
       drop8(m, j);
     }
     if (any8(match8(w, 0u))) return false;
-    b = (b + 1) & g.bmask;
+    b = (b + 1) & t.g.bmask;
   }
   return false;
 }
 
-// Insert k (one slot per insert, so duplicate keys take one slot each):
-// claim the first free tag of the first non-full bucket with a 16-bit CAS,
-// then write the key.  Returns the slot.
-__device__ __forceinline__ u64 tagged_insert(unsigned short* tags, i64* keys, Geo g, i64 k) {
-  const BucketTag bt = bucket_tag(k, g.shiftb);
+// Claim a slot for a key of home bucket bt.bucket (one slot per insert, so
+// duplicate keys take one slot each): the bucket's fill counter hands out
+// slots 0..7; a full bucket passes the key to the next one.  The tag is
+// written here; the caller writes the record.  Returns the slot.
+__device__ __forceinline__ u64 claim_from(const TableView& t, BucketTag bt, u32 first) {
   u64 b = bt.bucket;
-  for (u64 p = 0; p <= g.bmask; ++p) {
-    uint4 w;
-    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
-                 : "l"(tags + b * 8));
-    Mask8 e = match8(w, 0u);
-    while (any8(e)) {
-      const int j = first8(e);
-      if (atomicCAS(tags + b * 8 + j, (unsigned short)0, (unsigned short)bt.tag) == 0) {
-        keys[b * 8 + j] = k;
-        return b * 8 + j;
-      }
-      drop8(e, j);
+  u32 c = first;
+  for (u64 p = 0; p <= t.g.bmask; ++p) {
+    if (c < 8) {
+      t.tags[b * 8 + c] = (unsigned short)bt.tag;
+      return b * 8 + c;
     }
-    b = (b + 1) & g.bmask;
+    b = (b + 1) & t.g.bmask;
+    c = atomicAdd(t.bcnt + b, 1u);
   }
   return ~0ULL;  // unreachable: a table is never filled beyond its load factor
+}
+
+// A warp inserts the entries [i0, i0 + 128) of `src` (those below n): four
+// per lane, whose four slot claims (counter atomics) are in flight together.
+// on(k, slot) writes the record after each claim.
+template <typename OnSlot>
+__device__ __forceinline__ void insert_x4(const TableView& t, const i64* src, i64 i0, i64 n,
+                                          OnSlot on) {
+  const int lane = threadIdx.x & 31;
+  i64 k[4];
+  BucketTag bt[4];
+  u32 c[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const i64 idx = i0 + j * 32 + lane;
+    k[j] = idx < n ? src[idx] : kEmpty;
+    bt[j] = bucket_tag(k[j], t.g.shiftb);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (k[j] != kEmpty) c[j] = atomicAdd(t.bcnt + bt[j].bucket, 1u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (k[j] != kEmpty) on(k[j], claim_from(t, bt[j], c[j]));
 }
 
 // Four consecutive int32 values starting at row e0; `rem` rows remain in the
@@ -331,6 +482,7 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
     const signed char* d_seg = ov ? (const signed char*)b.ov.p[1] : q.d_seg;
     const i64 n = ov ? b.ov.n : q.n_d;
     const i64 base = (t - (ov ? 0 : b.tD[qi])) * kTD;
+    u64 lnmin = 0, lumax = 0;  // this lane's range of appended keys
     for (int it = 0; it < kTD / 512; ++it) {
       if (base + it * 512 >= n) break;
       const i64 e0 = base + it * 512 + lane * 16;
@@ -349,17 +501,27 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
       while (bits) {
         const int s = __ffs(bits) - 1;
         bits &= bits - 1;
-        q.dlist[at++] = (i64)__ldg(d_key + e0 + s);
+        const i64 k = (i64)__ldg(d_key + e0 + s);
+        q.dlist[at++] = k;
+        lnmin = max(lnmin, ~ukey(k));
+        lumax = max(lumax, ukey(k));
       }
     }
+    range_commit(lnmin, lumax, &q.ctr->d_nmin, &q.ctr->d_umax);
   }
   if (finish(b.work, kPhDscan)) {
     block_prefix(b.dyn, b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
       if (!q.build_dset) return 0;
-      const int e = cap_log2(ld_count(&q.ctr->dcount), q.lf1024);
+      const i64 cnt = ld_count(&q.ctr->dcount);
+      const int e = cap_log2(cnt, q.lf1024);
+      const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->d_nmin),
+                                      ld_volatile_u64(&q.ctr->d_umax), e);
       *q.dset_log2 = e;
-      return (((i64)1 << e) + kTC - 1) / kTC;
+      u64* hdr = reinterpret_cast<u64*>(q.dset_log2);
+      hdr[1] = rb.umin;
+      hdr[2] = rb.bits;
+      return fill_tiles(e, false, rb.bits);
     });
     block_prefix(b.dyn + (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
@@ -369,8 +531,8 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
 }
 
 // ------------------------------------------------------------------- fill ----
-// Clear the tags (2 bytes per slot) of the D-set (which = 0) or the M table
-// (which = 1); keys and sums are written by the inserting thread.
+// Clear the tags and the key-range bitmap of the D-set (which = 0) or the M
+// table (which = 1); keys and sums are written by the inserting thread.
 __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
   const i64* pre = b.dyn + (which == 0 ? 0 : 2) * (b.nq + 1);
   const int ph = which == 0 ? kPhDfill : kPhMfill;
@@ -381,48 +543,52 @@ __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
     const int e = which == 0 ? *q.dset_log2 : q.ctr->mlog2;
-    unsigned short* dst = which == 0 ? q.dset_tag : q.ht_tag;
-    const i64 n = (i64)1 << e;
-    const i64 s0 = (t - pre[qi]) * kTC;
-    for (i64 i = s0 + threadIdx.x * 8; i < s0 + kTC && i < n; i += 256 * 8)
-      *reinterpret_cast<int4*>(dst + i) = make_int4(0, 0, 0, 0);
+    const u64 bits = which == 0 ? reinterpret_cast<const u64*>(q.dset_log2)[2] : q.ctr->m_bits;
+    int4* base = reinterpret_cast<int4*>(which == 0 ? q.dset_tag : q.ht_tag);
+    const i64 units = clear_units(e, which == 1, bits);
+    const i64 u0 = (t - pre[qi]) * kTCU;
+    for (i64 u = u0 + threadIdx.x; u < u0 + kTCU && u < units; u += blockDim.x)
+      base[u] = make_int4(0, 0, 0, 0);
   }
   finish(b.work, ph);
 }
 
 // ----------------------------------------------------------------- dbuild ----
+// Warp tiles of 128 D-list entries (insert_x4), claimed per warp.
 __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
   const i64* pre = b.dyn + (b.nq + 1);
   const i64 total = pre[b.nq];
   while (true) {
-    const i64 t = claim(b.work, kPhDbuild);
+    const i64 t = warp_claim(b.work, kPhDbuild);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const Geo g = geo(*q.dset_log2);
-    const i64 n = (i64)q.ctr->dcount;
-    const i64 i0 = (t - pre[qi]) * kTB;
-    for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x)
-      tagged_insert(q.dset_tag, q.dset, g, q.dlist[i]);
+    const TableView tv = table_view(q.dset_tag, *q.dset_log2, false);
+    const u64* hdr = reinterpret_cast<const u64*>(q.dset_log2);
+    const u64 umin = hdr[1], bits = hdr[2];
+    insert_x4(tv, q.dlist, (t - pre[qi]) * kTB, (i64)q.ctr->dcount, [&](i64 k, u64 s) {
+      tv.rec[s] = k;
+      if (bits) bit_set(tv.keybm, ukey(k) - umin);
+    });
   }
   finish(b.work, kPhDbuild);
 }
 
 // ------------------------------------------------------------------ mscan ----
 // Warp tile of 2048 M rows, 128 per iteration (lane l: rows 4l .. 4l+3).
-// date is read two iterations ahead and dref one ahead, only for 4-row groups
-// with a date hit.  Date-passing (dref, row) pairs enter ring A and are
-// probed against the D-set 32 at a time; the keys of the members (read only
-// for them) enter ring B and leave for the M list in runs of 128 (one atomic
-// reservation per run).
+// Pipeline per lane: date is read two iterations ahead, dref one ahead (only
+// for 4-row groups with a date hit), the D-set bitmap words of the passing
+// drefs are loaded in the iteration the drefs arrive and tested in the next.
+// Member rows enter candidate ring C; rounds of 32 read their keys (only
+// theirs) into ring B, which leaves for the M list in runs of 128 (one
+// atomic reservation per run).  With no bitmap, every date-passing row is a
+// candidate and the D-set table decides.
 template <bool VEC>
-__global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
-  __shared__ int s_ad[8][kQ];
-  __shared__ u32 s_ar[8][kQ];
+__global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
+  __shared__ u32 s_c[8][kQ];
   __shared__ i64 s_rb[8][kQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* ad = s_ad[warp];
-  u32* ar = s_ar[warp];
+  u32* cr = s_c[warp];
   i64* rb = s_rb[warp];
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 2;
@@ -435,13 +601,17 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
     const i64* m_key = ov ? (const i64*)b.ov.p[0] : q.m_key;
     const int* m_dref = ov ? (const int*)b.ov.p[1] : q.m_dref;
     const int* m_date = ov ? (const int*)b.ov.p[2] : q.m_date;
-    const Geo dg = geo(*q.dset_log2);
+    const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
+    const u64* dhdr = reinterpret_cast<const u64*>(q.dset_log2);
+    const u64 d_umin = dhdr[1], d_bits = dhdr[2];
+    u64 lnmin = 0, lumax = 0;  // this lane's range of member keys
     const Pred32 pm = to32(q.pm);
     const i64 n = ov ? b.ov.n : q.n_m;
     const i64 base = (t - (ov ? 0 : b.tM[qi])) * kTM;
     const i64 lim = min(n - base, (i64)kTM);
     const int iters = (int)((lim + 127) / 128);
-    u32 ah = 0, at = 0, bh = 0, bt = 0;
+    const i64 r0 = lane * 4;
+    u32 ch = 0, ct = 0, bh = 0, bt = 0;
     auto flush_b = [&](u32 cnt) {
       u64 o = 0;
       if (lane == 0) o = atomicAdd(&q.ctr->mcount, (u64)cnt);
@@ -449,22 +619,34 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
       for (u32 j = lane; j < cnt; j += 32) q.mlist[o + j] = rb[(bh + j) & (kQ - 1)];
       bh += cnt;
     };
-    auto probe_a = [&](u32 cnt) {
+    auto resolve = [&](u32 cnt) {  // cnt <= 32 entries of C from ch
       bool mem = false;
       i64 key = 0;
       if ((u32)lane < cnt) {
-        const u32 j = (ah + lane) & (kQ - 1);
-        mem = set_contains(q.dset_tag, q.dset, dg, ad[j], keep);
-        if (mem) key = __ldg(m_key + base + ar[j]);
+        const u32 r = cr[(ch + lane) & (kQ - 1)];
+        mem = d_bits || set_contains(dt, (i64)__ldg(m_dref + base + r), keep);
+        if (mem) {
+          key = __ldg(m_key + base + r);
+          lnmin = max(lnmin, ~ukey(key));
+          lumax = max(lumax, ukey(key));
+        }
       }
       const u32 m = __ballot_sync(kFull, mem);
       if (mem) rb[(bt + __popc(m & lanemask_lt())) & (kQ - 1)] = key;
       bt += __popc(m);
-      ah += cnt;
+      ch += cnt;
       __syncwarp();
       if (bt - bh >= 128) flush_b(128);
     };
-    const i64 r0 = lane * 4;
+    auto append_c = [&](u32 hits, int it) {
+      if (__any_sync(kFull, hits)) {
+        __syncwarp();
+        ct += ring_append(hits, ct, [&](int s, u32 pos) {
+          cr[pos & (kQ - 1)] = (u32)(it * 128 + r0 + s);
+        });
+        __syncwarp();
+      }
+    };
     int4 dB = load_i32x4<VEC>(m_date, base + r0, lim - r0, strm);
     int4 dC = iters > 1 ? load_i32x4<VEC>(m_date, base + 128 + r0, lim - 128 - r0, strm)
                         : make_int4(0, 0, 0, 0);
@@ -472,6 +654,9 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
     int4 rA = hA ? load_i32x4<VEC>(m_dref, base + r0, lim - r0, strm) : make_int4(0, 0, 0, 0);
     dB = dC;
     if (iters > 2) dC = load_i32x4<VEC>(m_date, base + 256 + r0, lim - 256 - r0, strm);
+    BmStage wP;
+    wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
+    wP.sh = 0;
     for (int it = 0; it < iters; ++it) {
       const i64 rel1 = (it + 1) * 128 + r0;
       u32 hB = 0;
@@ -486,27 +671,34 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
         dC = load_i32x4<VEC>(m_date, base + rel3, lim - rel3, strm);
       }
       const int dr[4] = {rA.x, rA.y, rA.z, rA.w};
-      __syncwarp();
-      at += ring_append(hA, at, [&](int s, u32 pos) {
-        ad[pos & (kQ - 1)] = dr[s];
-        ar[pos & (kQ - 1)] = (u32)(it * 128 + r0 + s);
-      });
-      __syncwarp();
-      while (at - ah >= 32) probe_a(32);
+      BmStage wN;
+      bm_issue(wN, dt.keybm, d_umin, d_bits, hA, dr, keep);
+      if (it > 0) {
+        append_c(bm_hits(wP), it - 1);
+        while (ct - ch >= 32) resolve(32);
+      }
+      wP = wN;
       hA = hB;
       rA = rB;
     }
-    __syncwarp();
-    if (at - ah) probe_a(at - ah);
+    append_c(bm_hits(wP), iters - 1);
+    while (ct - ch >= 32) resolve(32);
+    if (ct - ch) resolve(ct - ch);
     if (bt - bh) flush_b(bt - bh);
     __syncwarp();
+    range_commit(lnmin, lumax, &q.ctr->m_nmin, &q.ctr->m_umax);
   }
   if (finish(b.work, kPhMscan)) {
     block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
-      const int e = cap_log2(ld_count(&q.ctr->mcount), q.lf1024);
+      const i64 cnt = ld_count(&q.ctr->mcount);
+      const int e = cap_log2(cnt, q.lf1024);
+      const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->m_nmin),
+                                      ld_volatile_u64(&q.ctr->m_umax), e);
       q.ctr->mlog2 = e;
-      return (((i64)1 << e) + kTC - 1) / kTC;
+      q.ctr->m_umin = rb.umin;
+      q.ctr->m_bits = rb.bits;
+      return fill_tiles(e, true, rb.bits);
     });
     block_prefix(b.dyn + 3 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       return (ld_count(&b.q[qi].ctr->mcount) + kTB - 1) / kTB;
@@ -515,114 +707,143 @@ __global__ void __launch_bounds__(256, 4) k_plan_mscan(Batch b) {
 }
 
 // ----------------------------------------------------------------- mbuild ----
+// Warp tiles of 128 M-list entries (insert_x4), claimed per warp.  A key equal
+// to the reserved INT64_MIN is reported and skipped.
 __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
   const i64* pre = b.dyn + 3 * (b.nq + 1);
   const i64 total = pre[b.nq];
+  const int lane = threadIdx.x & 31;
   while (true) {
-    const i64 t = claim(b.work, kPhMbuild);
+    const i64 t = warp_claim(b.work, kPhMbuild);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const Geo g = geo(q.ctr->mlog2);
+    const TableView tv = table_view(q.ht_tag, q.ctr->mlog2, true);
+    const u64 m_umin = q.ctr->m_umin, m_bits = q.ctr->m_bits;
     const i64 n = (i64)q.ctr->mcount;
     const i64 i0 = (t - pre[qi]) * kTB;
-    for (i64 i = i0 + threadIdx.x; i < i0 + kTB && i < n; i += blockDim.x) {
-      const i64 k = q.mlist[i];
-      if (k == kEmpty) {
-        q_latch(q.ctr, b.st, PQ_ERR_RESERVED_KEY, i);
-        continue;
-      }
-      const u64 s = tagged_insert(q.ht_tag, q.ht_keys, g, k);
-      q.ht_sums[s] = 0;
-      q.ht_cnt[s] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const i64 idx = i0 + j * 32 + lane;
+      if (idx < n && q.mlist[idx] == kEmpty) q_latch(q.ctr, b.st, PQ_ERR_RESERVED_KEY, idx);
     }
+    insert_x4(tv, q.mlist, i0, n, [&](i64 k, u64 s) {
+      *reinterpret_cast<longlong2*>(tv.rec + 2 * s) = make_longlong2(k, 0);  // {key, sum}
+      if (m_bits) bit_set(tv.keybm, ukey(k) - m_umin);
+    });
   }
   finish(b.work, kPhMbuild);
 }
 
 // ----------------------------------------------------------------- fprobe ----
+constexpr int kAgg = 512;    // entries of a block's shared-memory aggregation table
+constexpr int kH = 256;      // entries of a warp's hit ring
+
 struct ProbeCtx {
-  const unsigned short* tags;
-  const i64* keys;
-  i64* sums;
-  u32* cnt;
+  TableView t;
   u32* glist;
   QCtr* ctr;
+  const i64* mkey;
   const i64* price;
   const signed char* disc;
   DevStatus* st;
   i64 base;
   u64 keep;
-  Geo g;
+  u64 qtag;       // (plan index << 40) + 1: the aggregation key of slot s is qtag + s
+  u64* akey;      // the block's aggregation table (shared memory)
+  i64* asum;
 };
 
-// Finish the probe of key k (F row base + r) whose home bucket's tag word w
-// has been read: count the slots holding k (its multiplicity in M', found in
-// the home bucket and, while buckets are full, the next ones) and add the
-// row's exact revenue times that count into the first of them, recording
-// that slot as a group on its first hit.
-__device__ __forceinline__ void probe_finish(const ProbeCtx& c, i64 k, u32 r, BucketTag bt,
-                                             uint4 w) {
-  i64 first = -1, mult = 0;
+__device__ __forceinline__ bool add_overflows(i64 old, i64 v) {
+  return (v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v);
+}
+
+// Add v into the sum of M-table slot s and record s as a group on its first
+// hit (global memory).
+__device__ __forceinline__ void global_add(const TableView& t, u64 s, i64 v, u32* glist,
+                                           QCtr* ctr, DevStatus* st) {
+  const i64 old = (i64)atomicAdd((u64*)(t.rec + 2 * s + 1), (u64)v);
+  if (add_overflows(old, v)) q_latch(ctr, st, PQ_ERR_OVERFLOW, (i64)s);
+  const u32 bit = 1u << (s & 31);
+  if (!(atomicOr(t.hit + (s >> 5), bit) & bit)) {
+    const u64 gi = atomicAdd(&ctr->gcount, 1ULL);
+    glist[gi] = (u32)s;
+  }
+}
+
+// Add v into slot s through the block's direct-mapped shared-memory table:
+// the first slot to reach an entry keeps it for the rest of the kernel, so
+// the repeated hits of hot keys (skewed data) stay on chip; a slot whose
+// entry is taken goes to the global atomic.
+__device__ __forceinline__ void agg_add(const ProbeCtx& c, u64 s, i64 v) {
+  const u64 ak = c.qtag + s;
+  const u32 h = (u32)((ak * 0x9E3779B97F4A7C15ULL) >> 55);
+  u64 cur = *(volatile u64*)&c.akey[h];
+  if (cur == 0) {
+    cur = atomicCAS((unsigned long long*)&c.akey[h], 0ULL, ak);
+    if (cur == 0) cur = ak;
+  }
+  if (cur == ak) {
+    const i64 old = (i64)atomicAdd((unsigned long long*)&c.asum[h], (unsigned long long)v);
+    if (add_overflows(old, v)) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, (i64)s);
+  } else {
+    global_add(c.t, s, v, c.glist, c.ctr, c.st);
+  }
+}
+
+// Probe the M table with the key of F row base + r: count the slots holding
+// it (its multiplicity in M', found in the home bucket and, while buckets are
+// full, the next ones) and add the row's exact revenue times that count into
+// the first of them.
+__device__ __forceinline__ void probe_row(const ProbeCtx& c, u32 r) {
+  const i64 row = c.base + r;
+  const i64 k = __ldg(c.mkey + row);
+  const BucketTag bt = bucket_tag(k, c.t.g.shiftb);
   const unsigned v2 = bt.tag * 0x10001u;
   u64 b = bt.bucket;
-  for (u64 p = 0; p <= c.g.bmask; ++p) {
+  i64 first = -1, mult = 0;
+  for (u64 p = 0; p <= c.t.g.bmask; ++p) {
+    const uint4 w = ld_keep_v4u(c.t.tags + b * 8, c.keep);
     Mask8 m = match8(w, v2);
     while (any8(m)) {
       const int j = first8(m);
       const u64 slot = b * 8 + j;
-      if (ld_keep(c.keys + slot, c.keep) == k) {
+      if (ld_keep(c.t.rec + 2 * slot, c.keep) == k) {
         if (first < 0) first = (i64)slot;
         ++mult;
       }
       drop8(m, j);
     }
     if (any8(match8(w, 0u))) break;
-    b = (b + 1) & c.g.bmask;
-    w = ld_keep_v4u(c.tags + b * 8, c.keep);
+    b = (b + 1) & c.t.g.bmask;
   }
   if (first < 0) return;
-  const i64 row = c.base + r;
   // Exact revenue: the product is formed in 128 bits so that a value outside
   // int64 is reported instead of wrapping.
   const __int128 v128 =
       (__int128)mult * ((__int128)__ldg(c.price + row) * (100 - (i64)__ldg(c.disc + row)));
   const i64 v = (i64)v128;
   if (v128 != (__int128)v) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
-  const i64 old = (i64)atomicAdd((u64*)&c.sums[first], (u64)v);
-  if ((v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v))
-    q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
-  if (*(volatile u32*)&c.cnt[first] == 0 && atomicExch(&c.cnt[first], 1u) == 0u) {
-    const u64 gi = atomicAdd(&c.ctr->gcount, 1ULL);
-    c.glist[gi] = (u32)first;
-  }
+  agg_add(c, (u64)first, v);
 }
 
-__device__ __forceinline__ void probe1(const ProbeCtx& c, i64 k, u32 r) {
-  const BucketTag bt = bucket_tag(k, c.g.shiftb);
-  probe_finish(c, k, r, bt, ld_keep_v4u(c.tags + bt.bucket * 8, c.keep));
-}
-
-// Two probes per lane with both home-bucket loads in flight together.
-__device__ __forceinline__ void probe2(const ProbeCtx& c, i64 k0, u32 r0, i64 k1, u32 r1) {
-  const BucketTag b0 = bucket_tag(k0, c.g.shiftb), b1 = bucket_tag(k1, c.g.shiftb);
-  const uint4 w0 = ld_keep_v4u(c.tags + b0.bucket * 8, c.keep);
-  const uint4 w1 = ld_keep_v4u(c.tags + b1.bucket * 8, c.keep);
-  probe_finish(c, k0, r0, b0, w0);
-  probe_finish(c, k1, r1, b1, w1);
-}
-
-// Warp tile of 4096 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
-// date2 is read two iterations ahead and mkey one ahead, only for 4-row groups
-// (one 32-byte sector) with a passing row.  Passing (key, row) pairs enter the
-// warp's ring and are probed 64 at a time, two per lane.
+// Warp tile of 2048 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
+// Pipeline per lane: date2 is read two iterations ahead, mkey one ahead (only
+// for 4-row groups with a passing row), the key-range bitmap words of the
+// passing keys are loaded in the iteration the keys arrive and tested in the
+// next.  Only rows whose bit is set (the join hits) enter the warp's hit
+// ring, which probes the table 32 rows at a time with every lane busy.  With
+// no bitmap every passing row is a candidate and the probe decides.  Hits
+// aggregate in the block's shared table, flushed once at the end.
 template <bool VEC>
-__global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
-  __shared__ i64 s_qk[8][kQ];
-  __shared__ u32 s_qr[8][kQ];
+__global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
+  __shared__ u32 s_hr[8][kH];
+  __shared__ u64 s_akey[kAgg];
+  __shared__ i64 s_asum[kAgg];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  i64* qk = s_qk[warp];
-  u32* qr = s_qr[warp];
+  u32* hr = s_hr[warp];
+  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
+  __syncthreads();
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
@@ -636,24 +857,39 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
     const i64 n = ov ? b.ov.n : q.n_f;
     const i64 base = (t - (ov ? 0 : b.tF[qi])) * kTF;
     ProbeCtx pc;
-    pc.tags = q.ht_tag;
-    pc.keys = q.ht_keys;
-    pc.sums = q.ht_sums;
-    pc.cnt = q.ht_cnt;
+    pc.t = table_view(q.ht_tag, q.ctr->mlog2, true);
     pc.glist = q.glist;
     pc.ctr = q.ctr;
+    pc.mkey = f_mkey;
     pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
     pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
     pc.st = b.st;
     pc.base = base;
-    const int e = q.ctr->mlog2;
-    pc.g = geo(e);
     pc.keep = keep;
+    pc.qtag = ((u64)qi << 40) + 1;
+    pc.akey = s_akey;
+    pc.asum = s_asum;
+    const u32* bm = pc.t.keybm;
+    const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
     const Pred32 pf = to32(q.pf);
     const i64 lim = min(n - base, (i64)kTF);
     const int iters = (int)((lim + 127) / 128);
     const i64 r0 = lane * 4;
-    u32 head = 0, tail = 0;
+    u32 hh = 0, ht = 0;
+    auto append_hits = [&](u32 hits, int it) {
+      if (__any_sync(kFull, hits)) {
+        __syncwarp();
+        ht += ring_append(hits, ht, [&](int s, u32 pos) {
+          hr[pos & (kH - 1)] = (u32)(it * 128 + r0 + s);
+        });
+        __syncwarp();
+      }
+    };
+    auto probe_hits = [&](u32 cnt) {  // cnt <= 32 entries from hh
+      if ((u32)lane < cnt) probe_row(pc, hr[(hh + lane) & (kH - 1)]);
+      hh += cnt;
+      __syncwarp();
+    };
     int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
     int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, base + 128 + r0, lim - 128 - r0, strm)
                         : make_int4(0, 0, 0, 0);
@@ -662,6 +898,9 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
     if (bA) load_i64x4<VEC>(f_mkey, base + r0, lim - r0, bA, strm, mA);
     dB = dC;
     if (iters > 2) dC = load_i32x4<VEC>(f_date, base + 256 + r0, lim - 256 - r0, strm);
+    BmStage wP;
+    wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
+    wP.sh = 0;
     for (int it = 0; it < iters; ++it) {
       const i64 rel1 = (it + 1) * 128 + r0;
       u32 bB = 0;
@@ -675,32 +914,30 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
         const i64 rel3 = (it + 3) * 128 + r0;
         dC = load_i32x4<VEC>(f_date, base + rel3, lim - rel3, strm);
       }
-      __syncwarp();
-      tail += ring_append(bA, tail, [&](int s, u32 pos) {
-        qk[pos & (kQ - 1)] = mA[s];
-        qr[pos & (kQ - 1)] = (u32)(it * 128 + r0 + s);
-      });
-      __syncwarp();
-      while (tail - head >= 64) {
-        const u32 j0 = (head + lane) & (kQ - 1), j1 = (head + 32 + lane) & (kQ - 1);
-        probe2(pc, qk[j0], qr[j0], qk[j1], qr[j1]);
-        head += 64;
+      BmStage wN;
+      bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
+      if (it > 0) {
+        append_hits(bm_hits(wP), it - 1);
+        while (ht - hh >= 32) probe_hits(32);
       }
+      wP = wN;
       bA = bB;
 #pragma unroll
       for (int s = 0; s < 4; ++s) mA[s] = mB[s];
     }
-    __syncwarp();
-    if (tail - head >= 32) {
-      const u32 j = (head + lane) & (kQ - 1);
-      probe1(pc, qk[j], qr[j]);
-      head += 32;
-    }
-    if ((u32)lane < tail - head) {
-      const u32 j = (head + lane) & (kQ - 1);
-      probe1(pc, qk[j], qr[j]);
-    }
-    __syncwarp();
+    append_hits(bm_hits(wP), iters - 1);
+    while (ht - hh >= 32) probe_hits(32);
+    if (ht - hh) probe_hits(ht - hh);
+  }
+  // Flush the block's aggregated sums to the plans' tables.
+  __syncthreads();
+  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) {
+    const u64 ak = s_akey[i];
+    if (!ak) continue;
+    const int qi = (int)((ak - 1) >> 40);
+    const u64 s = (ak - 1) & ((1ULL << 40) - 1);
+    const PlanDev& q = b.q[qi];
+    global_add(table_view(q.ht_tag, q.ctr->mlog2, true), s, s_asum[i], q.glist, q.ctr, b.st);
   }
   if (finish(b.work, kPhFprobe)) {
     block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
@@ -716,17 +953,15 @@ __global__ void __launch_bounds__(256, 4) k_plan_fprobe(Batch b) {
 }
 
 // ------------------------------------------------------------------- topk ----
-// Per (plan, 1024 groups) block top-k; the block that finishes a plan's last
-// chunk merges the partial lists with all its warps, then warp 0 merges those.
+// Per (plan, 1024 groups) warp top-k; each lane keeps 8 group-list reads and
+// then 8 record reads in flight.  The warp that finishes a plan's last chunk
+// merges every chunk's partial list, reading 256 candidates per round.
 __global__ void __launch_bounds__(256) k_plan_topk(Batch b) {
-  __shared__ i64 sk[8 * kMaxK], ss[8 * kMaxK];
-  __shared__ int sc[8];
-  __shared__ bool s_last;
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   while (true) {
-    const i64 t = claim(b.work, kPhTopk);
+    const i64 t = warp_claim(b.work, kPhTopk);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -734,41 +969,53 @@ __global__ void __launch_bounds__(256) k_plan_topk(Batch b) {
     const i64 n = (i64)q.ctr->gcount;
     const i64 lt = t - pre[qi];
     const i64 i0 = lt * kTK, i1 = min(n, i0 + kTK);
+    const longlong2* rec = reinterpret_cast<const longlong2*>(
+        table_view(q.ht_tag, q.ctr->mlog2, true).rec);
     TopList L;
     L.clear();
-    for (i64 i = i0; i < i1; i += blockDim.x) {
-      const i64 j = i + threadIdx.x;
-      const bool v = j < i1;
-      const u32 s = v ? q.glist[j] : 0u;
-      L.offer(K, v, v ? q.ht_keys[s] : 0, v ? q.ht_sums[s] : 0);
-    }
-    tk_block_merge(L, K, sk, ss, sc);
-    if (threadIdx.x < 32) {
-      L.store(q.tk_k + lt * K, q.tk_s + lt * K);
-      if (lane == 0) q.tk_c[lt] = L.cnt;
-      __threadfence();
-      u32 tk = 0;
-      if (lane == 0) tk = atomicAdd(&q.ctr->tk_ticket, 1u);
-      tk = __shfl_sync(kFull, tk, 0);
-      const i64 parts = pre[qi + 1] - pre[qi];
-      if (lane == 0) s_last = ((i64)tk == parts - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      const i64 cand = (pre[qi + 1] - pre[qi]) * K;
-      L.clear();
-      for (i64 j = (i64)warp * 32; j < cand; j += blockDim.x) {
-        const i64 e = j + lane;
-        const bool v = e < cand && (int)(e % K) < *(volatile int*)&q.tk_c[e / K];
-        L.offer(K, v, v ? *(volatile i64*)&q.tk_k[e] : 0, v ? *(volatile i64*)&q.tk_s[e] : 0);
+    for (i64 i = i0; i < i1; i += 256) {
+      u32 sl[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const i64 j = i + u * 32 + lane;
+        sl[u] = j < i1 ? q.glist[j] : 0u;
       }
-      tk_block_merge(L, K, sk, ss, sc);
-      if (threadIdx.x < 32) {
-        L.store((i64*)q.out->keys, (i64*)q.out->sums);
-        if (lane == 0) q.out->n = L.cnt;
-      }
+      longlong2 ks[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        ks[u] = i + u * 32 + lane < i1 ? rec[sl[u]] : make_longlong2(0, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) L.offer(K, i + u * 32 + lane < i1, ks[u].x, ks[u].y);
     }
+    L.store(q.tk_k + lt * K, q.tk_s + lt * K);
+    if (lane == 0) q.tk_c[lt] = L.cnt;
+    __threadfence();
+    u32 tk = 0;
+    if (lane == 0) tk = atomicAdd(&q.ctr->tk_ticket, 1u);
+    tk = __shfl_sync(kFull, tk, 0);
+    const int parts = (int)(pre[qi + 1] - pre[qi]);
+    if ((int)tk != parts - 1) continue;
+    // This warp finished the plan's last chunk: merge every chunk's list
+    // (read through L2, where the other warps' fenced stores are visible).
+    __threadfence();
+    const int cand = parts * K;
+    L.clear();
+    for (int j = 0; j < cand; j += 256) {
+      bool v[8];
+      i64 ck[8], cs[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = j + u * 32 + lane;
+        const int p = e / K;
+        v[u] = e < cand && e - p * K < __ldcg(q.tk_c + p);
+        ck[u] = v[u] ? __ldcg(q.tk_k + e) : 0;
+        cs[u] = v[u] ? __ldcg(q.tk_s + e) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
+    }
+    L.store((i64*)q.out->keys, (i64*)q.out->sums);
+    if (lane == 0) q.out->n = L.cnt;
   }
   finish(b.work, kPhTopk);
 }

@@ -392,9 +392,10 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       dset_block_assign(blk, e, d);
       PQ_CUDA(ctx, upload_desc(0, r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
                                r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
-      // The dscan kernel sized the fill/build phases; it wrote the log2 into
-      // the placeholder, which is copied to the real block.
-      PQ_CUDA(ctx, cudaMemcpyAsync(d.dset_log2, dset_blk, 4, cudaMemcpyDeviceToDevice, s));
+      // The dscan kernel sized the fill/build phases; it wrote the header
+      // (log2, bitmap base and bits) into the placeholder, copied here to the
+      // real block.
+      PQ_CUDA(ctx, cudaMemcpyAsync(d.dset_log2, dset_blk, 24, cudaMemcpyDeviceToDevice, s));
       for (int ph : {kPhaseDfill, kPhaseDbuild}) {
         st = launch_phase(ctx, ph, b, true, s);
         if (st != PQ_OK) return st;
