@@ -359,7 +359,7 @@ pq_status pq_create(const pq_options* opt, void* arena, size_t arena_bytes, pq_c
             cudaHostAlloc((void**)&ctx->h_status, sizeof(pqk::DevStatus), 0) == cudaSuccess &&
             cudaHostAlloc((void**)&ctx->h_small, 4096, 0) == cudaSuccess &&
             cudaMemset(ctx->d_status, 0, 2 * sizeof(pqk::DevStatus)) == cudaSuccess &&
-            ctx->ring.init(64 << 10, 32);
+            ctx->ring.init(64 << 10, 32) && pqh::plan_kernels_init(ctx) == PQ_OK;
   for (int i = 0; ok && i < o.copy_streams; ++i) {
     cudaStream_t s;
     ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;

@@ -281,4 +281,5 @@ __device__ __forceinline__ i64 lookback_prefix(u64* state, i64 tile, i64 aggrega
   return prefix;
 }
 
+
 }  // namespace pqk

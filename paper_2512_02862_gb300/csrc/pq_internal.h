@@ -148,11 +148,15 @@ struct pq_ctx {
   // tuning (kernel launch shapes chosen by pq_autotune or the options)
   int tune_threads = 256;
   int tune_bps = 2;
+  // resident blocks per SM of each plan kernel (filled by plan_kernels_init)
+  int plan_occ[10] = {0};
 };
 
 namespace pqh {
 
 pq_status fail(pq_ctx* ctx, pq_status st, const char* fmt, ...);
+// Per-device set-up of the plan kernels (shared-memory limits, occupancy).
+pq_status plan_kernels_init(pq_ctx* ctx);
 pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what);
 
 #define PQ_CUDA(ctx, call)                                      \

@@ -61,7 +61,7 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
   d.n_f = r.n_f;
   r.e_d = cap_log2(r.n_d, d.lf1024);
   r.e_m = cap_log2(r.n_m, d.lf1024);
-  r.parts = std::max<i64>(1, (r.n_m + kTK - 1) / kTK);
+  r.parts = topk_parts(r.e_m);
   const pq_table* T[3] = {p.D, p.M, p.F};
   for (int t = 0; t < 3; ++t) {
     r.resident[t] = true;
@@ -94,9 +94,8 @@ size_t plan_bytes(const ResolvedPlan& r) {
   if (r.builds) b += al(r.n_d * 8);                                // D list
   if (r.builds && r.dset_from == -1) b += dset_block_bytes(r.e_d);  // own D-set
   b += al(r.n_m * 8);                    // M list
-  b += mtable_bytes(r.e_m);              // table tags, keys, sums, first-hit flags
-  b += al(r.n_m * 4);                    // group list
-  b += al(r.parts * r.dev.k * 8) * 2 + al(r.parts * 4);  // top-k partials
+  b += mtable_bytes(r.e_m);              // M table
+  b += al((r.parts + 32) * r.dev.k * 8) * 2 + al((r.parts + 32) * 4);  // top-k partials
   return b;
 }
 
@@ -113,10 +112,9 @@ void plan_assign(ResolvedPlan& r, char* base) {
   if (r.builds && r.dset_from == -1) dset_block_assign(take(dset_block_bytes(r.e_d)), r.e_d, d);
   d.mlist = (i64*)take(r.n_m * 8);
   p = mtable_assign(p, r.e_m, d);
-  d.glist = (u32*)take(r.n_m * 4);
-  d.tk_k = (i64*)take(r.parts * d.k * 8);
-  d.tk_s = (i64*)take(r.parts * d.k * 8);
-  d.tk_c = (int*)take(r.parts * 4);
+  d.tk_k = (i64*)take((r.parts + 32) * d.k * 8);  // tile lists, then group lists
+  d.tk_s = (i64*)take((r.parts + 32) * d.k * 8);
+  d.tk_c = (int*)take((r.parts + 32) * 4);
 }
 
 BatchLayout batch_layout(int nq) {
@@ -161,28 +159,52 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
 static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill", "plan_dbuild", "plan_mscan",
                                    "plan_mfill",  "plan_mbuild", "plan_fprobe", "plan_topk"};
 
+pq_status plan_kernels_init(pq_ctx* ctx) {
+  const void* fn[10] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
+                        (const void*)k_plan_dbuild,       (const void*)k_plan_mscan<true>,
+                        (const void*)k_plan_fill,         (const void*)k_plan_mbuild,
+                        (const void*)k_plan_fprobe<false>, (const void*)k_plan_topk,
+                        (const void*)k_plan_fprobe<true>,  (const void*)k_plan_mscan<false>};
+  for (int i = 0; i < 10; ++i) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], i == 7 ? 128 : 256, 0) !=
+        cudaSuccess)
+      return PQ_ERR_CUDA;
+    ctx->plan_occ[i] = std::max(n, 1);
+  }
+  return PQ_OK;
+}
+
+// Persistent grid of a plan kernel: the tuned blocks per SM, capped by what
+// fits on an SM at once (a block that only starts after others exit finds
+// no work left).
+static int plan_grid(pq_ctx* ctx, int occ_index) {
+  return ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
+}
+
 pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s) {
-  const int grid = grid_persistent(ctx, 256);
   cudaEvent_t stop;
   prof_begin(ctx, kPhaseName[phase], s, &stop);
   switch (phase) {
     case kPhaseD:
-      if (vec) k_plan_dscan<true><<<grid, 256, 0, s>>>(b);
-      else k_plan_dscan<false><<<grid, 256, 0, s>>>(b);
+      if (vec) k_plan_dscan<true><<<plan_grid(ctx, 0), 256, 0, s>>>(b);
+      else k_plan_dscan<false><<<plan_grid(ctx, 0), 256, 0, s>>>(b);
       break;
-    case kPhaseDfill: k_plan_fill<<<grid, 256, 0, s>>>(b, 0); break;
-    case kPhaseDbuild: k_plan_dbuild<<<grid, 256, 0, s>>>(b); break;
+    case kPhaseDfill: k_plan_fill<<<plan_grid(ctx, 1), 256, 0, s>>>(b, 0); break;
+    case kPhaseDbuild: k_plan_dbuild<<<plan_grid(ctx, 2), 256, 0, s>>>(b); break;
     case kPhaseM:
-      if (vec) k_plan_mscan<true><<<grid, 256, 0, s>>>(b);
-      else k_plan_mscan<false><<<grid, 256, 0, s>>>(b);
+      if (vec) k_plan_mscan<true><<<plan_grid(ctx, 3), 256, 0, s>>>(b);
+      else k_plan_mscan<false><<<plan_grid(ctx, 9), 256, 0, s>>>(b);
       break;
-    case kPhaseMfill: k_plan_fill<<<grid, 256, 0, s>>>(b, 1); break;
-    case kPhaseMbuild: k_plan_mbuild<<<grid, 256, 0, s>>>(b); break;
+    case kPhaseMfill: k_plan_fill<<<plan_grid(ctx, 4), 256, 0, s>>>(b, 1); break;
+    case kPhaseMbuild: k_plan_mbuild<<<plan_grid(ctx, 5), 256, 0, s>>>(b); break;
     case kPhaseF:
-      if (vec) k_plan_fprobe<true><<<grid, 256, 0, s>>>(b);
-      else k_plan_fprobe<false><<<grid, 256, 0, s>>>(b);
+      if (vec)
+        k_plan_fprobe<true><<<plan_grid(ctx, 8), 256, 0, s>>>(b);
+      else
+        k_plan_fprobe<false><<<plan_grid(ctx, 6), 256, 0, s>>>(b);
       break;
-    case kPhaseTopk: k_plan_topk<<<grid, 256, 0, s>>>(b); break;
+    case kPhaseTopk: k_plan_topk<<<plan_grid(ctx, 7), 128, 0, s>>>(b); break;
   }
   prof_end(stop, s);
   PQ_LAUNCHED(ctx);

@@ -36,7 +36,6 @@ constexpr int kTD = 1024;    // D rows per warp tile
 constexpr int kTM = 1024;    // M rows per warp tile
 constexpr int kTF = 2048;    // F rows per warp tile
 constexpr int kTB = 128;     // list entries inserted per warp tile (4 per lane)
-constexpr int kTK = 1024;    // groups per top-k warp tile
 constexpr int kQ = 256;      // entries of a warp's shared-memory ring
 
 struct QCtr {
@@ -51,6 +50,7 @@ struct QCtr {
   u64 m_umin;  // M bitmap: ukey of bit 0
   u64 m_bits;  // M bitmap: bit count (0 = no bitmap)
   u64 pad[2];
+  u32 tk_group[32];  // top-k: finished tiles per group of 32 tiles
 };
 
 // Key-range semi-join filter.  When the keys of a filtered build side span
@@ -104,6 +104,21 @@ __host__ __device__ __forceinline__ i64 clear_units(int e, bool with_sums, u64 b
 }
 __host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bits) {
   return (clear_units(e, with_sums, bits) + kTCU - 1) / kTCU;
+}
+
+// Top-k tiles of an M table of 2^e slots: ranges of its first-hit bitmap,
+// at least 512 words each and at most 1024 tiles per table (so that the
+// final merge reads at most 1024 partial lists).
+__host__ __device__ __forceinline__ i64 topk_tile_words(int e) {
+  const i64 words = ((1LL << e) + 31) >> 5;
+  i64 tw = 512;
+  while (words / tw > 1024) tw <<= 1;
+  return tw;
+}
+__host__ __device__ __forceinline__ i64 topk_parts(int e) {
+  const i64 words = ((1LL << e) + 31) >> 5;
+  const i64 tw = topk_tile_words(e);
+  return (words + tw - 1) / tw;
 }
 
 __device__ __forceinline__ bool bit_test(const u32* bm, u64 idx, u64 keep) {
@@ -188,7 +203,6 @@ struct PlanDev {
   unsigned short* dset_tag;  // D-set table (keys only), laid out by table_layout
   i64* mlist;
   unsigned short* ht_tag;    // M table ({key, sum} records), laid out by table_layout
-  u32* glist;
   i64* tk_k;
   i64* tk_s;
   int* tk_c;
@@ -736,68 +750,43 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
 }
 
 // ----------------------------------------------------------------- fprobe ----
-constexpr int kAgg = 512;    // entries of a block's shared-memory aggregation table
-constexpr int kH = 256;      // entries of a warp's hit ring
+constexpr int kAggLog2 = 8;
+constexpr int kAgg = 1 << kAggLog2;  // entries of a block's shared-memory aggregation table
+constexpr int kH = 256;              // entries of a warp's hit ring
 
 struct ProbeCtx {
   TableView t;
-  u32* glist;
-  QCtr* ctr;
   const i64* mkey;
   const i64* price;
   const signed char* disc;
+  QCtr* ctr;
   DevStatus* st;
   i64 base;
   u64 keep;
-  u64 qtag;       // (plan index << 40) + 1: the aggregation key of slot s is qtag + s
-  u64* akey;      // the block's aggregation table (shared memory)
-  i64* asum;
+  int qi;         // plan index in the batch
 };
 
 __device__ __forceinline__ bool add_overflows(i64 old, i64 v) {
   return (v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v);
 }
 
-// Add v into the sum of M-table slot s and record s as a group on its first
-// hit (global memory).
-__device__ __forceinline__ void global_add(const TableView& t, u64 s, i64 v, u32* glist,
-                                           QCtr* ctr, DevStatus* st) {
-  const i64 old = (i64)atomicAdd((u64*)(t.rec + 2 * s + 1), (u64)v);
-  if (add_overflows(old, v)) q_latch(ctr, st, PQ_ERR_OVERFLOW, (i64)s);
-  const u32 bit = 1u << (s & 31);
-  if (!(atomicOr(t.hit + (s >> 5), bit) & bit)) {
-    const u64 gi = atomicAdd(&ctr->gcount, 1ULL);
-    glist[gi] = (u32)s;
-  }
-}
-
-// Add v into slot s through the block's direct-mapped shared-memory table:
-// the first slot to reach an entry keeps it for the rest of the kernel, so
-// the repeated hits of hot keys (skewed data) stay on chip; a slot whose
-// entry is taken goes to the global atomic.
-__device__ __forceinline__ void agg_add(const ProbeCtx& c, u64 s, i64 v) {
-  const u64 ak = c.qtag + s;
-  const u32 h = (u32)((ak * 0x9E3779B97F4A7C15ULL) >> 55);
-  u64 cur = *(volatile u64*)&c.akey[h];
-  if (cur == 0) {
-    cur = atomicCAS((unsigned long long*)&c.akey[h], 0ULL, ak);
-    if (cur == 0) cur = ak;
-  }
-  if (cur == ak) {
-    const i64 old = (i64)atomicAdd((unsigned long long*)&c.asum[h], (unsigned long long)v);
-    if (add_overflows(old, v)) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, (i64)s);
-  } else {
-    global_add(c.t, s, v, c.glist, c.ctr, c.st);
-  }
-}
+// One probed F row: the M-table slot of its group and the revenue to add.
+struct Hit {
+  bool act;
+  u64 slot;
+  i64 v;
+};
 
 // Probe the M table with the key of F row base + r: count the slots holding
 // it (its multiplicity in M', found in the home bucket and, while buckets are
-// full, the next ones) and add the row's exact revenue times that count into
-// the first of them.
-__device__ __forceinline__ void probe_row(const ProbeCtx& c, u32 r) {
+// full, the next ones); the row adds its exact revenue times that count to
+// the group of the first of them.
+__device__ __forceinline__ Hit probe_row(const ProbeCtx& c, u32 r) {
+  Hit h = {false, 0, 0};
   const i64 row = c.base + r;
   const i64 k = __ldg(c.mkey + row);
+  const i64 price = __ldg(c.price + row);  // loaded with the key: one round trip
+  const i64 disc = __ldg(c.disc + row);
   const BucketTag bt = bucket_tag(k, c.t.g.shiftb);
   const unsigned v2 = bt.tag * 0x10001u;
   u64 b = bt.bucket;
@@ -817,14 +806,89 @@ __device__ __forceinline__ void probe_row(const ProbeCtx& c, u32 r) {
     if (any8(match8(w, 0u))) break;
     b = (b + 1) & c.t.g.bmask;
   }
-  if (first < 0) return;
+  if (first < 0) return h;
   // Exact revenue: the product is formed in 128 bits so that a value outside
   // int64 is reported instead of wrapping.
-  const __int128 v128 =
-      (__int128)mult * ((__int128)__ldg(c.price + row) * (100 - (i64)__ldg(c.disc + row)));
-  const i64 v = (i64)v128;
-  if (v128 != (__int128)v) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
-  agg_add(c, (u64)first, v);
+  const __int128 v128 = (__int128)mult * ((__int128)price * (100 - disc));
+  h.v = (i64)v128;
+  if (v128 != (__int128)h.v) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
+  h.act = true;
+  h.slot = (u64)first;
+  return h;
+}
+
+// Add v into the block's direct-mapped shared-memory table under key ak (plan
+// and slot): the first key to reach an entry keeps it for the rest of the
+// kernel, so the repeated hits of hot groups (skewed data) stay on chip.
+// False when the entry belongs to another key.
+__device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, bool& ovf) {
+  const u32 h = (u32)((ak * 0x9E3779B97F4A7C15ULL) >> (64 - kAggLog2));
+  u64 cur = *(volatile u64*)&akey[h];
+  if (cur == 0) {
+    cur = atomicCAS((unsigned long long*)&akey[h], 0ULL, ak);
+    if (cur == 0) cur = ak;
+  }
+  if (cur != ak) return false;
+  const i64 old = (i64)atomicAdd((unsigned long long*)&asum[h], (unsigned long long)v);
+  ovf = ovf || add_overflows(old, v);
+  return true;
+}
+
+// Warp-wide commit of per-lane sums (every lane calls; lanes with `act` add
+// v to slot s of plan qi).  Lanes with the same plan and slot combine first
+// (their lowest lane carries the exact total); that lane adds it to the
+// block's shared table when `akey` is given and the entry is free or its own,
+// else to the M table and sets the slot's first-hit bit (a reduction nobody
+// waits for).  The groups are read from the first-hit bits by the top-k
+// phase.  sc: the warp's 32-entry scratch.
+__device__ __forceinline__ void commit_hits(const Batch& b, i64* sc, u64* akey, i64* asum,
+                                            bool act, int qi, u64 s, i64 v) {
+  const int lane = threadIdx.x & 31;
+  const u64 ak = act ? ((u64)qi << 40) + s + 1 : 0;
+  const u32 peers = __match_any_sync(kFull, ak);
+  const bool lead = act && __ffs(peers) - 1 == lane;
+  sc[lane] = v;
+  __syncwarp();
+  i64 tot = v;
+  bool ovf = false;
+  if (lead && peers != (1u << lane)) {
+    __int128 acc = 0;
+    for (u32 m = peers; m; m &= m - 1) acc += sc[__ffs(m) - 1];
+    tot = (i64)acc;
+    ovf = acc != (__int128)tot;
+  }
+  __syncwarp();
+  if (lead) {
+    const PlanDev& q = b.q[qi];
+    if (!(akey && agg_try(akey, asum, ak, tot, ovf))) {
+      const TableView t = table_view(q.ht_tag, q.ctr->mlog2, true);
+      atomicOr(t.hit + (s >> 5), 1u << (s & 31));
+      const i64 old = (i64)atomicAdd((u64*)(t.rec + 2 * s + 1), (u64)tot);
+      ovf = ovf || add_overflows(old, tot);
+    }
+    if (ovf) q_latch(q.ctr, b.st, PQ_ERR_OVERFLOW, (i64)s);
+  }
+}
+
+// End of an F-probe kernel: flush the block's aggregated sums to the plans'
+// tables; the block that finishes last sizes the top-k phase.
+__device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_akey,
+                                                const i64* s_asum, i64* sc) {
+  __syncthreads();
+  for (int i0 = 0; i0 < kAgg; i0 += blockDim.x) {  // warp-uniform trip count
+    const int i = i0 + threadIdx.x;
+    const u64 ak = i < kAgg ? s_akey[i] : 0;
+    commit_hits(b, sc, nullptr, nullptr, ak != 0, ak ? (int)((ak - 1) >> 40) : 0,
+                (ak - 1) & ((1ULL << 40) - 1), ak ? s_asum[i] : 0);
+  }
+  if (finish(b.work, kPhFprobe)) {
+    block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+      const PlanDev& q = b.q[qi];
+      q.out->status = q.ctr->status;
+      q.out->reserved = 0;
+      return topk_parts(q.ctr->mlog2);
+    });
+  }
 }
 
 // Warp tile of 2048 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
@@ -840,13 +904,36 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
   __shared__ u32 s_hr[8][kH];
   __shared__ u64 s_akey[kAgg];
   __shared__ i64 s_asum[kAgg];
+  __shared__ i64 s_sc[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* hr = s_hr[warp];
+  i64* sc = s_sc[warp];
   for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
   __syncthreads();
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
+  const i64 r0 = lane * 4;
+  // The hit ring carries over from tile to tile of the same plan (entries
+  // are rows of the plan, so batches of 32 fill up); it is drained when the
+  // plan changes, or after every tile of a plan with 2^32 rows or more
+  // (entries are then rows of the tile).
+  ProbeCtx pc;
+  pc.qi = -1;
+  bool carry = false;
+  u32 hh = 0, ht = 0;
+  auto probe_hits = [&](u32 cnt) {  // cnt <= 32 entries from hh
+    Hit h = {false, 0, 0};
+    if ((u32)lane < cnt) h = probe_row(pc, hr[(hh + lane) & (kH - 1)]);
+    commit_hits(b, sc, s_akey, s_asum, h.act, pc.qi, h.slot, h.v);
+    hh += cnt;
+    __syncwarp();
+  };
+  auto drain = [&]() {
+    while (ht - hh >= 32) probe_hits(32);
+    if (ht - hh) probe_hits(ht - hh);
+    hh = ht = 0;
+  };
   while (true) {
     const i64 t = warp_claim(b.work, kPhFprobe);
     if (t >= total) break;
@@ -856,39 +943,33 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     const int* f_date = ov ? (const int*)b.ov.p[3] : q.f_date;
     const i64 n = ov ? b.ov.n : q.n_f;
     const i64 base = (t - (ov ? 0 : b.tF[qi])) * kTF;
-    ProbeCtx pc;
-    pc.t = table_view(q.ht_tag, q.ctr->mlog2, true);
-    pc.glist = q.glist;
-    pc.ctr = q.ctr;
-    pc.mkey = f_mkey;
-    pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
-    pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
-    pc.st = b.st;
-    pc.base = base;
-    pc.keep = keep;
-    pc.qtag = ((u64)qi << 40) + 1;
-    pc.akey = s_akey;
-    pc.asum = s_asum;
+    if (qi != pc.qi || !carry) {
+      if (pc.qi >= 0) drain();
+      carry = n < (1LL << 32);
+      pc.t = table_view(q.ht_tag, q.ctr->mlog2, true);
+      pc.mkey = f_mkey;
+      pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
+      pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+      pc.ctr = q.ctr;
+      pc.st = b.st;
+      pc.base = carry ? 0 : base;
+      pc.keep = keep;
+      pc.qi = qi;
+    }
+    const u32 rbase = carry ? (u32)base : 0u;
     const u32* bm = pc.t.keybm;
     const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
     const Pred32 pf = to32(q.pf);
     const i64 lim = min(n - base, (i64)kTF);
     const int iters = (int)((lim + 127) / 128);
-    const i64 r0 = lane * 4;
-    u32 hh = 0, ht = 0;
     auto append_hits = [&](u32 hits, int it) {
       if (__any_sync(kFull, hits)) {
         __syncwarp();
         ht += ring_append(hits, ht, [&](int s, u32 pos) {
-          hr[pos & (kH - 1)] = (u32)(it * 128 + r0 + s);
+          hr[pos & (kH - 1)] = rbase + (u32)(it * 128 + r0 + s);
         });
         __syncwarp();
       }
-    };
-    auto probe_hits = [&](u32 cnt) {  // cnt <= 32 entries from hh
-      if ((u32)lane < cnt) probe_row(pc, hr[(hh + lane) & (kH - 1)]);
-      hh += cnt;
-      __syncwarp();
     };
     int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
     int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, base + 128 + r0, lim - 128 - r0, strm)
@@ -927,95 +1008,148 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     }
     append_hits(bm_hits(wP), iters - 1);
     while (ht - hh >= 32) probe_hits(32);
-    if (ht - hh) probe_hits(ht - hh);
   }
-  // Flush the block's aggregated sums to the plans' tables.
-  __syncthreads();
-  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) {
-    const u64 ak = s_akey[i];
-    if (!ak) continue;
-    const int qi = (int)((ak - 1) >> 40);
-    const u64 s = (ak - 1) & ((1ULL << 40) - 1);
-    const PlanDev& q = b.q[qi];
-    global_add(table_view(q.ht_tag, q.ctr->mlog2, true), s, s_asum[i], q.glist, q.ctr, b.st);
-  }
-  if (finish(b.work, kPhFprobe)) {
-    block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      const PlanDev& q = b.q[qi];
-      const i64 g = ld_count(&q.ctr->gcount);
-      q.out->ngroups = g;
-      q.out->status = q.ctr->status;
-      q.out->reserved = 0;
-      if (g == 0) q.out->n = 0;
-      return (g + kTK - 1) / kTK;
-    });
-  }
+  if (pc.qi >= 0) drain();
+  fprobe_epilogue(b, s_akey, s_asum, sc);
 }
 
 // ------------------------------------------------------------------- topk ----
-// Per (plan, 1024 groups) warp top-k; each lane keeps 8 group-list reads and
-// then 8 record reads in flight.  The warp that finishes a plan's last chunk
-// merges every chunk's partial list, reading 256 candidates per round.
-__global__ void __launch_bounds__(256) k_plan_topk(Batch b) {
+// Merge n partial top-k lists (K entries each, list i holding cnt[i]) into L
+// with one warp: the counts are staged in shared memory (scnt, n entries),
+// then 256 candidates per round are read through L2 (where other warps'
+// fenced stores are visible), 8 per lane in flight.
+__device__ __forceinline__ void merge_lists(TopList& L, int K, int n, const i64* keys,
+                                            const i64* sums, const int* cnt, u32* scnt) {
+  const int lane = threadIdx.x & 31;
+  for (int p = lane; p < n; p += 32) scnt[p] = (u32)__ldcg(cnt + p);
+  __syncwarp();
+  L.clear();
+  const int cand = n * K;
+  for (int j = 0; j < cand; j += 256) {
+    bool v[8];
+    i64 ck[8], cs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int x = j + u * 32 + lane;
+      const int p = x / K;
+      v[u] = x < cand && (u32)(x - p * K) < scnt[p];
+      ck[u] = v[u] ? __ldcg(keys + x) : 0;
+      cs[u] = v[u] ? __ldcg(sums + x) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
+  }
+  __syncwarp();
+}
+
+// A warp tile is a range of the M table's first-hit bitmap (topk_tile_words).
+// The warp reads 8 steps of 32 words (one per lane and step) at a time,
+// writes the slots of their set bits into its shared-memory ring, and offers
+// the ring's records to its register top-k list 256 at a time (8 record
+// reads in flight per lane); the warp also counts the groups.  Lists merge
+// in two levels: the warp that finishes the last tile of a group of 32 tiles
+// merges that group's lists, and the warp that finishes the last group
+// merges the group lists and writes the result with the group count.
+constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
+__global__ void __launch_bounds__(128) k_plan_topk(Batch b) {
+  __shared__ u32 s_ring[4][kTKR];
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
   const int lane = threadIdx.x & 31;
+  u32* ring = s_ring[threadIdx.x >> 5];
   while (true) {
     const i64 t = warp_claim(b.work, kPhTopk);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
     const int K = q.k;
-    const i64 n = (i64)q.ctr->gcount;
+    const int e = q.ctr->mlog2;
+    const TableView tv = table_view(q.ht_tag, e, true);
+    const longlong2* rec = reinterpret_cast<const longlong2*>(tv.rec);
+    const i64 words = ((1LL << e) + 31) >> 5, tw = topk_tile_words(e);
     const i64 lt = t - pre[qi];
-    const i64 i0 = lt * kTK, i1 = min(n, i0 + kTK);
-    const longlong2* rec = reinterpret_cast<const longlong2*>(
-        table_view(q.ht_tag, q.ctr->mlog2, true).rec);
+    const i64 w0 = lt * tw, w1 = min(words, w0 + tw);
     TopList L;
     L.clear();
-    for (i64 i = i0; i < i1; i += 256) {
-      u32 sl[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const i64 j = i + u * 32 + lane;
-        sl[u] = j < i1 ? q.glist[j] : 0u;
-      }
+    u32 head = 0, tail = 0;
+    u64 groups = 0;
+    auto offer_ring = [&](u32 cnt) {  // cnt <= 256 entries from head
       longlong2 ks[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        ks[u] = i + u * 32 + lane < i1 ? rec[sl[u]] : make_longlong2(0, 0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) L.offer(K, i + u * 32 + lane < i1, ks[u].x, ks[u].y);
-    }
-    L.store(q.tk_k + lt * K, q.tk_s + lt * K);
-    if (lane == 0) q.tk_c[lt] = L.cnt;
-    __threadfence();
-    u32 tk = 0;
-    if (lane == 0) tk = atomicAdd(&q.ctr->tk_ticket, 1u);
-    tk = __shfl_sync(kFull, tk, 0);
-    const int parts = (int)(pre[qi + 1] - pre[qi]);
-    if ((int)tk != parts - 1) continue;
-    // This warp finished the plan's last chunk: merge every chunk's list
-    // (read through L2, where the other warps' fenced stores are visible).
-    __threadfence();
-    const int cand = parts * K;
-    L.clear();
-    for (int j = 0; j < cand; j += 256) {
-      bool v[8];
-      i64 ck[8], cs[8];
-#pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = j + u * 32 + lane;
-        const int p = e / K;
-        v[u] = e < cand && e - p * K < __ldcg(q.tk_c + p);
-        ck[u] = v[u] ? __ldcg(q.tk_k + e) : 0;
-        cs[u] = v[u] ? __ldcg(q.tk_s + e) : 0;
+        const u32 j = u * 32 + lane;
+        ks[u] = j < cnt ? rec[ring[(head + j) & (kTKR - 1)]] : make_longlong2(0, 0);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
+      for (int u = 0; u < 8; ++u) L.offer(K, (u32)(u * 32 + lane) < cnt, ks[u].x, ks[u].y);
+      head += cnt;
+      __syncwarp();
+    };
+    for (i64 w = w0; w < w1; w += 256) {
+      u32 wb[8];  // 8 steps of bitmap words in flight
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const i64 wi = w + u * 32 + lane;
+        wb[u] = wi < w1 ? __ldcg(tv.hit + wi) : 0u;
+      }
+#pragma unroll 1
+      for (int u = 0; u < 8; ++u) {
+        u32 bits = wb[0];
+#pragma unroll
+        for (int x = 0; x < 7; ++x) wb[x] = wb[x + 1];  // static indices only
+        const u32 c = __popc(bits);
+        groups += c;
+        u32 incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const u32 sb = (u32)(w + u * 32 + lane) * 32;
+        u32 pos = tail + incl - c;
+        while (bits) {
+          const int j = __ffs(bits) - 1;
+          bits &= bits - 1;
+          ring[pos++ & (kTKR - 1)] = sb + j;
+        }
+        tail += __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+        while (tail - head >= 256) offer_ring(256);
+      }
     }
+    if (tail - head) offer_ring(tail - head);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) groups += __shfl_xor_sync(kFull, groups, o);
+    L.store(q.tk_k + lt * K, q.tk_s + lt * K);
+    if (lane == 0) {
+      q.tk_c[lt] = L.cnt;
+      atomicAdd(&q.ctr->gcount, groups);
+    }
+    __threadfence();
+    const int parts = (int)(pre[qi + 1] - pre[qi]);
+    const int g = (int)(lt >> 5), ng = (parts + 31) >> 5;
+    const int gs = min(32, parts - g * 32);
+    u32 tk = 0;
+    if (lane == 0) tk = atomicAdd(&q.ctr->tk_group[g], 1u);
+    if ((int)__shfl_sync(kFull, tk, 0) != gs - 1) continue;
+    // Last tile of group g: merge the group's lists into list parts + g.
+    __threadfence();
+    merge_lists(L, K, gs, q.tk_k + (i64)g * 32 * K, q.tk_s + (i64)g * 32 * K, q.tk_c + g * 32,
+                ring);
+    L.store(q.tk_k + (i64)(parts + g) * K, q.tk_s + (i64)(parts + g) * K);
+    if (lane == 0) q.tk_c[parts + g] = L.cnt;
+    __threadfence();
+    if (lane == 0) tk = atomicAdd(&q.ctr->tk_ticket, 1u);
+    if ((int)__shfl_sync(kFull, tk, 0) != ng - 1) continue;
+    // Last group: merge the group lists.
+    __threadfence();
+    merge_lists(L, K, ng, q.tk_k + (i64)parts * K, q.tk_s + (i64)parts * K, q.tk_c + parts,
+                ring);
     L.store((i64*)q.out->keys, (i64*)q.out->sums);
-    if (lane == 0) q.out->n = L.cnt;
+    if (lane == 0) {
+      q.out->n = L.cnt;
+      q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
+    }
   }
   finish(b.work, kPhTopk);
 }

@@ -401,13 +401,10 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         if (st != PQ_OK) return st;
       }
     } else {
-      const i64 parts = std::max<i64>(1, (count + kTK - 1) / kTK);
-      char* blk = (char*)scr.get(mtable_bytes(e) + al(count * 4 + 4) + al(parts * d.k * 8) * 2 +
-                                 al(parts * 4));
+      const i64 parts = topk_parts(e) + 32;  // tile lists, then group lists
+      char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * d.k * 8) * 2 + al(parts * 4));
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: M table of 2^%d slots", e);
       char* p = mtable_assign(blk, e, d);
-      d.glist = (u32*)p;
-      p += al(count * 4 + 4);
       d.tk_k = (i64*)p;
       p += al(parts * d.k * 8);
       d.tk_s = (i64*)p;
