@@ -155,6 +155,12 @@ pq_status pq_get_stats(pq_ctx* ctx, pq_stats* out);
  * unknown name. */
 pq_status pq_profile_read(pq_ctx* ctx, const char* name, double* total_ms, int64_t* launches);
 pq_status pq_profile_reset(pq_ctx* ctx);
+/* Switch per-kernel timing on (1) or off (0) for the calls issued after it
+ * (the profile option at creation sets the initial state).  While it is on,
+ * plans run as separate launches with an event pair around each kernel;
+ * while it is off, a repeated plan replays its CUDA graph.  The caller issues
+ * no plan concurrently with the switch. */
+pq_status pq_profile_enable(pq_ctx* ctx, int32_t on);
 
 /* ---- tables --------------------------------------------------------------- */
 

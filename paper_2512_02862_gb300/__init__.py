@@ -109,6 +109,7 @@ def library():
         "pq_get_stats": [vp, POINTER(pq_stats)],
         "pq_profile_read": [vp, c_char_p, POINTER(c_double), POINTER(c_int64)],
         "pq_profile_reset": [vp],
+        "pq_profile_enable": [vp, c_int32],
         "pq_load_columns": [vp, POINTER(pq_source), i32, i64, i32, POINTER(vp), vp],
         "pq_table_free": [vp, vp, vp],
         "pq_ht_free": [vp, vp, vp],
@@ -239,6 +240,10 @@ class Context:
 
     def profile_reset(self):
         self.check(library().pq_profile_reset(self.h))
+
+    def profile_enable(self, on: bool):
+        """Per-kernel event timing on or off for the calls issued after this."""
+        self.check(library().pq_profile_enable(self.h, 1 if on else 0))
 
 
 # -------------------------------------------------------------- operators ----

@@ -436,6 +436,13 @@ pq_status pq_profile_read(pq_ctx* ctx, const char* name, double* total_ms, int64
   return PQ_OK;
 }
 
+pq_status pq_profile_enable(pq_ctx* ctx, int32_t on) {
+  if (!ctx || (on != 0 && on != 1)) return PQ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->opt.profile = on;
+  return PQ_OK;
+}
+
 pq_status pq_profile_reset(pq_ctx* ctx) {
   if (!ctx) return PQ_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(ctx->mu);

@@ -422,10 +422,12 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   __shared__ i64 sk[8 * kMaxK], ss[8 * kMaxK];
   __shared__ int sc[8];
   __shared__ bool s_last;
+  __shared__ i64 s_scr[8][64];
   const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
   const i64 per = (n + gridDim.x - 1) / gridDim.x;
   const i64 lo = min(n, per * blockIdx.x), hi = min(n, lo + per);
   TopList L;
+  L.bind(s_scr[threadIdx.x >> 5]);
   L.clear();
   for (i64 b = lo; b < hi; b += blockDim.x) {
     const i64 i = b + threadIdx.x;

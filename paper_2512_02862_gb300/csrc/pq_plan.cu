@@ -95,7 +95,8 @@ size_t plan_bytes(const ResolvedPlan& r) {
   if (r.builds && r.dset_from == -1) b += dset_block_bytes(r.e_d);  // own D-set
   b += al(r.n_m * 8);                    // M list
   b += mtable_bytes(r.e_m);              // M table
-  b += al((r.parts + 32) * r.dev.k * 8) * 2 + al((r.parts + 32) * 4);  // top-k partials
+  b += al(r.parts * 8) * 2 + al(r.parts * 4);                  // top-k tile maxima
+  b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k candidates
   return b;
 }
 
@@ -112,9 +113,11 @@ void plan_assign(ResolvedPlan& r, char* base) {
   if (r.builds && r.dset_from == -1) dset_block_assign(take(dset_block_bytes(r.e_d)), r.e_d, d);
   d.mlist = (i64*)take(r.n_m * 8);
   p = mtable_assign(p, r.e_m, d);
-  d.tk_k = (i64*)take((r.parts + 32) * d.k * 8);  // tile lists, then group lists
-  d.tk_s = (i64*)take((r.parts + 32) * d.k * 8);
-  d.tk_c = (int*)take((r.parts + 32) * 4);
+  d.tk_k = (i64*)take(r.parts * 8);
+  d.tk_s = (i64*)take(r.parts * 8);
+  d.tk_c = (int*)take(r.parts * 4);
+  d.cand_k = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
+  d.cand_s = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
 }
 
 BatchLayout batch_layout(int nq) {
@@ -156,19 +159,21 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
   return b;
 }
 
-static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill", "plan_dbuild", "plan_mscan",
-                                   "plan_mfill",  "plan_mbuild", "plan_fprobe", "plan_topk"};
+static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill",  "plan_dbuild",
+                                   "plan_mscan",  "plan_mfill",  "plan_mbuild",
+                                   "plan_fprobe", "plan_topk",   "plan_topk2"};
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[10] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
+  const void* fn[11] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
                         (const void*)k_plan_dbuild,       (const void*)k_plan_mscan<true>,
                         (const void*)k_plan_fill,         (const void*)k_plan_mbuild,
                         (const void*)k_plan_fprobe<false>, (const void*)k_plan_topk,
-                        (const void*)k_plan_fprobe<true>,  (const void*)k_plan_mscan<false>};
-  for (int i = 0; i < 10; ++i) {
+                        (const void*)k_plan_fprobe<true>,  (const void*)k_plan_mscan<false>,
+                        (const void*)k_plan_topk2};
+  for (int i = 0; i < 11; ++i) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], i == 7 ? 128 : 256, 0) !=
-        cudaSuccess)
+    const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
       return PQ_ERR_CUDA;
     ctx->plan_occ[i] = std::max(n, 1);
   }
@@ -204,7 +209,8 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
       else
         k_plan_fprobe<false><<<plan_grid(ctx, 6), 256, 0, s>>>(b);
       break;
-    case kPhaseTopk: k_plan_topk<<<plan_grid(ctx, 7), 128, 0, s>>>(b); break;
+    case kPhaseTopk: k_plan_topk<<<plan_grid(ctx, 7), kTKW * 32, 0, s>>>(b); break;
+    case kPhaseTopk2: k_plan_topk2<<<plan_grid(ctx, 10), kTKW * 32, 0, s>>>(b); break;
   }
   prof_end(stop, s);
   PQ_LAUNCHED(ctx);
@@ -220,6 +226,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   uint64_t last_use = 0;
+  int64_t kernels = 0;  // kernel nodes of the graph
 };
 
 struct PlanCache {
@@ -333,7 +340,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       PQ_CUDA(ctx, cudaEventRecord(e.done, s));
       ctx->replays++;
       ctx->plans++;
-      ctx->launches += 8;
+      ctx->launches += e.kernels;
       return read_back(ctx, results, e.out, 1, s);
     }
   }
@@ -449,7 +456,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
 
   auto chain = [&]() -> pq_status {
     PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
-    for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk; ++ph) {
+    for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
       pq_status st = launch_phase(ctx, ph, b, vec, s);
       if (st != PQ_OK) return st;
     }
@@ -461,6 +468,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const int64_t launches0 = ctx->launches.load();
     if (captured) {
       st = chain();
       cudaError_t e = cudaStreamEndCapture(s, &graph);
@@ -478,6 +486,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       e.ws = ws;
       e.out = out;
       e.exec = exec;
+      e.kernels = ctx->launches.load() - launches0;  // counted while capturing
       cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming);
       PQ_CUDA(ctx, cudaGraphLaunch(exec, s));
       PQ_CUDA(ctx, cudaEventRecord(e.done, s));

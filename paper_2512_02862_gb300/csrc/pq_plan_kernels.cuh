@@ -50,7 +50,13 @@ struct QCtr {
   u64 m_umin;  // M bitmap: ukey of bit 0
   u64 m_bits;  // M bitmap: bit count (0 = no bitmap)
   u64 pad[2];
-  u32 tk_group[32];  // top-k: finished tiles per group of 32 tiles
+  // Top-k: admission threshold (a record qualifies when it is not after
+  // (thr_s, thr_k) in the output order; thr_all: every record qualifies),
+  // candidate count, ticket of the selection pass.
+  i64 thr_k, thr_s;
+  int thr_all;
+  u32 tk_ticket2;
+  u64 ccount;
 };
 
 // Key-range semi-join filter.  When the keys of a filtered build side span
@@ -107,18 +113,25 @@ __host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bi
 }
 
 // Top-k tiles of an M table of 2^e slots: ranges of its first-hit bitmap,
-// at least 512 words each and at most 1024 tiles per table (so that the
-// final merge reads at most 1024 partial lists).
+// at least 1024 words each and at most 512 tiles per table (so that the
+// final merge reads at most 512 partial lists).
 __host__ __device__ __forceinline__ i64 topk_tile_words(int e) {
   const i64 words = ((1LL << e) + 31) >> 5;
-  i64 tw = 512;
-  while (words / tw > 1024) tw <<= 1;
+  i64 tw = 1024;
+  while (words / tw > 512) tw <<= 1;
   return tw;
 }
 __host__ __device__ __forceinline__ i64 topk_parts(int e) {
   const i64 words = ((1LL << e) + 31) >> 5;
   const i64 tw = topk_tile_words(e);
   return (words + tw - 1) / tw;
+}
+// Candidates of the selection pass: records not after the K-th best tile
+// maximum.  Only the K tiles with the best maxima can hold such records, so
+// K tiles' worth of slots (or the whole table) always suffices.
+__host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
+  const i64 slots = 1LL << e, tile_slots = topk_tile_words(e) * 32;
+  return slots < (i64)K * tile_slots ? slots : (i64)K * tile_slots;
 }
 
 __device__ __forceinline__ bool bit_test(const u32* bm, u64 idx, u64 keep) {
@@ -203,9 +216,11 @@ struct PlanDev {
   unsigned short* dset_tag;  // D-set table (keys only), laid out by table_layout
   i64* mlist;
   unsigned short* ht_tag;    // M table ({key, sum} records), laid out by table_layout
-  i64* tk_k;
-  i64* tk_s;
+  i64* tk_k;    // top-k: per tile, the best record (key, sum) and
+  i64* tk_s;    // whether the tile has any group
   int* tk_c;
+  i64* cand_k;  // top-k candidates (topk_cand_cap entries)
+  i64* cand_s;
   QCtr* ctr;
   pq_result* out;
 };
@@ -236,7 +251,8 @@ struct Batch {
   Ovr ov;
 };
 
-enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk };
+enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk,
+       kPhTopk2 };
 
 // The kernels below are defined in exactly one translation unit (pq_plan.cu),
 // which defines PQ_DEFINE_PLAN_KERNELS before including this header.
@@ -1014,144 +1030,256 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
 }
 
 // ------------------------------------------------------------------- topk ----
-// Merge n partial top-k lists (K entries each, list i holding cnt[i]) into L
-// with one warp: the counts are staged in shared memory (scnt, n entries),
-// then 256 candidates per round are read through L2 (where other warps'
-// fenced stores are visible), 8 per lane in flight.
-__device__ __forceinline__ void merge_lists(TopList& L, int K, int n, const i64* keys,
-                                            const i64* sums, const int* cnt, u32* scnt) {
-  const int lane = threadIdx.x & 31;
-  for (int p = lane; p < n; p += 32) scnt[p] = (u32)__ldcg(cnt + p);
-  __syncwarp();
-  L.clear();
-  const int cand = n * K;
-  for (int j = 0; j < cand; j += 256) {
-    bool v[8];
-    i64 ck[8], cs[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int x = j + u * 32 + lane;
-      const int p = x / K;
-      v[u] = x < cand && (u32)(x - p * K) < scnt[p];
-      ck[u] = v[u] ? __ldcg(keys + x) : 0;
-      cs[u] = v[u] ? __ldcg(sums + x) : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
-  }
-  __syncwarp();
+// Two passes over the M table's first-hit bitmap, tiled in block tiles
+// (topk_tile_words; each of a block's 4 warps takes a quarter).  A warp reads
+// 8 steps of 32 words (one per lane and step) at a time, writes the slots of
+// their set bits into its shared-memory ring, and reads the ring's records
+// 256 at a time (8 in flight per lane).
+//  A: every tile keeps its best record and counts its groups; the block that
+//     finishes a plan's last tile ranks the tile maxima in parallel and takes
+//     the K-th best as the threshold (no threshold with fewer than K
+//     non-empty tiles).  At least K records are not after it, so the top K
+//     are among the records that are not after it.
+//  B: the records not after the threshold are appended to the candidate
+//     list; the block that finishes the plan's last tile selects the top K
+//     of the candidates (four warp lists merged in shared memory) and writes
+//     the result with the group count.
+constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
+constexpr int kTKW = 4;     // warps per top-k block
+
+struct KS {
+  i64 k, s;
+  bool v;
+};
+// Output order on (key, sum) records: valid first, then sum desc, key asc.
+__device__ __forceinline__ bool ks_before(const KS& a, const KS& b) {
+  return a.v && (!b.v || tk_before(a.k, a.s, b.k, b.s));
 }
 
-// A warp tile is a range of the M table's first-hit bitmap (topk_tile_words).
-// The warp reads 8 steps of 32 words (one per lane and step) at a time,
-// writes the slots of their set bits into its shared-memory ring, and offers
-// the ring's records to its register top-k list 256 at a time (8 record
-// reads in flight per lane); the warp also counts the groups.  Lists merge
-// in two levels: the warp that finishes the last tile of a group of 32 tiles
-// merges that group's lists, and the warp that finishes the last group
-// merges the group lists and writes the result with the group count.
-constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
-__global__ void __launch_bounds__(128) k_plan_topk(Batch b) {
-  __shared__ u32 s_ring[4][kTKR];
+// Scan warp w's quarter of block tile lt of a table: calls on(KS) for 256
+// ring records at a time (each lane gets 8: invalid ones have v = false);
+// returns the number of set bits.
+template <typename On>
+__device__ __forceinline__ u64 tk_scan(const TableView& tv, i64 words, i64 tw, i64 lt, u32* ring,
+                                       On on) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const longlong2* rec = reinterpret_cast<const longlong2*>(tv.rec);
+  const i64 ww = tw / kTKW;
+  const i64 w0 = lt * tw + warp * ww, w1 = min(words, w0 + ww);
+  u32 head = 0, tail = 0;
+  u64 groups = 0;
+  auto drain = [&](u32 cnt) {  // cnt <= 256 entries from head
+    KS r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const u32 j = u * 32 + lane;
+      const longlong2 x = j < cnt ? rec[ring[(head + j) & (kTKR - 1)]] : make_longlong2(0, 0);
+      r[u].k = x.x, r[u].s = x.y, r[u].v = j < cnt;
+    }
+    on(r);
+    head += cnt;
+    __syncwarp();
+  };
+  for (i64 w = w0; w < w1; w += 256) {
+    u32 wb[8];  // 8 steps of bitmap words in flight
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const i64 wi = w + u * 32 + lane;
+      wb[u] = wi < w1 ? __ldcg(tv.hit + wi) : 0u;
+    }
+#pragma unroll 1
+    for (int u = 0; u < 8; ++u) {
+      u32 bits = wb[0];
+#pragma unroll
+      for (int x = 0; x < 7; ++x) wb[x] = wb[x + 1];  // static indices only
+      const u32 c = __popc(bits);
+      groups += c;
+      u32 incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const u32 sb = (u32)(w + u * 32 + lane) * 32;
+      u32 pos = tail + incl - c;
+      while (bits) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1;
+        ring[pos++ & (kTKR - 1)] = sb + j;
+      }
+      tail += __shfl_sync(kFull, incl, 31);
+      __syncwarp();
+      while (tail - head >= 256) drain(256);
+    }
+  }
+  if (tail - head) drain(tail - head);
+  return groups;
+}
+
+// Block-wide claim of the next top-k tile.
+__device__ __forceinline__ i64 tk_claim(u32* work, int ph, i64* s_t) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_t = atomicAdd(&work[ph], 1u);
+  __syncthreads();
+  return *s_t;
+}
+
+__global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
+  __shared__ u32 s_ring[kTKW][kTKR];
+  __shared__ KS s_best[kTKW];
+  __shared__ i64 s_t;
+  __shared__ bool s_last;
+  __shared__ int s_rank[1];
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
-  const int lane = threadIdx.x & 31;
-  u32* ring = s_ring[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhTopk);
+    const i64 t = tk_claim(b.work, kPhTopk, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int K = q.k;
     const int e = q.ctr->mlog2;
     const TableView tv = table_view(q.ht_tag, e, true);
-    const longlong2* rec = reinterpret_cast<const longlong2*>(tv.rec);
     const i64 words = ((1LL << e) + 31) >> 5, tw = topk_tile_words(e);
     const i64 lt = t - pre[qi];
-    const i64 w0 = lt * tw, w1 = min(words, w0 + tw);
-    TopList L;
-    L.clear();
-    u32 head = 0, tail = 0;
-    u64 groups = 0;
-    auto offer_ring = [&](u32 cnt) {  // cnt <= 256 entries from head
-      longlong2 ks[8];
+    KS best = {0, 0, false};
+    u64 groups = tk_scan(tv, words, tw, lt, s_ring[warp], [&](const KS* r) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const u32 j = u * 32 + lane;
-        ks[u] = j < cnt ? rec[ring[(head + j) & (kTKR - 1)]] : make_longlong2(0, 0);
-      }
+      for (int u = 0; u < 8; ++u)
+        if (ks_before(r[u], best)) best = r[u];
+    });
 #pragma unroll
-      for (int u = 0; u < 8; ++u) L.offer(K, (u32)(u * 32 + lane) < cnt, ks[u].x, ks[u].y);
-      head += cnt;
-      __syncwarp();
-    };
-    for (i64 w = w0; w < w1; w += 256) {
-      u32 wb[8];  // 8 steps of bitmap words in flight
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const i64 wi = w + u * 32 + lane;
-        wb[u] = wi < w1 ? __ldcg(tv.hit + wi) : 0u;
-      }
-#pragma unroll 1
-      for (int u = 0; u < 8; ++u) {
-        u32 bits = wb[0];
-#pragma unroll
-        for (int x = 0; x < 7; ++x) wb[x] = wb[x + 1];  // static indices only
-        const u32 c = __popc(bits);
-        groups += c;
-        u32 incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const u32 y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const u32 sb = (u32)(w + u * 32 + lane) * 32;
-        u32 pos = tail + incl - c;
-        while (bits) {
-          const int j = __ffs(bits) - 1;
-          bits &= bits - 1;
-          ring[pos++ & (kTKR - 1)] = sb + j;
-        }
-        tail += __shfl_sync(kFull, incl, 31);
-        __syncwarp();
-        while (tail - head >= 256) offer_ring(256);
-      }
+    for (int o = 16; o; o >>= 1) {
+      KS x;
+      x.k = __shfl_xor_sync(kFull, best.k, o);
+      x.s = __shfl_xor_sync(kFull, best.s, o);
+      x.v = __shfl_xor_sync(kFull, best.v, o);
+      if (ks_before(x, best)) best = x;
+      groups += __shfl_xor_sync(kFull, groups, o);
     }
-    if (tail - head) offer_ring(tail - head);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) groups += __shfl_xor_sync(kFull, groups, o);
-    L.store(q.tk_k + lt * K, q.tk_s + lt * K);
     if (lane == 0) {
-      q.tk_c[lt] = L.cnt;
-      atomicAdd(&q.ctr->gcount, groups);
+      s_best[warp] = best;
+      if (groups) atomicAdd(&q.ctr->gcount, groups);
     }
-    __threadfence();
+    __syncthreads();
     const int parts = (int)(pre[qi + 1] - pre[qi]);
-    const int g = (int)(lt >> 5), ng = (parts + 31) >> 5;
-    const int gs = min(32, parts - g * 32);
-    u32 tk = 0;
-    if (lane == 0) tk = atomicAdd(&q.ctr->tk_group[g], 1u);
-    if ((int)__shfl_sync(kFull, tk, 0) != gs - 1) continue;
-    // Last tile of group g: merge the group's lists into list parts + g.
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kTKW; ++w)
+        if (ks_before(s_best[w], best)) best = s_best[w];
+      q.tk_k[lt] = best.k;
+      q.tk_s[lt] = best.s;
+      q.tk_c[lt] = best.v ? 1 : 0;
+      __threadfence();
+      s_last = (int)atomicAdd(&q.ctr->tk_ticket, 1u) == parts - 1;
+      s_rank[0] = -1;
+    }
+    __syncthreads();
+    if (!s_last) continue;
+    // Last tile of the plan: rank the tile maxima (staged in shared memory
+    // through L2, where the other blocks' fenced stores are visible).
     __threadfence();
-    merge_lists(L, K, gs, q.tk_k + (i64)g * 32 * K, q.tk_s + (i64)g * 32 * K, q.tk_c + g * 32,
-                ring);
-    L.store(q.tk_k + (i64)(parts + g) * K, q.tk_s + (i64)(parts + g) * K);
-    if (lane == 0) q.tk_c[parts + g] = L.cnt;
-    __threadfence();
-    if (lane == 0) tk = atomicAdd(&q.ctr->tk_ticket, 1u);
-    if ((int)__shfl_sync(kFull, tk, 0) != ng - 1) continue;
-    // Last group: merge the group lists.
-    __threadfence();
-    merge_lists(L, K, ng, q.tk_k + (i64)parts * K, q.tk_s + (i64)parts * K, q.tk_c + parts,
-                ring);
-    L.store((i64*)q.out->keys, (i64*)q.out->sums);
-    if (lane == 0) {
-      q.out->n = L.cnt;
-      q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
+    KS* sm = reinterpret_cast<KS*>(&s_ring[0][0]);  // parts <= 512 entries
+    for (int p = threadIdx.x; p < parts; p += blockDim.x) {
+      sm[p].k = __ldcg(q.tk_k + p);
+      sm[p].s = __ldcg(q.tk_s + p);
+      sm[p].v = __ldcg(q.tk_c + p) != 0;
+    }
+    __syncthreads();
+    const int K = q.k;
+    for (int p = threadIdx.x; p < parts; p += blockDim.x) {
+      if (!sm[p].v) continue;
+      int rank = 0;
+      for (int x = 0; x < parts; ++x)
+        rank += ks_before(sm[x], sm[p]) || (x < p && sm[x].v && !ks_before(sm[p], sm[x]));
+      if (rank == K - 1) s_rank[0] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int p = s_rank[0];
+      q.ctr->thr_all = p < 0 ? 1 : 0;
+      q.ctr->thr_k = p < 0 ? 0 : sm[p].k;
+      q.ctr->thr_s = p < 0 ? 0 : sm[p].s;
     }
   }
   finish(b.work, kPhTopk);
+}
+
+__global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
+  __shared__ u32 s_ring[kTKW][kTKR];
+  __shared__ i64 s_scr[kTKW][64];
+  __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
+  __shared__ int s_mc[kTKW];
+  __shared__ i64 s_t;
+  __shared__ bool s_last;
+  const i64* pre = b.dyn + 4 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TopList L;
+  L.bind(s_scr[warp]);
+  while (true) {
+    const i64 t = tk_claim(b.work, kPhTopk2, &s_t);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    const int e = q.ctr->mlog2;
+    const int K = q.k;
+    const TableView tv = table_view(q.ht_tag, e, true);
+    const i64 words = ((1LL << e) + 31) >> 5, tw = topk_tile_words(e);
+    const i64 lt = t - pre[qi];
+    const KS thr = {q.ctr->thr_k, q.ctr->thr_s, true};
+    const bool all = q.ctr->thr_all != 0;
+    const u64 cap = (u64)topk_cand_cap(e, K);
+    tk_scan(tv, words, tw, lt, s_ring[warp], [&](const KS* r) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool keep = r[u].v && (all || !ks_before(thr, r[u]));
+        const u32 m = __ballot_sync(kFull, keep);
+        if (!m) continue;
+        u64 at = 0;
+        if (lane == __ffs(m) - 1) at = atomicAdd(&q.ctr->ccount, (u64)__popc(m));
+        at = __shfl_sync(kFull, at, __ffs(m) - 1) + __popc(m & lanemask_lt());
+        if (keep && at < cap) q.cand_k[at] = r[u].k, q.cand_s[at] = r[u].s;
+        if (keep && at >= cap) q_latch(q.ctr, b.st, PQ_ERR_CAPACITY, (i64)at);  // not reached
+      }
+    });
+    __syncthreads();
+    const int parts = (int)(pre[qi + 1] - pre[qi]);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = (int)atomicAdd(&q.ctr->tk_ticket2, 1u) == parts - 1;
+    }
+    __syncthreads();
+    if (!s_last) continue;
+    // Last tile: the top K of the candidates, a quarter per warp, then the
+    // warps' lists merged in shared memory.
+    __threadfence();
+    const i64 c = min((i64)ld_volatile_u64(&q.ctr->ccount), (i64)cap);
+    const i64 per = (c + kTKW - 1) / kTKW;
+    const i64 c0 = min(c, warp * per), c1 = min(c, c0 + per);
+    L.clear();
+    for (i64 j = c0; j < c1; j += 256) {
+      bool v[8];
+      i64 ck[8], cs[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const i64 x = j + u * 32 + lane;
+        v[u] = x < c1;
+        ck[u] = v[u] ? __ldcg(q.cand_k + x) : 0;
+        cs[u] = v[u] ? __ldcg(q.cand_s + x) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
+    }
+    tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
+    if (warp == 0) {
+      L.store((i64*)q.out->keys, (i64*)q.out->sums);
+      if (lane == 0) {
+        q.out->n = L.cnt;
+        q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
+      }
+    }
+  }
+  finish(b.work, kPhTopk2);
 }
 
 #endif  // PQ_DEFINE_PLAN_KERNELS

@@ -401,15 +401,20 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         if (st != PQ_OK) return st;
       }
     } else {
-      const i64 parts = topk_parts(e) + 32;  // tile lists, then group lists
-      char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * d.k * 8) * 2 + al(parts * 4));
+      const i64 parts = topk_parts(e), cap = topk_cand_cap(e, d.k);
+      char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 8) * 2 + al(parts * 4) +
+                                 al(cap * 8) * 2);
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: M table of 2^%d slots", e);
       char* p = mtable_assign(blk, e, d);
       d.tk_k = (i64*)p;
-      p += al(parts * d.k * 8);
+      p += al(parts * 8);
       d.tk_s = (i64*)p;
-      p += al(parts * d.k * 8);
+      p += al(parts * 8);
       d.tk_c = (int*)p;
+      p += al(parts * 4);
+      d.cand_k = (i64*)p;
+      p += al(cap * 8);
+      d.cand_s = (i64*)p;
       PQ_CUDA(ctx, upload_desc(0, 0, r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
       for (int ph : {kPhaseMfill, kPhaseMbuild}) {
         st = launch_phase(ctx, ph, b, true, s);
@@ -418,6 +423,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     }
   }
   st = launch_phase(ctx, kPhaseTopk, b, true, s);
+  if (st == PQ_OK) st = launch_phase(ctx, kPhaseTopk2, b, true, s);
   if (st != PQ_OK) return st;
   ctx->plans++;
   const size_t bytes = sizeof(pq_result);

@@ -3,9 +3,12 @@
 // Order: larger sum first, ties by smaller key (ORDER BY sum DESC, key ASC).
 // A warp keeps its best K <= 64 entries sorted in registers: lane j holds
 // entries j and 32 + j.  Candidates are tested 32 at a time against the
-// current K-th entry, and the few that beat it are inserted one by one with
-// a warp-wide shift, so after the list fills most candidates cost one
-// comparison.
+// current K-th entry, so after the list fills most candidates cost one
+// comparison.  For K <= 32 the candidates that beat it enter together: each
+// list entry and each candidate computes its rank in the merged order (one
+// broadcast per candidate), and the first K land in place through a
+// 32-entry shared-memory scratch per warp.  For larger K they enter one by
+// one with a warp-wide shift.
 #pragma once
 #include "pq_dev.cuh"
 
@@ -18,12 +21,14 @@ __device__ __forceinline__ bool tk_before(i64 ka, i64 sa, i64 kb, i64 sb) {
 struct TopList {
   i64 k0, s0, k1, s1;  // entries lane and 32 + lane
   int cnt;             // warp-uniform number of valid entries
+  i64* scr;            // the warp's scratch: 32 keys, then 32 sums (K <= 32)
 
   __device__ void clear() {
     k0 = k1 = 0;
     s0 = s1 = 0;
     cnt = 0;
   }
+  __device__ void bind(i64* scratch) { scr = scratch; }
 
   // Entry K-1 (the admission threshold), valid when cnt == K.
   __device__ __forceinline__ void last(int K, i64& k, i64& s) const {
@@ -61,6 +66,34 @@ struct TopList {
     cnt = cnt + 1 < K ? cnt + 1 : K;
   }
 
+  // Merge the candidates of the lanes in m (K <= 32).  The merged order is
+  // (sum desc, key asc), then list entries before equal candidates, then
+  // candidates by lane, so every rank is distinct.
+  __device__ __forceinline__ void merge32(int K, u32 m, bool want, i64 ck, i64 cs) {
+    const int lane = threadIdx.x & 31;
+    const bool has = lane < cnt;
+    int re = lane;  // rank of this lane's list entry
+    int rc = 0;     // rank of this lane's candidate
+    for (u32 mm = m; mm; mm &= mm - 1) {
+      const int j = __ffs(mm) - 1;
+      const i64 bk = __shfl_sync(kFull, ck, j), bs = __shfl_sync(kFull, cs, j);
+      const bool cand_first = has && tk_before(bk, bs, k0, s0);
+      re += cand_first;
+      const int before_j = __popc(__ballot_sync(kFull, has && !cand_first));
+      if (lane == j) rc += before_j;
+      if (want && j != lane && (tk_before(bk, bs, ck, cs) || (!tk_before(ck, cs, bk, bs) && j < lane)))
+        ++rc;
+    }
+    __syncwarp();
+    if (has && re < K) scr[re] = k0, scr[32 + re] = s0;
+    if (want && rc < K) scr[rc] = ck, scr[32 + rc] = cs;
+    __syncwarp();
+    const int nc = min(K, cnt + __popc(m));
+    if (lane < nc) k0 = scr[lane], s0 = scr[32 + lane];
+    __syncwarp();
+    cnt = nc;
+  }
+
   // Offer one candidate per lane (valid lanes only); warp-uniform call.
   __device__ __forceinline__ void offer(int K, bool valid, i64 ck, i64 cs) {
     bool want = valid;
@@ -70,6 +103,11 @@ struct TopList {
       want = valid && tk_before(ck, cs, tk, ts);
     }
     u32 m = __ballot_sync(kFull, want);
+    if (!m) return;
+    if (K <= 32) {
+      merge32(K, m, want, ck, cs);
+      return;
+    }
     while (m) {
       const int src = __ffs(m) - 1;
       m &= m - 1;
@@ -103,6 +141,28 @@ __device__ __forceinline__ void tk_block_merge(TopList& L, int K, i64* sk, i64* 
         const i64 k = v ? sk[w * K + j + lane] : 0, s = v ? ss[w * K + j + lane] : 0;
         L.offer(K, v, k, s);
       }
+    }
+  }
+  __syncthreads();
+}
+
+
+// Merge the lists of all nw warps of the block into warp 0's list: every
+// warp stores its list in shared memory (sk, ss: nw * K entries, sc: nw
+// counts), then warp 0 offers all stored entries, 32 per call.
+__device__ __forceinline__ void tk_block_merge_all(TopList& L, int K, i64* sk, i64* ss, int* sc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  L.store(sk + warp * K, ss + warp * K);
+  if (lane == 0) sc[warp] = L.cnt;
+  __syncthreads();
+  if (warp == 0) {
+    L.clear();
+    const int total = nw * K;
+    for (int j = 0; j < total; j += 32) {
+      const int e = j + lane;
+      const int p = e / K;
+      const bool v = e < total && e - p * K < sc[p];
+      L.offer(K, v, v ? sk[e] : 0, v ? ss[e] : 0);
     }
   }
   __syncthreads();

@@ -205,7 +205,7 @@ def test_groupby_capacity_overflow(ctx, stream):
 
 
 @pytest.mark.parametrize("n", [0, 1, 5, 1000, 100_003, 2_000_000])
-@pytest.mark.parametrize("k", [1, 10, 64])
+@pytest.mark.parametrize("k", [1, 10, 32, 33, 64])
 def test_topk_matches_oracle(ctx, stream, n, k):
     rng = np.random.default_rng(n * 3 + k)
     keys = rng.permutation(max(4 * n, 1))[:n].astype(np.int64)
@@ -216,6 +216,21 @@ def test_topk_matches_oracle(ctx, stream, n, k):
         ctx.sync(stream)
     m = int(cnt.item())
     assert m == len(wk)
+    assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
+
+
+@pytest.mark.parametrize("k", [10, 32, 64])
+def test_topk_identical_entries(ctx, stream, k):
+    # Repeated (key, sum) pairs: the list must keep every copy, in order.
+    rng = np.random.default_rng(k)
+    keys = rng.integers(0, 40, size=50_000).astype(np.int64)
+    sums = (keys % 7).astype(np.int64)
+    wk, ws = oracle.topk(keys, sums, k)
+    with torch.cuda.stream(stream):
+        ok, os_, cnt = pq.pq_topk(ctx, dev(keys), dev(sums), k, stream=stream)
+        ctx.sync(stream)
+    m = int(cnt.item())
+    assert m == len(wk) == k
     assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
 
 
