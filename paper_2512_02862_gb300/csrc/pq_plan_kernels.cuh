@@ -1127,9 +1127,11 @@ __device__ __forceinline__ i64 tk_claim(u32* work, int ph, i64* s_t) {
 __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
   __shared__ u32 s_ring[kTKW][kTKR];
   __shared__ KS s_best[kTKW];
+  __shared__ i64 s_scr[kTKW][64];
+  __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
+  __shared__ int s_mc[kTKW];
   __shared__ i64 s_t;
   __shared__ bool s_last;
-  __shared__ int s_rank[1];
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1171,34 +1173,33 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
       q.tk_c[lt] = best.v ? 1 : 0;
       __threadfence();
       s_last = (int)atomicAdd(&q.ctr->tk_ticket, 1u) == parts - 1;
-      s_rank[0] = -1;
     }
     __syncthreads();
     if (!s_last) continue;
-    // Last tile of the plan: rank the tile maxima (staged in shared memory
-    // through L2, where the other blocks' fenced stores are visible).
+    // Last tile of the plan: the K best tile maxima (read through L2, where
+    // the other blocks' fenced stores are visible), a quarter per warp, then
+    // the warps' lists merged in shared memory.
     __threadfence();
-    KS* sm = reinterpret_cast<KS*>(&s_ring[0][0]);  // parts <= 512 entries
-    for (int p = threadIdx.x; p < parts; p += blockDim.x) {
-      sm[p].k = __ldcg(q.tk_k + p);
-      sm[p].s = __ldcg(q.tk_s + p);
-      sm[p].v = __ldcg(q.tk_c + p) != 0;
-    }
-    __syncthreads();
     const int K = q.k;
-    for (int p = threadIdx.x; p < parts; p += blockDim.x) {
-      if (!sm[p].v) continue;
-      int rank = 0;
-      for (int x = 0; x < parts; ++x)
-        rank += ks_before(sm[x], sm[p]) || (x < p && sm[x].v && !ks_before(sm[p], sm[x]));
-      if (rank == K - 1) s_rank[0] = p;
+    TopList L;
+    L.bind(s_scr[warp]);
+    L.clear();
+    const int per = (parts + kTKW - 1) / kTKW;
+    const int p0 = min(parts, warp * per), p1 = min(parts, p0 + per);
+    for (int j = p0; j < p1; j += 32) {
+      const int p = j + lane;
+      const bool v = p < p1 && __ldcg(q.tk_c + p) != 0;
+      L.offer(K, v, v ? __ldcg(q.tk_k + p) : 0, v ? __ldcg(q.tk_s + p) : 0);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int p = s_rank[0];
-      q.ctr->thr_all = p < 0 ? 1 : 0;
-      q.ctr->thr_k = p < 0 ? 0 : sm[p].k;
-      q.ctr->thr_s = p < 0 ? 0 : sm[p].s;
+    tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
+    if (warp == 0) {
+      i64 tk = 0, ts = 0;
+      if (L.cnt == K) L.last(K, tk, ts);
+      if (lane == 0) {
+        q.ctr->thr_all = L.cnt < K ? 1 : 0;
+        q.ctr->thr_k = tk;
+        q.ctr->thr_s = ts;
+      }
     }
   }
   finish(b.work, kPhTopk);
@@ -1254,6 +1255,19 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
     // warps' lists merged in shared memory.
     __threadfence();
     const i64 c = min((i64)ld_volatile_u64(&q.ctr->ccount), (i64)cap);
+    if (c <= 32 && K <= 32) {  // usual case: one warp sorts the candidates
+      if (warp == 0) {
+        bool v = lane < c;
+        i64 ck = v ? __ldcg(q.cand_k + lane) : 0, cs = v ? __ldcg(q.cand_s + lane) : 0;
+        tk_sort32(ck, cs, v);
+        if (lane < K && v) q.out->keys[lane] = ck, q.out->sums[lane] = cs;
+        if (lane == 0) {
+          q.out->n = (int)min((i64)K, c);
+          q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
+        }
+      }
+      continue;
+    }
     const i64 per = (c + kTKW - 1) / kTKW;
     const i64 c0 = min(c, warp * per), c1 = min(c, c0 + per);
     L.clear();

@@ -4,11 +4,12 @@
 // A warp keeps its best K <= 64 entries sorted in registers: lane j holds
 // entries j and 32 + j.  Candidates are tested 32 at a time against the
 // current K-th entry, so after the list fills most candidates cost one
-// comparison.  For K <= 32 the candidates that beat it enter together: each
-// list entry and each candidate computes its rank in the merged order (one
-// broadcast per candidate), and the first K land in place through a
-// 32-entry shared-memory scratch per warp.  For larger K they enter one by
-// one with a warp-wide shift.
+// comparison.  For K <= 32 the candidates that beat it enter together: a few
+// of them by rank (each list entry and candidate counts what precedes it in
+// the merged order, one broadcast per candidate; the first K land in place
+// through a 32-entry shared-memory scratch per warp), more of them by a
+// bitonic sort of the 32 lanes followed by a bitonic merge with the list.
+// For larger K they enter one by one with a warp-wide shift.
 #pragma once
 #include "pq_dev.cuh"
 
@@ -16,6 +17,33 @@ namespace pqk {
 
 __device__ __forceinline__ bool tk_before(i64 ka, i64 sa, i64 kb, i64 sb) {
   return sa > sb || (sa == sb && ka < kb);
+}
+// The same order with validity: valid entries first.
+__device__ __forceinline__ bool tk_before_v(i64 ka, i64 sa, bool va, i64 kb, i64 sb, bool vb) {
+  return va && (!vb || tk_before(ka, sa, kb, sb));
+}
+
+// One step of a bitonic network across the warp: exchange with lane ^ stride
+// and keep the earlier entry at the lower lane of a pair when `first` (the
+// pair's block is ordered earliest first), else the later one.
+__device__ __forceinline__ void tk_cmpx(i64& k, i64& s, bool& v, int stride, bool first) {
+  const int lane = threadIdx.x & 31;
+  const i64 ok = __shfl_xor_sync(kFull, k, stride), os = __shfl_xor_sync(kFull, s, stride);
+  const bool ov = __shfl_xor_sync(kFull, v ? 1 : 0, stride) != 0;
+  const bool lower = (lane & stride) == 0;
+  const bool take = lower == first ? tk_before_v(ok, os, ov, k, s, v)
+                                   : tk_before_v(k, s, v, ok, os, ov);
+  if (take) k = ok, s = os, v = ov;
+}
+
+// Bitonic sort of one entry per lane: lane 0 gets the earliest.
+__device__ __forceinline__ void tk_sort32(i64& k, i64& s, bool& v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1)
+      tk_cmpx(k, s, v, stride, (lane & size) == 0 || size == 32);
 }
 
 struct TopList {
@@ -94,6 +122,23 @@ struct TopList {
     cnt = nc;
   }
 
+  // Merge many candidates (K <= 32): sort the lanes' candidates, pair the
+  // list (earliest first) with the reversed candidates and keep the earlier
+  // of each pair (the 32 earliest of both, as a bitonic sequence), then
+  // finish with a bitonic merge.
+  __device__ __forceinline__ void merge_sorted(int K, u32 m, bool want, i64 ck, i64 cs) {
+    const int lane = threadIdx.x & 31;
+    bool cv = want;
+    tk_sort32(ck, cs, cv);
+    const i64 rk = __shfl_sync(kFull, ck, 31 - lane), rs = __shfl_sync(kFull, cs, 31 - lane);
+    const bool rv = __shfl_sync(kFull, cv ? 1 : 0, 31 - lane) != 0;
+    bool v = lane < cnt;
+    if (tk_before_v(rk, rs, rv, k0, s0, v)) k0 = rk, s0 = rs, v = rv;
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) tk_cmpx(k0, s0, v, stride, true);
+    cnt = min(K, cnt + __popc(m));
+  }
+
   // Offer one candidate per lane (valid lanes only); warp-uniform call.
   __device__ __forceinline__ void offer(int K, bool valid, i64 ck, i64 cs) {
     bool want = valid;
@@ -105,7 +150,10 @@ struct TopList {
     u32 m = __ballot_sync(kFull, want);
     if (!m) return;
     if (K <= 32) {
-      merge32(K, m, want, ck, cs);
+      if (__popc(m) <= 3)
+        merge32(K, m, want, ck, cs);
+      else
+        merge_sorted(K, m, want, ck, cs);
       return;
     }
     while (m) {
