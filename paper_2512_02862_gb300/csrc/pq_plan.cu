@@ -59,6 +59,9 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
   d.n_d = r.n_d;
   d.n_m = r.n_m;
   d.n_f = r.n_f;
+  d.d_tile = scan_tile(r.n_d, 512, kTD, resident_warps(ctx, 0));
+  d.m_tile = scan_tile(r.n_m, 128, kTM, resident_warps(ctx, 3));
+  d.f_tile = scan_tile(r.n_f, 128, kTF, resident_warps(ctx, 8));
   r.e_d = cap_log2(r.n_d, d.lf1024);
   r.e_m = cap_log2(r.n_m, d.lf1024);
   r.parts = topk_parts(r.e_m);
@@ -444,9 +447,9 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     any_build = any_build || r.builds;
     vec = vec && d.vec;
     descs[i] = d;
-    tD[i + 1] = tD[i] + (r.builds ? (r.n_d + kTD - 1) / kTD : 0);
-    tM[i + 1] = tM[i] + (r.n_m + kTM - 1) / kTM;
-    tF[i + 1] = tF[i] + (r.n_f + kTF - 1) / kTF;
+    tD[i + 1] = tD[i] + (r.builds ? (r.n_d + r.dev.d_tile - 1) / r.dev.d_tile : 0);
+    tM[i + 1] = tM[i] + (r.n_m + r.dev.m_tile - 1) / r.dev.m_tile;
+    tF[i + 1] = tF[i] + (r.n_f + r.dev.f_tile - 1) / r.dev.f_tile;
   }
   lk.unlock();
 

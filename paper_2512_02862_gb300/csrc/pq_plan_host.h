@@ -26,6 +26,18 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
 
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Rows per warp tile of a scan over n rows: the largest unit * 2^j, up to
+// max_rows, that still gives each of `warps` resident warps two tiles.
+inline int scan_tile(i64 n, int unit, int max_rows, i64 warps) {
+  int t = max_rows;
+  while (t > unit && (n + t - 1) / t < 2 * warps) t >>= 1;
+  return t;
+}
+// Resident warps of plan kernel `occ_index` (see plan_kernels_init).
+inline i64 resident_warps(const pq_ctx* ctx, int occ_index) {
+  return (i64)ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index])) * 8;
+}
+
 // A D-set block of 2^e slots: a 256-byte header (the log2 of the slot count
 // in use, then the key-range bitmap's base and bit count) followed by a key
 // set laid out by pqk::table_layout.

@@ -32,9 +32,12 @@
 
 namespace pqk {
 
-constexpr int kTD = 1024;    // D rows per warp tile
-constexpr int kTM = 1024;    // M rows per warp tile
-constexpr int kTF = 2048;    // F rows per warp tile
+// Largest rows per warp tile of the D, M and F scans; a plan uses smaller
+// tiles (down to 512, 128 and 128 rows) when its table would otherwise leave
+// resident warps without a tile.
+constexpr int kTD = 1024;
+constexpr int kTM = 1024;
+constexpr int kTF = 2048;
 constexpr int kTB = 128;     // list entries inserted per warp tile (4 per lane)
 constexpr int kQ = 256;      // entries of a warp's shared-memory ring
 
@@ -113,12 +116,12 @@ __host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bi
 }
 
 // Top-k tiles of an M table of 2^e slots: ranges of its first-hit bitmap,
-// at least 1024 words each and at most 512 tiles per table (so that the
-// final merge reads at most 512 partial lists).
+// at least 32 words each and at most 128 tiles per table (so that the
+// threshold is taken over at most 128 tile maxima).
 __host__ __device__ __forceinline__ i64 topk_tile_words(int e) {
   const i64 words = ((1LL << e) + 31) >> 5;
-  i64 tw = 1024;
-  while (words / tw > 512) tw <<= 1;
+  i64 tw = 32;
+  while (words / tw > 128) tw <<= 1;
   return tw;
 }
 __host__ __device__ __forceinline__ i64 topk_parts(int e) {
@@ -206,6 +209,8 @@ struct PlanDev {
   const signed char* f_disc;
   const int* f_date;
   i64 n_f;
+  int d_tile, m_tile, f_tile;  // rows per warp tile of the D, M and F scans
+  int tile_pad;
   Pred pd, pm, pf;
   int k, lf1024;
   int build_dset;   // this plan fills its D-set in this batch
@@ -234,7 +239,7 @@ struct Ovr {
   i64 n;
   i64 tiles;
   int table;
-  int pad;
+  int tile;  // rows per warp tile
 };
 
 struct Batch {
@@ -511,9 +516,10 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
     const int* d_key = ov ? (const int*)b.ov.p[0] : q.d_key;
     const signed char* d_seg = ov ? (const signed char*)b.ov.p[1] : q.d_seg;
     const i64 n = ov ? b.ov.n : q.n_d;
-    const i64 base = (t - (ov ? 0 : b.tD[qi])) * kTD;
+    const int tile = ov ? b.ov.tile : q.d_tile;
+    const i64 base = (t - (ov ? 0 : b.tD[qi])) * tile;
     u64 lnmin = 0, lumax = 0;  // this lane's range of appended keys
-    for (int it = 0; it < kTD / 512; ++it) {
+    for (int it = 0; it < tile / 512; ++it) {
       if (base + it * 512 >= n) break;
       const i64 e0 = base + it * 512 + lane * 16;
       u32 bits = 0;
@@ -637,8 +643,9 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     u64 lnmin = 0, lumax = 0;  // this lane's range of member keys
     const Pred32 pm = to32(q.pm);
     const i64 n = ov ? b.ov.n : q.n_m;
-    const i64 base = (t - (ov ? 0 : b.tM[qi])) * kTM;
-    const i64 lim = min(n - base, (i64)kTM);
+    const int tile = ov ? b.ov.tile : q.m_tile;
+    const i64 base = (t - (ov ? 0 : b.tM[qi])) * tile;
+    const i64 lim = min(n - base, (i64)tile);
     const int iters = (int)((lim + 127) / 128);
     const i64 r0 = lane * 4;
     u32 ch = 0, ct = 0, bh = 0, bt = 0;
@@ -958,7 +965,8 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     const i64* f_mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
     const int* f_date = ov ? (const int*)b.ov.p[3] : q.f_date;
     const i64 n = ov ? b.ov.n : q.n_f;
-    const i64 base = (t - (ov ? 0 : b.tF[qi])) * kTF;
+    const int tile = ov ? b.ov.tile : q.f_tile;
+    const i64 base = (t - (ov ? 0 : b.tF[qi])) * tile;
     if (qi != pc.qi || !carry) {
       if (pc.qi >= 0) drain();
       carry = n < (1LL << 32);
@@ -976,7 +984,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     const u32* bm = pc.t.keybm;
     const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
     const Pred32 pf = to32(q.pf);
-    const i64 lim = min(n - base, (i64)kTF);
+    const i64 lim = min(n - base, (i64)tile);
     const int iters = (int)((lim + 127) / 128);
     auto append_hits = [&](u32 hits, int it) {
       if (__any_sync(kFull, hits)) {

@@ -270,9 +270,9 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   char* dset_blk = (char*)scr.get(dset_block_bytes(6));
   if (!dset_blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set");
   dset_block_assign(dset_blk, 6, d);
-  PQ_CUDA(ctx, upload_desc(r.resident[0] ? (r.n_d + kTD - 1) / kTD : 0,
-                           r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
-                           r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+  PQ_CUDA(ctx, upload_desc(r.resident[0] ? (r.n_d + d.d_tile - 1) / d.d_tile : 0,
+                           r.resident[1] ? (r.n_m + d.m_tile - 1) / d.m_tile : 0,
+                           r.resident[2] ? (r.n_f + d.f_tile - 1) / d.f_tile : 0));
   PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
   Batch b = make_batch(ctx, ws, 1, L);
 
@@ -362,7 +362,10 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         Batch bc = b;
         bc.ov.table = t + 1;
         bc.ov.n = ch.rows;
-        const int tile = t == 0 ? kTD : t == 1 ? kTM : kTF;
+        const int tile = t == 0   ? scan_tile(ch.rows, 512, kTD, resident_warps(ctx, 0))
+                         : t == 1 ? scan_tile(ch.rows, 128, kTM, resident_warps(ctx, 3))
+                                  : scan_tile(ch.rows, 128, kTF, resident_warps(ctx, 8));
+        bc.ov.tile = tile;
         bc.ov.tiles = (ch.rows + tile - 1) / tile;
         for (int j = 0; j < T.ncols; ++j) bc.ov.p[j] = src + col_offset(T, ch.rows, j);
         st = launch_phase(ctx, phase_of[t], bc, true, s);
@@ -390,8 +393,8 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       char* blk = (char*)scr.get(dset_block_bytes(e));
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: D-set of 2^%d slots", e);
       dset_block_assign(blk, e, d);
-      PQ_CUDA(ctx, upload_desc(0, r.resident[1] ? (r.n_m + kTM - 1) / kTM : 0,
-                               r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+      PQ_CUDA(ctx, upload_desc(0, r.resident[1] ? (r.n_m + d.m_tile - 1) / d.m_tile : 0,
+                               r.resident[2] ? (r.n_f + d.f_tile - 1) / d.f_tile : 0));
       // The dscan kernel sized the fill/build phases; it wrote the header
       // (log2, bitmap base and bits) into the placeholder, copied here to the
       // real block.
@@ -415,7 +418,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       d.cand_k = (i64*)p;
       p += al(cap * 8);
       d.cand_s = (i64*)p;
-      PQ_CUDA(ctx, upload_desc(0, 0, r.resident[2] ? (r.n_f + kTF - 1) / kTF : 0));
+      PQ_CUDA(ctx, upload_desc(0, 0, r.resident[2] ? (r.n_f + d.f_tile - 1) / d.f_tile : 0));
       for (int ph : {kPhaseMfill, kPhaseMbuild}) {
         st = launch_phase(ctx, ph, b, true, s);
         if (st != PQ_OK) return st;
