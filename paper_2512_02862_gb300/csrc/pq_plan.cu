@@ -185,37 +185,73 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
 
 // Persistent grid of a plan kernel: the tuned blocks per SM, capped by what
 // fits on an SM at once (a block that only starts after others exit finds
-// no work left).
-static int plan_grid(pq_ctx* ctx, int occ_index) {
-  return ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
+// no work left) and by the phase's largest possible tile count.
+static thread_local i64 t_tiles_max = -1;
+static int plan_grid(pq_ctx* ctx, int occ_index, int tiles_per_block = 8) {
+  const i64 g = (i64)ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
+  if (t_tiles_max < 0) return (int)g;
+  return (int)std::max<i64>(1, std::min(g, (t_tiles_max + tiles_per_block - 1) / tiles_per_block));
 }
 
-pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s) {
+// Launch a plan kernel with programmatic stream serialization, so that its
+// launch overlaps the end of the previous kernel on the stream (the kernel
+// itself waits for that kernel's completion in chain_begin).  Not while the
+// stream is being captured: in a replayed graph the early blocks of the next
+// kernel were measured to slow the chain down.
+static thread_local bool t_chain = true;
+template <typename... P, typename... A>
+static cudaError_t launch_chained(void (*k)(P...), int grid, int block, cudaStream_t s,
+                                  A... args) {
+  if (!t_chain) {
+    k<<<grid, block, 0, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s,
+                       i64 tiles_max) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  t_chain = cap == cudaStreamCaptureStatusNone;
+  t_tiles_max = tiles_max;
   cudaEvent_t stop;
   prof_begin(ctx, kPhaseName[phase], s, &stop);
+  cudaError_t e = cudaSuccess;
   switch (phase) {
     case kPhaseD:
-      if (vec) k_plan_dscan<true><<<plan_grid(ctx, 0), 256, 0, s>>>(b);
-      else k_plan_dscan<false><<<plan_grid(ctx, 0), 256, 0, s>>>(b);
+      e = vec ? launch_chained(k_plan_dscan<true>, plan_grid(ctx, 0), 256, s, b)
+              : launch_chained(k_plan_dscan<false>, plan_grid(ctx, 0), 256, s, b);
       break;
-    case kPhaseDfill: k_plan_fill<<<plan_grid(ctx, 1), 256, 0, s>>>(b, 0); break;
-    case kPhaseDbuild: k_plan_dbuild<<<plan_grid(ctx, 2), 256, 0, s>>>(b); break;
+    case kPhaseDfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 1, 1), 256, s, b, 0); break;
+    case kPhaseDbuild: e = launch_chained(k_plan_dbuild, plan_grid(ctx, 2), 256, s, b); break;
     case kPhaseM:
-      if (vec) k_plan_mscan<true><<<plan_grid(ctx, 3), 256, 0, s>>>(b);
-      else k_plan_mscan<false><<<plan_grid(ctx, 9), 256, 0, s>>>(b);
+      e = vec ? launch_chained(k_plan_mscan<true>, plan_grid(ctx, 3), 256, s, b)
+              : launch_chained(k_plan_mscan<false>, plan_grid(ctx, 9), 256, s, b);
       break;
-    case kPhaseMfill: k_plan_fill<<<plan_grid(ctx, 4), 256, 0, s>>>(b, 1); break;
-    case kPhaseMbuild: k_plan_mbuild<<<plan_grid(ctx, 5), 256, 0, s>>>(b); break;
+    case kPhaseMfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 4, 1), 256, s, b, 1); break;
+    case kPhaseMbuild: e = launch_chained(k_plan_mbuild, plan_grid(ctx, 5), 256, s, b); break;
     case kPhaseF:
-      if (vec)
-        k_plan_fprobe<true><<<plan_grid(ctx, 8), 256, 0, s>>>(b);
-      else
-        k_plan_fprobe<false><<<plan_grid(ctx, 6), 256, 0, s>>>(b);
+      e = vec ? launch_chained(k_plan_fprobe<true>, plan_grid(ctx, 8), 256, s, b)
+              : launch_chained(k_plan_fprobe<false>, plan_grid(ctx, 6), 256, s, b);
       break;
-    case kPhaseTopk: k_plan_topk<<<plan_grid(ctx, 7), kTKW * 32, 0, s>>>(b); break;
-    case kPhaseTopk2: k_plan_topk2<<<plan_grid(ctx, 10), kTKW * 32, 0, s>>>(b); break;
+    case kPhaseTopk: e = launch_chained(k_plan_topk, plan_grid(ctx, 7, 1), kTKW * 32, s, b); break;
+    case kPhaseTopk2:
+      e = launch_chained(k_plan_topk2, plan_grid(ctx, 10, 1), kTKW * 32, s, b);
+      break;
   }
   prof_end(stop, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan kernel launch");
   PQ_LAUNCHED(ctx);
   return PQ_OK;
 }
@@ -423,6 +459,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
                 total, ctx->arena.largest_free());
   }
   bool any_build = false, vec = true;
+  i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
   std::vector<char> host(L.upload_bytes());
   PlanDev* descs = (PlanDev*)host.data();
   i64* tD = (i64*)(host.data() + (L.tD - L.desc));
@@ -450,8 +487,19 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     tD[i + 1] = tD[i] + (r.builds ? (r.n_d + r.dev.d_tile - 1) / r.dev.d_tile : 0);
     tM[i + 1] = tM[i] + (r.n_m + r.dev.m_tile - 1) / r.dev.m_tile;
     tF[i + 1] = tF[i] + (r.n_f + r.dev.f_tile - 1) / r.dev.f_tile;
+    if (r.builds) {
+      tmax[kPhaseDfill] += fill_tiles(r.e_d, false, 32ULL << r.e_d);
+      tmax[kPhaseDbuild] += (r.n_d + kTB - 1) / kTB;
+    }
+    tmax[kPhaseMfill] += fill_tiles(r.e_m, true, 32ULL << r.e_m);
+    tmax[kPhaseMbuild] += (r.n_m + kTB - 1) / kTB;
+    tmax[kPhaseTopk] += topk_parts(r.e_m);
   }
   lk.unlock();
+  tmax[kPhaseD] = tD[n];
+  tmax[kPhaseM] = tM[n];
+  tmax[kPhaseF] = tF[n];
+  tmax[kPhaseTopk2] = tmax[kPhaseTopk];
 
   for (auto ev : waits) PQ_CUDA(ctx, cudaStreamWaitEvent(s, ev, 0));
   PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
@@ -460,7 +508,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   auto chain = [&]() -> pq_status {
     PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
     for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
-      pq_status st = launch_phase(ctx, ph, b, vec, s);
+      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph]);
       if (st != PQ_OK) return st;
     }
     return PQ_OK;

@@ -73,10 +73,11 @@ BatchLayout batch_layout(int nq);
 // The batch argument of every plan kernel for a workspace at `ws`.
 pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
 
-// Launch the chain of plan kernels for the whole batch (phases D, M, F and
-// top-k).  any_build: at least one plan fills a D-set.  vec: every column
-// pointer 16-byte aligned.
-pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s);
+// Launch one phase of the plan chain for the whole batch.  vec: every column
+// pointer 16-byte aligned.  tiles_max: the phase's largest possible tile
+// count (-1 unknown), which caps the grid.
+pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s,
+                       i64 tiles_max = -1);
 
 enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseF,
        kPhaseTopk, kPhaseTopk2 };

@@ -273,21 +273,36 @@ __device__ __forceinline__ int find_q(const i64* pre, int nq, i64 t) {
   return lo;
 }
 
-// Claim the next tile of phase `ph` for the whole block.
-__device__ __forceinline__ i64 claim(u32* work, int ph) {
-  __shared__ i64 s_t;
-  __syncthreads();
-  if (threadIdx.x == 0) s_t = atomicAdd(&work[ph], 1u);
-  __syncthreads();
-  return s_t;
-}
-
-// Claim the next tile of phase `ph` for one warp (no block barrier).
-__device__ __forceinline__ i64 warp_claim(u32* work, int ph) {
-  u32 t = 0;
-  if ((threadIdx.x & 31) == 0) t = atomicAdd(&work[ph], 1u);
-  return (i64)__shfl_sync(kFull, t, 0);
-}
+// Tile claims of the persistent plan kernels.  A warp's (block's) first
+// tile is its own index in the grid; later ones come from the phase's ticket
+// counter, offset by the number of warps (blocks), so a phase with fewer
+// tiles than warps takes no ticket at all.
+struct WarpClaim {
+  bool first = true;
+  __device__ __forceinline__ i64 next(u32* work, int ph) {
+    const i64 nw = (i64)gridDim.x * (blockDim.x >> 5);
+    if (first) {
+      first = false;
+      return (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    }
+    u32 t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(&work[ph], 1u);
+    return (i64)__shfl_sync(kFull, t, 0) + nw;
+  }
+};
+struct BlockClaim {
+  bool first = true;
+  __device__ __forceinline__ i64 next(u32* work, int ph, i64* s_t) {
+    if (first) {
+      first = false;
+      return blockIdx.x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *s_t = atomicAdd(&work[ph], 1u);
+    __syncthreads();
+    return *s_t + gridDim.x;
+  }
+};
 
 // Returns true in the block that finishes last; that block also resets the
 // phase's tickets so that the next launch starts from zero.
@@ -351,6 +366,15 @@ __device__ void block_prefix(i64* pre, int nq, F f) {
 __device__ __forceinline__ void q_latch(QCtr* c, DevStatus* st, int code, i64 detail) {
   atomicCAS(&c->status, 0, code);
   latch(st, code, detail);
+}
+
+// Programmatic dependent launch: every plan kernel is launched so that it may
+// start while the previous kernel of the chain finishes.  It first waits
+// until that kernel has completed and its writes are visible, then lets the
+// next kernel of the chain launch early in turn.
+__device__ __forceinline__ void chain_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Geometry of a bucketized table of 2^e slots: bucket mask and the shift that
@@ -504,12 +528,14 @@ __device__ __forceinline__ u32 ring_append(u32 bits, u32 tail, W write) {
 // 16l .. 16l+15 with one 128-bit load; keys only where seg passes.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
+  chain_begin();
   const bool ov = b.ov.table == 1;
   const i64 total = ov ? b.ov.tiles : b.tD[b.nq];
   const int lane = threadIdx.x & 31;
   const u64 strm = policy_stream();
+  WarpClaim wc;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhDscan);
+    const i64 t = wc.next(b.work, kPhDscan);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tD, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -570,11 +596,14 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
 // Clear the tags and the key-range bitmap of the D-set (which = 0) or the M
 // table (which = 1); keys and sums are written by the inserting thread.
 __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
+  chain_begin();
   const i64* pre = b.dyn + (which == 0 ? 0 : 2) * (b.nq + 1);
   const int ph = which == 0 ? kPhDfill : kPhMfill;
   const i64 total = pre[b.nq];
+  __shared__ i64 s_t;
+  BlockClaim bc;
   while (true) {
-    const i64 t = claim(b.work, ph);
+    const i64 t = bc.next(b.work, ph, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -592,10 +621,12 @@ __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
 // ----------------------------------------------------------------- dbuild ----
 // Warp tiles of 128 D-list entries (insert_x4), claimed per warp.
 __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
+  chain_begin();
   const i64* pre = b.dyn + (b.nq + 1);
   const i64 total = pre[b.nq];
+  WarpClaim wc;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhDbuild);
+    const i64 t = wc.next(b.work, kPhDbuild);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -621,6 +652,7 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
 // candidate and the D-set table decides.
 template <bool VEC>
 __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
+  chain_begin();
   __shared__ u32 s_c[8][kQ];
   __shared__ i64 s_rb[8][kQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -629,8 +661,9 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 2;
   const i64 total = ov ? b.ov.tiles : b.tM[b.nq];
+  WarpClaim wc;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhMscan);
+    const i64 t = wc.next(b.work, kPhMscan);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tM, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -747,11 +780,13 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
 // Warp tiles of 128 M-list entries (insert_x4), claimed per warp.  A key equal
 // to the reserved INT64_MIN is reported and skipped.
 __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
+  chain_begin();
   const i64* pre = b.dyn + 3 * (b.nq + 1);
   const i64 total = pre[b.nq];
   const int lane = threadIdx.x & 31;
+  WarpClaim wc;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhMbuild);
+    const i64 t = wc.next(b.work, kPhMbuild);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -924,6 +959,7 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
 // aggregate in the block's shared table, flushed once at the end.
 template <bool VEC>
 __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
+  chain_begin();
   __shared__ u32 s_hr[8][kH];
   __shared__ u64 s_akey[kAgg];
   __shared__ i64 s_asum[kAgg];
@@ -957,8 +993,9 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     if (ht - hh) probe_hits(ht - hh);
     hh = ht = 0;
   };
+  WarpClaim wc;
   while (true) {
-    const i64 t = warp_claim(b.work, kPhFprobe);
+    const i64 t = wc.next(b.work, kPhFprobe);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tF, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -1124,15 +1161,8 @@ __device__ __forceinline__ u64 tk_scan(const TableView& tv, i64 words, i64 tw, i
   return groups;
 }
 
-// Block-wide claim of the next top-k tile.
-__device__ __forceinline__ i64 tk_claim(u32* work, int ph, i64* s_t) {
-  __syncthreads();
-  if (threadIdx.x == 0) *s_t = atomicAdd(&work[ph], 1u);
-  __syncthreads();
-  return *s_t;
-}
-
 __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
+  chain_begin();
   __shared__ u32 s_ring[kTKW][kTKR];
   __shared__ KS s_best[kTKW];
   __shared__ i64 s_scr[kTKW][64];
@@ -1143,8 +1173,9 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  BlockClaim bc;
   while (true) {
-    const i64 t = tk_claim(b.work, kPhTopk, &s_t);
+    const i64 t = bc.next(b.work, kPhTopk, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -1214,6 +1245,7 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
 }
 
 __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
+  chain_begin();
   __shared__ u32 s_ring[kTKW][kTKR];
   __shared__ i64 s_scr[kTKW][64];
   __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
@@ -1225,8 +1257,9 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TopList L;
   L.bind(s_scr[warp]);
+  BlockClaim bc;
   while (true) {
-    const i64 t = tk_claim(b.work, kPhTopk2, &s_t);
+    const i64 t = bc.next(b.work, kPhTopk2, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
