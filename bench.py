@@ -738,7 +738,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream", "ops"])
     ap.add_argument("--workload", default="x100", choices=["small", "x100", "x2000", "skew"])
-    ap.add_argument("--arena-gb", type=int, default=6)
+    ap.add_argument("--arena-gb", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-f-rows", type=int, default=20_000_000)
     ap.add_argument("--queries", type=int, default=2000)
