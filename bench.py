@@ -315,7 +315,8 @@ def run_ours(args):
     fprobe_ms, fprobe_n = ctx.profile("plan_fprobe")
     per_stage = {}
     for nm in ("plan_dscan", "plan_dfill", "plan_dbuild", "plan_mscan", "plan_mfill",
-               "plan_mbuild", "plan_fprobe", "plan_topk", "plan_topk2"):
+               "plan_mbuild", "plan_mrank", "plan_mdup", "plan_fprobe", "plan_topk",
+               "plan_topk2"):
         try:
             ms, n = ctx.profile(nm)
             per_stage[nm] = round(ms / max(n, 1), 5)

@@ -136,7 +136,7 @@ BatchLayout batch_layout(int nq) {
   L.tF = o;
   o += 8 * (nq + 1);
   L.dyn = al(o);
-  o = L.dyn + 8 * 5 * (nq + 1);
+  o = L.dyn + 8 * 7 * (nq + 1);
   L.work = al(o);
   o = L.work + 256;
   L.ctr = o;
@@ -162,18 +162,19 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
   return b;
 }
 
-static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill",  "plan_dbuild",
-                                   "plan_mscan",  "plan_mfill",  "plan_mbuild",
-                                   "plan_fprobe", "plan_topk",   "plan_topk2"};
+static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill", "plan_dbuild", "plan_mscan",
+                                   "plan_mfill",  "plan_mbuild", "plan_mrank", "plan_mdup",
+                                   "plan_fprobe", "plan_topk",  "plan_topk2"};
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[11] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
+  const void* fn[13] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
                         (const void*)k_plan_dbuild,       (const void*)k_plan_mscan<true>,
                         (const void*)k_plan_fill,         (const void*)k_plan_mbuild,
                         (const void*)k_plan_fprobe<false>, (const void*)k_plan_topk,
                         (const void*)k_plan_fprobe<true>,  (const void*)k_plan_mscan<false>,
-                        (const void*)k_plan_topk2};
-  for (int i = 0; i < 11; ++i) {
+                        (const void*)k_plan_topk2,        (const void*)k_plan_mrank,
+                        (const void*)k_plan_mdup};
+  for (int i = 0; i < 13; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -241,6 +242,8 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
       break;
     case kPhaseMfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 4, 1), 256, s, b, 1); break;
     case kPhaseMbuild: e = launch_chained(k_plan_mbuild, plan_grid(ctx, 5), 256, s, b); break;
+    case kPhaseMrank: e = launch_chained(k_plan_mrank, plan_grid(ctx, 11), 256, s, b); break;
+    case kPhaseMdup: e = launch_chained(k_plan_mdup, plan_grid(ctx, 12), 256, s, b); break;
     case kPhaseF:
       e = vec ? launch_chained(k_plan_fprobe<true>, plan_grid(ctx, 8), 256, s, b)
               : launch_chained(k_plan_fprobe<false>, plan_grid(ctx, 6), 256, s, b);
@@ -493,6 +496,8 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     }
     tmax[kPhaseMfill] += fill_tiles(r.e_m, true, 32ULL << r.e_m);
     tmax[kPhaseMbuild] += (r.n_m + kTB - 1) / kTB;
+    tmax[kPhaseMrank] += ((32LL << r.e_m) / 512 + kRankTile - 1) / kRankTile;
+    tmax[kPhaseMdup] += (r.n_m + kTB - 1) / kTB;
     tmax[kPhaseTopk] += topk_parts(r.e_m);
   }
   lk.unlock();

@@ -79,7 +79,7 @@ pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
 pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s,
                        i64 tiles_max = -1);
 
-enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseF,
-       kPhaseTopk, kPhaseTopk2 };
+enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseMrank,
+       kPhaseMdup, kPhaseF, kPhaseTopk, kPhaseTopk2 };
 
 }  // namespace pqh

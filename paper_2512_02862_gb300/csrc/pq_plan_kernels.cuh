@@ -43,7 +43,7 @@ constexpr int kQ = 256;      // entries of a warp's shared-memory ring
 
 struct QCtr {
   u64 dcount, mcount, gcount;
-  int dup;
+  int dup;          // dense M dictionary: the M list repeats keys
   u32 tk_ticket;
   int status;
   int mlog2;
@@ -60,6 +60,10 @@ struct QCtr {
   int thr_all;
   u32 tk_ticket2;
   u64 ccount;
+  // Regions the D and M fills clear: byte offset from the table's start and
+  // 16-byte units (set by the scans' last blocks).
+  u64 d_fill_off, d_fill_units, m_fill_off, m_fill_units;
+  u64 m_distinct;  // dense M dictionary: distinct keys (the rank pass)
 };
 
 // Key-range semi-join filter.  When the keys of a filtered build side span
@@ -135,6 +139,47 @@ __host__ __device__ __forceinline__ i64 topk_parts(int e) {
 __host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
   const i64 slots = 1LL << e, tile_slots = topk_tile_words(e) * 32;
   return slots < (i64)K * tile_slots ? slots : (i64)K * tile_slots;
+}
+
+// Dense M dictionary.  When the M' keys have a key-range bitmap, the M side
+// is not a hash table: a group's slot is the rank of its key among the
+// distinct M' keys (the set bits before its bit), read from a two-level
+// directory (set bits before each tile of kRankTile 512-bit blocks, and
+// before each block within its tile) plus the block's words.  Slots follow
+// key order.  Layout in the M table's region, for c entries in the M list
+// and `bits` bitmap bits (byte offsets; the fill clears everything before
+// `tdir`):
+//   hit   first-hit bit per slot              c/8 B
+//   sums  i64 sum per slot                    8c B
+//   cnt   u32 copies of the key per slot      4c B (written only when the
+//         M list repeats keys)
+//   bm    the key-range bitmap                64 B per 512-bit block
+//   tdir  u32 set bits before each tile, then the total
+//   bdir  u16 set bits before each block within its tile
+constexpr int kRankTile = 64;   // bitmap blocks per tile (at most 32768 bits)
+struct DenseLayout {
+  u64 hit, sums, cnt, bm, tdir, bdir, total;
+};
+__host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
+  auto a = [](u64 x) { return (x + 255) & ~255ULL; };
+  const u64 blocks = (bits + 511) / 512, tiles = (blocks + kRankTile - 1) / kRankTile;
+  DenseLayout L;
+  L.hit = 0;
+  L.sums = a(((u64)c + 7) / 8);
+  L.cnt = L.sums + a(8 * (u64)c);
+  L.bm = L.cnt + a(4 * (u64)c);
+  L.tdir = L.bm + a(64 * blocks);
+  L.bdir = L.tdir + a(4 * (tiles + 1));
+  L.total = L.bdir + a(2 * blocks);
+  return L;
+}
+
+// Top-k tiling over a first-hit bitmap of `words` words (the hash table's
+// slots, or the dense dictionary's slots).
+__host__ __device__ __forceinline__ i64 topk_tile_words_w(i64 words) {
+  i64 tw = 32;
+  while (words / tw > 128) tw <<= 1;
+  return tw;
 }
 
 __device__ __forceinline__ bool bit_test(const u32* bm, u64 idx, u64 keep) {
@@ -257,7 +302,7 @@ struct Batch {
 };
 
 enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk,
-       kPhTopk2 };
+       kPhTopk2, kPhMrank, kPhMdup };
 
 // The kernels below are defined in exactly one translation unit (pq_plan.cu),
 // which defines PQ_DEFINE_PLAN_KERNELS before including this header.
@@ -311,16 +356,43 @@ __device__ __forceinline__ bool finish(u32* work, int ph) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    const u32 t = atomicAdd(&work[8 + ph], 1u);
+    const u32 t = atomicAdd(&work[16 + ph], 1u);
     s_last = (t == gridDim.x - 1);
     if (s_last) {
       work[ph] = 0;
-      work[8 + ph] = 0;
+      work[16 + ph] = 0;
     }
   }
   __syncthreads();
   if (s_last) __threadfence();
   return s_last;
+}
+
+// Block-wide exclusive sum of one value per thread (every thread calls; the
+// caller synchronises before calling it again).
+__device__ __forceinline__ u32 block_exclusive_sum(u32 v) {
+  __shared__ u32 s_w[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u32 x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 c = lane < nw ? s_w[lane] : 0u;
+    u32 y = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 z = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < nw) s_w[lane] = y - c;
+  }
+  __syncthreads();
+  return s_w[warp] + x - v;
 }
 
 // Block-wide exclusive scan over nq values produced by `f(q)`; writes
@@ -583,7 +655,12 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
       u64* hdr = reinterpret_cast<u64*>(q.dset_log2);
       hdr[1] = rb.umin;
       hdr[2] = rb.bits;
-      return fill_tiles(e, false, rb.bits);
+      // With a bitmap the D-set is the bitmap alone (membership is all that
+      // the M scan asks); otherwise tags and bucket counters.
+      const TableLayout L = table_layout(e, false);
+      q.ctr->d_fill_off = rb.bits ? L.keybm : 0;
+      q.ctr->d_fill_units = rb.bits ? (rb.bits + 127) / 128 : L.keybm / 16;
+      return ((i64)q.ctr->d_fill_units + kTCU - 1) / kTCU;
     });
     block_prefix(b.dyn + (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
@@ -593,8 +670,9 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
 }
 
 // ------------------------------------------------------------------- fill ----
-// Clear the tags and the key-range bitmap of the D-set (which = 0) or the M
-// table (which = 1); keys and sums are written by the inserting thread.
+// Clear the region of the D-set (which = 0) or the M side (which = 1) that
+// the scan's last block recorded: tags and counters of a hash table, or the
+// bitmap (and for M the dense arrays); records are written by the builds.
 __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
   chain_begin();
   const i64* pre = b.dyn + (which == 0 ? 0 : 2) * (b.nq + 1);
@@ -607,10 +685,10 @@ __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int e = which == 0 ? *q.dset_log2 : q.ctr->mlog2;
-    const u64 bits = which == 0 ? reinterpret_cast<const u64*>(q.dset_log2)[2] : q.ctr->m_bits;
-    int4* base = reinterpret_cast<int4*>(which == 0 ? q.dset_tag : q.ht_tag);
-    const i64 units = clear_units(e, which == 1, bits);
+    const u64 off = which == 0 ? q.ctr->d_fill_off : q.ctr->m_fill_off;
+    const i64 units = (i64)(which == 0 ? q.ctr->d_fill_units : q.ctr->m_fill_units);
+    int4* base = reinterpret_cast<int4*>(
+        reinterpret_cast<char*>(which == 0 ? (void*)q.dset_tag : (void*)q.ht_tag) + off);
     const i64 u0 = (t - pre[qi]) * kTCU;
     for (i64 u = u0 + threadIdx.x; u < u0 + kTCU && u < units; u += blockDim.x)
       base[u] = make_int4(0, 0, 0, 0);
@@ -619,7 +697,8 @@ __global__ void __launch_bounds__(256) k_plan_fill(Batch b, int which) {
 }
 
 // ----------------------------------------------------------------- dbuild ----
-// Warp tiles of 128 D-list entries (insert_x4), claimed per warp.
+// Warp tiles of 128 D-list entries, claimed per warp: bitmap bits when the
+// D-set is a bitmap, else table inserts (insert_x4).
 __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
   chain_begin();
   const i64* pre = b.dyn + (b.nq + 1);
@@ -633,10 +712,16 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
     const TableView tv = table_view(q.dset_tag, *q.dset_log2, false);
     const u64* hdr = reinterpret_cast<const u64*>(q.dset_log2);
     const u64 umin = hdr[1], bits = hdr[2];
-    insert_x4(tv, q.dlist, (t - pre[qi]) * kTB, (i64)q.ctr->dcount, [&](i64 k, u64 s) {
-      tv.rec[s] = k;
-      if (bits) bit_set(tv.keybm, ukey(k) - umin);
-    });
+    const i64 i0 = (t - pre[qi]) * kTB, n = (i64)q.ctr->dcount;
+    if (bits) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const i64 idx = i0 + j * 32 + (threadIdx.x & 31);
+        if (idx < n) bit_set(tv.keybm, ukey(q.dlist[idx]) - umin);
+      }
+    } else {
+      insert_x4(tv, q.dlist, i0, n, [&](i64 k, u64 s) { tv.rec[s] = k; });
+    }
   }
   finish(b.work, kPhDbuild);
 }
@@ -768,7 +853,11 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
       q.ctr->mlog2 = e;
       q.ctr->m_umin = rb.umin;
       q.ctr->m_bits = rb.bits;
-      return fill_tiles(e, true, rb.bits);
+      // With a bitmap the M side is a dense dictionary, else a hash table.
+      q.ctr->m_fill_off = 0;
+      q.ctr->m_fill_units = rb.bits ? dense_layout(cnt, rb.bits).tdir / 16
+                                    : table_layout(e, true).keybm / 16;
+      return ((i64)q.ctr->m_fill_units + kTCU - 1) / kTCU;
     });
     block_prefix(b.dyn + 3 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       return (ld_count(&b.q[qi].ctr->mcount) + kTB - 1) / kTB;
@@ -777,8 +866,10 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
 }
 
 // ----------------------------------------------------------------- mbuild ----
-// Warp tiles of 128 M-list entries (insert_x4), claimed per warp.  A key equal
-// to the reserved INT64_MIN is reported and skipped.
+// Warp tiles of 128 M-list entries, claimed per warp.  Dense dictionary: set
+// the keys' bitmap bits (reductions nobody waits for).  Hash table: insert
+// {key, 0} records (insert_x4); a key equal to the reserved INT64_MIN is
+// reported and skipped.
 __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
   chain_begin();
   const i64* pre = b.dyn + 3 * (b.nq + 1);
@@ -790,10 +881,20 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const TableView tv = table_view(q.ht_tag, q.ctr->mlog2, true);
     const u64 m_umin = q.ctr->m_umin, m_bits = q.ctr->m_bits;
     const i64 n = (i64)q.ctr->mcount;
     const i64 i0 = (t - pre[qi]) * kTB;
+    if (m_bits) {
+      u32* bm = reinterpret_cast<u32*>(reinterpret_cast<char*>(q.ht_tag) +
+                                       dense_layout(n, m_bits).bm);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const i64 idx = i0 + j * 32 + lane;
+        if (idx < n) bit_set(bm, ukey(q.mlist[idx]) - m_umin);
+      }
+      continue;
+    }
+    const TableView tv = table_view(q.ht_tag, q.ctr->mlog2, true);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const i64 idx = i0 + j * 32 + lane;
@@ -801,10 +902,197 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
     }
     insert_x4(tv, q.mlist, i0, n, [&](i64 k, u64 s) {
       *reinterpret_cast<longlong2*>(tv.rec + 2 * s) = make_longlong2(k, 0);  // {key, sum}
-      if (m_bits) bit_set(tv.keybm, ukey(k) - m_umin);
     });
   }
-  finish(b.work, kPhMbuild);
+  if (finish(b.work, kPhMbuild)) {
+    block_prefix(b.dyn + 5 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+      const QCtr* c = b.q[qi].ctr;
+      const u64 blocks = (c->m_bits + 511) / 512;
+      return c->m_bits ? (i64)((blocks + kRankTile - 1) / kRankTile) : 0;
+    });
+  }
+}
+
+// ------------------------------------------------------ dense dictionary ----
+// Pointers of a plan's dense dictionary.
+struct DenseView {
+  const u32* bm;
+  const u32* tdir;
+  const unsigned short* bdir;
+  u64 blocks;
+};
+__device__ __forceinline__ DenseView dense_view(const void* region, i64 c, u64 bits) {
+  const DenseLayout L = dense_layout(c, bits);
+  const char* base = reinterpret_cast<const char*>(region);
+  DenseView v;
+  v.bm = reinterpret_cast<const u32*>(base + L.bm);
+  v.tdir = reinterpret_cast<const u32*>(base + L.tdir);
+  v.bdir = reinterpret_cast<const unsigned short*>(base + L.bdir);
+  v.blocks = (bits + 511) / 512;
+  return v;
+}
+
+// Rank of bitmap bit idx (which is set): set bits before it.
+__device__ __forceinline__ u64 dense_rank(const DenseView& d, u64 idx, u64 keep) {
+  const u64 blk = idx >> 9;
+  const int wi = (int)((idx >> 5) & 15);
+  const u32 below = (1u << (idx & 31)) - 1u;
+  const uint4* w4 = reinterpret_cast<const uint4*>(d.bm + blk * 16);
+  u32 r;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;"
+      : "=r"(r) : "l"(d.tdir + blk / kRankTile), "l"(keep));
+  r += ld_keep_u16(d.bdir + blk, keep);
+#pragma unroll
+  for (int qd = 0; qd < 4; ++qd) {
+    const uint4 v = ld_keep_v4u(w4 + qd, keep);
+    const u32 w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int x = qd * 4 + j;
+      r += x < wi ? __popc(w[j]) : x == wi ? __popc(w[j] & below) : 0u;
+    }
+  }
+  return r;
+}
+
+// Key of dense slot `rank` (< distinct keys): the rank-th set bit.
+__device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank) {
+  const u64 tiles = (d.blocks + kRankTile - 1) / kRankTile;
+  u64 lo = 0, hi = tiles;  // tdir[tiles] = total > rank
+  while (hi - lo > 1) {
+    const u64 mid = (lo + hi) >> 1;
+    if (d.tdir[mid] <= rank) lo = mid;
+    else hi = mid;
+  }
+  u32 r = (u32)(rank - d.tdir[lo]);
+  u64 b0 = lo * kRankTile, b1 = min(d.blocks, b0 + kRankTile);
+  while (b1 - b0 > 1) {  // last block of the tile with bdir <= r
+    const u64 mid = (b0 + b1) >> 1;
+    if (d.bdir[mid] <= r) b0 = mid;
+    else b1 = mid;
+  }
+  r -= d.bdir[b0];
+  const u32* w = d.bm + b0 * 16;
+  for (int i = 0; i < 16; ++i) {
+    const u32 c = __popc(w[i]);
+    if (r < c) {
+      u32 x = w[i];
+      for (; r; --r) x &= x - 1;
+      const u64 u = umin + b0 * 512 + (u64)i * 32 + (u64)(__ffs(x) - 1);
+      return (i64)(u ^ (1ULL << 63));
+    }
+    r -= c;
+  }
+  return 0;  // not reached: rank < total
+}
+
+// Rank pass: one warp per tile of kRankTile blocks writes each block's set
+// bits before it within the tile and the tile's total; the block that
+// finishes last turns the tile totals into prefixes, writes the number of
+// distinct keys and notes whether the M list repeats keys.
+__global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
+  chain_begin();
+  const i64* pre = b.dyn + 5 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  const int lane = threadIdx.x & 31;
+  WarpClaim wc;
+  while (true) {
+    const i64 t = wc.next(b.work, kPhMrank);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    const u64 bits = q.ctr->m_bits;
+    const DenseLayout L = dense_layout((i64)q.ctr->mcount, bits);
+    char* base = reinterpret_cast<char*>(q.ht_tag);
+    const uint4* bm = reinterpret_cast<const uint4*>(base + L.bm);
+    u32* tdir = reinterpret_cast<u32*>(base + L.tdir);
+    unsigned short* bdir = reinterpret_cast<unsigned short*>(base + L.bdir);
+    const u64 blocks = (bits + 511) / 512;
+    const i64 lt = t - pre[qi];
+    const u64 b0 = (u64)lt * kRankTile, b1 = min(blocks, b0 + kRankTile);
+    u32 run = 0;
+    for (u64 j0 = b0; j0 < b1; j0 += 32) {
+      const u64 j = j0 + lane;
+      u32 p = 0;
+      if (j < b1) {
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+          const uint4 v = __ldcg(bm + j * 4 + qd);
+          p += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+      }
+      u32 incl = p;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (j < b1) bdir[j] = (unsigned short)(run + incl - p);
+      run += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0) tdir[lt] = run;  // the tile's total, a prefix after the scan
+  }
+  if (finish(b.work, kPhMrank)) {
+    for (int qi = 0; qi < b.nq; ++qi) {  // exclusive scan of each dense plan's tile totals
+      const PlanDev& q = b.q[qi];
+      const u64 bits = q.ctr->m_bits;
+      if (!bits) continue;
+      u32* tdir = reinterpret_cast<u32*>(reinterpret_cast<char*>(q.ht_tag) +
+                                         dense_layout((i64)q.ctr->mcount, bits).tdir);
+      const i64 tiles = (i64)(((bits + 511) / 512 + kRankTile - 1) / kRankTile);
+      __shared__ u32 s_carry;
+      if (threadIdx.x == 0) s_carry = 0;
+      __syncthreads();
+      for (i64 t0 = 0; t0 < tiles; t0 += blockDim.x) {
+        const i64 t = t0 + threadIdx.x;
+        const u32 v = t < tiles ? __ldcg(tdir + t) : 0u;
+        const u32 ex = block_exclusive_sum(v);
+        if (t < tiles) tdir[t] = s_carry + ex;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry += ex + v;
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        tdir[tiles] = s_carry;
+        q.ctr->m_distinct = s_carry;
+        q.ctr->dup = s_carry != (u32)q.ctr->mcount ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    block_prefix(b.dyn + 6 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+      const QCtr* c = b.q[qi].ctr;
+      return c->m_bits && c->dup ? (i64)((c->mcount + kTB - 1) / kTB) : 0;
+    });
+  }
+}
+
+// Copies per key when the M list repeats keys: count the entries of each
+// dense slot (the F probe multiplies a row's revenue by it).
+__global__ void __launch_bounds__(256) k_plan_mdup(Batch b) {
+  chain_begin();
+  const i64* pre = b.dyn + 6 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  const int lane = threadIdx.x & 31;
+  const u64 keep = policy_keep();
+  WarpClaim wc;
+  while (true) {
+    const i64 t = wc.next(b.work, kPhMdup);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    const i64 n = (i64)q.ctr->mcount;
+    const DenseView dv = dense_view(q.ht_tag, n, q.ctr->m_bits);
+    u32* cnt = reinterpret_cast<u32*>(reinterpret_cast<char*>(q.ht_tag) +
+                                      dense_layout(n, q.ctr->m_bits).cnt);
+    const u64 umin = q.ctr->m_umin;
+    const i64 i0 = (t - pre[qi]) * kTB;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const i64 idx = i0 + j * 32 + lane;
+      if (idx < n) atomicAdd(cnt + dense_rank(dv, ukey(q.mlist[idx]) - umin, keep), 1u);
+    }
+  }
+  finish(b.work, kPhMdup);
 }
 
 // ----------------------------------------------------------------- fprobe ----
@@ -812,16 +1100,15 @@ constexpr int kAggLog2 = 8;
 constexpr int kAgg = 1 << kAggLog2;  // entries of a block's shared-memory aggregation table
 constexpr int kH = 256;              // entries of a warp's hit ring
 
+// What a probe needs besides the plan (kept small: it lives in registers
+// across the scan loop; the table details are derived in the probe).
 struct ProbeCtx {
-  TableView t;
   const i64* mkey;
   const i64* price;
   const signed char* disc;
-  QCtr* ctr;
-  DevStatus* st;
   i64 base;
   u64 keep;
-  int qi;         // plan index in the batch
+  int qi;  // plan index in the batch
 };
 
 __device__ __forceinline__ bool add_overflows(i64 old, i64 v) {
@@ -835,41 +1122,55 @@ struct Hit {
   i64 v;
 };
 
-// Probe the M table with the key of F row base + r: count the slots holding
-// it (its multiplicity in M', found in the home bucket and, while buckets are
-// full, the next ones); the row adds its exact revenue times that count to
-// the group of the first of them.
-__device__ __forceinline__ Hit probe_row(const ProbeCtx& c, u32 r) {
+// Probe the M side with the key of F row base + r.  Dense dictionary: the
+// slot is the rank of the key's bit (set: the caller tested it) and the
+// multiplicity its copy count.  Hash table: count the slots holding the key
+// (its multiplicity in M', found in the home bucket and, while buckets are
+// full, the next ones) and take the first.  The row adds its exact revenue
+// times the multiplicity to the group of that slot.
+__device__ __forceinline__ Hit probe_row(const Batch& bt_, const ProbeCtx& c, u32 r) {
+  const PlanDev& q = bt_.q[c.qi];
   Hit h = {false, 0, 0};
   const i64 row = c.base + r;
   const i64 k = __ldg(c.mkey + row);
   const i64 price = __ldg(c.price + row);  // loaded with the key: one round trip
   const i64 disc = __ldg(c.disc + row);
-  const BucketTag bt = bucket_tag(k, c.t.g.shiftb);
-  const unsigned v2 = bt.tag * 0x10001u;
-  u64 b = bt.bucket;
   i64 first = -1, mult = 0;
-  for (u64 p = 0; p <= c.t.g.bmask; ++p) {
-    const uint4 w = ld_keep_v4u(c.t.tags + b * 8, c.keep);
-    Mask8 m = match8(w, v2);
-    while (any8(m)) {
-      const int j = first8(m);
-      const u64 slot = b * 8 + j;
-      if (ld_keep(c.t.rec + 2 * slot, c.keep) == k) {
-        if (first < 0) first = (i64)slot;
-        ++mult;
+  if (q.ctr->m_bits) {
+    const DenseView dv = dense_view(q.ht_tag, (i64)q.ctr->mcount, q.ctr->m_bits);
+    first = (i64)dense_rank(dv, ukey(k) - q.ctr->m_umin, c.keep);
+    mult = q.ctr->dup ? (i64)__ldg(reinterpret_cast<const u32*>(
+                                       reinterpret_cast<const char*>(q.ht_tag) +
+                                       dense_layout((i64)q.ctr->mcount, q.ctr->m_bits).cnt) +
+                                   first)
+                      : 1;
+  } else {
+    const TableView t = table_view(q.ht_tag, q.ctr->mlog2, true);
+    const BucketTag bt = bucket_tag(k, t.g.shiftb);
+    const unsigned v2 = bt.tag * 0x10001u;
+    u64 b = bt.bucket;
+    for (u64 p = 0; p <= t.g.bmask; ++p) {
+      const uint4 w = ld_keep_v4u(t.tags + b * 8, c.keep);
+      Mask8 m = match8(w, v2);
+      while (any8(m)) {
+        const int j = first8(m);
+        const u64 slot = b * 8 + j;
+        if (ld_keep(t.rec + 2 * slot, c.keep) == k) {
+          if (first < 0) first = (i64)slot;
+          ++mult;
+        }
+        drop8(m, j);
       }
-      drop8(m, j);
+      if (any8(match8(w, 0u))) break;
+      b = (b + 1) & t.g.bmask;
     }
-    if (any8(match8(w, 0u))) break;
-    b = (b + 1) & c.t.g.bmask;
   }
   if (first < 0) return h;
   // Exact revenue: the product is formed in 128 bits so that a value outside
   // int64 is reported instead of wrapping.
   const __int128 v128 = (__int128)mult * ((__int128)price * (100 - disc));
   h.v = (i64)v128;
-  if (v128 != (__int128)h.v) q_latch(c.ctr, c.st, PQ_ERR_OVERFLOW, k);
+  if (v128 != (__int128)h.v) q_latch(q.ctr, bt_.st, PQ_ERR_OVERFLOW, k);
   h.act = true;
   h.slot = (u64)first;
   return h;
@@ -890,6 +1191,30 @@ __device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, boo
   const i64 old = (i64)atomicAdd((unsigned long long*)&asum[h], (unsigned long long)v);
   ovf = ovf || add_overflows(old, v);
   return true;
+}
+
+// Where a plan's groups keep their sums and first-hit bits: the dense
+// dictionary's arrays, or the hash table's records (sum in the second word).
+struct GroupStore {
+  u32* hit;
+  i64* sums;
+  int stride;
+};
+__device__ __forceinline__ GroupStore group_store(const PlanDev& q) {
+  GroupStore g;
+  if (q.ctr->m_bits) {
+    const DenseLayout L = dense_layout((i64)q.ctr->mcount, q.ctr->m_bits);
+    char* base = reinterpret_cast<char*>(q.ht_tag);
+    g.hit = reinterpret_cast<u32*>(base + L.hit);
+    g.sums = reinterpret_cast<i64*>(base + L.sums);
+    g.stride = 1;
+  } else {
+    const TableView t = table_view(q.ht_tag, q.ctr->mlog2, true);
+    g.hit = t.hit;
+    g.sums = t.rec + 1;
+    g.stride = 2;
+  }
+  return g;
 }
 
 // Warp-wide commit of per-lane sums (every lane calls; lanes with `act` add
@@ -919,13 +1244,19 @@ __device__ __forceinline__ void commit_hits(const Batch& b, i64* sc, u64* akey, 
   if (lead) {
     const PlanDev& q = b.q[qi];
     if (!(akey && agg_try(akey, asum, ak, tot, ovf))) {
-      const TableView t = table_view(q.ht_tag, q.ctr->mlog2, true);
-      atomicOr(t.hit + (s >> 5), 1u << (s & 31));
-      const i64 old = (i64)atomicAdd((u64*)(t.rec + 2 * s + 1), (u64)tot);
+      const GroupStore g = group_store(q);
+      atomicOr(g.hit + (s >> 5), 1u << (s & 31));
+      const i64 old = (i64)atomicAdd((u64*)(g.sums + s * g.stride), (u64)tot);
       ovf = ovf || add_overflows(old, tot);
     }
     if (ovf) q_latch(q.ctr, b.st, PQ_ERR_OVERFLOW, (i64)s);
   }
+}
+
+// Words of a plan's first-hit bitmap: dense slots, or hash-table slots.
+__device__ __forceinline__ i64 topk_words(const PlanDev& q) {
+  const i64 slots = q.ctr->m_bits ? (i64)q.ctr->mcount : (1LL << q.ctr->mlog2);
+  return (slots + 31) >> 5;
 }
 
 // End of an F-probe kernel: flush the block's aggregated sums to the plans'
@@ -944,7 +1275,8 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
       const PlanDev& q = b.q[qi];
       q.out->status = q.ctr->status;
       q.out->reserved = 0;
-      return topk_parts(q.ctr->mlog2);
+      return (topk_words(q) + topk_tile_words_w(topk_words(q)) - 1) /
+             topk_tile_words_w(topk_words(q));
     });
   }
 }
@@ -983,7 +1315,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
   u32 hh = 0, ht = 0;
   auto probe_hits = [&](u32 cnt) {  // cnt <= 32 entries from hh
     Hit h = {false, 0, 0};
-    if ((u32)lane < cnt) h = probe_row(pc, hr[(hh + lane) & (kH - 1)]);
+    if ((u32)lane < cnt) h = probe_row(b, pc, hr[(hh + lane) & (kH - 1)]);
     commit_hits(b, sc, s_akey, s_asum, h.act, pc.qi, h.slot, h.v);
     hh += cnt;
     __syncwarp();
@@ -1007,19 +1339,19 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
     if (qi != pc.qi || !carry) {
       if (pc.qi >= 0) drain();
       carry = n < (1LL << 32);
-      pc.t = table_view(q.ht_tag, q.ctr->mlog2, true);
       pc.mkey = f_mkey;
       pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
       pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
-      pc.ctr = q.ctr;
-      pc.st = b.st;
       pc.base = carry ? 0 : base;
       pc.keep = keep;
       pc.qi = qi;
     }
     const u32 rbase = carry ? (u32)base : 0u;
-    const u32* bm = pc.t.keybm;
     const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
+    const u32* bm = bm_bits ? reinterpret_cast<const u32*>(
+                                  reinterpret_cast<const char*>(q.ht_tag) +
+                                  dense_layout((i64)q.ctr->mcount, bm_bits).bm)
+                            : nullptr;
     const Pred32 pf = to32(q.pf);
     const i64 lim = min(n - base, (i64)tile);
     const int iters = (int)((lim + 127) / 128);
@@ -1104,11 +1436,45 @@ __device__ __forceinline__ bool ks_before(const KS& a, const KS& b) {
 // Scan warp w's quarter of block tile lt of a table: calls on(KS) for 256
 // ring records at a time (each lane gets 8: invalid ones have v = false);
 // returns the number of set bits.
+// A plan's groups for top-k: the first-hit bitmap and, per slot, the record
+// {key, sum} of the hash table or the dense sum (the slot standing for the
+// key: slots follow key order).
+struct TopkSrc {
+  const u32* hit;
+  const longlong2* rec;
+  const i64* sums;
+  i64 words;
+  bool dense;
+};
+__device__ __forceinline__ TopkSrc topk_src(const PlanDev& q) {
+  TopkSrc t;
+  t.dense = q.ctr->m_bits != 0;
+  if (t.dense) {
+    const DenseLayout L = dense_layout((i64)q.ctr->mcount, q.ctr->m_bits);
+    const char* base = reinterpret_cast<const char*>(q.ht_tag);
+    t.hit = reinterpret_cast<const u32*>(base + L.hit);
+    t.rec = nullptr;
+    t.sums = reinterpret_cast<const i64*>(base + L.sums);
+  } else {
+    const TableView tv = table_view(q.ht_tag, q.ctr->mlog2, true);
+    t.hit = tv.hit;
+    t.rec = reinterpret_cast<const longlong2*>(tv.rec);
+    t.sums = nullptr;
+  }
+  t.words = topk_words(q);
+  return t;
+}
+// The key of an output entry: dense entries carry their slot.
+__device__ __forceinline__ i64 topk_out_key(const PlanDev& q, bool dense, i64 k) {
+  if (!dense) return k;
+  return dense_key(dense_view(q.ht_tag, (i64)q.ctr->mcount, q.ctr->m_bits), q.ctr->m_umin,
+                   (u64)k);
+}
+
 template <typename On>
-__device__ __forceinline__ u64 tk_scan(const TableView& tv, i64 words, i64 tw, i64 lt, u32* ring,
-                                       On on) {
+__device__ __forceinline__ u64 tk_scan(const TopkSrc& src, i64 tw, i64 lt, u32* ring, On on) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const longlong2* rec = reinterpret_cast<const longlong2*>(tv.rec);
+  const i64 words = src.words;
   const i64 ww = tw / kTKW;
   const i64 w0 = lt * tw + warp * ww, w1 = min(words, w0 + ww);
   u32 head = 0, tail = 0;
@@ -1118,7 +1484,10 @@ __device__ __forceinline__ u64 tk_scan(const TableView& tv, i64 words, i64 tw, i
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const u32 j = u * 32 + lane;
-      const longlong2 x = j < cnt ? rec[ring[(head + j) & (kTKR - 1)]] : make_longlong2(0, 0);
+      const u32 slot = j < cnt ? ring[(head + j) & (kTKR - 1)] : 0u;
+      const longlong2 x = j >= cnt    ? make_longlong2(0, 0)
+                          : src.rec   ? src.rec[slot]
+                                      : make_longlong2((i64)slot, src.sums[slot]);
       r[u].k = x.x, r[u].s = x.y, r[u].v = j < cnt;
     }
     on(r);
@@ -1130,7 +1499,7 @@ __device__ __forceinline__ u64 tk_scan(const TableView& tv, i64 words, i64 tw, i
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const i64 wi = w + u * 32 + lane;
-      wb[u] = wi < w1 ? __ldcg(tv.hit + wi) : 0u;
+      wb[u] = wi < w1 ? __ldcg(src.hit + wi) : 0u;
     }
 #pragma unroll 1
     for (int u = 0; u < 8; ++u) {
@@ -1179,12 +1548,11 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int e = q.ctr->mlog2;
-    const TableView tv = table_view(q.ht_tag, e, true);
-    const i64 words = ((1LL << e) + 31) >> 5, tw = topk_tile_words(e);
+    const TopkSrc src = topk_src(q);
+    const i64 tw = topk_tile_words_w(src.words);
     const i64 lt = t - pre[qi];
     KS best = {0, 0, false};
-    u64 groups = tk_scan(tv, words, tw, lt, s_ring[warp], [&](const KS* r) {
+    u64 groups = tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (ks_before(r[u], best)) best = r[u];
@@ -1263,15 +1631,14 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
-    const int e = q.ctr->mlog2;
     const int K = q.k;
-    const TableView tv = table_view(q.ht_tag, e, true);
-    const i64 words = ((1LL << e) + 31) >> 5, tw = topk_tile_words(e);
+    const TopkSrc src = topk_src(q);
+    const i64 tw = topk_tile_words_w(src.words);
     const i64 lt = t - pre[qi];
     const KS thr = {q.ctr->thr_k, q.ctr->thr_s, true};
     const bool all = q.ctr->thr_all != 0;
-    const u64 cap = (u64)topk_cand_cap(e, K);
-    tk_scan(tv, words, tw, lt, s_ring[warp], [&](const KS* r) {
+    const u64 cap = (u64)min((i64)topk_cand_cap(q.ctr->mlog2, K), (i64)K * tw * 32);
+    tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const bool keep = r[u].v && (all || !ks_before(thr, r[u]));
@@ -1301,7 +1668,7 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
         bool v = lane < c;
         i64 ck = v ? __ldcg(q.cand_k + lane) : 0, cs = v ? __ldcg(q.cand_s + lane) : 0;
         tk_sort32(ck, cs, v);
-        if (lane < K && v) q.out->keys[lane] = ck, q.out->sums[lane] = cs;
+        if (lane < K && v) q.out->keys[lane] = topk_out_key(q, src.dense, ck), q.out->sums[lane] = cs;
         if (lane == 0) {
           q.out->n = (int)min((i64)K, c);
           q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
@@ -1328,6 +1695,8 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
     tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
     if (warp == 0) {
       L.store((i64*)q.out->keys, (i64*)q.out->sums);
+      for (int i = lane; i < L.cnt; i += 32)  // each lane converts what it stored
+        q.out->keys[i] = topk_out_key(q, src.dense, q.out->keys[i]);
       if (lane == 0) {
         q.out->n = L.cnt;
         q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);

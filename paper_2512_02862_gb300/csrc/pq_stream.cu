@@ -419,7 +419,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       p += al(cap * 8);
       d.cand_s = (i64*)p;
       PQ_CUDA(ctx, upload_desc(0, 0, r.resident[2] ? (r.n_f + d.f_tile - 1) / d.f_tile : 0));
-      for (int ph : {kPhaseMfill, kPhaseMbuild}) {
+      for (int ph : {kPhaseMfill, kPhaseMbuild, kPhaseMrank, kPhaseMdup}) {
         st = launch_phase(ctx, ph, b, true, s);
         if (st != PQ_OK) return st;
       }
