@@ -127,6 +127,66 @@ def test_duplicate_build_keys(ctx, stream):
     assert_same(got, want)
 
 
+def remap_keys(D, M, F, seed, sparse=True, shift=0):
+    """The same plan with the keys renamed: M keys to distinct random int64
+    values of both signs (sparse: no key-range bitmap, hash tables) or to
+    key + shift (dense, possibly negative), D keys to distinct random int32
+    values; references (M.dref, F.mkey) follow."""
+    rng = np.random.default_rng(seed)
+    M, D, F = dict(M), dict(D), dict(F)
+    old_m = M["key"]
+    if sparse:
+        new_m = rng.choice(np.iinfo(np.int64).max, size=len(old_m), replace=False)
+        new_m = (new_m - (np.iinfo(np.int64).max // 2)).astype(np.int64)
+    else:
+        new_m = (old_m + shift).astype(np.int64)
+    order = np.argsort(old_m)
+    F["mkey"] = new_m[order[np.searchsorted(old_m[order], F["mkey"])]]
+    M["key"] = new_m
+    old_d = D["key"]
+    new_d = rng.choice(2**31 - 1, size=len(old_d), replace=False).astype(np.int32) - 2**30
+    od = np.argsort(old_d)
+    M["dref"] = new_d[od[np.searchsorted(old_d[od], M["dref"])]].astype(np.int32)
+    D["key"] = new_d.astype(np.int32)
+    return D, M, F
+
+
+@pytest.mark.parametrize("sparse,shift", [(True, 0), (False, -(10**15)), (False, -7)],
+                         ids=["sparse-hash", "dense-negative", "dense-around-zero"])
+def test_renamed_keys(ctx, stream, sparse, shift):
+    """Sparse keys take the hash-table paths (D-set and M table); dense keys
+    of any sign take the bitmap and the rank dictionary."""
+    D, M, F = datagen.make(5000, 60_000, 250_000, seed=21)
+    D, M, F = remap_keys(D, M, F, seed=22, sparse=sparse, shift=shift)
+    for p in ({}, dict(seg=3, mc=2000, fc=300)):
+        want = oracle_plan(D, M, F, k=10, **p)
+        with torch.cuda.stream(stream):
+            TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+        kw = dict(seg=p.get("seg", 1), m_date_lt=p.get("mc", 1200), f_date_gt=p.get("fc", 1200))
+        got = run(ctx, stream, pq.make_plan(TD, TM, TF, k=10, **kw))
+        assert_same(got, want, str(p))
+        for t in (TD, TM, TF):
+            t.free(stream)
+
+
+def test_batch_mixing_hash_and_dense_plans(ctx, stream, small, small_tables):
+    D, M, F = remap_keys(*datagen.make(4000, 50_000, 200_000, seed=23), seed=24, sparse=True)
+    with torch.cuda.stream(stream):
+        SD, SM, SF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    TD, TM, TF, _ = small_tables
+    plans = [pq.make_plan(SD, SM, SF, k=10), pq.make_plan(TD, TM, TF, k=10),
+             pq.make_plan(SD, SM, SF, seg=2, m_date_lt=2000, f_date_gt=100, k=10)]
+    wants = [oracle_plan(D, M, F, k=10), oracle_plan(*small, k=10),
+             oracle_plan(D, M, F, seg=2, mc=2000, fc=100, k=10)]
+    with torch.cuda.stream(stream):
+        res = pq.pq_run_batch(ctx, plans, stream=stream)
+        ctx.sync(stream)
+    for r, w in zip(res, wants):
+        assert_same(r.as_dict(), w)
+    for t in (SD, SM, SF):
+        t.free(stream)
+
+
 @pytest.mark.parametrize("rows", [dict(m=(16, 30_000), f=(4096, 200_000)),
                                   dict(d=(1, 5000), m=(3, 77_777), f=(5, 123_457)),
                                   dict(f=(599_999, 1)), dict(m=(0, 0))])
