@@ -312,11 +312,11 @@ def run_ours(args):
             pq.pq_run_plan(ctx, plan, res[0], stream=s)
         ctx.sync(s)
     ctx.profile_enable(False)
-    fprobe_ms, fprobe_n = ctx.profile("plan_fprobe")
+    fscan_ms, fscan_n = ctx.profile("plan_fscan")
     per_stage = {}
     for nm in ("plan_dscan", "plan_dfill", "plan_dbuild", "plan_mscan", "plan_mfill",
-               "plan_mbuild", "plan_mrank", "plan_mdup", "plan_fprobe", "plan_topk",
-               "plan_topk2"):
+               "plan_mbuild", "plan_mrank", "plan_mdup", "plan_fscan", "plan_fprobe",
+               "plan_topk", "plan_topk2"):
         try:
             ms, n = ctx.profile(nm)
             per_stage[nm] = round(ms / max(n, 1), 5)
@@ -328,19 +328,19 @@ def run_ours(args):
     plan_bytes = table_bytes(n_d, n_m, n_f)
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    # Dominant kernel: the F probe.  Algorithmic bytes per launch: date2 and
+    # Dominant kernel: the F scan.  Algorithmic bytes per launch: date2 and
     # mkey of every F row (12 B/row); price and disc of the ~0.5 % matching
-    # rows are not counted.
-    fprobe_bytes = 12 * n_f
-    fprobe_avg_s = fprobe_ms / max(fprobe_n, 1) / 1e3
-    achieved = fprobe_bytes / fprobe_avg_s / 1e9
-    roofline = {"kernel": "k_plan_fprobe", "bound": "hbm", "achieved": round(achieved, 1),
+    # rows are read by the probe kernel and not counted.
+    fscan_bytes = 12 * n_f
+    fscan_avg_s = fscan_ms / max(fscan_n, 1) / 1e3
+    achieved = fscan_bytes / fscan_avg_s / 1e9
+    roofline = {"kernel": "k_plan_fscan", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": ncu_traffic("k_plan_fprobe", args.workload),
+                "traffic": ncu_traffic("k_plan_fscan", args.workload),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src ==
                 "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": fprobe_bytes,
-                "avg_launch_ms": round(fprobe_avg_s * 1e3, 5), "launches": fprobe_n,
+                "algorithmic_bytes_per_launch": fscan_bytes,
+                "avg_launch_ms": round(fscan_avg_s * 1e3, 5), "launches": fscan_n,
                 "timing": "CUDA events around each launch on its stream, in a second pass of "
                           "the same steps run as separate launches"}
 

@@ -59,6 +59,9 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
   d.n_d = r.n_d;
   d.n_m = r.n_m;
   d.n_f = r.n_f;
+  if (r.n_f >= (1LL << 32))
+    return fail(ctx, PQ_ERR_INVALID_ARG, "plan: %lld F rows (at most 2^32 - 1 per plan)",
+                (long long)r.n_f);
   d.d_tile = scan_tile(r.n_d, 512, kTD, resident_warps(ctx, 0));
   d.m_tile = scan_tile(r.n_m, 128, kTM, resident_warps(ctx, 3));
   d.f_tile = scan_tile(r.n_f, 128, kTF, resident_warps(ctx, 8));
@@ -100,6 +103,7 @@ size_t plan_bytes(const ResolvedPlan& r) {
   b += mtable_bytes(r.e_m);              // M table
   b += al(r.parts * 8) * 2 + al(r.parts * 4);                  // top-k tile maxima
   b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k candidates
+  b += al(r.n_f * 4);                                           // F hit list
   return b;
 }
 
@@ -121,6 +125,7 @@ void plan_assign(ResolvedPlan& r, char* base) {
   d.tk_c = (int*)take(r.parts * 4);
   d.cand_k = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
   d.cand_s = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
+  d.hlist = (u32*)take(r.n_f * 4);
 }
 
 BatchLayout batch_layout(int nq) {
@@ -136,7 +141,7 @@ BatchLayout batch_layout(int nq) {
   L.tF = o;
   o += 8 * (nq + 1);
   L.dyn = al(o);
-  o = L.dyn + 8 * 7 * (nq + 1);
+  o = L.dyn + 8 * 8 * (nq + 1);
   L.work = al(o);
   o = L.work + 256;
   L.ctr = o;
@@ -162,19 +167,19 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
   return b;
 }
 
-static const char* kPhaseName[] = {"plan_dscan",  "plan_dfill", "plan_dbuild", "plan_mscan",
-                                   "plan_mfill",  "plan_mbuild", "plan_mrank", "plan_mdup",
-                                   "plan_fprobe", "plan_topk",  "plan_topk2"};
+static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "plan_mscan",
+                                   "plan_mfill", "plan_mbuild", "plan_mrank",  "plan_mdup",
+                                   "plan_fscan", "plan_fprobe", "plan_topk",   "plan_topk2"};
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[13] = {(const void*)k_plan_dscan<true>,  (const void*)k_plan_fill,
-                        (const void*)k_plan_dbuild,       (const void*)k_plan_mscan<true>,
-                        (const void*)k_plan_fill,         (const void*)k_plan_mbuild,
-                        (const void*)k_plan_fprobe<false>, (const void*)k_plan_topk,
-                        (const void*)k_plan_fprobe<true>,  (const void*)k_plan_mscan<false>,
-                        (const void*)k_plan_topk2,        (const void*)k_plan_mrank,
-                        (const void*)k_plan_mdup};
-  for (int i = 0; i < 13; ++i) {
+  const void* fn[14] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
+                        (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true>,
+                        (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
+                        (const void*)k_plan_fscan<false>, (const void*)k_plan_topk,
+                        (const void*)k_plan_fscan<true>,  (const void*)k_plan_mscan<false>,
+                        (const void*)k_plan_topk2,       (const void*)k_plan_mrank,
+                        (const void*)k_plan_mdup,        (const void*)k_plan_fprobe};
+  for (int i = 0; i < 14; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -244,10 +249,11 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseMbuild: e = launch_chained(k_plan_mbuild, plan_grid(ctx, 5), 256, s, b); break;
     case kPhaseMrank: e = launch_chained(k_plan_mrank, plan_grid(ctx, 11), 256, s, b); break;
     case kPhaseMdup: e = launch_chained(k_plan_mdup, plan_grid(ctx, 12), 256, s, b); break;
-    case kPhaseF:
-      e = vec ? launch_chained(k_plan_fprobe<true>, plan_grid(ctx, 8), 256, s, b)
-              : launch_chained(k_plan_fprobe<false>, plan_grid(ctx, 6), 256, s, b);
+    case kPhaseFscan:
+      e = vec ? launch_chained(k_plan_fscan<true>, plan_grid(ctx, 8), 256, s, b)
+              : launch_chained(k_plan_fscan<false>, plan_grid(ctx, 6), 256, s, b);
       break;
+    case kPhaseF: e = launch_chained(k_plan_fprobe, plan_grid(ctx, 13), 256, s, b); break;
     case kPhaseTopk: e = launch_chained(k_plan_topk, plan_grid(ctx, 7, 1), kTKW * 32, s, b); break;
     case kPhaseTopk2:
       e = launch_chained(k_plan_topk2, plan_grid(ctx, 10, 1), kTKW * 32, s, b);
@@ -503,7 +509,9 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   lk.unlock();
   tmax[kPhaseD] = tD[n];
   tmax[kPhaseM] = tM[n];
-  tmax[kPhaseF] = tF[n];
+  tmax[kPhaseFscan] = tF[n];
+  tmax[kPhaseF] = 0;
+  for (int i = 0; i < n; ++i) tmax[kPhaseF] += (R[i].n_f + 63) / 64;
   tmax[kPhaseTopk2] = tmax[kPhaseTopk];
 
   for (auto ev : waits) PQ_CUDA(ctx, cudaStreamWaitEvent(s, ev, 0));

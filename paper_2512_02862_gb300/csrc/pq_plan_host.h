@@ -80,6 +80,6 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cu
                        i64 tiles_max = -1);
 
 enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseMrank,
-       kPhaseMdup, kPhaseF, kPhaseTopk, kPhaseTopk2 };
+       kPhaseMdup, kPhaseFscan, kPhaseF, kPhaseTopk, kPhaseTopk2 };
 
 }  // namespace pqh

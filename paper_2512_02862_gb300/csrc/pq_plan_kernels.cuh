@@ -64,6 +64,8 @@ struct QCtr {
   // 16-byte units (set by the scans' last blocks).
   u64 d_fill_off, d_fill_units, m_fill_off, m_fill_units;
   u64 m_distinct;  // dense M dictionary: distinct keys (the rank pass)
+  u64 hcount;      // F rows in the hit list
+  i64 hp_tile;     // hits per warp tile of the probe
 };
 
 // Key-range semi-join filter.  When the keys of a filtered build side span
@@ -271,6 +273,7 @@ struct PlanDev {
   int* tk_c;
   i64* cand_k;  // top-k candidates (topk_cand_cap entries)
   i64* cand_s;
+  u32* hlist;   // F rows that hit (n_f entries, rows of the plan)
   QCtr* ctr;
   pq_result* out;
 };
@@ -302,7 +305,7 @@ struct Batch {
 };
 
 enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk,
-       kPhTopk2, kPhMrank, kPhMdup };
+       kPhTopk2, kPhMrank, kPhMdup, kPhFscan };
 
 // The kernels below are defined in exactly one translation unit (pq_plan.cu),
 // which defines PQ_DEFINE_PLAN_KERNELS before including this header.
@@ -1275,78 +1278,60 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
       const PlanDev& q = b.q[qi];
       q.out->status = q.ctr->status;
       q.out->reserved = 0;
+      q.ctr->hcount = 0;  // a streamed F table probes chunk by chunk
       return (topk_words(q) + topk_tile_words_w(topk_words(q)) - 1) /
              topk_tile_words_w(topk_words(q));
     });
   }
 }
 
-// Warp tile of 2048 F rows, 128 per iteration (lane l: rows 4l .. 4l+3).
-// Pipeline per lane: date2 is read two iterations ahead, mkey one ahead (only
-// for 4-row groups with a passing row), the key-range bitmap words of the
-// passing keys are loaded in the iteration the keys arrive and tested in the
-// next.  Only rows whose bit is set (the join hits) enter the warp's hit
-// ring, which probes the table 32 rows at a time with every lane busy.  With
-// no bitmap every passing row is a candidate and the probe decides.  Hits
-// aggregate in the block's shared table, flushed once at the end.
+// F scan: warp tiles of F rows (up to 2048), 128 per step (lane l: rows
+// 4l .. 4l+3).  Pipeline per lane: date2 is read two steps ahead, mkey one
+// ahead (only for 4-row groups with a passing row), the key-range bitmap
+// words of the passing keys are loaded in the step the keys arrive and
+// tested in the next.  Rows whose bit is set (the join hits) enter the
+// warp's ring as rows of the plan; runs of 128 leave for the plan's hit list
+// with one atomic reservation each.  With no bitmap every passing row is a
+// hit candidate and the probe decides.  The ring carries over from tile to
+// tile of the same plan.  The kernel does nothing else, so that it stays
+// small enough for four blocks per SM.
 template <bool VEC>
-__global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
+__global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   chain_begin();
   __shared__ u32 s_hr[8][kH];
-  __shared__ u64 s_akey[kAgg];
-  __shared__ i64 s_asum[kAgg];
-  __shared__ i64 s_sc[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* hr = s_hr[warp];
-  i64* sc = s_sc[warp];
-  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
-  __syncthreads();
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
   const i64 r0 = lane * 4;
-  // The hit ring carries over from tile to tile of the same plan (entries
-  // are rows of the plan, so batches of 32 fill up); it is drained when the
-  // plan changes, or after every tile of a plan with 2^32 rows or more
-  // (entries are then rows of the tile).
-  ProbeCtx pc;
-  pc.qi = -1;
-  bool carry = false;
+  int cq = -1;  // plan of the rows in the ring
   u32 hh = 0, ht = 0;
-  auto probe_hits = [&](u32 cnt) {  // cnt <= 32 entries from hh
-    Hit h = {false, 0, 0};
-    if ((u32)lane < cnt) h = probe_row(b, pc, hr[(hh + lane) & (kH - 1)]);
-    commit_hits(b, sc, s_akey, s_asum, h.act, pc.qi, h.slot, h.v);
+  auto flush = [&](u32 cnt) {  // cnt entries from hh to plan cq's hit list
+    const PlanDev& q = b.q[cq];
+    u64 at = 0;
+    if (lane == 0) at = atomicAdd(&q.ctr->hcount, (u64)cnt);
+    at = __shfl_sync(kFull, at, 0);
+    for (u32 j = lane; j < cnt; j += 32) q.hlist[at + j] = hr[(hh + j) & (kH - 1)];
     hh += cnt;
     __syncwarp();
   };
-  auto drain = [&]() {
-    while (ht - hh >= 32) probe_hits(32);
-    if (ht - hh) probe_hits(ht - hh);
-    hh = ht = 0;
-  };
   WarpClaim wc;
   while (true) {
-    const i64 t = wc.next(b.work, kPhFprobe);
+    const i64 t = wc.next(b.work, kPhFscan);
     if (t >= total) break;
     const int qi = ov ? 0 : find_q(b.tF, b.nq, t);
     const PlanDev& q = b.q[qi];
+    if (qi != cq) {
+      if (cq >= 0 && ht != hh) flush(ht - hh);
+      cq = qi;
+      hh = ht = 0;
+    }
     const i64* f_mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
     const int* f_date = ov ? (const int*)b.ov.p[3] : q.f_date;
     const i64 n = ov ? b.ov.n : q.n_f;
     const int tile = ov ? b.ov.tile : q.f_tile;
     const i64 base = (t - (ov ? 0 : b.tF[qi])) * tile;
-    if (qi != pc.qi || !carry) {
-      if (pc.qi >= 0) drain();
-      carry = n < (1LL << 32);
-      pc.mkey = f_mkey;
-      pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
-      pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
-      pc.base = carry ? 0 : base;
-      pc.keep = keep;
-      pc.qi = qi;
-    }
-    const u32 rbase = carry ? (u32)base : 0u;
     const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
     const u32* bm = bm_bits ? reinterpret_cast<const u32*>(
                                   reinterpret_cast<const char*>(q.ht_tag) +
@@ -1359,9 +1344,10 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
       if (__any_sync(kFull, hits)) {
         __syncwarp();
         ht += ring_append(hits, ht, [&](int s, u32 pos) {
-          hr[pos & (kH - 1)] = rbase + (u32)(it * 128 + r0 + s);
+          hr[pos & (kH - 1)] = (u32)(base + it * 128 + r0 + s);
         });
         __syncwarp();
+        if (ht - hh >= 128) flush(128);
       }
     };
     int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
@@ -1390,19 +1376,70 @@ __global__ void __launch_bounds__(256, 3) k_plan_fprobe(Batch b) {
       }
       BmStage wN;
       bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
-      if (it > 0) {
-        append_hits(bm_hits(wP), it - 1);
-        while (ht - hh >= 32) probe_hits(32);
-      }
+      if (it > 0) append_hits(bm_hits(wP), it - 1);
       wP = wN;
       bA = bB;
 #pragma unroll
       for (int s = 0; s < 4; ++s) mA[s] = mB[s];
     }
     append_hits(bm_hits(wP), iters - 1);
-    while (ht - hh >= 32) probe_hits(32);
   }
-  if (pc.qi >= 0) drain();
+  if (cq >= 0 && ht != hh) flush(ht - hh);
+  if (finish(b.work, kPhFscan)) {
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    block_prefix(b.dyn + 7 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+      QCtr* c = b.q[qi].ctr;
+      const i64 h = ld_count(&c->hcount);
+      // Hits per probe tile: about two tiles per warp of this grid, in
+      // multiples of 32, between 64 and 4096.
+      i64 tl = (h / (2 * warps) + 31) / 32 * 32;
+      tl = tl < 64 ? 64 : tl > 4096 ? 4096 : tl;
+      c->hp_tile = tl;
+      return (h + tl - 1) / tl;
+    });
+  }
+}
+
+// F probe: warp tiles of the hit list (hp_tile rows), 32 per batch: each
+// lane re-reads its row's key, price and discount, finds the group (dense:
+// rank of the key's bit; hash: probe), and the batch commits (lanes of the
+// same group combined, the block's shared aggregation table for hot groups,
+// else the group's sum and first-hit bit in global memory).
+__global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
+  chain_begin();
+  __shared__ u64 s_akey[kAgg];
+  __shared__ i64 s_asum[kAgg];
+  __shared__ i64 s_sc[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  i64* sc = s_sc[warp];
+  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
+  __syncthreads();
+  const u64 keep = policy_keep();
+  const bool ov = b.ov.table == 3;
+  const i64* pre = b.dyn + 7 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  WarpClaim wc;
+  while (true) {
+    const i64 t = wc.next(b.work, kPhFprobe);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    ProbeCtx pc;
+    pc.mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
+    pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
+    pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+    pc.base = 0;
+    pc.keep = keep;
+    pc.qi = qi;
+    const i64 tl = q.ctr->hp_tile, h = (i64)q.ctr->hcount;
+    const i64 i0 = (t - pre[qi]) * tl, i1 = min(h, i0 + tl);
+    for (i64 i = i0; i < i1; i += 32) {
+      const bool act = i + lane < i1;
+      Hit x = {false, 0, 0};
+      if (act) x = probe_row(b, pc, __ldg(q.hlist + i + lane));
+      commit_hits(b, sc, s_akey, s_asum, x.act, qi, x.slot, x.v);
+    }
+  }
   fprobe_epilogue(b, s_akey, s_asum, sc);
 }
 

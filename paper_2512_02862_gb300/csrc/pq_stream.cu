@@ -228,7 +228,11 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   const BatchLayout L = batch_layout(1);
   const int nslots = std::max(2, ctx->opt.ring_slots);
   Scratch scr(ctx, s);
-  char* ws = (char*)scr.get(L.end + al(r.n_d * 8) + al(r.n_m * 8));
+  // F hit list: the rows of one F chunk (or of the resident F table).
+  i64 f_hits = r.resident[2] ? r.n_f : 0;
+  for (const Chunk& ch : chunks)
+    if (ch.table == 2) f_hits = std::max(f_hits, ch.rows);
+  char* ws = (char*)scr.get(L.end + al(r.n_d * 8) + al(r.n_m * 8) + al(f_hits * 4 + 4));
   char* ring = chunks.empty() ? nullptr : (char*)scr.get((chunk_bytes + 1024) * nslots);
   if (!ws || (!chunks.empty() && !ring))
     return fail(ctx, PQ_ERR_BUDGET, "streaming plan: workspace and %d chunk slots of %zu bytes",
@@ -237,6 +241,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   d.build_dset = 1;
   d.dlist = (i64*)(ws + L.end);
   d.mlist = (i64*)(ws + L.end + al(r.n_d * 8));
+  d.hlist = (u32*)(ws + L.end + al(r.n_d * 8) + al(r.n_m * 8));
   QCtr* ctr = (QCtr*)(ws + L.ctr);
   d.ctr = ctr;
   d.out = (pq_result*)(ws + L.out);
@@ -335,11 +340,17 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     }
     return PQ_OK;
   };
-  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseF};
+  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseFscan};
+  // The F table's phase is the scan and the probe of its hits.
+  auto launch_table = [&](int t, const Batch& bt, bool v) -> pq_status {
+    pq_status e = launch_phase(ctx, phase_of[t], bt, v, s);
+    if (e == PQ_OK && t == 2) e = launch_phase(ctx, kPhaseF, bt, v, s);
+    return e;
+  };
   size_t c = 0;
   for (int t = 0; t < 3; ++t) {
     if (r.resident[t]) {
-      st = launch_phase(ctx, phase_of[t], b, vec && d.vec, s);
+      st = launch_table(t, b, vec && d.vec);
       if (st != PQ_OK) return st;
     } else if (nrows[t] == 0) {
       // An empty streamed table: one launch with no tiles still lets the
@@ -348,7 +359,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       bc.ov.table = t + 1;
       bc.ov.n = 0;
       bc.ov.tiles = 0;
-      st = launch_phase(ctx, phase_of[t], bc, true, s);
+      st = launch_table(t, bc, true);
       if (st != PQ_OK) return st;
     } else {
       for (; c < chunks.size() && chunks[c].table == t; ++c) {
@@ -368,7 +379,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         bc.ov.tile = tile;
         bc.ov.tiles = (ch.rows + tile - 1) / tile;
         for (int j = 0; j < T.ncols; ++j) bc.ov.p[j] = src + col_offset(T, ch.rows, j);
-        st = launch_phase(ctx, phase_of[t], bc, true, s);
+        st = launch_table(t, bc, true);
         if (st != PQ_OK) return st;
         PQ_CUDA(ctx, cudaEventRecord(slot_free[slot], s));
       }
