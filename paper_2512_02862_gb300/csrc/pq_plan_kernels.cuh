@@ -1267,7 +1267,9 @@ __device__ __forceinline__ i64 topk_words(const PlanDev& q) {
 __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_akey,
                                                 const i64* s_asum, i64* sc) {
   __syncthreads();
-  for (int i0 = 0; i0 < kAgg; i0 += blockDim.x) {  // warp-uniform trip count
+  int used = 0;
+  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) used |= s_akey[i] != 0;
+  for (int i0 = 0; __syncthreads_or(used) && i0 < kAgg; i0 += blockDim.x) {  // uniform
     const int i = i0 + threadIdx.x;
     const u64 ak = i < kAgg ? s_akey[i] : 0;
     commit_hits(b, sc, nullptr, nullptr, ak != 0, ak ? (int)((ak - 1) >> 40) : 0,
@@ -1403,8 +1405,10 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
 // F probe: warp tiles of the hit list (hp_tile rows), 32 per batch: each
 // lane re-reads its row's key, price and discount, finds the group (dense:
 // rank of the key's bit; hash: probe), and the batch commits (lanes of the
-// same group combined, the block's shared aggregation table for hot groups,
-// else the group's sum and first-hit bit in global memory).
+// same group combined, then the group's sum and first-hit bit in global
+// memory).  A plan with at least 2048 hits per block of the grid (skewed or
+// pass-all data, where groups repeat within a block) first tries the
+// block's shared aggregation table.
 __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
   chain_begin();
   __shared__ u64 s_akey[kAgg];
@@ -1414,6 +1418,7 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
   i64* sc = s_sc[warp];
   for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
   __syncthreads();
+  const u64 agg_min = (u64)gridDim.x * 2048;
   const u64 keep = policy_keep();
   const bool ov = b.ov.table == 3;
   const i64* pre = b.dyn + 7 * (b.nq + 1);
@@ -1433,11 +1438,12 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
     pc.qi = qi;
     const i64 tl = q.ctr->hp_tile, h = (i64)q.ctr->hcount;
     const i64 i0 = (t - pre[qi]) * tl, i1 = min(h, i0 + tl);
+    const bool agg = (u64)h >= agg_min;
     for (i64 i = i0; i < i1; i += 32) {
       const bool act = i + lane < i1;
       Hit x = {false, 0, 0};
       if (act) x = probe_row(b, pc, __ldg(q.hlist + i + lane));
-      commit_hits(b, sc, s_akey, s_asum, x.act, qi, x.slot, x.v);
+      commit_hits(b, sc, agg ? s_akey : nullptr, s_asum, x.act, qi, x.slot, x.v);
     }
   }
   fprobe_epilogue(b, s_akey, s_asum, sc);
