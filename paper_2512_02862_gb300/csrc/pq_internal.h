@@ -78,6 +78,10 @@ struct Column {
   bool pinned = false;    // host source is page-locked
   void* owned = nullptr;  // arena block owned by the table
   std::string path;
+  // Range of an integer key column of a resident table (order-preserving
+  // ukey = key xor 2^63), measured on first use by a plan and kept.
+  mutable bool has_range = false;
+  mutable uint64_t umin = 0, umax = 0;
 };
 
 }  // namespace pqh

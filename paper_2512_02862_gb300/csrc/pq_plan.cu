@@ -35,6 +35,71 @@ static bool check_types(const pq_table* t, std::initializer_list<int> types) {
   return true;
 }
 
+// Range of an int32 / int64 key column (order-preserving ukey): out[0] holds
+// ~min, out[1] the max, both zero-initialised and grown with atomicMax.
+__global__ void k_key_range(const void* col, int is64, i64 n, u64* out) {
+  u64 nmin = 0, umax = 0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
+       i += (i64)gridDim.x * blockDim.x) {
+    const i64 k = is64 ? __ldg(reinterpret_cast<const i64*>(col) + i)
+                       : (i64)__ldg(reinterpret_cast<const int*>(col) + i);
+    nmin = max(nmin, ~ukey(k));
+    umax = max(umax, ukey(k));
+  }
+  range_commit(nmin, umax, out, out + 1);
+}
+
+// The key range of column c of a resident table, measured once (one kernel
+// and a read-back on stream s) and kept with the column.
+static bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
+  const Column& col = t->cols[c];
+  if (col.has_range) return true;
+  if (!col.dev || t->nrows <= 0) return false;
+  std::lock_guard<std::mutex> g(ctx->small_mu);
+  u64* d = (u64*)ctx->arena.alloc(256);
+  if (!d) return false;
+  bool ok = cudaMemsetAsync(d, 0, 16, s) == cudaSuccess;
+  if (ok) {
+    const int grid = (int)std::min<i64>((t->nrows + 255) / 256, (i64)ctx->num_sms * 8);
+    k_key_range<<<grid, 256, 0, s>>>(col.dev, col.type == PQ_INT64 ? 1 : 0, t->nrows, d);
+    ok = cudaGetLastError() == cudaSuccess &&
+         cudaMemcpyAsync(ctx->h_small, d, 16, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+    ctx->launches++;
+  }
+  ctx->arena.release(d, s);
+  if (!ok) {
+    cudaGetLastError();
+    return false;
+  }
+  col.umin = ~(u64)ctx->h_small[0];
+  col.umax = (u64)ctx->h_small[1];
+  col.has_range = true;
+  return true;
+}
+
+// Static key bitmaps (see PlanDev): a side whose table is resident and whose
+// key range fits in 32 bits per slot of its table (sized for the table's
+// rows) gets a bitmap over that whole range, known before the plan runs.
+// While the stream is being captured nothing new is measured.
+static void plan_static(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, cudaStream_t s,
+                        bool capturing) {
+  PlanDev& d = r.dev;
+  d.d_e = r.e_d;
+  d.m_e = r.e_m;
+  auto fits = [&](const pq_table* t, int e, u64* su, u64* sb) -> bool {
+    const Column& c = t->cols[0];
+    if (!c.has_range && (capturing || !ensure_range(ctx, t, 0, s))) return false;
+    const u64 span = c.umax - c.umin;  // bits - 1
+    if (c.umax < c.umin || span >= (32ULL << e)) return false;
+    *su = c.umin;
+    *sb = span + 1;
+    return true;
+  };
+  d.d_static = r.resident[0] && fits(p.D, r.e_d, &d.d_su, &d.d_sb) ? 1 : 0;
+  d.m_static = r.resident[1] && fits(p.M, r.e_m, &d.m_su, &d.m_sb) ? 1 : 0;
+}
+
 pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need_resident) {
   r = ResolvedPlan();
   if (!p.D || !p.M || !p.F) return fail(ctx, PQ_ERR_INVALID_ARG, "plan: missing table");
@@ -365,13 +430,14 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
                              cudaStream_t s, bool allow_graph) {
   if (n <= 0 || !plans || !results) return fail(ctx, PQ_ERR_INVALID_ARG, "batch: bad arguments");
   std::vector<ResolvedPlan> R(n);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
   for (int i = 0; i < n; ++i) {
     pq_status st = resolve_plan(ctx, plans[i], R[i], true);
     if (st != PQ_OK) return st;
+    plan_static(ctx, plans[i], R[i], s, cap != cudaStreamCaptureStatusNone);
   }
   // Graph replay for a repeated single plan.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
   const bool graphable = allow_graph && n == 1 && s != nullptr && !ctx->opt.profile &&
                          cap == cudaStreamCaptureStatusNone &&
                          !(plans[0].flags & (PQ_PLAN_NO_GRAPH | PQ_PLAN_CACHE_DSET));
@@ -467,7 +533,8 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     return fail(ctx, PQ_ERR_BUDGET, "batch of %d plans needs %zu bytes (largest free %zu)", n,
                 total, ctx->arena.largest_free());
   }
-  bool any_build = false, vec = true;
+  bool any_build = false, vec = true, list_d = false, list_m = false;
+  std::vector<std::pair<void*, size_t>> clears;  // static bitmaps to zero first
   i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
   std::vector<char> host(L.upload_bytes());
   PlanDev* descs = (PlanDev*)host.data();
@@ -492,6 +559,12 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     d.out = out + i;
     any_build = any_build || r.builds;
     vec = vec && d.vec;
+    if (r.builds && d.d_static)
+      clears.push_back({(char*)d.dset_tag + table_layout(r.e_d, false).keybm,
+                        (size_t)((d.d_sb + 127) / 128 * 16)});
+    if (d.m_static) clears.push_back({(void*)d.ht_tag, (size_t)dense_layout(0, d.m_sb).tdir});
+    list_d = list_d || (r.builds && !d.d_static);
+    list_m = list_m || !d.m_static;
     descs[i] = d;
     tD[i + 1] = tD[i] + (r.builds ? (r.n_d + r.dev.d_tile - 1) / r.dev.d_tile : 0);
     tM[i + 1] = tM[i] + (r.n_m + r.dev.m_tile - 1) / r.dev.m_tile;
@@ -520,7 +593,11 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
 
   auto chain = [&]() -> pq_status {
     PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
+    for (auto& c : clears) PQ_CUDA(ctx, cudaMemsetAsync(c.first, 0, c.second, s));
     for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
+      // Phases only plans with key lists need.
+      if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
+      if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;
       pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph]);
       if (st != PQ_OK) return st;
     }

@@ -149,30 +149,32 @@ __host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
 // directory (set bits before each tile of kRankTile 512-bit blocks, and
 // before each block within its tile) plus the block's words.  Slots follow
 // key order.  Layout in the M table's region, for c entries in the M list
-// and `bits` bitmap bits (byte offsets; the fill clears everything before
-// `tdir`):
-//   hit   first-hit bit per slot              c/8 B
-//   sums  i64 sum per slot                    8c B
-//   cnt   u32 copies of the key per slot      4c B (written only when the
-//         M list repeats keys)
+// (members of M') and `bits` bitmap bits (byte offsets; the bitmap comes
+// first so that its place does not depend on c):
 //   bm    the key-range bitmap                64 B per 512-bit block
 //   tdir  u32 set bits before each tile, then the total
 //   bdir  u16 set bits before each block within its tile
+//   hit   first-hit bit per slot              c/8 B
+//   sums  i64 sum per slot                    8c B
+//   cnt   u32 copies of the key per slot      4c B (written only when the
+//         members repeat keys)
+// The bitmap is cleared before the bits are set (by the host, or by the M
+// fill); the rank pass writes the directories and clears hit, sums, cnt.
 constexpr int kRankTile = 64;   // bitmap blocks per tile (at most 32768 bits)
 struct DenseLayout {
-  u64 hit, sums, cnt, bm, tdir, bdir, total;
+  u64 bm, tdir, bdir, hit, sums, cnt, total;
 };
 __host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
   auto a = [](u64 x) { return (x + 255) & ~255ULL; };
   const u64 blocks = (bits + 511) / 512, tiles = (blocks + kRankTile - 1) / kRankTile;
   DenseLayout L;
-  L.hit = 0;
-  L.sums = a(((u64)c + 7) / 8);
-  L.cnt = L.sums + a(8 * (u64)c);
-  L.bm = L.cnt + a(4 * (u64)c);
-  L.tdir = L.bm + a(64 * blocks);
+  L.bm = 0;
+  L.tdir = a(64 * blocks);
   L.bdir = L.tdir + a(4 * (tiles + 1));
-  L.total = L.bdir + a(2 * blocks);
+  L.hit = L.bdir + a(2 * blocks);
+  L.sums = L.hit + a(((u64)c + 7) / 8);
+  L.cnt = L.sums + a(8 * (u64)c);
+  L.total = L.cnt + a(4 * (u64)c);
   return L;
 }
 
@@ -257,7 +259,12 @@ struct PlanDev {
   const int* f_date;
   i64 n_f;
   int d_tile, m_tile, f_tile;  // rows per warp tile of the D, M and F scans
-  int tile_pad;
+  // Key bitmaps over the whole key range of a resident table, known before
+  // the plan runs: the D (M) scan sets the bits of its passing (member) keys
+  // directly, with no key list and no build phase.  The host clears them.
+  int d_static, m_static;
+  int d_e, m_e;  // log2 slots of the D-set and the M table for the table's rows
+  u64 d_su, d_sb, m_su, m_sb;  // base ukey and bit count of those bitmaps
   Pred pd, pm, pf;
   int k, lf1024;
   int build_dset;   // this plan fills its D-set in this batch
@@ -619,6 +626,9 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
     const i64 n = ov ? b.ov.n : q.n_d;
     const int tile = ov ? b.ov.tile : q.d_tile;
     const i64 base = (t - (ov ? 0 : b.tD[qi])) * tile;
+    // Static bitmap: set the passing keys' bits (no list, no build phase).
+    const bool stat = !ov && q.d_static;
+    u32* sbm = stat ? table_view(q.dset_tag, q.d_e, false).keybm : nullptr;
     u64 lnmin = 0, lumax = 0;  // this lane's range of appended keys
     for (int it = 0; it < tile / 512; ++it) {
       if (base + it * 512 >= n) break;
@@ -633,6 +643,14 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
 #pragma unroll
         for (int s = 0; s < 16; ++s)
           if (e0 + s < n) bits |= (u32)pass(q.pd, ld_stream(d_seg + e0 + s)) << s;
+      }
+      if (stat) {
+        while (bits) {
+          const int s = __ffs(bits) - 1;
+          bits &= bits - 1;
+          bit_set(sbm, ukey((i64)__ldg(d_key + e0 + s)) - q.d_su);
+        }
+        continue;
       }
       u64 at = warp_reserve(&q.ctr->dcount, (u32)__popc(bits));
       while (bits) {
@@ -650,6 +668,14 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
     block_prefix(b.dyn, b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
       if (!q.build_dset) return 0;
+      if (q.d_static) {  // bitmap over the table's key range, cleared by the host
+        *q.dset_log2 = q.d_e;
+        u64* hdr = reinterpret_cast<u64*>(q.dset_log2);
+        hdr[1] = q.d_su;
+        hdr[2] = q.d_sb;
+        q.ctr->d_fill_units = 0;
+        return 0;
+      }
       const i64 cnt = ld_count(&q.ctr->dcount);
       const int e = cap_log2(cnt, q.lf1024);
       const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->d_nmin),
@@ -667,7 +693,7 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
     });
     block_prefix(b.dyn + (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
-      return q.build_dset ? (ld_count(&q.ctr->dcount) + kTB - 1) / kTB : 0;
+      return q.build_dset && !q.d_static ? (ld_count(&q.ctr->dcount) + kTB - 1) / kTB : 0;
     });
   }
 }
@@ -769,6 +795,9 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     const i64 lim = min(n - base, (i64)tile);
     const int iters = (int)((lim + 127) / 128);
     const i64 r0 = lane * 4;
+    // Static bitmap: members set their key's bit and are counted; no list.
+    const bool stat = !ov && q.m_static;
+    u32* sbm = stat ? reinterpret_cast<u32*>(q.ht_tag) : nullptr;  // dense layout: bm at 0
     u32 ch = 0, ct = 0, bh = 0, bt = 0;
     auto flush_b = [&](u32 cnt) {
       u64 o = 0;
@@ -785,11 +814,21 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
         mem = d_bits || set_contains(dt, (i64)__ldg(m_dref + base + r), keep);
         if (mem) {
           key = __ldg(m_key + base + r);
-          lnmin = max(lnmin, ~ukey(key));
-          lumax = max(lumax, ukey(key));
+          if (stat) {
+            bit_set(sbm, ukey(key) - q.m_su);
+          } else {
+            lnmin = max(lnmin, ~ukey(key));
+            lumax = max(lumax, ukey(key));
+          }
         }
       }
       const u32 m = __ballot_sync(kFull, mem);
+      if (stat) {
+        if (lane == 0 && m) atomicAdd(&q.ctr->mcount, (u64)__popc(m));
+        ch += cnt;
+        __syncwarp();
+        return;
+      }
       if (mem) rb[(bt + __popc(m & lanemask_lt())) & (kQ - 1)] = key;
       bt += __popc(m);
       ch += cnt;
@@ -849,6 +888,13 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
   if (finish(b.work, kPhMscan)) {
     block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
+      if (q.m_static) {  // bitmap over the table's key range, set by this scan
+        q.ctr->mlog2 = q.m_e;
+        q.ctr->m_umin = q.m_su;
+        q.ctr->m_bits = q.m_sb;
+        q.ctr->m_fill_units = 0;
+        return 0;
+      }
       const i64 cnt = ld_count(&q.ctr->mcount);
       const int e = cap_log2(cnt, q.lf1024);
       const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->m_nmin),
@@ -863,7 +909,13 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
       return ((i64)q.ctr->m_fill_units + kTCU - 1) / kTCU;
     });
     block_prefix(b.dyn + 3 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      return (ld_count(&b.q[qi].ctr->mcount) + kTB - 1) / kTB;
+      const PlanDev& q = b.q[qi];
+      return q.m_static ? 0 : (ld_count(&q.ctr->mcount) + kTB - 1) / kTB;
+    });
+    block_prefix(b.dyn + 5 * (b.nq + 1), b.nq, [&](int qi) -> i64 {  // rank tiles
+      const QCtr* c = b.q[qi].ctr;
+      const u64 blocks = (c->m_bits + 511) / 512;
+      return c->m_bits ? (i64)((blocks + kRankTile - 1) / kRankTile) : 0;
     });
   }
 }
@@ -907,13 +959,7 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
       *reinterpret_cast<longlong2*>(tv.rec + 2 * s) = make_longlong2(k, 0);  // {key, sum}
     });
   }
-  if (finish(b.work, kPhMbuild)) {
-    block_prefix(b.dyn + 5 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      const QCtr* c = b.q[qi].ctr;
-      const u64 blocks = (c->m_bits + 511) / 512;
-      return c->m_bits ? (i64)((blocks + kRankTile - 1) / kRankTile) : 0;
-    });
-  }
+  finish(b.work, kPhMbuild);
 }
 
 // ------------------------------------------------------ dense dictionary ----
@@ -990,9 +1036,10 @@ __device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank)
 }
 
 // Rank pass: one warp per tile of kRankTile blocks writes each block's set
-// bits before it within the tile and the tile's total; the block that
-// finishes last turns the tile totals into prefixes, writes the number of
-// distinct keys and notes whether the M list repeats keys.
+// bits before it within the tile and the tile's total, and clears its share
+// of the slot arrays (hit bits, sums, copy counts); the block that finishes
+// last turns the tile totals into prefixes, writes the number of distinct
+// keys and notes whether the members repeat keys.
 __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
   chain_begin();
   const i64* pre = b.dyn + 5 * (b.nq + 1);
@@ -1013,6 +1060,12 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
     const u64 blocks = (bits + 511) / 512;
     const i64 lt = t - pre[qi];
     const u64 b0 = (u64)lt * kRankTile, b1 = min(blocks, b0 + kRankTile);
+    {  // this tile's share of [hit, total), in 16-byte units
+      const i64 units = (i64)(L.total - L.hit) / 16, tiles = pre[qi + 1] - pre[qi];
+      const i64 u0 = units * lt / tiles, u1 = units * (lt + 1) / tiles;
+      int4* z = reinterpret_cast<int4*>(base + L.hit);
+      for (i64 u = u0 + lane; u < u1; u += 32) z[u] = make_int4(0, 0, 0, 0);
+    }
     u32 run = 0;
     for (u64 j0 = b0; j0 < b1; j0 += 32) {
       const u64 j = j0 + lane;
@@ -1063,14 +1116,19 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
       __syncthreads();
     }
     block_prefix(b.dyn + 6 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      const QCtr* c = b.q[qi].ctr;
-      return c->m_bits && c->dup ? (i64)((c->mcount + kTB - 1) / kTB) : 0;
+      const PlanDev& q = b.q[qi];
+      const QCtr* c = q.ctr;
+      if (!c->m_bits || !c->dup) return 0;
+      return q.m_static ? (q.n_m + q.m_tile - 1) / q.m_tile  // rescan M
+                        : (i64)((c->mcount + kTB - 1) / kTB);
     });
   }
 }
 
-// Copies per key when the M list repeats keys: count the entries of each
-// dense slot (the F probe multiplies a row's revenue by it).
+// Copies per key when the members repeat keys: count the members of each
+// dense slot (the F probe multiplies a row's revenue by it).  With a key list
+// (tiles of 128 entries) the keys come from it; with a static bitmap (tiles
+// of M rows) the M rows are tested again (date, D-set) for their members.
 __global__ void __launch_bounds__(256) k_plan_mdup(Batch b) {
   chain_begin();
   const i64* pre = b.dyn + 6 * (b.nq + 1);
@@ -1088,6 +1146,21 @@ __global__ void __launch_bounds__(256) k_plan_mdup(Batch b) {
     u32* cnt = reinterpret_cast<u32*>(reinterpret_cast<char*>(q.ht_tag) +
                                       dense_layout(n, q.ctr->m_bits).cnt);
     const u64 umin = q.ctr->m_umin;
+    if (q.m_static) {
+      const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
+      const u64* dhdr = reinterpret_cast<const u64*>(q.dset_log2);
+      const u64 d_umin = dhdr[1], d_bits = dhdr[2];
+      const i64 r0 = (t - pre[qi]) * q.m_tile, r1 = min(q.n_m, r0 + q.m_tile);
+      for (i64 r = r0 + lane; r < r1; r += 32) {
+        if (!pass(q.pm, __ldg(q.m_date + r))) continue;
+        const i64 dr = __ldg(q.m_dref + r);
+        const u64 di = ukey(dr) - d_umin;
+        const bool mem = d_bits ? di < d_bits && bit_test(dt.keybm, di, keep)
+                                : set_contains(dt, dr, keep);
+        if (mem) atomicAdd(cnt + dense_rank(dv, ukey(__ldg(q.m_key + r)) - umin, keep), 1u);
+      }
+      continue;
+    }
     const i64 i0 = (t - pre[qi]) * kTB;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1281,8 +1354,8 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
       q.out->status = q.ctr->status;
       q.out->reserved = 0;
       q.ctr->hcount = 0;  // a streamed F table probes chunk by chunk
-      return (topk_words(q) + topk_tile_words_w(topk_words(q)) - 1) /
-             topk_tile_words_w(topk_words(q));
+      const i64 w = topk_words(q);
+      return max((i64)1, (w + topk_tile_words_w(w) - 1) / topk_tile_words_w(w));
     });
   }
 }
