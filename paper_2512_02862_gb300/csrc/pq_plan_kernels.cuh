@@ -798,6 +798,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     // Static bitmap: members set their key's bit and are counted; no list.
     const bool stat = !ov && q.m_static;
     u32* sbm = stat ? reinterpret_cast<u32*>(q.ht_tag) : nullptr;  // dense layout: bm at 0
+    u64 members = 0;
     u32 ch = 0, ct = 0, bh = 0, bt = 0;
     auto flush_b = [&](u32 cnt) {
       u64 o = 0;
@@ -814,9 +815,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
         mem = d_bits || set_contains(dt, (i64)__ldg(m_dref + base + r), keep);
         if (mem) {
           key = __ldg(m_key + base + r);
-          if (stat) {
-            bit_set(sbm, ukey(key) - q.m_su);
-          } else {
+          if (!stat) {
             lnmin = max(lnmin, ~ukey(key));
             lumax = max(lumax, ukey(key));
           }
@@ -824,7 +823,8 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
       }
       const u32 m = __ballot_sync(kFull, mem);
       if (stat) {
-        if (lane == 0 && m) atomicAdd(&q.ctr->mcount, (u64)__popc(m));
+        if (mem) bit_set(sbm, ukey(key) - q.m_su);
+        members += __popc(m);  // added to the plan's count once per tile
         ch += cnt;
         __syncwarp();
         return;
@@ -883,7 +883,11 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     if (ct - ch) resolve(ct - ch);
     if (bt - bh) flush_b(bt - bh);
     __syncwarp();
-    range_commit(lnmin, lumax, &q.ctr->m_nmin, &q.ctr->m_umax);
+    if (stat) {
+      if (lane == 0 && members) atomicAdd(&q.ctr->mcount, members);
+    } else {
+      range_commit(lnmin, lumax, &q.ctr->m_nmin, &q.ctr->m_umax);
+    }
   }
   if (finish(b.work, kPhMscan)) {
     block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
