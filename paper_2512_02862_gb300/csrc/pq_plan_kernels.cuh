@@ -1179,6 +1179,7 @@ __global__ void __launch_bounds__(256) k_plan_mdup(Batch b) {
 constexpr int kAggLog2 = 8;
 constexpr int kAgg = 1 << kAggLog2;  // entries of a block's shared-memory aggregation table
 constexpr int kH = 256;              // entries of a warp's hit ring
+constexpr int kHF = 1024;            // entries of a warp's ring in the F scan
 
 // What a probe needs besides the plan (kept small: it lives in registers
 // across the scan loop; the table details are derived in the probe).
@@ -1259,7 +1260,8 @@ __device__ __forceinline__ Hit probe_row(const Batch& bt_, const ProbeCtx& c, u3
 // Add v into the block's direct-mapped shared-memory table under key ak (plan
 // and slot): the first key to reach an entry keeps it for the rest of the
 // kernel, so the repeated hits of hot groups (skewed data) stay on chip.
-// False when the entry belongs to another key.
+// False when the entry belongs to another key.  (Measured on Zipf data: a
+// 2048-entry table with 4-way probing was slower than this one.)
 __device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, bool& ovf) {
   const u32 h = (u32)((ak * 0x9E3779B97F4A7C15ULL) >> (64 - kAggLog2));
   u64 cur = *(volatile u64*)&akey[h];
@@ -1369,7 +1371,7 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
 // ahead (only for 4-row groups with a passing row), the key-range bitmap
 // words of the passing keys are loaded in the step the keys arrive and
 // tested in the next.  Rows whose bit is set (the join hits) enter the
-// warp's ring as rows of the plan; runs of 128 leave for the plan's hit list
+// warp's ring as rows of the plan; runs of 512 leave for the plan's hit list
 // with one atomic reservation each.  With no bitmap every passing row is a
 // hit candidate and the probe decides.  The ring carries over from tile to
 // tile of the same plan.  The kernel does nothing else, so that it stays
@@ -1377,7 +1379,7 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
 template <bool VEC>
 __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   chain_begin();
-  __shared__ u32 s_hr[8][kH];
+  __shared__ u32 s_hr[8][kHF];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* hr = s_hr[warp];
   const u64 keep = policy_keep(), strm = policy_stream();
@@ -1391,7 +1393,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
     u64 at = 0;
     if (lane == 0) at = atomicAdd(&q.ctr->hcount, (u64)cnt);
     at = __shfl_sync(kFull, at, 0);
-    for (u32 j = lane; j < cnt; j += 32) q.hlist[at + j] = hr[(hh + j) & (kH - 1)];
+    for (u32 j = lane; j < cnt; j += 32) q.hlist[at + j] = hr[(hh + j) & (kHF - 1)];
     hh += cnt;
     __syncwarp();
   };
@@ -1423,10 +1425,10 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
       if (__any_sync(kFull, hits)) {
         __syncwarp();
         ht += ring_append(hits, ht, [&](int s, u32 pos) {
-          hr[pos & (kH - 1)] = (u32)(base + it * 128 + r0 + s);
+          hr[pos & (kHF - 1)] = (u32)(base + it * 128 + r0 + s);
         });
         __syncwarp();
-        if (ht - hh >= 128) flush(128);
+        if (ht - hh >= 512) flush(512);
       }
     };
     int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
