@@ -237,14 +237,16 @@ static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "
                                    "plan_fscan", "plan_fprobe", "plan_topk",   "plan_topk2"};
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[14] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
-                        (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true>,
+  const void* fn[16] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
+                        (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true, true>,
                         (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
                         (const void*)k_plan_fscan<false>, (const void*)k_plan_topk,
-                        (const void*)k_plan_fscan<true>,  (const void*)k_plan_mscan<false>,
+                        (const void*)k_plan_fscan<true>,  (const void*)k_plan_mscan<false, true>,
                         (const void*)k_plan_topk2,       (const void*)k_plan_mrank,
-                        (const void*)k_plan_mdup,        (const void*)k_plan_fprobe};
-  for (int i = 0; i < 14; ++i) {
+                        (const void*)k_plan_mdup,        (const void*)k_plan_fprobe,
+                        (const void*)k_plan_mscan<true, false>,
+                        (const void*)k_plan_mscan<false, false>};
+  for (int i = 0; i < 16; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -258,6 +260,7 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
 // fits on an SM at once (a block that only starts after others exit finds
 // no work left) and by the phase's largest possible tile count.
 static thread_local i64 t_tiles_max = -1;
+static thread_local bool t_list_m = true;  // some plan of the batch keeps an M key list
 static int plan_grid(pq_ctx* ctx, int occ_index, int tiles_per_block = 8) {
   const i64 g = (i64)ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
   if (t_tiles_max < 0) return (int)g;
@@ -291,7 +294,8 @@ static cudaError_t launch_chained(void (*k)(P...), int grid, int block, cudaStre
 }
 
 pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s,
-                       i64 tiles_max) {
+                       i64 tiles_max, bool list_m) {
+  t_list_m = list_m;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   t_chain = cap == cudaStreamCaptureStatusNone;
@@ -307,8 +311,12 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseDfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 1, 1), 256, s, b, 0); break;
     case kPhaseDbuild: e = launch_chained(k_plan_dbuild, plan_grid(ctx, 2), 256, s, b); break;
     case kPhaseM:
-      e = vec ? launch_chained(k_plan_mscan<true>, plan_grid(ctx, 3), 256, s, b)
-              : launch_chained(k_plan_mscan<false>, plan_grid(ctx, 9), 256, s, b);
+      if (t_list_m)
+        e = vec ? launch_chained(k_plan_mscan<true, true>, plan_grid(ctx, 3), 256, s, b)
+                : launch_chained(k_plan_mscan<false, true>, plan_grid(ctx, 9), 256, s, b);
+      else
+        e = vec ? launch_chained(k_plan_mscan<true, false>, plan_grid(ctx, 14), 256, s, b)
+                : launch_chained(k_plan_mscan<false, false>, plan_grid(ctx, 15), 256, s, b);
       break;
     case kPhaseMfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 4, 1), 256, s, b, 1); break;
     case kPhaseMbuild: e = launch_chained(k_plan_mbuild, plan_grid(ctx, 5), 256, s, b); break;
@@ -598,7 +606,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       // Phases only plans with key lists need.
       if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
       if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;
-      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph]);
+      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph], list_m);
       if (st != PQ_OK) return st;
     }
     return PQ_OK;

@@ -764,11 +764,13 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
 // theirs) into ring B, which leaves for the M list in runs of 128 (one
 // atomic reservation per run).  With no bitmap, every date-passing row is a
 // candidate and the D-set table decides.
-template <bool VEC>
+// LIST = false: every plan of the batch has a static M bitmap (no key list,
+// ring B or key range), which keeps the kernel small.
+template <bool VEC, bool LIST>
 __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
   chain_begin();
   __shared__ u32 s_c[8][kQ];
-  __shared__ i64 s_rb[8][kQ];
+  __shared__ i64 s_rb[8][LIST ? kQ : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* cr = s_c[warp];
   i64* rb = s_rb[warp];
@@ -796,11 +798,12 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     const int iters = (int)((lim + 127) / 128);
     const i64 r0 = lane * 4;
     // Static bitmap: members set their key's bit and are counted; no list.
-    const bool stat = !ov && q.m_static;
+    const bool stat = !LIST || (!ov && q.m_static);
     u32* sbm = stat ? reinterpret_cast<u32*>(q.ht_tag) : nullptr;  // dense layout: bm at 0
     u64 members = 0;
     u32 ch = 0, ct = 0, bh = 0, bt = 0;
     auto flush_b = [&](u32 cnt) {
+      if (!LIST) return;
       u64 o = 0;
       if (lane == 0) o = atomicAdd(&q.ctr->mcount, (u64)cnt);
       o = __shfl_sync(kFull, o, 0);
@@ -822,7 +825,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
         }
       }
       const u32 m = __ballot_sync(kFull, mem);
-      if (stat) {
+      if (!LIST || stat) {
         if (mem) bit_set(sbm, ukey(key) - q.m_su);
         members += __popc(m);  // added to the plan's count once per tile
         ch += cnt;
@@ -883,7 +886,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
     if (ct - ch) resolve(ct - ch);
     if (bt - bh) flush_b(bt - bh);
     __syncwarp();
-    if (stat) {
+    if (!LIST || stat) {
       if (lane == 0 && members) atomicAdd(&q.ctr->mcount, members);
     } else {
       range_commit(lnmin, lumax, &q.ctr->m_nmin, &q.ctr->m_umax);
