@@ -77,6 +77,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.time()  # the timed region starts once sampling has started
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
+            self.lines.clear()
         except FileNotFoundError:
             self.proc = None
         return self
@@ -207,8 +211,10 @@ def run_reference(args):
     D, M, F = datagen.workload(args.workload)
     q = query(args.workload)
     # Each step runs the oracle on a bounded F prefix (D and M whole) so that
-    # warm-up plus timed steps end within a few minutes.
-    f_sample = min(len(F["mkey"]), args.ref_f_rows)
+    # warm-up plus timed steps end within a few minutes: at most
+    # --ref-f-rows per step and about 200M F rows over the whole run.
+    f_sample = min(len(F["mkey"]), args.ref_f_rows,
+                   max(100_000, 200_000_000 // max(1, args.steps + args.warmup)))
     Fs = {k: v[:f_sample] for k, v in F.items()}
     for _ in range(args.warmup):
         oracle.run_plan(D, M, Fs, **q)
@@ -734,7 +740,9 @@ def run_stream(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # Default steps per mode: plan 2000 (~0.6 s timed, so that the clocks get
+    # sampled), reference 20, stream 3, serve and ops 20.
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream", "ops"])
@@ -749,6 +757,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = (20 if args.impl == "reference" else 3 if args.mode == "stream"
+                      else 2000 if args.mode == "plan" else 20)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "serve":
