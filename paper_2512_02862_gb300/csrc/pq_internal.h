@@ -122,6 +122,7 @@ struct DsetEntry {
   void* block;        // arena block: header word (log2 of the slot count), slots
   pqk::i64* keys;
   int log2max;
+  bool bm;            // built as a static key bitmap
   cudaEvent_t ready;  // recorded after the set is built
   uint64_t last_use;
 };

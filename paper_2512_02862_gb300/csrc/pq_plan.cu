@@ -237,7 +237,7 @@ static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "
                                    "plan_fscan", "plan_fprobe", "plan_topk",   "plan_topk2"};
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[16] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
+  const void* fn[18] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
                         (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true, true>,
                         (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
                         (const void*)k_plan_fscan<false>, (const void*)k_plan_topk,
@@ -245,8 +245,10 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
                         (const void*)k_plan_topk2,       (const void*)k_plan_mrank,
                         (const void*)k_plan_mdup,        (const void*)k_plan_fprobe,
                         (const void*)k_plan_mscan<true, false>,
-                        (const void*)k_plan_mscan<false, false>};
-  for (int i = 0; i < 16; ++i) {
+                        (const void*)k_plan_mscan<false, false>,
+                        (const void*)k_plan_mscan_bm<true>,
+                        (const void*)k_plan_mscan_bm<false>};
+  for (int i = 0; i < 18; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -261,6 +263,7 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
 // no work left) and by the phase's largest possible tile count.
 static thread_local i64 t_tiles_max = -1;
 static thread_local bool t_list_m = true;  // some plan of the batch keeps an M key list
+static thread_local bool t_bm_dm = false;  // every plan: static M bitmap, D-set bitmap
 static int plan_grid(pq_ctx* ctx, int occ_index, int tiles_per_block = 8) {
   const i64 g = (i64)ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
   if (t_tiles_max < 0) return (int)g;
@@ -294,8 +297,9 @@ static cudaError_t launch_chained(void (*k)(P...), int grid, int block, cudaStre
 }
 
 pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s,
-                       i64 tiles_max, bool list_m) {
+                       i64 tiles_max, bool list_m, bool bm_dm) {
   t_list_m = list_m;
+  t_bm_dm = bm_dm && !list_m;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   t_chain = cap == cudaStreamCaptureStatusNone;
@@ -311,7 +315,10 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseDfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 1, 1), 256, s, b, 0); break;
     case kPhaseDbuild: e = launch_chained(k_plan_dbuild, plan_grid(ctx, 2), 256, s, b); break;
     case kPhaseM:
-      if (t_list_m)
+      if (t_bm_dm)
+        e = vec ? launch_chained(k_plan_mscan_bm<true>, plan_grid(ctx, 16), 256, s, b)
+                : launch_chained(k_plan_mscan_bm<false>, plan_grid(ctx, 17), 256, s, b);
+      else if (t_list_m)
         e = vec ? launch_chained(k_plan_mscan<true, true>, plan_grid(ctx, 3), 256, s, b)
                 : launch_chained(k_plan_mscan<false, true>, plan_grid(ctx, 9), 256, s, b);
       else
@@ -499,6 +506,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       e.pred = r.dev.pd;
       e.lf1024 = r.dev.lf1024;
       e.log2max = r.e_d;
+      e.bm = r.dev.d_static != 0;  // built from the static range
       e.block = ctx->arena.alloc(dset_block_bytes(r.e_d));
       if (!e.block) continue;  // no room to cache: build in the workspace
       if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
@@ -541,7 +549,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     return fail(ctx, PQ_ERR_BUDGET, "batch of %d plans needs %zu bytes (largest free %zu)", n,
                 total, ctx->arena.largest_free());
   }
-  bool any_build = false, vec = true, list_d = false, list_m = false;
+  bool any_build = false, vec = true, list_d = false, list_m = false, bm_dm = true;
   std::vector<std::pair<void*, size_t>> clears;  // static bitmaps to zero first
   i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
   std::vector<char> host(L.upload_bytes());
@@ -573,6 +581,13 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     if (d.m_static) clears.push_back({(void*)d.ht_tag, (size_t)dense_layout(0, d.m_sb).tdir});
     list_d = list_d || (r.builds && !d.d_static);
     list_m = list_m || !d.m_static;
+    // The D-set is a bitmap for certain when it is built here from a static
+    // range, or was built so (an earlier plan of the batch, or the cache).
+    const bool d_bm = r.builds                ? d.d_static != 0
+                      : r.dset_from >= 0      ? R[r.dset_from].builds && R[r.dset_from].dev.d_static
+                      : r.cache != nullptr    ? r.cache->bm
+                                              : false;
+    bm_dm = bm_dm && d.m_static && d_bm;
     descs[i] = d;
     tD[i + 1] = tD[i] + (r.builds ? (r.n_d + r.dev.d_tile - 1) / r.dev.d_tile : 0);
     tM[i + 1] = tM[i] + (r.n_m + r.dev.m_tile - 1) / r.dev.m_tile;
@@ -606,7 +621,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       // Phases only plans with key lists need.
       if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
       if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;
-      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph], list_m);
+      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph], list_m, bm_dm);
       if (st != PQ_OK) return st;
     }
     return PQ_OK;

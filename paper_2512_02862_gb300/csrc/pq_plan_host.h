@@ -76,9 +76,10 @@ pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
 // Launch one phase of the plan chain for the whole batch.  vec: every column
 // pointer 16-byte aligned.  tiles_max: the phase's largest possible tile
 // count (-1 unknown), which caps the grid.  list_m: some plan keeps an M key
-// list (else the M scan without list code runs).
+// list (else the M scan without list code runs).  bm_dm: every plan has a
+// static M bitmap and a D-set bitmap (the ring-free M scan runs).
 pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s,
-                       i64 tiles_max = -1, bool list_m = true);
+                       i64 tiles_max = -1, bool list_m = true, bool bm_dm = false);
 
 enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseMrank,
        kPhaseMdup, kPhaseFscan, kPhaseF, kPhaseTopk, kPhaseTopk2 };

@@ -644,19 +644,30 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
         for (int s = 0; s < 16; ++s)
           if (e0 + s < n) bits |= (u32)pass(q.pd, ld_stream(d_seg + e0 + s)) << s;
       }
-      if (stat) {
-        while (bits) {
-          const int s = __ffs(bits) - 1;
-          bits &= bits - 1;
-          bit_set(sbm, ukey((i64)__ldg(d_key + e0 + s)) - q.d_su);
+      // The lane's 16 keys at once (four 128-bit loads), not one dependent
+      // load per passing row.
+      int kk[16];
+      if (VEC && e0 + 16 <= n) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int4 x = bits ? ld_stream_v4(d_key + e0 + 4 * v, strm) : make_int4(0, 0, 0, 0);
+          kk[4 * v] = x.x, kk[4 * v + 1] = x.y, kk[4 * v + 2] = x.z, kk[4 * v + 3] = x.w;
         }
+      } else {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) kk[s] = (bits >> s) & 1u ? __ldg(d_key + e0 + s) : 0;
+      }
+      if (stat) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s)
+          if ((bits >> s) & 1u) bit_set(sbm, ukey((i64)kk[s]) - q.d_su);
         continue;
       }
       u64 at = warp_reserve(&q.ctr->dcount, (u32)__popc(bits));
-      while (bits) {
-        const int s = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const i64 k = (i64)__ldg(d_key + e0 + s);
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        if (!((bits >> s) & 1u)) continue;
+        const i64 k = (i64)kk[s];
         q.dlist[at++] = k;
         lnmin = max(lnmin, ~ukey(k));
         lumax = max(lumax, ukey(k));
@@ -756,7 +767,45 @@ __global__ void __launch_bounds__(256) k_plan_dbuild(Batch b) {
 }
 
 // ------------------------------------------------------------------ mscan ----
-// Warp tile of 2048 M rows, 128 per iteration (lane l: rows 4l .. 4l+3).
+// The M scan's last block: the M side's layout per plan (static bitmap, or
+// sized from the members' count and key range) and the tile counts of the
+// phases that follow.
+__device__ void mscan_finish(const Batch& b) {
+  block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+    const PlanDev& q = b.q[qi];
+    if (q.m_static) {  // bitmap over the table's key range, set by this scan
+      q.ctr->mlog2 = q.m_e;
+      q.ctr->m_umin = q.m_su;
+      q.ctr->m_bits = q.m_sb;
+      q.ctr->m_fill_units = 0;
+      return 0;
+    }
+    const i64 cnt = ld_count(&q.ctr->mcount);
+    const int e = cap_log2(cnt, q.lf1024);
+    const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->m_nmin),
+                                    ld_volatile_u64(&q.ctr->m_umax), e);
+    q.ctr->mlog2 = e;
+    q.ctr->m_umin = rb.umin;
+    q.ctr->m_bits = rb.bits;
+    // With a bitmap the M side is a dense dictionary, else a hash table.
+    q.ctr->m_fill_off = 0;
+    q.ctr->m_fill_units = rb.bits ? dense_layout(cnt, rb.bits).tdir / 16
+                                  : table_layout(e, true).keybm / 16;
+    return ((i64)q.ctr->m_fill_units + kTCU - 1) / kTCU;
+  });
+  block_prefix(b.dyn + 3 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+    const PlanDev& q = b.q[qi];
+    return q.m_static ? 0 : (ld_count(&q.ctr->mcount) + kTB - 1) / kTB;
+  });
+  block_prefix(b.dyn + 5 * (b.nq + 1), b.nq, [&](int qi) -> i64 {  // rank tiles
+    const QCtr* c = b.q[qi].ctr;
+    const u64 blocks = (c->m_bits + 511) / 512;
+    return c->m_bits ? (i64)((blocks + kRankTile - 1) / kRankTile) : 0;
+  });
+}
+
+// Warp tiles of up to 1024 M rows (sized per plan), 128 per iteration
+// (lane l: rows 4l .. 4l+3).
 // Pipeline per lane: date is read two iterations ahead, dref one ahead (only
 // for 4-row groups with a date hit), the D-set bitmap words of the passing
 // drefs are loaded in the iteration the drefs arrive and tested in the next.
@@ -892,39 +941,115 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
       range_commit(lnmin, lumax, &q.ctr->m_nmin, &q.ctr->m_umax);
     }
   }
-  if (finish(b.work, kPhMscan)) {
-    block_prefix(b.dyn + 2 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      const PlanDev& q = b.q[qi];
-      if (q.m_static) {  // bitmap over the table's key range, set by this scan
-        q.ctr->mlog2 = q.m_e;
-        q.ctr->m_umin = q.m_su;
-        q.ctr->m_bits = q.m_sb;
-        q.ctr->m_fill_units = 0;
-        return 0;
+  if (finish(b.work, kPhMscan)) mscan_finish(b);
+}
+
+// Every plan of the batch has a static M bitmap and a D-set bitmap: each
+// lane keeps its own 4 rows per iteration in registers, no ring.  date is
+// read two iterations ahead, dref one ahead (4-row groups with a date hit),
+// the D bitmap words are loaded when the drefs arrive and tested one
+// iteration later; then the members' keys are loaded, and one iteration
+// after that their bits are set (reductions nobody waits for).
+template <bool VEC>
+__global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
+  chain_begin();
+  const int lane = threadIdx.x & 31;
+  const u64 keep = policy_keep(), strm = policy_stream();
+  const i64 total = b.tM[b.nq];
+  const int r0 = lane * 4;
+  WarpClaim wc;
+  while (true) {
+    const i64 t = wc.next(b.work, kPhMscan);
+    if (t >= total) break;
+    const int qi = find_q(b.tM, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    const i64* m_key = q.m_key;
+    const int* m_dref = q.m_dref;
+    const int* m_date = q.m_date;
+    const u64* dhdr = reinterpret_cast<const u64*>(q.dset_log2);
+    const u64 d_umin = dhdr[1], d_bits = dhdr[2];
+    const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
+    u32* sbm = reinterpret_cast<u32*>(q.ht_tag);  // dense layout: bm at 0
+    const u64 m_su = q.m_su;
+    const Pred32 pm = to32(q.pm);
+    const i64 base = (t - b.tM[qi]) * q.m_tile;
+    const int lim = (int)min(q.n_m - base, (i64)q.m_tile);
+    // The tile's rows, addressed with 32-bit offsets.
+    const int* pdate = m_date + base;
+    const int* pdref = m_dref + base;
+    const i64* pkey = m_key + base;
+    u32 members = 0;  // this lane's
+    auto set_bits = [&](u32 m, const i64 k[4]) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if ((m >> s) & 1u) bit_set(sbm, ukey(k[s]) - m_su);
+      members += __popc(m);
+    };
+    if (d_bits == 0) {
+      // A D-set that is a hash table (the host does not choose this kernel
+      // then): row by row.
+      for (int r = lane; r < lim; r += 32) {
+        if (!pass32(pm, ld_stream(pdate + r))) continue;
+        if (!set_contains(dt, (i64)__ldg(pdref + r), keep)) continue;
+        bit_set(sbm, ukey(__ldg(pkey + r)) - m_su);
+        ++members;
       }
-      const i64 cnt = ld_count(&q.ctr->mcount);
-      const int e = cap_log2(cnt, q.lf1024);
-      const RangeBits rb = range_bits(cnt, ld_volatile_u64(&q.ctr->m_nmin),
-                                      ld_volatile_u64(&q.ctr->m_umax), e);
-      q.ctr->mlog2 = e;
-      q.ctr->m_umin = rb.umin;
-      q.ctr->m_bits = rb.bits;
-      // With a bitmap the M side is a dense dictionary, else a hash table.
-      q.ctr->m_fill_off = 0;
-      q.ctr->m_fill_units = rb.bits ? dense_layout(cnt, rb.bits).tdir / 16
-                                    : table_layout(e, true).keybm / 16;
-      return ((i64)q.ctr->m_fill_units + kTCU - 1) / kTCU;
-    });
-    block_prefix(b.dyn + 3 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      const PlanDev& q = b.q[qi];
-      return q.m_static ? 0 : (ld_count(&q.ctr->mcount) + kTB - 1) / kTB;
-    });
-    block_prefix(b.dyn + 5 * (b.nq + 1), b.nq, [&](int qi) -> i64 {  // rank tiles
-      const QCtr* c = b.q[qi].ctr;
-      const u64 blocks = (c->m_bits + 511) / 512;
-      return c->m_bits ? (i64)((blocks + kRankTile - 1) / kRankTile) : 0;
-    });
+    } else {
+      const int iters = (int)((lim + 127) / 128);
+      int4 dB = load_i32x4<VEC>(pdate, r0, lim - r0, strm);
+      int4 dC = iters > 1 ? load_i32x4<VEC>(pdate, 128 + r0, lim - 128 - r0, strm)
+                          : make_int4(0, 0, 0, 0);
+      u32 hA = pass4(pm, dB, lim - r0);
+      int4 rA = hA ? load_i32x4<VEC>(pdref, r0, lim - r0, strm) : make_int4(0, 0, 0, 0);
+      dB = dC;
+      if (iters > 2) dC = load_i32x4<VEC>(pdate, 256 + r0, lim - 256 - r0, strm);
+      BmStage wP;
+      wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
+      wP.sh = 0;
+      u32 mP = 0;  // members of iteration it - 2, keys in kP
+      i64 kP[4] = {0, 0, 0, 0};
+      for (int it = 0; it < iters; ++it) {
+        const int rel1 = (it + 1) * 128 + r0;
+        u32 hB = 0;
+        int4 rB = make_int4(0, 0, 0, 0);
+        if (it + 1 < iters) {
+          hB = pass4(pm, dB, lim - rel1);
+          if (hB) rB = load_i32x4<VEC>(pdref, rel1, lim - rel1, strm);
+        }
+        dB = dC;
+        if (it + 3 < iters) {
+          const int rel3 = (it + 3) * 128 + r0;
+          dC = load_i32x4<VEC>(pdate, rel3, lim - rel3, strm);
+        }
+        const int dr[4] = {rA.x, rA.y, rA.z, rA.w};
+        BmStage wN;
+        bm_issue(wN, dt.keybm, d_umin, d_bits, hA, dr, keep);
+        u32 mN = 0;  // members of iteration it - 1
+        i64 kN[4] = {0, 0, 0, 0};
+        if (it > 0) {
+          mN = bm_hits(wP);
+          const int rel = (it - 1) * 128 + r0;
+          if (mN) load_i64x4<VEC>(pkey, rel, lim - rel, mN, strm, kN);
+        }
+        set_bits(mP, kP);
+        wP = wN;
+        hA = hB;
+        rA = rB;
+        mP = mN;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) kP[s] = kN[s];
+      }
+      set_bits(mP, kP);
+      const u32 mL = bm_hits(wP);
+      i64 kL[4] = {0, 0, 0, 0};
+      const int relL = (iters - 1) * 128 + r0;
+      if (mL) load_i64x4<VEC>(pkey, relL, lim - relL, mL, strm, kL);
+      set_bits(mL, kL);
+    }
+    const u32 wm = __reduce_add_sync(kFull, members);
+    if (lane == 0 && wm) atomicAdd(&q.ctr->mcount, (u64)wm);
   }
+  if (finish(b.work, kPhMscan)) mscan_finish(b);
 }
 
 // ----------------------------------------------------------------- mbuild ----
