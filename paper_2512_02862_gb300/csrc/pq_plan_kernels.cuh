@@ -127,7 +127,7 @@ __host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bi
 __host__ __device__ __forceinline__ i64 topk_tile_words(int e) {
   const i64 words = ((1LL << e) + 31) >> 5;
   i64 tw = 32;
-  while (words / tw > 128) tw <<= 1;
+  while ((words + tw - 1) / tw > 128) tw <<= 1;
   return tw;
 }
 __host__ __device__ __forceinline__ i64 topk_parts(int e) {
@@ -182,7 +182,7 @@ __host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
 // slots, or the dense dictionary's slots).
 __host__ __device__ __forceinline__ i64 topk_tile_words_w(i64 words) {
   i64 tw = 32;
-  while (words / tw > 128) tw <<= 1;
+  while ((words + tw - 1) / tw > 128) tw <<= 1;  // at most 128 tiles
   return tw;
 }
 
@@ -1782,11 +1782,9 @@ __device__ __forceinline__ u64 tk_scan(const TopkSrc& src, i64 tw, i64 lt, u32* 
 
 __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
   chain_begin();
-  __shared__ u32 s_ring[kTKW][kTKR];
+  __shared__ __align__(16) u32 s_ring[kTKW][kTKR];
   __shared__ KS s_best[kTKW];
-  __shared__ i64 s_scr[kTKW][64];
-  __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
-  __shared__ int s_mc[kTKW];
+  __shared__ int s_thr_found;
   __shared__ i64 s_t;
   __shared__ bool s_last;
   const i64* pre = b.dyn + 4 * (b.nq + 1);
@@ -1833,31 +1831,34 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
     }
     __syncthreads();
     if (!s_last) continue;
-    // Last tile of the plan: the K best tile maxima (read through L2, where
-    // the other blocks' fenced stores are visible), a quarter per warp, then
-    // the warps' lists merged in shared memory.
+    // Last tile of the plan: rank the tile maxima (all pairs, in shared
+    // memory; the maxima are distinct records, so the ranks are distinct)
+    // and take the K-th best as the threshold.
     __threadfence();
-    const int K = q.k;
-    TopList L;
-    L.bind(s_scr[warp]);
-    L.clear();
-    const int per = (parts + kTKW - 1) / kTKW;
-    const int p0 = min(parts, warp * per), p1 = min(parts, p0 + per);
-    for (int j = p0; j < p1; j += 32) {
-      const int p = j + lane;
-      const bool v = p < p1 && __ldcg(q.tk_c + p) != 0;
-      L.offer(K, v, v ? __ldcg(q.tk_k + p) : 0, v ? __ldcg(q.tk_s + p) : 0);
+    KS* sm = reinterpret_cast<KS*>(&s_ring[0][0]);  // parts <= 128 entries
+    if (threadIdx.x == 0) s_thr_found = 0;
+    for (int i = threadIdx.x; i < parts; i += blockDim.x) {
+      KS x;
+      x.v = __ldcg(q.tk_c + i) != 0;
+      x.k = x.v ? __ldcg(q.tk_k + i) : 0;
+      x.s = x.v ? __ldcg(q.tk_s + i) : 0;
+      sm[i] = x;
     }
-    tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
-    if (warp == 0) {
-      i64 tk = 0, ts = 0;
-      if (L.cnt == K) L.last(K, tk, ts);
-      if (lane == 0) {
-        q.ctr->thr_all = L.cnt < K ? 1 : 0;
-        q.ctr->thr_k = tk;
-        q.ctr->thr_s = ts;
+    __syncthreads();
+    const int K = q.k;
+    for (int i = threadIdx.x; i < parts; i += blockDim.x) {
+      const KS x = sm[i];
+      if (!x.v) continue;
+      int r = 0;
+      for (int j = 0; j < parts; ++j) r += ks_before(sm[j], x);
+      if (r == K - 1) {
+        q.ctr->thr_k = x.k;
+        q.ctr->thr_s = x.s;
+        s_thr_found = 1;
       }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) q.ctr->thr_all = s_thr_found ? 0 : 1;
   }
   finish(b.work, kPhTopk);
 }

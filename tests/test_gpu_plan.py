@@ -127,6 +127,22 @@ def test_duplicate_build_keys(ctx, stream):
     assert_same(got, want)
 
 
+@pytest.mark.parametrize("n_m", [131_072, 131_073, 131_104])
+def test_topk_tiles_at_the_bound(ctx, stream, n_m):
+    """Distinct member counts just above 128 top-k tiles of 32 bitmap words:
+    the tiling must stay within 128 tiles (the tile arrays' size)."""
+    D, M, F = datagen.make(2000, n_m, 300_000, seed=11)
+    ops = dict(d_op="all", m_op="all", f_op="all")
+    want = oracle_plan(D, M, F, seg=0, mc=0, fc=0, k=10, **ops)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=0, m_date_lt=0, f_date_gt=0, k=10,
+                                        flags=pq.PQ_PLAN_NO_GRAPH, **ops))
+    assert_same(got, want, str(n_m))
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
 def remap_keys(D, M, F, seed, sparse=True, shift=0):
     """The same plan with the keys renamed: M keys to distinct random int64
     values of both signs (sparse: no key-range bitmap, hash tables) or to
