@@ -614,15 +614,26 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
   const Batch b = make_batch(ctx, ws, n, L);
 
-  auto chain = [&]() -> pq_status {
+  // The chain of phases.  With a side stream (graph capture), the rank and
+  // copy-count passes of the M dictionary run beside the F scan, which only
+  // tests the M bitmap; the F probe waits for both.
+  auto chain = [&](cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) -> pq_status {
     PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
     for (auto& c : clears) PQ_CUDA(ctx, cudaMemsetAsync(c.first, 0, c.second, s));
     for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
       // Phases only plans with key lists need.
       if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
       if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;
-      pq_status st = launch_phase(ctx, ph, b, vec, s, tmax[ph], list_m, bm_dm);
+      cudaStream_t on = s;
+      if (side && ph == kPhaseMrank) {
+        PQ_CUDA(ctx, cudaEventRecord(fork, s));
+        PQ_CUDA(ctx, cudaStreamWaitEvent(side, fork, 0));
+      }
+      if (side && (ph == kPhaseMrank || ph == kPhaseMdup)) on = side;
+      if (side && ph == kPhaseF) PQ_CUDA(ctx, cudaStreamWaitEvent(s, join, 0));
+      pq_status st = launch_phase(ctx, ph, b, vec, on, tmax[ph], list_m, bm_dm);
       if (st != PQ_OK) return st;
+      if (side && ph == kPhaseMdup) PQ_CUDA(ctx, cudaEventRecord(join, side));
     }
     return PQ_OK;
   };
@@ -631,15 +642,23 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   if (graphable) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    bool captured = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool captured = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     const int64_t launches0 = ctx->launches.load();
     if (captured) {
-      st = chain();
+      st = chain(side, fork, join);
       cudaError_t e = cudaStreamEndCapture(s, &graph);
       captured = st == PQ_OK && e == cudaSuccess &&
                  cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
       if (graph) cudaGraphDestroy(graph);
     }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
     cudaGetLastError();
     if (captured) {
       GraphEntry e;
@@ -677,7 +696,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       return st;
     }
   }
-  st = chain();
+  st = chain(nullptr, nullptr, nullptr);
   if (st == PQ_OK) {
     for (int i = 0; i < n; ++i)
       if (R[i].cache_new && R[i].cache) cudaEventRecord(R[i].cache->ready, s);

@@ -1231,13 +1231,25 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
       __shared__ u32 s_carry;
       if (threadIdx.x == 0) s_carry = 0;
       __syncthreads();
-      for (i64 t0 = 0; t0 < tiles; t0 += blockDim.x) {
-        const i64 t = t0 + threadIdx.x;
-        const u32 v = t < tiles ? __ldcg(tdir + t) : 0u;
-        const u32 ex = block_exclusive_sum(v);
-        if (t < tiles) tdir[t] = s_carry + ex;
+      // Each thread takes 16 consecutive totals per pass (loaded together),
+      // so a pass costs one round trip to memory.
+      for (i64 t0 = 0; t0 < tiles; t0 += (i64)blockDim.x * 16) {
+        const i64 tb = t0 + (i64)threadIdx.x * 16;
+        u32 v[16], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          v[j] = tb + j < tiles ? __ldcg(tdir + tb + j) : 0u;
+          sum += v[j];
+        }
+        const u32 ex = block_exclusive_sum(sum);
+        u32 run = s_carry + ex;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (tb + j < tiles) tdir[tb + j] = run;
+          run += v[j];
+        }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry += ex + v;
+        if (threadIdx.x == blockDim.x - 1) s_carry += ex + sum;
         __syncthreads();
       }
       if (threadIdx.x == 0) {
