@@ -550,7 +550,8 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
                 total, ctx->arena.largest_free());
   }
   bool any_build = false, vec = true, list_d = false, list_m = false, bm_dm = true;
-  std::vector<std::pair<void*, size_t>> clears;  // static bitmaps to zero first
+  std::vector<std::pair<void*, size_t>> clears;  // static D bitmaps to zero first
+  std::vector<std::pair<void*, size_t>> m_clears;  // static M bitmaps: the D scan clears them
   i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
   std::vector<char> host(L.upload_bytes());
   PlanDev* descs = (PlanDev*)host.data();
@@ -578,7 +579,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     if (r.builds && d.d_static)
       clears.push_back({(char*)d.dset_tag + table_layout(r.e_d, false).keybm,
                         (size_t)((d.d_sb + 127) / 128 * 16)});
-    if (d.m_static) clears.push_back({(void*)d.ht_tag, (size_t)dense_layout(0, d.m_sb).tdir});
+    if (d.m_static) m_clears.push_back({(void*)d.ht_tag, (size_t)dense_layout(0, d.m_sb).tdir});
     list_d = list_d || (r.builds && !d.d_static);
     list_m = list_m || !d.m_static;
     // The D-set is a bitmap for certain when it is built here from a static
@@ -598,7 +599,8 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     }
     tmax[kPhaseMfill] += fill_tiles(r.e_m, true, 32ULL << r.e_m);
     tmax[kPhaseMbuild] += (r.n_m + kTB - 1) / kTB;
-    tmax[kPhaseMrank] += ((32LL << r.e_m) / 512 + kRankTile - 1) / kRankTile;
+    const u64 mbits = d.m_static ? d.m_sb : (32ULL << r.e_m);  // bound on the M bitmap
+    tmax[kPhaseMrank] += (i64)(((mbits + 511) / 512 + kRankTile - 1) / kRankTile);
     tmax[kPhaseMdup] += (r.n_m + kTB - 1) / kTB;
     tmax[kPhaseTopk] += topk_parts(r.e_m);
   }
@@ -612,7 +614,9 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
 
   for (auto ev : waits) PQ_CUDA(ctx, cudaStreamWaitEvent(s, ev, 0));
   PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
-  const Batch b = make_batch(ctx, ws, n, L);
+  Batch b = make_batch(ctx, ws, n, L);
+  b.clear_m = any_build ? 1 : 0;  // else no D scan runs: the memsets clear them
+  if (!any_build) clears.insert(clears.end(), m_clears.begin(), m_clears.end());
 
   // The chain of phases.  With a side stream (graph capture), the rank and
   // copy-count passes of the M dictionary run beside the F scan, which only

@@ -300,7 +300,7 @@ struct Ovr {
 struct Batch {
   PlanDev* q;
   int nq;
-  int pad;
+  int clear_m;    // the D scan clears the plans' static M bitmaps
   const i64* tD;  // static tile prefixes [nq + 1]
   const i64* tM;
   const i64* tF;
@@ -615,6 +615,16 @@ __global__ void __launch_bounds__(256) k_plan_dscan(Batch b) {
   const i64 total = ov ? b.ov.tiles : b.tD[b.nq];
   const int lane = threadIdx.x & 31;
   const u64 strm = policy_stream();
+  if (b.clear_m) {  // the M scan sets these bits next
+    const i64 nt = (i64)gridDim.x * blockDim.x, tid = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int qi = 0; qi < b.nq; ++qi) {
+      const PlanDev& q = b.q[qi];
+      if (!q.m_static) continue;
+      int4* z = reinterpret_cast<int4*>(q.ht_tag);  // dense layout: bitmap at 0
+      const i64 units = (i64)(dense_layout(0, q.m_sb).tdir / 16);
+      for (i64 u = tid; u < units; u += nt) z[u] = make_int4(0, 0, 0, 0);
+    }
+  }
   WarpClaim wc;
   while (true) {
     const i64 t = wc.next(b.work, kPhDscan);
@@ -945,11 +955,10 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
 }
 
 // Every plan of the batch has a static M bitmap and a D-set bitmap: each
-// lane keeps its own 4 rows per iteration in registers, no ring.  date is
-// read two iterations ahead, dref one ahead (4-row groups with a date hit),
-// the D bitmap words are loaded when the drefs arrive and tested one
-// iteration later; then the members' keys are loaded, and one iteration
-// after that their bits are set (reductions nobody waits for).
+// lane keeps its own 4 rows per step in registers, no ring.  date and dref
+// are read two steps ahead, the D bitmap words are loaded when they arrive
+// and tested one step later; then the members' keys are loaded, and two
+// steps after that their bits are set (reductions nobody waits for).
 template <bool VEC>
 __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
   chain_begin();
@@ -969,6 +978,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
     const u64* dhdr = reinterpret_cast<const u64*>(q.dset_log2);
     const u64 d_umin = dhdr[1], d_bits = dhdr[2];
     const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
+    const u32* dt_keybm = dt.keybm;
     u32* sbm = reinterpret_cast<u32*>(q.ht_tag);  // dense layout: bm at 0
     const u64 m_su = q.m_su;
     const Pred32 pm = to32(q.pm);
@@ -995,52 +1005,48 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
         ++members;
       }
     } else {
-      const int iters = (int)((lim + 127) / 128);
-      int4 dB = load_i32x4<VEC>(pdate, r0, lim - r0, strm);
-      int4 dC = iters > 1 ? load_i32x4<VEC>(pdate, 128 + r0, lim - 128 - r0, strm)
-                          : make_int4(0, 0, 0, 0);
-      u32 hA = pass4(pm, dB, lim - r0);
-      int4 rA = hA ? load_i32x4<VEC>(pdref, r0, lim - r0, strm) : make_int4(0, 0, 0, 0);
-      dB = dC;
-      if (iters > 2) dC = load_i32x4<VEC>(pdate, 256 + r0, lim - 256 - r0, strm);
-      BmStage wP;
-      wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
-      wP.sh = 0;
-      u32 mP = 0;  // members of iteration it - 2, keys in kP
-      i64 kP[4] = {0, 0, 0, 0};
-      for (int it = 0; it < iters; ++it) {
-        const int rel1 = (it + 1) * 128 + r0;
-        u32 hB = 0;
-        int4 rB = make_int4(0, 0, 0, 0);
-        if (it + 1 < iters) {
-          hB = pass4(pm, dB, lim - rel1);
-          if (hB) rB = load_i32x4<VEC>(pdref, rel1, lim - rel1, strm);
-        }
-        dB = dC;
-        if (it + 3 < iters) {
-          const int rel3 = (it + 3) * 128 + r0;
-          dC = load_i32x4<VEC>(pdate, rel3, lim - rel3, strm);
-        }
-        const int dr[4] = {rA.x, rA.y, rA.z, rA.w};
-        BmStage wN;
-        bm_issue(wN, dt.keybm, d_umin, d_bits, hA, dr, keep);
-        u32 mN = 0;  // members of iteration it - 1
-        i64 kN[4] = {0, 0, 0, 0};
-        if (it > 0) {
-          mN = bm_hits(wP);
-          const int rel = (it - 1) * 128 + r0;
-          if (mN) load_i64x4<VEC>(pkey, rel, lim - rel, mN, strm, kN);
-        }
-        set_bits(mP, kP);
-        wP = wN;
-        hA = hB;
-        rA = rB;
-        mP = mN;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) kP[s] = kN[s];
+      // Slot p = it % 2 holds date and dref of step it (read two steps
+      // ahead, for every row); the key slots hold the member keys of two
+      // earlier steps, read one step after their bitmap test and used two
+      // steps later.  The loop is unrolled by two so that slots keep their
+      // registers.
+      const int iters = (lim + 127) / 128;
+      int4 dt0 = load_i32x4<VEC>(pdate, r0, lim - r0, strm);
+      int4 dr0 = load_i32x4<VEC>(pdref, r0, lim - r0, strm);
+      int4 dt1 = make_int4(0, 0, 0, 0), dr1 = make_int4(0, 0, 0, 0);
+      if (iters > 1) {
+        dt1 = load_i32x4<VEC>(pdate, 128 + r0, lim - 128 - r0, strm);
+        dr1 = load_i32x4<VEC>(pdref, 128 + r0, lim - 128 - r0, strm);
       }
-      set_bits(mP, kP);
-      const u32 mL = bm_hits(wP);
+      BmStage W;  // D-bitmap words of the previous step's drefs
+      W.w[0] = W.w[1] = W.w[2] = W.w[3] = 0;
+      W.sh = 0;
+      u32 km0 = 0, km1 = 0;  // member masks of the key slots
+      i64 k0[4] = {0, 0, 0, 0}, k1[4] = {0, 0, 0, 0};
+      auto step = [&](int it, int4& dt, int4& dr, u32& km, i64 (&kk)[4]) {
+        set_bits(km, kk);  // members of step it - 3
+        km = bm_hits(W);   // members of step it - 1: read their keys
+        if (km) {
+          const int rel = (it - 1) * 128 + r0;
+          load_i64x4<VEC>(pkey, rel, lim - rel, km, strm, kk);
+        }
+        const int rel0 = it * 128 + r0;
+        const u32 h = pass4(pm, dt, lim - rel0);
+        const int drv[4] = {dr.x, dr.y, dr.z, dr.w};
+        bm_issue(W, dt_keybm, d_umin, d_bits, h, drv, keep);
+        if (it + 2 < iters) {
+          const int rel2 = rel0 + 256;
+          dt = load_i32x4<VEC>(pdate, rel2, lim - rel2, strm);
+          dr = load_i32x4<VEC>(pdref, rel2, lim - rel2, strm);
+        }
+      };
+      for (int it = 0; it < iters; it += 2) {
+        step(it, dt0, dr0, km1, k1);
+        if (it + 1 < iters) step(it + 1, dt1, dr1, km0, k0);
+      }
+      set_bits(km0, k0);
+      set_bits(km1, k1);
+      const u32 mL = bm_hits(W);
       i64 kL[4] = {0, 0, 0, 0};
       const int relL = (iters - 1) * 128 + r0;
       if (mL) load_i64x4<VEC>(pkey, relL, lim - relL, mL, strm, kL);
