@@ -91,7 +91,7 @@ static void plan_static(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, cudaStre
     const Column& c = t->cols[0];
     if (!c.has_range && (capturing || !ensure_range(ctx, t, 0, s))) return false;
     const u64 span = c.umax - c.umin;  // bits - 1
-    if (c.umax < c.umin || span >= (32ULL << e)) return false;
+    if (c.umax < c.umin || span >= (32ULL << e) || span >= kMaxBmBits) return false;
     *su = c.umin;
     *sb = span + 1;
     return true;

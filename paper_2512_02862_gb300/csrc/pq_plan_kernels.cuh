@@ -77,14 +77,16 @@ __device__ __forceinline__ u64 ukey(i64 k) { return (u64)k ^ 0x8000000000000000U
 struct RangeBits {
   u64 umin, bits;
 };
+// Largest key-range bitmap, in bits (bitmap word indices fit in 32 bits).
+constexpr u64 kMaxBmBits = 1ULL << 37;
 // Choose a bitmap for `count` keys spanning [~nmin, umax] (ukeys) in a table
-// of 2^e slots: used when the span is below 32 * 2^e bits.
+// of 2^e slots: used when the span is below 32 * 2^e bits (and kMaxBmBits).
 __device__ __forceinline__ RangeBits range_bits(i64 count, u64 nmin, u64 umax, int e) {
   RangeBits r{0, 0};
   if (count <= 0) return r;
   const u64 umin = ~nmin;
   const u64 span = umax - umin;  // bits - 1
-  if (umax >= umin && span < (32ULL << e)) {
+  if (umax >= umin && span < (32ULL << e) && span < kMaxBmBits) {
     r.umin = umin;
     r.bits = span + 1;
   }
@@ -222,6 +224,26 @@ __device__ __forceinline__ void bm_issue(BmStage& st, const u32* bm, u64 umin, u
     }
     st.w[s] = w;
     st.sh |= (u32)(idx & 31) << (5 * s);
+  }
+}
+// bm_issue for a bitmap that exists (bits > 0), with fewer instructions:
+// ubase = umin xor 2^63, so that key - ubase (mod 2^64) is the key's bit
+// index, and the word index is the low 32 bits of idx >> 5 (in range,
+// idx < bits <= kMaxBmBits).
+template <typename K>
+__device__ __forceinline__ void bm_issue_fast(BmStage& st, const u32* bm, u64 ubase, u64 bits,
+                                              u32 valid, const K k[4], u64 keep) {
+  st.sh = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const u64 idx = (u64)(i64)k[s] - ubase;
+    u32 w = 0;
+    if (((valid >> s) & 1u) && idx < bits) {
+      const u32 wi = (u32)(idx >> 5);
+      asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(w) : "l"(bm + wi), "l"(keep));
+    }
+    st.w[s] = w;
+    st.sh |= ((u32)idx & 31u) << (5 * s);
   }
 }
 __device__ __forceinline__ u32 bm_hits(const BmStage& st) {
@@ -1033,7 +1055,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
         const int rel0 = it * 128 + r0;
         const u32 h = pass4(pm, dt, lim - rel0);
         const int drv[4] = {dr.x, dr.y, dr.z, dr.w};
-        bm_issue(W, dt_keybm, d_umin, d_bits, h, drv, keep);
+        bm_issue_fast(W, dt_keybm, d_umin ^ 0x8000000000000000ULL, d_bits, h, drv, keep);
         if (it + 2 < iters) {
           const int rel2 = rel0 + 256;
           dt = load_i32x4<VEC>(pdate, rel2, lim - rel2, strm);
@@ -1531,7 +1553,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
-  const i64 r0 = lane * 4;
+  const int r0 = lane * 4;
   int cq = -1;  // plan of the rows in the ring
   u32 hh = 0, ht = 0;
   auto flush = [&](u32 cnt) {  // cnt entries from hh to plan cq's hit list
@@ -1554,19 +1576,20 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
       cq = qi;
       hh = ht = 0;
     }
-    const i64* f_mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
-    const int* f_date = ov ? (const int*)b.ov.p[3] : q.f_date;
     const i64 n = ov ? b.ov.n : q.n_f;
     const int tile = ov ? b.ov.tile : q.f_tile;
     const i64 base = (t - (ov ? 0 : b.tF[qi])) * tile;
+    // The tile's rows, addressed with 32-bit offsets.
+    const i64* f_mkey = (ov ? (const i64*)b.ov.p[0] : q.f_mkey) + base;
+    const int* f_date = (ov ? (const int*)b.ov.p[3] : q.f_date) + base;
     const u64 bm_umin = q.ctr->m_umin, bm_bits = q.ctr->m_bits;
     const u32* bm = bm_bits ? reinterpret_cast<const u32*>(
                                   reinterpret_cast<const char*>(q.ht_tag) +
                                   dense_layout((i64)q.ctr->mcount, bm_bits).bm)
                             : nullptr;
     const Pred32 pf = to32(q.pf);
-    const i64 lim = min(n - base, (i64)tile);
-    const int iters = (int)((lim + 127) / 128);
+    const int lim = (int)min(n - base, (i64)tile);
+    const int iters = (lim + 127) / 128;
     auto append_hits = [&](u32 hits, int it) {
       if (__any_sync(kFull, hits)) {
         __syncwarp();
@@ -1577,32 +1600,33 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
         if (ht - hh >= 512) flush(512);
       }
     };
-    int4 dB = load_i32x4<VEC>(f_date, base + r0, lim - r0, strm);
-    int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, base + 128 + r0, lim - 128 - r0, strm)
+    int4 dB = load_i32x4<VEC>(f_date, r0, lim - r0, strm);
+    int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, 128 + r0, lim - 128 - r0, strm)
                         : make_int4(0, 0, 0, 0);
     u32 bA = pass4(pf, dB, lim - r0);
     i64 mA[4] = {0, 0, 0, 0};
-    if (bA) load_i64x4<VEC>(f_mkey, base + r0, lim - r0, bA, strm, mA);
+    if (bA) load_i64x4<VEC>(f_mkey, r0, lim - r0, bA, strm, mA);
     dB = dC;
-    if (iters > 2) dC = load_i32x4<VEC>(f_date, base + 256 + r0, lim - 256 - r0, strm);
+    if (iters > 2) dC = load_i32x4<VEC>(f_date, 256 + r0, lim - 256 - r0, strm);
     BmStage wP;
     wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
     wP.sh = 0;
     for (int it = 0; it < iters; ++it) {
-      const i64 rel1 = (it + 1) * 128 + r0;
+      const int rel1 = (it + 1) * 128 + r0;
       u32 bB = 0;
       i64 mB[4] = {0, 0, 0, 0};
       if (it + 1 < iters) {
         bB = pass4(pf, dB, lim - rel1);
-        if (bB) load_i64x4<VEC>(f_mkey, base + rel1, lim - rel1, bB, strm, mB);
+        if (bB) load_i64x4<VEC>(f_mkey, rel1, lim - rel1, bB, strm, mB);
       }
       dB = dC;
       if (it + 3 < iters) {
-        const i64 rel3 = (it + 3) * 128 + r0;
-        dC = load_i32x4<VEC>(f_date, base + rel3, lim - rel3, strm);
+        const int rel3 = (it + 3) * 128 + r0;
+        dC = load_i32x4<VEC>(f_date, rel3, lim - rel3, strm);
       }
       BmStage wN;
-      bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
+      if (bm_bits) bm_issue_fast(wN, bm, bm_umin ^ 0x8000000000000000ULL, bm_bits, bA, mA, keep);
+      else bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
       if (it > 0) append_hits(bm_hits(wP), it - 1);
       wP = wN;
       bA = bB;
