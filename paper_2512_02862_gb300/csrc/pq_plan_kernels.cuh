@@ -26,6 +26,8 @@
 // policy and hash-table probes with evict-last, so the tables stay in L2
 // while the columns stream past.
 #pragma once
+#include <type_traits>
+
 #include "../../include/pq.h"
 #include "pq_dev.cuh"
 #include "pq_topk.cuh"
@@ -1600,40 +1602,62 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
         if (ht - hh >= 512) flush(512);
       }
     };
-    int4 dB = load_i32x4<VEC>(f_date, r0, lim - r0, strm);
-    int4 dC = iters > 1 ? load_i32x4<VEC>(f_date, 128 + r0, lim - 128 - r0, strm)
-                        : make_int4(0, 0, 0, 0);
-    u32 bA = pass4(pf, dB, lim - r0);
-    i64 mA[4] = {0, 0, 0, 0};
-    if (bA) load_i64x4<VEC>(f_mkey, r0, lim - r0, bA, strm, mA);
-    dB = dC;
-    if (iters > 2) dC = load_i32x4<VEC>(f_date, 256 + r0, lim - 256 - r0, strm);
-    BmStage wP;
-    wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
-    wP.sh = 0;
-    for (int it = 0; it < iters; ++it) {
-      const int rel1 = (it + 1) * 128 + r0;
-      u32 bB = 0;
-      i64 mB[4] = {0, 0, 0, 0};
-      if (it + 1 < iters) {
-        bB = pass4(pf, dB, lim - rel1);
-        if (bB) load_i64x4<VEC>(f_mkey, rel1, lim - rel1, bB, strm, mB);
-      }
+    // The step loop, compiled for full tiles of aligned columns (no row
+    // limits) and for a bitmap that exists, and in general.
+    auto run = [&](auto full_c, auto fast_c) {
+      constexpr bool FULL = decltype(full_c)::value, FAST = decltype(fast_c)::value;
+      auto ld_d = [&](int e0) -> int4 {
+        return FULL ? ld_stream_v4(f_date + e0, strm) : load_i32x4<VEC>(f_date, e0, lim - e0, strm);
+      };
+      auto ld_k = [&](int e0, u32 bits, i64 v[4]) {
+        if (FULL) {
+          const longlong2 x = ld_stream_v2(f_mkey + e0, strm), y = ld_stream_v2(f_mkey + e0 + 2, strm);
+          v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+        } else {
+          load_i64x4<VEC>(f_mkey, e0, lim - e0, bits, strm, v);
+        }
+      };
+      auto p4 = [&](int4 d, int e0) { return pass4(pf, d, FULL ? 4 : lim - e0); };
+      int4 dB = ld_d(r0);
+      int4 dC = iters > 1 ? ld_d(128 + r0) : make_int4(0, 0, 0, 0);
+      u32 bA = p4(dB, r0);
+      i64 mA[4] = {0, 0, 0, 0};
+      if (bA) ld_k(r0, bA, mA);
       dB = dC;
-      if (it + 3 < iters) {
-        const int rel3 = (it + 3) * 128 + r0;
-        dC = load_i32x4<VEC>(f_date, rel3, lim - rel3, strm);
-      }
-      BmStage wN;
-      if (bm_bits) bm_issue_fast(wN, bm, bm_umin ^ 0x8000000000000000ULL, bm_bits, bA, mA, keep);
-      else bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
-      if (it > 0) append_hits(bm_hits(wP), it - 1);
-      wP = wN;
-      bA = bB;
+      if (iters > 2) dC = ld_d(256 + r0);
+      BmStage wP;
+      wP.w[0] = wP.w[1] = wP.w[2] = wP.w[3] = 0;
+      wP.sh = 0;
+      for (int it = 0; it < iters; ++it) {
+        const int rel1 = (it + 1) * 128 + r0;
+        u32 bB = 0;
+        i64 mB[4] = {0, 0, 0, 0};
+        if (it + 1 < iters) {
+          bB = p4(dB, rel1);
+          if (bB) ld_k(rel1, bB, mB);
+        }
+        dB = dC;
+        if (it + 3 < iters) dC = ld_d((it + 3) * 128 + r0);
+        BmStage wN;
+        if (FAST) bm_issue_fast(wN, bm, bm_umin ^ 0x8000000000000000ULL, bm_bits, bA, mA, keep);
+        else bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
+        if (it > 0) append_hits(bm_hits(wP), it - 1);
+        wP = wN;
+        bA = bB;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) mA[s] = mB[s];
+        for (int s = 0; s < 4; ++s) mA[s] = mB[s];
+      }
+      append_hits(bm_hits(wP), iters - 1);
+    };
+    using T = std::true_type;
+    using F = std::false_type;
+    if (VEC && lim == iters * 128) {
+      if (bm_bits) run(T{}, T{});
+      else run(T{}, F{});
+    } else {
+      if (bm_bits) run(F{}, T{});
+      else run(F{}, F{});
     }
-    append_hits(bm_hits(wP), iters - 1);
   }
   if (cq >= 0 && ht != hh) flush(ht - hh);
   if (finish(b.work, kPhFscan)) {
