@@ -1035,46 +1035,59 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
       // steps later.  The loop is unrolled by two so that slots keep their
       // registers.
       const int iters = (lim + 127) / 128;
-      int4 dt0 = load_i32x4<VEC>(pdate, r0, lim - r0, strm);
-      int4 dr0 = load_i32x4<VEC>(pdref, r0, lim - r0, strm);
-      int4 dt1 = make_int4(0, 0, 0, 0), dr1 = make_int4(0, 0, 0, 0);
-      if (iters > 1) {
-        dt1 = load_i32x4<VEC>(pdate, 128 + r0, lim - 128 - r0, strm);
-        dr1 = load_i32x4<VEC>(pdref, 128 + r0, lim - 128 - r0, strm);
-      }
-      BmStage W;  // D-bitmap words of the previous step's drefs
-      W.w[0] = W.w[1] = W.w[2] = W.w[3] = 0;
-      W.sh = 0;
-      u32 km0 = 0, km1 = 0;  // member masks of the key slots
-      i64 k0[4] = {0, 0, 0, 0}, k1[4] = {0, 0, 0, 0};
-      auto step = [&](int it, int4& dt, int4& dr, u32& km, i64 (&kk)[4]) {
-        set_bits(km, kk);  // members of step it - 3
-        km = bm_hits(W);   // members of step it - 1: read their keys
-        if (km) {
-          const int rel = (it - 1) * 128 + r0;
-          load_i64x4<VEC>(pkey, rel, lim - rel, km, strm, kk);
+      // Compiled for full tiles of aligned columns (no row limits) and in
+      // general.
+      auto run = [&](auto full_c) {
+        constexpr bool FULL = decltype(full_c)::value;
+        auto ld4 = [&](const int* p, int e0) -> int4 {
+          return FULL ? ld_stream_v4(p + e0, strm) : load_i32x4<VEC>(p, e0, lim - e0, strm);
+        };
+        auto ldk = [&](int e0, u32 bits, i64 v[4]) {
+          if (FULL) {
+            const longlong2 x = ld_stream_v2(pkey + e0, strm), y = ld_stream_v2(pkey + e0 + 2, strm);
+            v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+          } else {
+            load_i64x4<VEC>(pkey, e0, lim - e0, bits, strm, v);
+          }
+        };
+        int4 dt0 = ld4(pdate, r0);
+        int4 dr0 = ld4(pdref, r0);
+        int4 dt1 = make_int4(0, 0, 0, 0), dr1 = make_int4(0, 0, 0, 0);
+        if (iters > 1) {
+          dt1 = ld4(pdate, 128 + r0);
+          dr1 = ld4(pdref, 128 + r0);
         }
-        const int rel0 = it * 128 + r0;
-        const u32 h = pass4(pm, dt, lim - rel0);
-        const int drv[4] = {dr.x, dr.y, dr.z, dr.w};
-        bm_issue_fast(W, dt_keybm, d_umin ^ 0x8000000000000000ULL, d_bits, h, drv, keep);
-        if (it + 2 < iters) {
-          const int rel2 = rel0 + 256;
-          dt = load_i32x4<VEC>(pdate, rel2, lim - rel2, strm);
-          dr = load_i32x4<VEC>(pdref, rel2, lim - rel2, strm);
+        BmStage W;  // D-bitmap words of the previous step's drefs
+        W.w[0] = W.w[1] = W.w[2] = W.w[3] = 0;
+        W.sh = 0;
+        u32 km0 = 0, km1 = 0;  // member masks of the key slots
+        i64 k0[4] = {0, 0, 0, 0}, k1[4] = {0, 0, 0, 0};
+        auto step = [&](int it, int4& dt, int4& dr, u32& km, i64 (&kk)[4]) {
+          set_bits(km, kk);  // members of step it - 3
+          km = bm_hits(W);   // members of step it - 1: read their keys
+          if (km) ldk((it - 1) * 128 + r0, km, kk);
+          const int rel0 = it * 128 + r0;
+          const u32 h = pass4(pm, dt, FULL ? 4 : lim - rel0);
+          const int drv[4] = {dr.x, dr.y, dr.z, dr.w};
+          bm_issue_fast(W, dt_keybm, d_umin ^ 0x8000000000000000ULL, d_bits, h, drv, keep);
+          if (it + 2 < iters) {
+            dt = ld4(pdate, rel0 + 256);
+            dr = ld4(pdref, rel0 + 256);
+          }
+        };
+        for (int it = 0; it < iters; it += 2) {
+          step(it, dt0, dr0, km1, k1);
+          if (it + 1 < iters) step(it + 1, dt1, dr1, km0, k0);
         }
+        set_bits(km0, k0);
+        set_bits(km1, k1);
+        const u32 mL = bm_hits(W);
+        i64 kL[4] = {0, 0, 0, 0};
+        if (mL) ldk((iters - 1) * 128 + r0, mL, kL);
+        set_bits(mL, kL);
       };
-      for (int it = 0; it < iters; it += 2) {
-        step(it, dt0, dr0, km1, k1);
-        if (it + 1 < iters) step(it + 1, dt1, dr1, km0, k0);
-      }
-      set_bits(km0, k0);
-      set_bits(km1, k1);
-      const u32 mL = bm_hits(W);
-      i64 kL[4] = {0, 0, 0, 0};
-      const int relL = (iters - 1) * 128 + r0;
-      if (mL) load_i64x4<VEC>(pkey, relL, lim - relL, mL, strm, kL);
-      set_bits(mL, kL);
+      if (VEC && lim == iters * 128) run(std::true_type{});
+      else run(std::false_type{});
     }
     const u32 wm = __reduce_add_sync(kFull, members);
     if (lane == 0 && wm) atomicAdd(&q.ctr->mcount, (u64)wm);
