@@ -182,8 +182,16 @@ typedef struct pq_source {
 
 typedef enum pq_load_mode {
   PQ_RESIDENT = 0,    /* copy into the arena now (device sources are borrowed) */
-  PQ_STREAMING = 1    /* keep on the host; plans stream it in chunks of
+  PQ_STREAMING = 1,   /* keep on the host; plans stream it in chunks of
                          `chunk_bytes` through the ingest ring (Sec. 3.2, 4.2) */
+  PQ_MAPPED = 2       /* keep in page-locked host memory (cudaHostAlloc'd or
+                         cudaHostRegister'ed; device sources are borrowed) and
+                         let the plan kernels read it in place over the host
+                         link: a plan runs like one on resident tables and
+                         moves only the bytes its kernels load (the
+                         late-materialised columns only for the rows that
+                         need them).  Pageable memory and files are refused
+                         with PQ_ERR_INVALID_ARG. */
 } pq_load_mode;
 
 /* Describe (and for PQ_RESIDENT, copy in) a table of `ncols` columns of
@@ -192,8 +200,8 @@ typedef enum pq_load_mode {
 pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t nrows,
                           int mode, pq_table** out, void* stream);
 
-/* Number of rows of a table, and the device pointer of a resident column
- * (NULL for a streaming table). */
+/* Number of rows of a table, and the device-accessible pointer of a resident
+ * or mapped column (NULL for a streaming table). */
 int64_t pq_table_rows(const pq_table* t);
 const void* pq_table_column(const pq_table* t, int col);
 
@@ -320,6 +328,7 @@ typedef struct pq_result {
   int64_t sums[PQ_MAX_K];
   int32_t status;             /* pq_status of this plan's device work          */
   int32_t reserved;
+  int64_t hits;               /* F rows that joined (the probe's inputs)       */
 } pq_result;
 
 /* Run one plan on `stream`.  Resident tables run as one chain of kernels with

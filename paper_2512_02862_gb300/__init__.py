@@ -34,7 +34,7 @@ PQ_ERR_IO, PQ_ERR_TIMEOUT, PQ_ERR_OVERFLOW, PQ_ERR_BUSY, PQ_ERR_RESERVED_KEY = 5
 PQ_INT8, PQ_INT32, PQ_INT64 = 1, 2, 3
 CMP = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5, "all": 6}
 PQ_SRC_DEVICE, PQ_SRC_HOST, PQ_SRC_FILE = 0, 1, 2
-PQ_RESIDENT, PQ_STREAMING = 0, 1
+PQ_RESIDENT, PQ_STREAMING, PQ_MAPPED = 0, 1, 2
 PQ_PLAN_PARTITIONED, PQ_PLAN_CACHE_DSET, PQ_PLAN_NO_GRAPH = 1, 2, 4
 
 
@@ -74,7 +74,8 @@ class pq_plan(Structure):
 
 class pq_result(Structure):
     _fields_ = [("n", c_int64), ("ngroups", c_int64), ("keys", c_int64 * PQ_MAX_K),
-                ("sums", c_int64 * PQ_MAX_K), ("status", c_int32), ("reserved", c_int32)]
+                ("sums", c_int64 * PQ_MAX_K), ("status", c_int32), ("reserved", c_int32),
+                ("hits", c_int64)]
 
     def as_dict(self):
         n = int(self.n)

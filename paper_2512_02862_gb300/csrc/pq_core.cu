@@ -457,7 +457,7 @@ static pq_status copy_host_to_device(pq_ctx* ctx, void* dst, const pqh::Column& 
 pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t nrows, int mode,
                           pq_table** out, void* stream) {
   if (!ctx || !out || !srcs || ncols <= 0 || ncols > 64 || nrows < 0 ||
-      (mode != PQ_RESIDENT && mode != PQ_STREAMING))
+      (mode != PQ_RESIDENT && mode != PQ_STREAMING && mode != PQ_MAPPED))
     return fail(ctx, PQ_ERR_INVALID_ARG, "pq_load_columns: bad arguments");
   *out = nullptr;
   cudaStream_t s = S(stream);
@@ -482,9 +482,16 @@ pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t
         c.pinned = cudaPointerGetAttributes(&at, src.ptr) == cudaSuccess &&
                    at.type == cudaMemoryTypeHost;
         cudaGetLastError();
+        if (mode == PQ_MAPPED) {  // read in place by the kernels
+          if (nrows && (!c.pinned || !at.devicePointer))
+            return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: mapped tables need page-locked host memory", i);
+          c.dev = nrows ? at.devicePointer : src.ptr;
+        }
         break;
       }
       case PQ_SRC_FILE:
+        if (mode == PQ_MAPPED)
+          return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: files cannot be mapped", i);
         if (!src.path) return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: no path", i);
         c.path = src.path;
         c.src.path = c.path.c_str();

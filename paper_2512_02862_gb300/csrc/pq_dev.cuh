@@ -165,6 +165,13 @@ __device__ __forceinline__ int4 ld_stream_v4(const void* ptr, u64 pol) {
                : "l"(ptr), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int2 ld_stream_v2i(const void* ptr, u64 pol) {
+  int2 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ longlong2 ld_stream_v2(const void* ptr, u64 pol) {
   longlong2 v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s64 {%0, %1}, [%2], %3;"

@@ -157,6 +157,8 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
                          d.f_mkey, d.f_price, d.f_disc, d.f_date};
   d.vec = 1;
   for (auto q : ptrs) d.vec &= (((uintptr_t)q) & 15) == 0;
+  d.m_pair = p.M->mode == PQ_MAPPED ? 1 : 0;
+  d.f_pair = p.F->mode == PQ_MAPPED ? 1 : 0;
   return PQ_OK;
 }
 

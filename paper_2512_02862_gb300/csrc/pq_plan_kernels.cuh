@@ -67,6 +67,7 @@ struct QCtr {
   u64 d_fill_off, d_fill_units, m_fill_off, m_fill_units;
   u64 m_distinct;  // dense M dictionary: distinct keys (the rank pass)
   u64 hcount;      // F rows in the hit list
+  u64 hits_total;  // F rows that joined, over all chunks
   i64 hp_tile;     // hits per warp tile of the probe
 };
 
@@ -287,6 +288,11 @@ struct PlanDev {
   // the plan runs: the D (M) scan sets the bits of its passing (member) keys
   // directly, with no key list and no build phase.  The host clears them.
   int d_static, m_static;
+  // The M (F) columns are host memory read in place (mapped tables): the
+  // scans then give lane l rows 2l, 2l+1, 64+2l, 65+2l of each 128-row step,
+  // so that every load instruction of a warp reads one contiguous run (the
+  // host link moves whole lines; on HBM the 4l .. 4l+3 layout is cheaper).
+  int m_pair, f_pair;
   int d_e, m_e;  // log2 slots of the D-set and the M table for the table's rows
   u64 d_su, d_sb, m_su, m_sb;  // base ukey and bit count of those bitmaps
   Pred pd, pm, pf;
@@ -989,7 +995,6 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
   const int lane = threadIdx.x & 31;
   const u64 keep = policy_keep(), strm = policy_stream();
   const i64 total = b.tM[b.nq];
-  const int r0 = lane * 4;
   WarpClaim wc;
   while (true) {
     const i64 t = wc.next(b.work, kPhMscan);
@@ -1037,13 +1042,28 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
       const int iters = (lim + 127) / 128;
       // Compiled for full tiles of aligned columns (no row limits) and in
       // general.
-      auto run = [&](auto full_c) {
-        constexpr bool FULL = decltype(full_c)::value;
+      auto run = [&](auto full_c, auto pair_c) {
+        constexpr bool FULL = decltype(full_c)::value, PAIR = decltype(pair_c)::value;
+        // e0: the step's first row + the lane's first row (4l, or 2l).
+        const int r0 = PAIR ? 2 * lane : 4 * lane;
         auto ld4 = [&](const int* p, int e0) -> int4 {
+          if (PAIR) {
+            const int2 a = ld_stream_v2i(p + e0, strm), c = ld_stream_v2i(p + e0 + 64, strm);
+            return make_int4(a.x, a.y, c.x, c.y);
+          }
           return FULL ? ld_stream_v4(p + e0, strm) : load_i32x4<VEC>(p, e0, lim - e0, strm);
         };
         auto ldk = [&](int e0, u32 bits, i64 v[4]) {
-          if (FULL) {
+          if (PAIR) {
+            if (bits & 3u) {
+              const longlong2 x = ld_stream_v2(pkey + e0, strm);
+              v[0] = x.x, v[1] = x.y;
+            }
+            if (bits & 12u) {
+              const longlong2 y = ld_stream_v2(pkey + e0 + 64, strm);
+              v[2] = y.x, v[3] = y.y;
+            }
+          } else if (FULL) {
             const longlong2 x = ld_stream_v2(pkey + e0, strm), y = ld_stream_v2(pkey + e0 + 2, strm);
             v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
           } else {
@@ -1086,8 +1106,12 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
         if (mL) ldk((iters - 1) * 128 + r0, mL, kL);
         set_bits(mL, kL);
       };
-      if (VEC && lim == iters * 128) run(std::true_type{});
-      else run(std::false_type{});
+      if (VEC && lim == iters * 128) {
+        if (q.m_pair) run(std::true_type{}, std::true_type{});
+        else run(std::true_type{}, std::false_type{});
+      } else {
+        run(std::false_type{}, std::false_type{});
+      }
     }
     const u32 wm = __reduce_add_sync(kFull, members);
     if (lane == 0 && wm) atomicAdd(&q.ctr->mcount, (u64)wm);
@@ -1542,6 +1566,8 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
       const PlanDev& q = b.q[qi];
       q.out->status = q.ctr->status;
       q.out->reserved = 0;
+      q.ctr->hits_total += (u64)ld_count(&q.ctr->hcount);
+      q.out->hits = (i64)q.ctr->hits_total;
       q.ctr->hcount = 0;  // a streamed F table probes chunk by chunk
       const i64 w = topk_words(q);
       return max((i64)1, (w + topk_tile_words_w(w) - 1) / topk_tile_words_w(w));
@@ -1568,7 +1594,6 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   const u64 keep = policy_keep(), strm = policy_stream();
   const bool ov = b.ov.table == 3;
   const i64 total = ov ? b.ov.tiles : b.tF[b.nq];
-  const int r0 = lane * 4;
   int cq = -1;  // plan of the rows in the ring
   u32 hh = 0, ht = 0;
   auto flush = [&](u32 cnt) {  // cnt entries from hh to plan cq's hit list
@@ -1605,11 +1630,12 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
     const Pred32 pf = to32(q.pf);
     const int lim = (int)min(n - base, (i64)tile);
     const int iters = (lim + 127) / 128;
-    auto append_hits = [&](u32 hits, int it) {
+    auto append_hits = [&](u32 hits, int it, bool pair) {
       if (__any_sync(kFull, hits)) {
         __syncwarp();
         ht += ring_append(hits, ht, [&](int s, u32 pos) {
-          hr[pos & (kHF - 1)] = (u32)(base + it * 128 + r0 + s);
+          const int off = pair ? 2 * lane + (s & 1) + (s >> 1) * 64 : 4 * lane + s;
+          hr[pos & (kHF - 1)] = (u32)(base + it * 128 + off);
         });
         __syncwarp();
         if (ht - hh >= 512) flush(512);
@@ -1617,13 +1643,29 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
     };
     // The step loop, compiled for full tiles of aligned columns (no row
     // limits) and for a bitmap that exists, and in general.
-    auto run = [&](auto full_c, auto fast_c) {
+    auto run = [&](auto full_c, auto fast_c, auto pair_c) {
       constexpr bool FULL = decltype(full_c)::value, FAST = decltype(fast_c)::value;
+      constexpr bool PAIR = decltype(pair_c)::value;
+      // e0: the step's first row + the lane's first row (4l, or 2l).
+      const int r0 = PAIR ? 2 * lane : 4 * lane;
       auto ld_d = [&](int e0) -> int4 {
+        if (PAIR) {
+          const int2 a = ld_stream_v2i(f_date + e0, strm), c = ld_stream_v2i(f_date + e0 + 64, strm);
+          return make_int4(a.x, a.y, c.x, c.y);
+        }
         return FULL ? ld_stream_v4(f_date + e0, strm) : load_i32x4<VEC>(f_date, e0, lim - e0, strm);
       };
       auto ld_k = [&](int e0, u32 bits, i64 v[4]) {
-        if (FULL) {
+        if (PAIR) {
+          if (bits & 3u) {
+            const longlong2 x = ld_stream_v2(f_mkey + e0, strm);
+            v[0] = x.x, v[1] = x.y;
+          }
+          if (bits & 12u) {
+            const longlong2 y = ld_stream_v2(f_mkey + e0 + 64, strm);
+            v[2] = y.x, v[3] = y.y;
+          }
+        } else if (FULL) {
           const longlong2 x = ld_stream_v2(f_mkey + e0, strm), y = ld_stream_v2(f_mkey + e0 + 2, strm);
           v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
         } else {
@@ -1654,22 +1696,23 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
         BmStage wN;
         if (FAST) bm_issue_fast(wN, bm, bm_umin ^ 0x8000000000000000ULL, bm_bits, bA, mA, keep);
         else bm_issue(wN, bm, bm_umin, bm_bits, bA, mA, keep);
-        if (it > 0) append_hits(bm_hits(wP), it - 1);
+        if (it > 0) append_hits(bm_hits(wP), it - 1, PAIR);
         wP = wN;
         bA = bB;
 #pragma unroll
         for (int s = 0; s < 4; ++s) mA[s] = mB[s];
       }
-      append_hits(bm_hits(wP), iters - 1);
+      append_hits(bm_hits(wP), iters - 1, PAIR);
     };
     using T = std::true_type;
     using F = std::false_type;
     if (VEC && lim == iters * 128) {
-      if (bm_bits) run(T{}, T{});
-      else run(T{}, F{});
+      if (bm_bits && q.f_pair && !ov) run(T{}, T{}, T{});
+      else if (bm_bits) run(T{}, T{}, F{});
+      else run(T{}, F{}, F{});
     } else {
-      if (bm_bits) run(F{}, T{});
-      else run(F{}, F{});
+      if (bm_bits) run(F{}, T{}, F{});
+      else run(F{}, F{}, F{});
     }
   }
   if (cq >= 0 && ht != hh) flush(ht - hh);

@@ -143,6 +143,51 @@ def test_topk_tiles_at_the_bound(ctx, stream, n_m):
         t.free(stream)
 
 
+def test_mapped_tables_match_oracle(ctx, stream, small):
+    """PQ_MAPPED: the plan kernels read pinned host columns in place."""
+    D, M, F = small
+    pin = lambda t: {k: torch.from_numpy(v).pin_memory() for k, v in t.items()}
+    d, m, f = pin(D), pin(M), pin(F)
+    with torch.cuda.stream(stream):
+        TD = pq.pq_load_columns(ctx, [d["key"], d["seg"]], mode=pq.PQ_MAPPED, stream=stream)
+        TM = pq.pq_load_columns(ctx, [m[c] for c in ("key", "dref", "date")],
+                                mode=pq.PQ_MAPPED, stream=stream)
+        TF = pq.pq_load_columns(ctx, [f[c] for c in ("mkey", "price", "disc", "date2")],
+                                mode=pq.PQ_MAPPED, stream=stream)
+    assert TF.column_ptr(0) == f["mkey"].data_ptr()   # in place, not copied
+    for p in PREDS[:3] + PREDS[-1:]:
+        kw = dict(seg=p["seg"], m_date_lt=p["mc"], f_date_gt=p["fc"], k=10,
+                  d_op=p.get("d_op", "=="), m_op=p.get("m_op", "<"), f_op=p.get("f_op", ">"))
+        want = oracle_plan(*small, seg=p["seg"], mc=p["mc"], fc=p["fc"], k=10,
+                           d_op=kw["d_op"], m_op=kw["m_op"], f_op=kw["f_op"])
+        for flags in (pq.PQ_PLAN_NO_GRAPH, 0, 0):   # separate launches, capture, replay
+            assert_same(run(ctx, stream, pq.make_plan(TD, TM, TF, flags=flags, **kw)), want,
+                        str(p))
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
+def test_mapped_refuses_pageable_and_files(ctx, small, tmp_path):
+    D, _, _ = small
+    with pytest.raises(pq.PQError, match="INVALID_ARG"):
+        pq.pq_load_columns(ctx, [D["key"], D["seg"]], mode=pq.PQ_MAPPED)
+    path = tmp_path / "key.bin"
+    D["key"].tofile(path)
+    with pytest.raises(pq.PQError, match="INVALID_ARG"):
+        pq.pq_load_columns(ctx, [(str(path), pq.PQ_INT32, 0, len(D["key"])),
+                                 torch.from_numpy(D["seg"]).pin_memory()], mode=pq.PQ_MAPPED)
+
+
+def test_joined_row_count(ctx, stream, small, small_tables):
+    """The result's hit count: every F row joins when all predicates pass."""
+    TD, TM, TF, _ = small_tables
+    with torch.cuda.stream(stream):
+        res = pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF, d_op="all", m_op="all", f_op="all",
+                                               flags=pq.PQ_PLAN_NO_GRAPH), stream=stream)
+        ctx.sync(stream)
+    assert res.hits == len(small[2]["mkey"])
+
+
 def remap_keys(D, M, F, seed, sparse=True, shift=0):
     """The same plan with the keys renamed: M keys to distinct random int64
     values of both signs (sparse: no key-range bitmap, hash tables) or to
