@@ -162,12 +162,18 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
   return PQ_OK;
 }
 
+// M side of a plan: a static bitmap means a dense dictionary of at most
+// n_m members over the table's key range, else a hash table of 2^e_m slots.
+static size_t mside_bytes(const ResolvedPlan& r) {
+  return r.dev.m_static ? al256(dense_layout(r.n_m, r.dev.m_sb).total) : mtable_bytes(r.e_m);
+}
+
 size_t plan_bytes(const ResolvedPlan& r) {
   size_t b = 0;
-  if (r.builds) b += al(r.n_d * 8);                                // D list
+  if (r.builds && !r.dev.d_static) b += al(r.n_d * 8);             // D list
   if (r.builds && r.dset_from == -1) b += dset_block_bytes(r.e_d);  // own D-set
-  b += al(r.n_m * 8);                    // M list
-  b += mtable_bytes(r.e_m);              // M table
+  if (!r.dev.m_static) b += al(r.n_m * 8);                          // M list
+  b += mside_bytes(r);                   // M dictionary or table
   b += al(r.parts * 8) * 2 + al(r.parts * 4);                  // top-k tile maxima
   b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k candidates
   b += al(r.n_f * 4);                                           // F hit list
@@ -183,10 +189,10 @@ void plan_assign(ResolvedPlan& r, char* base) {
     return q;
   };
   d.build_dset = r.builds ? 1 : 0;
-  d.dlist = r.builds ? (i64*)take(r.n_d * 8) : nullptr;
+  d.dlist = r.builds && !d.d_static ? (i64*)take(r.n_d * 8) : nullptr;
   if (r.builds && r.dset_from == -1) dset_block_assign(take(dset_block_bytes(r.e_d)), r.e_d, d);
-  d.mlist = (i64*)take(r.n_m * 8);
-  p = mtable_assign(p, r.e_m, d);
+  d.mlist = d.m_static ? nullptr : (i64*)take(r.n_m * 8);
+  d.ht_tag = (unsigned short*)take(mside_bytes(r));
   d.tk_k = (i64*)take(r.parts * 8);
   d.tk_s = (i64*)take(r.parts * 8);
   d.tk_c = (int*)take(r.parts * 4);

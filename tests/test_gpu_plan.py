@@ -401,7 +401,9 @@ def test_overflow_is_reported(ctx, stream, price):
 
 
 def test_budget_and_argument_errors(stream, small):
-    c = pq.Context(arena_bytes=8 << 20)
+    # The small plan's workspace (hit list 2.4 MB, dictionary 1.9 MB, D-set)
+    # does not fit in 2 MB.
+    c = pq.Context(arena_bytes=2 << 20)
     D, M, F = small
     with torch.cuda.stream(stream):
         TD, TM, TF, keep = load_tables(pq, c, D, M, F, stream=stream)
