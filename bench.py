@@ -358,13 +358,14 @@ def run_ours(args):
     # tables are copied to the device chunk by chunk every step).
     e2e = None
     if not args.no_e2e:
-        def host_plan_rate(ctx2, mode):
+        def host_plan_rate(ctx2, mode, src=None):
+            src = src or host
             with torch.cuda.stream(s):
-                HD = pq.pq_load_columns(ctx2, [host["D"]["key"], host["D"]["seg"]], mode=mode)
-                HM = pq.pq_load_columns(ctx2, [host["M"][c] for c in ("key", "dref", "date")],
+                HD = pq.pq_load_columns(ctx2, [src["D"]["key"], src["D"]["seg"]], mode=mode)
+                HM = pq.pq_load_columns(ctx2, [src["M"][c] for c in ("key", "dref", "date")],
                                         mode=mode)
-                HF = pq.pq_load_columns(ctx2, [host["F"][c] for c in ("mkey", "price", "disc",
-                                                                     "date2")], mode=mode)
+                HF = pq.pq_load_columns(ctx2, [src["F"][c] for c in ("mkey", "price", "disc",
+                                                                    "date2")], mode=mode)
                 hplan = pq.make_plan(HD, HM, HF, **q)
                 hres = pq.pinned_results(1)
                 pq.pq_run_plan(ctx2, hplan, hres[0], stream=s)
@@ -391,16 +392,33 @@ def run_ours(args):
                     "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // k_e2e,
                     "steps": k_e2e, "ms_per_step": 1e3 * t_e2e / k_e2e}
 
+        # The host tables in their packed storage form (frame of reference +
+        # bit packing, made once by pq_pack_column, like files written ahead):
+        # every step copies the packed bytes and decodes them on the device.
+        t0 = time.perf_counter()
+        packed = {tn: {c: pq.pq_pack_column(t) for c, t in cols.items()}
+                  for tn, cols in host.items()}
+        t_pack = time.perf_counter() - t0
+        packed_bytes = sum(p.nbytes for cols in packed.values() for p in cols.values())
         ctx2 = pq.Context(arena_bytes=args.arena_gb << 30)
-        e2e = host_plan_rate(ctx2, pq.PQ_MAPPED)
-        e2e["path"] = ("pq_run_plan on PQ_MAPPED tables in pinned host memory: the plan "
-                       "kernels read the columns in place over the host link")
+        e2e = host_plan_rate(ctx2, pq.PQ_STREAMING, packed)
+        e2e["path"] = ("pq_run_plan on PQ_STREAMING tables of packed columns in pinned host "
+                       "memory: chunked copies of the packed bytes, decoded on the device")
+        e2e["packed"] = {"bytes": packed_bytes, "plain_bytes": plan_bytes,
+                         "ratio": round(plan_bytes / packed_bytes, 2),
+                         "pack_s": round(t_pack, 2)}
         ctx2.close()
         ctx3 = pq.Context(arena_bytes=args.arena_gb << 30)
-        e2e["streaming"] = host_plan_rate(ctx3, pq.PQ_STREAMING)
-        e2e["streaming"]["path"] = ("pq_run_plan on PQ_STREAMING tables in pinned host memory "
-                                    "(chunked host-to-device copies)")
+        e2e["mapped"] = host_plan_rate(ctx3, pq.PQ_MAPPED)
+        e2e["mapped"]["path"] = ("pq_run_plan on PQ_MAPPED tables in pinned host memory: the "
+                                 "plan kernels read the plain columns in place")
         ctx3.close()
+        ctx4 = pq.Context(arena_bytes=args.arena_gb << 30)
+        e2e["streaming"] = host_plan_rate(ctx4, pq.PQ_STREAMING)
+        e2e["streaming"]["path"] = ("pq_run_plan on PQ_STREAMING tables of plain columns in "
+                                    "pinned host memory (chunked host-to-device copies)")
+        ctx4.close()
+        del packed
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -753,6 +771,45 @@ def run_stream(args):
             ctx.sync(s)
             mtimes.append(time.perf_counter() - t0)
     mt = float(np.median(mtimes))
+    ctx.close()
+
+    # The same tables packed (frame of reference + bit packing, made once
+    # ahead like files on storage): the ingest ring copies the packed bytes
+    # and the device decodes each chunk before its scan.
+    t0 = time.perf_counter()
+    packed = {tn: {c: pq.pq_pack_column(t) for c, t in cols.items()} for tn, cols in host.items()}
+    t_pack = time.perf_counter() - t0
+    pk_bytes = sum(p.nbytes for cols in packed.values() for p in cols.values())
+    ctx = pq.Context(arena_bytes=16 << 30, chunk_bytes=128 << 20, ring_slots=6, copy_streams=2)
+    PD = pq.pq_load_columns(ctx, [packed["D"]["key"], packed["D"]["seg"]], mode=pq.PQ_STREAMING)
+    PM = pq.pq_load_columns(ctx, [packed["M"][c] for c in ("key", "dref", "date")],
+                            mode=pq.PQ_STREAMING)
+    PF = pq.pq_load_columns(ctx, [packed["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                            mode=pq.PQ_STREAMING)
+    pplan = pq.make_plan(PD, PM, PF, **q)
+    pres = pq.pinned_results(1)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pq.pq_run_plan(ctx, pplan, pres[0], stream=s)
+            ctx.sync(s)
+        pst0 = ctx.stats()
+        ptimes = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pq.pq_run_plan(ctx, pplan, pres[0], stream=s)
+            ctx.sync(s)
+            ptimes.append(time.perf_counter() - t0)
+        pst1 = ctx.stats()
+    pt = float(np.median(ptimes))
+    pbytes = (pst1["h2d_bytes"] - pst0["h2d_bytes"]) / args.steps
+    packed_line = {"value": n_f / pt, "unit": "rows/s", "ms_per_step": 1e3 * pt,
+                   "h2d_gb_per_step": round(pbytes / 1e9, 3),
+                   "gb_per_s": round(pbytes / pt / 1e9, 1),
+                   "plain_gb": round(table_bytes(n_d, n_m, n_f) / 1e9, 2),
+                   "packed_gb": round(pk_bytes / 1e9, 2), "pack_s": round(t_pack, 1),
+                   "result_matches_streaming": pres[0].as_dict() == res[0].as_dict()}
+    ctx.close()
+    del packed
     mbytes = 5 * n_d + 16 * n_m + 12 * n_f + 17 * int(mres[0].hits)
     mapped = {"value": n_f / mt, "unit": "rows/s", "ms_per_step": 1e3 * mt,
               "link_gb_per_step": round(mbytes / 1e9, 3),
@@ -778,10 +835,11 @@ def run_stream(args):
         "result": {"ngroups": got["ngroups"], "top_keys": got["keys"][:3]},
         "sampled_check": {"groups_checked": len(keys), "sums_match": checked},
         "mapped": mapped,
+        "packed": packed_line,
     }
     print(json.dumps(line))
-    ctx.close()
-    return 0 if checked and mapped["result_matches_streaming"] else 1
+    ok = checked and mapped["result_matches_streaming"] and packed_line["result_matches_streaming"]
+    return 0 if ok else 1
 
 
 def main(argv=None):

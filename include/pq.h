@@ -168,8 +168,14 @@ typedef enum pq_src_kind {
   PQ_SRC_DEVICE = 0,  /* `ptr` is device memory (borrowed, never copied)       */
   PQ_SRC_HOST = 1,    /* `ptr` is host memory; pinned memory is copied
                          directly, pageable memory through pinned staging      */
-  PQ_SRC_FILE = 2     /* raw little-endian column file `path`, data starting at
+  PQ_SRC_FILE = 2,    /* raw little-endian column file `path`, data starting at
                          byte `offset`, read with pread by the ingest threads  */
+  PQ_SRC_PACKED = 3   /* `ptr` is a packed column (pq_pack_column) in page-
+                         locked host memory; `type` is the column's type.  A
+                         RESIDENT table decodes it into the arena once; a
+                         STREAMING table copies each chunk's packed bytes and
+                         decodes them on the device (Sec. 4.1: compressed
+                         data decoded on the GPU); MAPPED refuses it.       */
 } pq_src_kind;
 
 typedef struct pq_source {
@@ -199,6 +205,28 @@ typedef enum pq_load_mode {
  * table is freed.  *out receives a library-owned handle. */
 pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t nrows,
                           int mode, pq_table** out, void* stream);
+
+/* Packed columns (frame of reference + bit packing): the rows are cut into
+ * blocks of PQ_PACK_BLOCK rows; a block stores its smallest value and every
+ * value's difference from it in the fewest bits that hold the block's largest
+ * difference (0 to 64), one bit stream per block.  Layout of a packed column
+ * (all little-endian):
+ *   header (32 B): u32 magic "PQPK", u32 version 1, i32 type, u32 block rows,
+ *                  i64 nrows, i64 nblocks;
+ *   block table: nblocks + 1 entries of 16 B {i64 base, u32 first word,
+ *                u8 width, 3 B zero}; the last entry holds the total words;
+ *   payload: u32 words from the next 16-byte boundary; value i of a block is
+ *   bits [i*width, (i+1)*width) of the block's stream (LSB first), followed
+ *   by 4 zero words.
+ * pq_pack_bound gives the largest packed size of `nrows` values of `type`;
+ * pq_pack_column packs host memory into `out` (host memory, `cap` bytes) and
+ * writes the size used to *out_bytes.  Host-only (no device work); returns
+ * PQ_ERR_INVALID_ARG for a bad type or pointer and PQ_ERR_CAPACITY when `cap`
+ * is too small. */
+#define PQ_PACK_BLOCK 4096
+int64_t pq_pack_bound(int64_t nrows, int32_t type);
+pq_status pq_pack_column(const void* src, int32_t type, int64_t nrows, void* out, int64_t cap,
+                         int64_t* out_bytes);
 
 /* Number of rows of a table, and the device-accessible pointer of a resident
  * or mapped column (NULL for a streaming table). */

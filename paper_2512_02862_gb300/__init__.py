@@ -33,7 +33,8 @@ PQ_ERR_IO, PQ_ERR_TIMEOUT, PQ_ERR_OVERFLOW, PQ_ERR_BUSY, PQ_ERR_RESERVED_KEY = 5
 
 PQ_INT8, PQ_INT32, PQ_INT64 = 1, 2, 3
 CMP = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5, "all": 6}
-PQ_SRC_DEVICE, PQ_SRC_HOST, PQ_SRC_FILE = 0, 1, 2
+PQ_SRC_DEVICE, PQ_SRC_HOST, PQ_SRC_FILE, PQ_SRC_PACKED = 0, 1, 2, 3
+PQ_PACK_BLOCK = 4096
 PQ_RESIDENT, PQ_STREAMING, PQ_MAPPED = 0, 1, 2
 PQ_PLAN_PARTITIONED, PQ_PLAN_CACHE_DSET, PQ_PLAN_NO_GRAPH = 1, 2, 4
 
@@ -126,6 +127,7 @@ def library():
         "pq_poll": [vp, c_uint64, POINTER(pq_result), i32],
         "pq_autotune": [vp, POINTER(pq_plan), POINTER(pq_tuning)],
         "pq_filter_noalloc": [pq_col, i32, i64, vp, i64, vp, vp, vp, vp],
+        "pq_pack_column": [vp, i32, i64, vp, i64, POINTER(c_int64)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -141,6 +143,8 @@ def library():
     lib.pq_table_column.restype = c_void_p
     lib.pq_last_latency_us.argtypes = [vp]
     lib.pq_last_latency_us.restype = c_double
+    lib.pq_pack_bound.argtypes = [i64, c_int32]
+    lib.pq_pack_bound.restype = c_int64
     _lib = lib
     return lib
 
@@ -349,6 +353,37 @@ class Table:
             self.h = None
 
 
+class Packed:
+    """A packed column (frame of reference + bit packing, pq_pack_column) in a
+    byte buffer: ``data`` (a pinned uint8 tensor unless packed with
+    ``pinned=False``), the column type code and its row count."""
+
+    def __init__(self, data, type_code: int, nrows: int):
+        self.data, self.type, self.nrows = data, type_code, nrows
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.data.numel())
+
+
+def pq_pack_column(column, pinned: bool = True) -> Packed:
+    """Pack a host column (numpy array or CPU tensor) on the host."""
+    import numpy as np
+    torch = _torch()
+    a = column.numpy() if isinstance(column, torch.Tensor) else np.ascontiguousarray(column)
+    code = {np.dtype(np.int8): PQ_INT8, np.dtype(np.int32): PQ_INT32,
+            np.dtype(np.int64): PQ_INT64}[a.dtype]
+    n = len(a)
+    cap = library().pq_pack_bound(n, code)
+    buf = torch.empty(cap, dtype=torch.uint8, pin_memory=pinned)
+    used = c_int64(0)
+    st = library().pq_pack_column(a.ctypes.data if n else None, code, n, buf.data_ptr(), cap,
+                                  ctypes.byref(used))
+    if st != 0:
+        raise PQError(st, "pq_pack_column")
+    return Packed(buf[:used.value], code, n)
+
+
 def pq_load_columns(ctx: Context, columns, mode: int = PQ_RESIDENT, stream=None) -> Table:
     """Load a table.  ``columns`` are CUDA tensors (borrowed), CPU tensors or
     numpy arrays (host memory; pinned tensors are copied directly), or
@@ -359,7 +394,11 @@ def pq_load_columns(ctx: Context, columns, mode: int = PQ_RESIDENT, stream=None)
     keep = []
     nrows = None
     for i, c in enumerate(columns):
-        if isinstance(c, tuple):
+        if isinstance(c, Packed):
+            keep.append(c)
+            n = c.nrows
+            srcs[i] = pq_source(PQ_SRC_PACKED, c.type, c.data.data_ptr(), None, 0)
+        elif isinstance(c, tuple):
             path, code, off, n = c
             p = path.encode()
             keep.append(p)

@@ -453,6 +453,8 @@ pq_status pq_profile_reset(pq_ctx* ctx) {
 // ---------------------------------------------------------------- tables ----
 static pq_status copy_host_to_device(pq_ctx* ctx, void* dst, const pqh::Column& c, int64_t off,
                                      size_t bytes, cudaStream_t s);
+static pq_status unpack_to_device(pq_ctx* ctx, void* dst, const pqh::Column& c, int64_t nrows,
+                                  cudaStream_t s);
 
 pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t nrows, int mode,
                           pq_table** out, void* stream) {
@@ -489,6 +491,22 @@ pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t
         }
         break;
       }
+      case PQ_SRC_PACKED: {
+        if (!src.ptr) return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: null", i);
+        if (mode == PQ_MAPPED)
+          return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: packed columns cannot be mapped", i);
+        cudaPointerAttributes at{};
+        c.pinned = cudaPointerGetAttributes(&at, src.ptr) == cudaSuccess &&
+                   at.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (!c.pinned)
+          return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: packed columns need page-locked memory", i);
+        if (!pqh::packed_info(src.ptr, src.type, nrows, &c.pk))
+          return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: not a packed column of %lld rows of this type",
+                      i, (long long)nrows);
+        c.packed = true;
+        break;
+      }
       case PQ_SRC_FILE:
         if (mode == PQ_MAPPED)
           return fail(ctx, PQ_ERR_INVALID_ARG, "column %d: files cannot be mapped", i);
@@ -511,7 +529,8 @@ pq_status pq_load_columns(pq_ctx* ctx, const pq_source* srcs, int ncols, int64_t
         return fail(ctx, PQ_ERR_BUDGET, "resident table needs %zu more bytes", bytes);
       }
       c.dev = c.owned;
-      pq_status st = copy_host_to_device(ctx, c.owned, c, 0, bytes, s);
+      pq_status st = c.packed ? unpack_to_device(ctx, c.owned, c, nrows, s)
+                              : copy_host_to_device(ctx, c.owned, c, 0, bytes, s);
       if (st != PQ_OK) {
         for (auto& d : t->cols) ctx->arena.release(d.owned, s);
         return st;
@@ -555,6 +574,27 @@ pq_status pq_ht_free(pq_ctx* ctx, pq_ht* ht, void* stream) {
 }
 
 }  // extern "C"
+
+// A packed column decoded into `dst` (nrows values): the packed bytes are
+// copied into a scratch block of the arena and decoded there.
+static pq_status unpack_to_device(pq_ctx* ctx, void* dst, const pqh::Column& c, int64_t nrows,
+                                  cudaStream_t s) {
+  const char* base = (const char*)c.src.ptr;
+  const size_t tab = (const char*)c.pk.blocks - base;
+  const size_t pay = (const char*)c.pk.words - base;
+  const size_t bytes = pay + 4 * (size_t)(c.pk.total_words + 4);
+  char* tmp = (char*)ctx->arena.alloc(bytes);
+  if (!tmp) return fail(ctx, PQ_ERR_BUDGET, "decoding a packed column needs %zu bytes", bytes);
+  cudaError_t e = cudaMemcpyAsync(tmp, base, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = pqh::unpack_launch((const pqh::PackBlock*)(tmp + tab), (const uint32_t*)(tmp + pay), 0, 0,
+                           nrows, c.type, dst, ctx->num_sms, s);
+  ctx->arena.release(tmp, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "packed column decode");
+  ctx->h2d += (int64_t)bytes;
+  ctx->launches++;
+  return PQ_OK;
+}
 
 // Host -> device copy of `bytes` bytes of column `c` starting at byte `off`:
 // pinned memory goes straight to the copy engine; pageable memory and files go

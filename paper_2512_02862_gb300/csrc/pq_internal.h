@@ -71,8 +71,35 @@ class PinnedRing {
   std::mutex mu_;
 };
 
+// Packed columns (pq_pack.cu; layout in pq.h).
+struct PackBlock {
+  int64_t base;    // smallest value of the block
+  uint32_t word;   // first payload word of the block's bit stream
+  uint8_t width;   // bits per value (0..64)
+  uint8_t pad[3];
+};
+static_assert(sizeof(PackBlock) == 16, "packed block entry");
+struct PackedView {
+  const PackBlock* blocks = nullptr;  // nblocks + 1 entries
+  const uint32_t* words = nullptr;
+  int64_t nblocks = 0, total_words = 0;
+};
+struct PackedRange {
+  int64_t b0, b1;  // blocks holding the rows
+  int64_t w0, w1;  // payload words to copy (with the decoder's padding)
+};
+// Check a packed column's header against its type and row count.
+bool packed_info(const void* p, int type, int64_t nrows, PackedView* v);
+PackedRange packed_range(const PackedView& v, int64_t row0, int64_t n);
+// Decode rows [row0, row0 + n) (column rows) from device copies of the block
+// table (from block row0 / PQ_PACK_BLOCK) and payload (from word w0).
+cudaError_t unpack_launch(const PackBlock* dblk, const uint32_t* dwords, int64_t w0, int64_t row0,
+                          int64_t n, int type, void* out, int num_sms, cudaStream_t s);
+
 struct Column {
   int type = 0;           // pq_dtype
+  bool packed = false;    // source is a packed column (PQ_SRC_PACKED)
+  PackedView pk;
   const void* dev = nullptr;   // device pointer (resident) or nullptr
   pq_source src{};        // original source (streaming)
   bool pinned = false;    // host source is page-locked

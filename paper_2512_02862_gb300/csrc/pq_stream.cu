@@ -46,6 +46,7 @@ struct TableIn {
   int ncols = 0;
   size_t esize[4] = {0, 0, 0, 0};
   size_t row_bytes = 0;
+  bool packed = false;  // some column is packed (chunks start on pack blocks)
 };
 
 // Column j of chunk c laid out in a slot: columns one after another, each
@@ -144,6 +145,7 @@ class Stager {
     const TableIn& T = tabs_[ch.table];
     for (int j = 0; j < T.ncols; ++j) {
       const Column& col = T.t->cols[j];
+      if (col.packed) continue;  // copied straight from its page-locked buffer
       const size_t es = T.esize[j];
       const size_t bytes = es * ch.rows;
       const size_t src_off = es * (T.row0 + ch.row0);
@@ -215,10 +217,12 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     for (int j = 0; j < T.ncols; ++j) {
       const Column& c = T.t->cols[j];
       if (c.dev) return fail(ctx, PQ_ERR_INVALID_ARG, "streaming table mixes device columns");
-      if (!(c.src.kind == PQ_SRC_HOST && c.pinned)) need_stage = true;
+      if (c.packed) T.packed = true;
+      else if (!(c.src.kind == PQ_SRC_HOST && c.pinned)) need_stage = true;
     }
     i64 rows_per = (i64)((chunk_bytes - 4 * 256) / T.row_bytes) / 64 * 64;
     rows_per = std::max<i64>(rows_per, 64);
+    if (T.packed) rows_per = std::max<i64>(rows_per / PQ_PACK_BLOCK, 1) * PQ_PACK_BLOCK;
     for (i64 a = 0; a < nrows[t]; a += rows_per)
       chunks.push_back({t, a, std::min(rows_per, nrows[t] - a)});
   }
@@ -233,7 +237,13 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   for (const Chunk& ch : chunks)
     if (ch.table == 2) f_hits = std::max(f_hits, ch.rows);
   char* ws = (char*)scr.get(L.end + al(r.n_d * 8) + al(r.n_m * 8) + al(f_hits * 4 + 4));
-  char* ring = chunks.empty() ? nullptr : (char*)scr.get((chunk_bytes + 1024) * nslots);
+  // A slot holds a chunk's plain columns and, for packed columns, their
+  // packed bytes behind them (never more than the plain bytes plus the block
+  // tables and padding).
+  bool any_packed = false;
+  for (int t = 0; t < 3; ++t) any_packed = any_packed || (!r.resident[t] && tabs[t].packed);
+  const size_t slot_bytes = any_packed ? 2 * chunk_bytes + (64 << 10) : chunk_bytes + 1024;
+  char* ring = chunks.empty() ? nullptr : (char*)scr.get(slot_bytes * nslots);
   if (!ws || (!chunks.empty() && !ring))
     return fail(ctx, PQ_ERR_BUDGET, "streaming plan: workspace and %d chunk slots of %zu bytes",
                 nslots, chunk_bytes);
@@ -309,7 +319,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     const TableIn& T = tabs[ch.table];
     const int slot = (int)(c % nslots);
     cudaStream_t cs = ctx->copy_streams[c % ncs];
-    char* dst = ring + slot * (chunk_bytes + 1024);
+    char* dst = ring + slot * slot_bytes;
     PQ_CUDA(ctx, cudaStreamWaitEvent(cs, slot_free[slot], 0));
     int sb = -1;
     if (stager) {
@@ -317,11 +327,31 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       if (sb < 0) return fail(ctx, PQ_ERR_IO, "streaming plan: %s", stager->error().c_str());
     }
     size_t total = 0;
+    size_t pk_off = col_offset(T, ch.rows, T.ncols);  // packed bytes after the plain columns
     for (int j = 0; j < T.ncols; ++j) {
-      const size_t bytes = T.esize[j] * ch.rows;
+      const Column& col = T.t->cols[j];
       const size_t off = col_offset(T, ch.rows, j);
+      if (col.packed) {
+        // The chunk's block table entries and payload words, then the decode
+        // into the plain column's place on the same copy stream.
+        const i64 row = T.row0 + ch.row0;
+        const PackedRange pr = packed_range(col.pk, row, ch.rows);
+        const size_t tb = (size_t)(pr.b1 - pr.b0) * sizeof(PackBlock);
+        const size_t wb = (size_t)(pr.w1 - pr.w0) * 4;
+        char* dtab = dst + pk_off;
+        char* dwords = dst + pk_off + al(tb);
+        PQ_CUDA(ctx, cudaMemcpyAsync(dtab, col.pk.blocks + pr.b0, tb, cudaMemcpyHostToDevice, cs));
+        PQ_CUDA(ctx, cudaMemcpyAsync(dwords, col.pk.words + pr.w0, wb, cudaMemcpyHostToDevice, cs));
+        PQ_CUDA(ctx, unpack_launch((const PackBlock*)dtab, (const uint32_t*)dwords, pr.w0, row,
+                                   ch.rows, col.type, dst + off, ctx->num_sms, cs));
+        ctx->launches++;
+        pk_off += al(tb) + al(wb);
+        total += tb + wb;
+        continue;
+      }
+      const size_t bytes = T.esize[j] * ch.rows;
       const void* src = stager ? (const void*)(stager->buf(sb) + off)
-                               : (const void*)((const char*)T.t->cols[j].src.ptr +
+                               : (const void*)((const char*)col.src.ptr +
                                                T.esize[j] * (T.row0 + ch.row0));
       PQ_CUDA(ctx, cudaMemcpyAsync(dst + off, src, bytes, cudaMemcpyHostToDevice, cs));
       total += bytes;
@@ -368,7 +398,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         const Chunk& ch = chunks[c];
         const TableIn& T = tabs[t];
         const int slot = (int)(c % nslots);
-        char* src = ring + slot * (chunk_bytes + 1024);
+        char* src = ring + slot * slot_bytes;
         PQ_CUDA(ctx, cudaStreamWaitEvent(s, copy_done[slot], 0));
         Batch bc = b;
         bc.ov.table = t + 1;

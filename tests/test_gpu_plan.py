@@ -309,16 +309,20 @@ def stream_ctx():
     c.close()
 
 
-@pytest.mark.parametrize("source", ["pinned", "pageable", "file"])
+@pytest.mark.parametrize("source", ["pinned", "pageable", "file", "packed", "mixed"])
 def test_streaming_plan_matches_oracle(stream_ctx, stream, small, tmp_path, source):
     D, M, F = small
     ctx = stream_ctx
 
     def cols(tab, names):
         out = []
-        for nm in names:
+        for i, nm in enumerate(names):
             a = np.ascontiguousarray(tab[nm])
-            if source == "pinned":
+            if source == "packed" or (source == "mixed" and i % 2 == 0):
+                out.append(pq.pq_pack_column(a))      # decoded on the device per chunk
+            elif source == "mixed" and i % 3 == 1:
+                out.append(a)
+            elif source in ("pinned", "mixed"):
                 out.append(torch.from_numpy(a).pin_memory())
             elif source == "pageable":
                 out.append(a)
@@ -340,6 +344,41 @@ def test_streaming_plan_matches_oracle(stream_ctx, stream, small, tmp_path, sour
             ctx.sync(stream)
             assert_same(got.as_dict(), oracle_plan(D, M, F, k=32, **p), source)
         assert ctx.stats()["chunks_ingested"] > 20
+
+
+class _DevView:
+    """A device array seen through __cuda_array_interface__ (the test only reads it)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3}
+
+
+def test_packed_columns_resident_and_row_ranges(stream_ctx, stream, small):
+    """Packed sources: a resident table decodes them once (bit-exact copies of
+    the plain columns); a streamed packed F table with row ranges that do not
+    start on a pack block matches the oracle."""
+    D, M, F = small
+    ctx = stream_ctx
+    names = ("mkey", "price", "disc", "date2")
+    with torch.cuda.stream(stream):
+        TF = pq.pq_load_columns(ctx, [pq.pq_pack_column(F[c]) for c in names], stream=stream)
+        ctx.sync(stream)
+        for j, c in enumerate(names):
+            a = F[c]
+            v = _DevView(TF.column_ptr(j), len(a), np.dtype(a.dtype).str)
+            assert np.array_equal(torch.as_tensor(v, device="cuda").cpu().numpy(), a), c
+        TF.free(stream)
+        d, m = to_dev(D), to_dev(M)
+        TD = pq.pq_load_columns(ctx, [d["key"], d["seg"]])
+        TM = pq.pq_load_columns(ctx, [m["key"], m["dref"], m["date"]])
+        PF = pq.pq_load_columns(ctx, [pq.pq_pack_column(F[c]) for c in names],
+                                mode=pq.PQ_STREAMING)
+        for rows in (dict(f=(1000, 500_000)), dict(f=(4096 * 3 - 7, 9000))):
+            got = pq.pq_run_plan(ctx, pq.make_plan(TD, TM, PF, rows=rows), stream=stream)
+            ctx.sync(stream)
+            assert_same(got.as_dict(), oracle_plan(D, M, F, rows=rows), str(rows))
+        assert ctx.stats()["chunks_ingested"] > 0
 
 
 def test_streaming_fact_table_with_resident_dimensions(stream_ctx, stream, small):
