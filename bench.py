@@ -780,7 +780,10 @@ def run_stream(args):
     packed = {tn: {c: pq.pq_pack_column(t) for c, t in cols.items()} for tn, cols in host.items()}
     t_pack = time.perf_counter() - t0
     pk_bytes = sum(p.nbytes for cols in packed.values() for p in cols.values())
-    ctx = pq.Context(arena_bytes=16 << 30, chunk_bytes=128 << 20, ring_slots=6, copy_streams=2)
+    # Chunks of 256 MB of plain rows (about 85 MB packed) on three copy
+    # streams: with a third of the bytes per row, the ring needs more rows in
+    # flight to keep the link busy (128 MB chunks on two streams: 55.6 ms).
+    ctx = pq.Context(arena_bytes=16 << 30, chunk_bytes=256 << 20, ring_slots=6, copy_streams=3)
     PD = pq.pq_load_columns(ctx, [packed["D"]["key"], packed["D"]["seg"]], mode=pq.PQ_STREAMING)
     PM = pq.pq_load_columns(ctx, [packed["M"][c] for c in ("key", "dref", "date")],
                             mode=pq.PQ_STREAMING)
@@ -807,6 +810,7 @@ def run_stream(args):
                    "gb_per_s": round(pbytes / pt / 1e9, 1),
                    "plain_gb": round(table_bytes(n_d, n_m, n_f) / 1e9, 2),
                    "packed_gb": round(pk_bytes / 1e9, 2), "pack_s": round(t_pack, 1),
+                   "chunk_bytes": 256 << 20, "ring_slots": 6, "copy_streams": 3,
                    "result_matches_streaming": pres[0].as_dict() == res[0].as_dict()}
     ctx.close()
     del packed
