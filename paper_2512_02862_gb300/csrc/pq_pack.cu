@@ -76,34 +76,61 @@ bool packed_info(const void* p, int type, int64_t nrows, PackedView* v) {
   return true;
 }
 
+// One value of a packed column: base + bits [i*width, (i+1)*width) of its
+// block's stream (`words` starts at payload word w0), read from the two or
+// three words that hold them.
+__device__ __forceinline__ int64_t unpack_one(const PackBlock& b, const uint32_t* words, int64_t w0,
+                                              int64_t i) {
+  if (!b.width) return b.base;
+  const uint64_t bit = (uint64_t)i * b.width;
+  const uint32_t* w = words + (b.word - w0) + (bit >> 5);
+  const uint32_t sh = (uint32_t)(bit & 31);
+  const uint64_t lo = (uint64_t)__ldg(w) | ((uint64_t)__ldg(w + 1) << 32);
+  uint64_t d = lo >> sh;
+  if (sh + b.width > 64) d |= (uint64_t)__ldg(w + 2) << (64 - sh);
+  if (b.width < 64) d &= (1ULL << b.width) - 1;
+  return (int64_t)((uint64_t)b.base + d);
+}
+
 // Decode rows [row0, row0 + n) of a packed column into `out` (element size of
-// `type`).  `blk` and `words` are the chunk's copies of the block table
-// (starting at the block holding row0, whose index in the column is b0) and
-// of the payload (starting at that block's first word, w0).  One thread per
-// output row: value = base + bits [i*width, (i+1)*width) of its block's
-// stream, read from the two or three words that hold them.
+// `type`, 16-byte aligned).  `blk` and `words` are the chunk's copies of the
+// block table (starting at the block holding row0) and of the payload
+// (starting at that block's first word, w0).  Each thread decodes four
+// consecutive output rows and stores them with one vector store; it reloads
+// the block entry only when its rows cross into the next block.
+template <typename T>
 __global__ void __launch_bounds__(256) k_unpack(const PackBlock* blk, const uint32_t* words,
-                                                int64_t w0, int64_t row0, int64_t n, int type,
-                                                void* out) {
+                                                int64_t w0, int64_t row0, int64_t n, T* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-    const int64_t pos = row0 % PQ_PACK_BLOCK + r;  // row within the chunk's first block onward
-    const PackBlock b = blk[pos / PQ_PACK_BLOCK];
-    const uint64_t bit = (uint64_t)(pos % PQ_PACK_BLOCK) * b.width;
-    int64_t v = b.base;
-    if (b.width) {
-      const uint32_t* w = words + (b.word - w0) + (bit >> 5);
-      const uint32_t sh = (uint32_t)(bit & 31);
-      const uint64_t lo = (uint64_t)__ldg(w) | ((uint64_t)__ldg(w + 1) << 32);
-      uint64_t d = lo >> sh;
-      if (sh + b.width > 64) d |= (uint64_t)__ldg(w + 2) << (64 - sh);
-      if (b.width < 64) d &= (1ULL << b.width) - 1;
-      v = (int64_t)((uint64_t)b.base + d);
+  const int64_t first = row0 % PQ_PACK_BLOCK;  // position of output row 0 in block 0
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * g < n; g += stride) {
+    const int64_t r = 4 * g;
+    int64_t pos = first + r;
+    int64_t bi = pos / PQ_PACK_BLOCK;
+    PackBlock b = blk[bi];
+    T v[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k, ++pos) {
+      if (r + k < n) {
+        if (pos / PQ_PACK_BLOCK != bi) b = blk[++bi];
+        v[k] = (T)unpack_one(b, words, w0, pos % PQ_PACK_BLOCK);
+      }
     }
-    switch (type) {
-      case PQ_INT8: static_cast<int8_t*>(out)[r] = (int8_t)v; break;
-      case PQ_INT32: static_cast<int32_t*>(out)[r] = (int32_t)v; break;
-      default: static_cast<int64_t*>(out)[r] = v; break;
+    if (r + 4 <= n) {
+      if (sizeof(T) == 8) {
+        reinterpret_cast<longlong2*>(out + r)[0] = make_longlong2((int64_t)v[0], (int64_t)v[1]);
+        reinterpret_cast<longlong2*>(out + r)[1] = make_longlong2((int64_t)v[2], (int64_t)v[3]);
+      } else if (sizeof(T) == 4) {
+        *reinterpret_cast<int4*>(out + r) = make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]);
+      } else {
+        const uint32_t x = (uint32_t)(uint8_t)v[0] | (uint32_t)(uint8_t)v[1] << 8 |
+                           (uint32_t)(uint8_t)v[2] << 16 | (uint32_t)(uint8_t)v[3] << 24;
+        *reinterpret_cast<uint32_t*>(out + r) = x;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (r + k < n) out[r + k] = v[k];
     }
   }
 }
@@ -120,8 +147,18 @@ PackedRange packed_range(const PackedView& v, int64_t row0, int64_t n) {
 cudaError_t unpack_launch(const PackBlock* dblk, const uint32_t* dwords, int64_t w0, int64_t row0,
                           int64_t n, int type, void* out, int num_sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8);
-  k_unpack<<<(int)blocks, 256, 0, s>>>(dblk, dwords, w0, row0, n, type, out);
+  const int64_t blocks = std::min<int64_t>((n + 1023) / 1024, (int64_t)num_sms * 8);
+  switch (type) {
+    case PQ_INT8:
+      k_unpack<<<(int)blocks, 256, 0, s>>>(dblk, dwords, w0, row0, n, static_cast<int8_t*>(out));
+      break;
+    case PQ_INT32:
+      k_unpack<<<(int)blocks, 256, 0, s>>>(dblk, dwords, w0, row0, n, static_cast<int32_t*>(out));
+      break;
+    default:
+      k_unpack<<<(int)blocks, 256, 0, s>>>(dblk, dwords, w0, row0, n, static_cast<int64_t*>(out));
+      break;
+  }
   return cudaGetLastError();
 }
 
