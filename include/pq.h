@@ -367,19 +367,25 @@ typedef struct pq_result {
  * is valid after pq_sync(ctx, stream); otherwise the call waits. */
 pq_status pq_run_plan(pq_ctx* ctx, const pq_plan* plan, pq_result* result, void* stream);
 
-/* Run `n` plans on resident tables in one batch: each kernel of the chain is
- * launched once for all plans, its persistent blocks stealing tiles from a
- * flattened work list, so plans of very different sizes share the GPU.
- * Results as for pq_run_plan (pinned -> asynchronous). */
+/* Run `n` plans in one batch: each kernel of the chain is launched once for
+ * all plans, its persistent blocks stealing tiles from a flattened work list,
+ * so plans of very different sizes share the GPU.  When the plans stream
+ * their tables and all name the same D, M and F tables, each chunk of a
+ * streamed table is read and copied once for the whole batch and every plan
+ * scans its own rows of it (reader combining, Sec. 5.2); plans over
+ * different streamed tables run one after another.  Results as for
+ * pq_run_plan (pinned -> asynchronous). */
 pq_status pq_run_batch(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
                        void* stream);
 
 /* ---- serving ---------------------------------------------------------------- */
 
-/* Continuous batching: hand a plan (resident tables) to the context's serving
- * loop, which admits it as soon as a slot and arena memory are free, batches
- * it with the other admitted requests and runs the batch on one of
- * `serve_slots` streams while earlier batches are still on the GPU.
+/* Continuous batching: hand a plan to the context's serving loop, which
+ * admits it as soon as a slot and arena memory are free, batches it with the
+ * other admitted requests and runs the batch on one of `serve_slots` streams
+ * while earlier batches are still on the GPU.  Plans over streamed tables are
+ * batched like pq_run_batch batches them: one ingest pass per batch for the
+ * tables they share.
  * *ticket identifies the request.  PQ_ERR_BUSY if `serve_queue` requests are
  * already pending. */
 pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket);

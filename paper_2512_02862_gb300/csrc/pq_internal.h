@@ -243,6 +243,13 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
 size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n);
 pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result,
                              cudaStream_t s);
+// A batch with streamed tables: one ingest pass over the tables shared by all
+// plans (pq_stream.cu).
+pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
+                              cudaStream_t s);
+// Copy n results from the device (pinned destination: asynchronous).
+pq_status read_back(pq_ctx* ctx, pq_result* results, const pq_result* dev, int n,
+                    cudaStream_t s);
 bool is_pinned(const void* p);
 void plan_cache_destroy(pq_ctx* ctx);
 // Drop cached graphs that reference table `id`.

@@ -414,8 +414,8 @@ void forget_table(pq_ctx* ctx, uint64_t id, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ batch ----
-static pq_status read_back(pq_ctx* ctx, pq_result* results, const pq_result* dev, int n,
-                           cudaStream_t s) {
+pq_status read_back(pq_ctx* ctx, pq_result* results, const pq_result* dev, int n,
+                    cudaStream_t s) {
   const size_t bytes = sizeof(pq_result) * n;
   ctx->d2h += (int64_t)bytes;
   if (is_pinned(results)) {
@@ -456,8 +456,10 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   for (int i = 0; i < n; ++i) {
-    pq_status st = resolve_plan(ctx, plans[i], R[i], true);
+    pq_status st = resolve_plan(ctx, plans[i], R[i], false);
     if (st != PQ_OK) return st;
+    if (!R[i].resident[0] || !R[i].resident[1] || !R[i].resident[2])
+      return run_batch_streaming(ctx, plans, n, results, s);  // some table is streamed
     plan_static(ctx, plans[i], R[i], s, cap != cudaStreamCaptureStatusNone);
   }
   // Graph replay for a repeated single plan.

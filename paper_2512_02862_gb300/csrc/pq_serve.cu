@@ -203,8 +203,9 @@ extern "C" {
 pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket) {
   if (!ctx || !plan || !ticket) return PQ_ERR_INVALID_ARG;
   ResolvedPlan r;
-  pq_status st = resolve_plan(ctx, *plan, r, true);
+  pq_status st = resolve_plan(ctx, *plan, r, false);
   if (st != PQ_OK) return st;
+  const bool streamed = !r.resident[0] || !r.resident[1] || !r.resident[2];
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     st = server_start(ctx);
@@ -214,7 +215,12 @@ pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket) {
   Request q;
   q.plan = *plan;
   q.plan.flags |= PQ_PLAN_CACHE_DSET;
-  q.bytes = plan_bytes(r) + 256;
+  // A batch of streamed plans also holds the chunk ring: a share of it per
+  // request (a batch that still does not fit is retried when others finish).
+  q.bytes = plan_bytes(r) + 256 +
+            (streamed ? (size_t)std::max(2, ctx->opt.ring_slots) *
+                            (size_t)(2 * ctx->opt.chunk_bytes) / 8
+                      : 0);
   q.t0 = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> g(srv->mu);

@@ -487,3 +487,326 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
 }
 
 }  // namespace pqh
+
+namespace pqh {
+
+// A batch of plans over the same streamed tables (reader combining, Sec.
+// 5.2): each chunk of a streamed table is read and copied once, and every
+// plan scans the rows of the chunk that fall in its own row range -- its
+// descriptors point into the chunk's slot for that launch.  Counts are read
+// back once per table for all plans (the D-sets and M tables are sized
+// exactly, as for one plan); resident tables of the batch are scanned in
+// place.  Plans whose streamed tables differ run one after another.
+pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
+                              cudaStream_t s) {
+  std::vector<ResolvedPlan> R(n);
+  for (int i = 0; i < n; ++i) {
+    pq_status st = resolve_plan(ctx, plans[i], R[i], false);
+    if (st != PQ_OK) return st;
+  }
+  const pq_table* T3[3] = {plans[0].D, plans[0].M, plans[0].F};
+  bool shared = true;
+  for (int i = 0; i < n; ++i) {
+    const pq_table* Ti[3] = {plans[i].D, plans[i].M, plans[i].F};
+    for (int t = 0; t < 3; ++t) shared = shared && Ti[t] == T3[t];
+  }
+  if (!shared || n == 1) {
+    for (int i = 0; i < n; ++i) {
+      pq_status st = run_plan_streaming(ctx, &plans[i], &results[i], s);
+      if (st != PQ_OK) return st;
+    }
+    return PQ_OK;
+  }
+  bool streamed[3];
+  for (int t = 0; t < 3; ++t) streamed[t] = !R[0].resident[t];
+  auto prow0 = [&](int i, int t) { return t == 0 ? R[i].d_row0 : t == 1 ? R[i].m_row0 : R[i].f_row0; };
+  auto prows = [&](int i, int t) { return t == 0 ? R[i].n_d : t == 1 ? R[i].n_m : R[i].n_f; };
+
+  // Chunks over the union of the plans' row ranges of each streamed table.
+  TableIn tabs[3];
+  i64 urows[3] = {0, 0, 0};
+  const size_t chunk_bytes = (size_t)ctx->opt.chunk_bytes;
+  std::vector<Chunk> chunks;
+  bool need_stage = false;
+  for (int t = 0; t < 3; ++t) {
+    TableIn& T = tabs[t];
+    T.t = T3[t];
+    T.ncols = t == 0 ? 2 : t == 1 ? 3 : 4;
+    for (int j = 0; j < T.ncols; ++j) {
+      T.esize[j] = dtype_size(T.t->cols[j].type);
+      T.row_bytes += T.esize[j];
+    }
+    if (!streamed[t]) continue;
+    i64 lo = prow0(0, t), hi = lo;
+    for (int i = 0; i < n; ++i) {
+      if (prows(i, t) == 0) continue;
+      if (hi == lo) lo = prow0(i, t), hi = lo + prows(i, t);
+      lo = std::min(lo, prow0(i, t));
+      hi = std::max(hi, prow0(i, t) + prows(i, t));
+    }
+    T.row0 = lo;
+    urows[t] = hi - lo;
+    for (int j = 0; j < T.ncols; ++j) {
+      const Column& c = T.t->cols[j];
+      if (c.dev) return fail(ctx, PQ_ERR_INVALID_ARG, "streaming table mixes device columns");
+      if (c.packed) T.packed = true;
+      else if (!(c.src.kind == PQ_SRC_HOST && c.pinned)) need_stage = true;
+    }
+    i64 rows_per = (i64)((chunk_bytes - 4 * 256) / T.row_bytes) / 64 * 64;
+    rows_per = std::max<i64>(rows_per, 64);
+    if (T.packed) rows_per = std::max<i64>(rows_per / PQ_PACK_BLOCK, 1) * PQ_PACK_BLOCK;
+    for (i64 a = 0; a < urows[t]; a += rows_per)
+      chunks.push_back({t, a, std::min(rows_per, urows[t] - a)});
+  }
+
+  // Workspace: the batch header, per plan the D and M key lists, a hit list
+  // for its rows of one F chunk (or of a resident F) and a placeholder D-set;
+  // the D-sets and M tables are sized after the scans.
+  const BatchLayout L = batch_layout(n);
+  const int nslots = std::max(2, ctx->opt.ring_slots);
+  Scratch scr(ctx, s);
+  i64 f_chunk = 0;
+  for (const Chunk& ch : chunks)
+    if (ch.table == 2) f_chunk = std::max(f_chunk, ch.rows);
+  char* ws = (char*)scr.get(L.end);
+  bool any_packed = false;
+  for (int t = 0; t < 3; ++t) any_packed = any_packed || (streamed[t] && tabs[t].packed);
+  const size_t slot_bytes = any_packed ? 2 * chunk_bytes + (64 << 10) : chunk_bytes + 1024;
+  char* ring = chunks.empty() ? nullptr : (char*)scr.get(slot_bytes * nslots);
+  if (!ws || (!chunks.empty() && !ring))
+    return fail(ctx, PQ_ERR_BUDGET, "streaming batch: workspace and %d chunk slots", nslots);
+  QCtr* ctr = (QCtr*)(ws + L.ctr);
+  pq_result* out = (pq_result*)(ws + L.out);
+  std::vector<PlanDev> base(n);
+  std::vector<char*> dset_ph(n);
+  for (int i = 0; i < n; ++i) {
+    PlanDev& d = R[i].dev;
+    d.build_dset = 1;
+    const i64 hl = streamed[2] ? std::min(R[i].n_f, f_chunk) : R[i].n_f;
+    char* p = (char*)scr.get(al(R[i].n_d * 8) + al(R[i].n_m * 8) + al(hl * 4 + 4) +
+                             dset_block_bytes(6));
+    if (!p) return fail(ctx, PQ_ERR_BUDGET, "streaming batch: lists of plan %d", i);
+    d.dlist = (i64*)p;
+    d.mlist = (i64*)(p + al(R[i].n_d * 8));
+    d.hlist = (u32*)(p + al(R[i].n_d * 8) + al(R[i].n_m * 8));
+    dset_ph[i] = p + al(R[i].n_d * 8) + al(R[i].n_m * 8) + al(hl * 4 + 4);
+    dset_block_assign(dset_ph[i], 6, d);
+    d.ctr = ctr + i;
+    d.out = out + i;
+    base[i] = d;
+  }
+
+  // Descriptors for one launch: table t's rows of chunk `ch` (each plan's
+  // window of it), or the resident tables in place (ch == nullptr).
+  std::vector<char> host(L.upload_bytes());
+  bool vec = true;
+  auto upload = [&](int t, const Chunk* ch, const char* slot) -> pq_status {
+    PlanDev* descs = (PlanDev*)host.data();
+    i64* tX[3] = {(i64*)(host.data() + (L.tD - L.desc)), (i64*)(host.data() + (L.tM - L.desc)),
+                  (i64*)(host.data() + (L.tF - L.desc))};
+    for (int k = 0; k < 3; ++k) tX[k][0] = 0;
+    vec = true;
+    for (int i = 0; i < n; ++i) {
+      PlanDev d = base[i];
+      i64 tiles = 0;
+      if (t >= 0) {
+        const TableIn& T = tabs[t];
+        i64 w0 = prow0(i, t), wn = prows(i, t);
+        const void* cols[4] = {nullptr, nullptr, nullptr, nullptr};
+        if (ch) {  // the plan's rows inside this chunk
+          const i64 A = T.row0 + ch->row0, B = A + ch->rows;
+          const i64 a = std::max(A, w0), b = std::min(B, w0 + wn);
+          w0 = a;
+          wn = std::max<i64>(0, b - a);
+          for (int j = 0; j < T.ncols; ++j) {
+            cols[j] = slot + col_offset(T, ch->rows, j) + (size_t)(a - A) * T.esize[j];
+            vec = vec && (((uintptr_t)cols[j]) & 15) == 0;
+          }
+        } else {
+          vec = vec && d.vec;
+        }
+        if (t == 0) {
+          if (ch) d.d_key = (const int*)cols[0], d.d_seg = (const signed char*)cols[1];
+          d.n_d = wn;
+          d.d_tile = scan_tile(wn, 512, kTD, resident_warps(ctx, 0));
+          tiles = (wn + d.d_tile - 1) / d.d_tile;
+        } else if (t == 1) {
+          if (ch) d.m_key = (const i64*)cols[0], d.m_dref = (const int*)cols[1],
+                  d.m_date = (const int*)cols[2];
+          d.n_m = wn;
+          d.m_tile = scan_tile(wn, 128, kTM, resident_warps(ctx, 3));
+          tiles = (wn + d.m_tile - 1) / d.m_tile;
+        } else {
+          if (ch) d.f_mkey = (const i64*)cols[0], d.f_price = (const i64*)cols[1],
+                  d.f_disc = (const signed char*)cols[2], d.f_date = (const int*)cols[3];
+          d.n_f = wn;
+          d.f_tile = scan_tile(wn, 128, kTF, resident_warps(ctx, 8));
+          tiles = (wn + d.f_tile - 1) / d.f_tile;
+        }
+      }
+      descs[i] = d;
+      for (int k = 0; k < 3; ++k) tX[k][i + 1] = tX[k][i] + (k == t ? tiles : 0);
+    }
+    PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
+    return PQ_OK;
+  };
+
+  std::unique_ptr<Stager> stager;
+  if (need_stage) {
+    stager.reset(new Stager(ctx, tabs, chunks, chunk_bytes + 1024,
+                            std::max(2, ctx->opt.ring_slots), std::max(1, ctx->opt.ingest_threads)));
+    if (!stager->ok()) return fail(ctx, PQ_ERR_CUDA, "streaming batch: pinned staging");
+  }
+  std::vector<cudaEvent_t> slot_free(nslots), copy_done(nslots);
+  for (int i = 0; i < nslots; ++i) {
+    cudaEventCreateWithFlags(&slot_free[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&copy_done[i], cudaEventDisableTiming);
+  }
+  struct EvGuard {
+    std::vector<cudaEvent_t>& a;
+    std::vector<cudaEvent_t>& b;
+    ~EvGuard() {
+      for (auto e : a) cudaEventSynchronize(e), cudaEventDestroy(e);
+      for (auto e : b) cudaEventSynchronize(e), cudaEventDestroy(e);
+    }
+  } guard{slot_free, copy_done};
+  const int ncs = (int)ctx->copy_streams.size();
+  size_t issued = 0;
+  auto issue = [&](size_t c) -> pq_status {
+    const Chunk& ch = chunks[c];
+    const TableIn& T = tabs[ch.table];
+    const int slot = (int)(c % nslots);
+    cudaStream_t cs = ctx->copy_streams[c % ncs];
+    char* dst = ring + slot * slot_bytes;
+    PQ_CUDA(ctx, cudaStreamWaitEvent(cs, slot_free[slot], 0));
+    int sb = -1;
+    if (stager) {
+      sb = stager->wait(c);
+      if (sb < 0) return fail(ctx, PQ_ERR_IO, "streaming batch: %s", stager->error().c_str());
+    }
+    size_t total = 0;
+    size_t pk_off = col_offset(T, ch.rows, T.ncols);
+    for (int j = 0; j < T.ncols; ++j) {
+      const Column& col = T.t->cols[j];
+      const size_t off = col_offset(T, ch.rows, j);
+      const i64 row = T.row0 + ch.row0;
+      if (col.packed) {
+        const PackedRange pr = packed_range(col.pk, row, ch.rows);
+        const size_t tb = (size_t)(pr.b1 - pr.b0) * sizeof(PackBlock);
+        const size_t wb = (size_t)(pr.w1 - pr.w0) * 4;
+        char* dtab = dst + pk_off;
+        char* dwords = dst + pk_off + al(tb);
+        PQ_CUDA(ctx, cudaMemcpyAsync(dtab, col.pk.blocks + pr.b0, tb, cudaMemcpyHostToDevice, cs));
+        PQ_CUDA(ctx, cudaMemcpyAsync(dwords, col.pk.words + pr.w0, wb, cudaMemcpyHostToDevice, cs));
+        PQ_CUDA(ctx, unpack_launch((const PackBlock*)dtab, (const uint32_t*)dwords, pr.w0, row,
+                                   ch.rows, col.type, dst + off, ctx->num_sms, cs));
+        ctx->launches++;
+        pk_off += al(tb) + al(wb);
+        total += tb + wb;
+        continue;
+      }
+      const size_t bytes = T.esize[j] * ch.rows;
+      const void* src = stager ? (const void*)(stager->buf(sb) + off)
+                               : (const void*)((const char*)col.src.ptr + T.esize[j] * row);
+      PQ_CUDA(ctx, cudaMemcpyAsync(dst + off, src, bytes, cudaMemcpyHostToDevice, cs));
+      total += bytes;
+    }
+    PQ_CUDA(ctx, cudaEventRecord(copy_done[slot], cs));
+    if (stager) stager->release(sb, cs);
+    ctx->h2d += (int64_t)total;
+    ctx->chunks++;
+    return PQ_OK;
+  };
+  auto prefetch = [&](size_t upto) -> pq_status {
+    while (issued < chunks.size() && issued < upto) {
+      pq_status e = issue(issued);
+      if (e != PQ_OK) return e;
+      ++issued;
+    }
+    return PQ_OK;
+  };
+
+  pq_status st = upload(-1, nullptr, nullptr);
+  if (st != PQ_OK) return st;
+  PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
+  const Batch b = make_batch(ctx, ws, n, L);
+  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseFscan};
+  auto launch_table = [&](int t, bool v) -> pq_status {
+    pq_status e = launch_phase(ctx, phase_of[t], b, v, s);
+    if (e == PQ_OK && t == 2) e = launch_phase(ctx, kPhaseF, b, v, s);
+    return e;
+  };
+  std::vector<QCtr> hctr(n);
+  auto read_counters = [&]() -> pq_status {
+    PQ_CUDA(ctx, cudaMemcpyAsync(hctr.data(), ctr, sizeof(QCtr) * n, cudaMemcpyDeviceToHost, s));
+    PQ_CUDA(ctx, cudaStreamSynchronize(s));
+    return PQ_OK;
+  };
+  size_t c = 0;
+  for (int t = 0; t < 3; ++t) {
+    if (!streamed[t] || urows[t] == 0) {
+      st = upload(t, nullptr, nullptr);
+      if (st == PQ_OK) st = launch_table(t, vec);
+      if (st != PQ_OK) return st;
+    } else {
+      for (; c < chunks.size() && chunks[c].table == t; ++c) {
+        st = prefetch(c + nslots);
+        if (st != PQ_OK) return st;
+        const int slot = (int)(c % nslots);
+        PQ_CUDA(ctx, cudaStreamWaitEvent(s, copy_done[slot], 0));
+        st = upload(t, &chunks[c], ring + slot * slot_bytes);
+        if (st == PQ_OK) st = launch_table(t, vec);
+        if (st != PQ_OK) return st;
+        PQ_CUDA(ctx, cudaEventRecord(slot_free[slot], s));
+      }
+    }
+    if (t == 2) break;
+    // Size every plan's next structure from its count (one host wait).
+    st = prefetch(c + nslots);
+    if (st == PQ_OK) st = read_counters();
+    if (st != PQ_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      PlanDev& d = base[i];
+      const i64 count = (i64)(t == 0 ? hctr[i].dcount : hctr[i].mcount);
+      const int e = cap_log2(count, d.lf1024);
+      if (t == 0) {
+        char* blk = (char*)scr.get(dset_block_bytes(e));
+        if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming batch: D-set of 2^%d slots", e);
+        dset_block_assign(blk, e, d);
+        // The D scan's last block wrote the header into the placeholder.
+        PQ_CUDA(ctx, cudaMemcpyAsync(d.dset_log2, dset_ph[i], 24, cudaMemcpyDeviceToDevice, s));
+      } else {
+        const i64 parts = topk_parts(e), cap = topk_cand_cap(e, d.k);
+        char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 8) * 2 + al(parts * 4) +
+                                   al(cap * 8) * 2);
+        if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming batch: M table of 2^%d slots", e);
+        char* p = mtable_assign(blk, e, d);
+        d.tk_k = (i64*)p;
+        p += al(parts * 8);
+        d.tk_s = (i64*)p;
+        p += al(parts * 8);
+        d.tk_c = (int*)p;
+        p += al(parts * 4);
+        d.cand_k = (i64*)p;
+        p += al(cap * 8);
+        d.cand_s = (i64*)p;
+      }
+    }
+    st = upload(-1, nullptr, nullptr);
+    if (st != PQ_OK) return st;
+    const int next[2][4] = {{kPhaseDfill, kPhaseDbuild, -1, -1},
+                            {kPhaseMfill, kPhaseMbuild, kPhaseMrank, kPhaseMdup}};
+    for (int ph : next[t]) {
+      if (ph < 0) continue;
+      st = launch_phase(ctx, ph, b, true, s);
+      if (st != PQ_OK) return st;
+    }
+  }
+  st = launch_phase(ctx, kPhaseTopk, b, true, s);
+  if (st == PQ_OK) st = launch_phase(ctx, kPhaseTopk2, b, true, s);
+  if (st != PQ_OK) return st;
+  ctx->plans += n;
+  return read_back(ctx, results, out, n, s);
+}
+
+}  // namespace pqh

@@ -381,6 +381,63 @@ def test_packed_columns_resident_and_row_ranges(stream_ctx, stream, small):
         assert ctx.stats()["chunks_ingested"] > 0
 
 
+@pytest.mark.parametrize("source", ["pinned", "packed", "pageable"])
+def test_streamed_batch_shares_one_ingest(stream_ctx, stream, small, source):
+    """A batch of plans over the same streamed tables (random M and F slices,
+    predicates and k): every result matches the oracle, and the batch copies
+    each chunk of the tables once -- no more chunks than one plan over the
+    whole tables."""
+    D, M, F = small
+    ctx = stream_ctx
+
+    def col(a):
+        a = np.ascontiguousarray(a)
+        return (pq.pq_pack_column(a) if source == "packed" else
+                torch.from_numpy(a).pin_memory() if source == "pinned" else a)
+
+    with torch.cuda.stream(stream):
+        TD = pq.pq_load_columns(ctx, [col(D[c]) for c in ("key", "seg")], mode=pq.PQ_STREAMING)
+        TM = pq.pq_load_columns(ctx, [col(M[c]) for c in ("key", "dref", "date")],
+                                mode=pq.PQ_STREAMING)
+        TF = pq.pq_load_columns(ctx, [col(F[c]) for c in ("mkey", "price", "disc", "date2")],
+                                mode=pq.PQ_STREAMING)
+        c0 = ctx.stats()["chunks_ingested"]
+        pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF), stream=stream)
+        ctx.sync(stream)
+        whole = ctx.stats()["chunks_ingested"] - c0
+        starts = datagen.f_starts(1, len(M["key"]), len(F["mkey"]))
+        rng = np.random.default_rng(55)
+        plans, specs = random_plans(rng, (TD, TM, TF), 24, len(M["key"]), len(F["mkey"]),
+                                    starts)
+        c0 = ctx.stats()["chunks_ingested"]
+        res = pq.pq_run_batch(ctx, plans, stream=stream)
+        ctx.sync(stream)
+        assert ctx.stats()["chunks_ingested"] - c0 <= whole
+    for i, sp in enumerate(specs):
+        assert_same(res[i].as_dict(), oracle_plan(D, M, F, **sp), f"{source} plan {i}")
+
+
+def test_serving_over_streamed_tables(stream_ctx, stream, small):
+    """Requests over host-resident (streamed) tables: served results equal
+    the oracle's."""
+    D, M, F = small
+    ctx = stream_ctx
+    pin = lambda t, names: [torch.from_numpy(np.ascontiguousarray(t[c])).pin_memory()
+                            for c in names]
+    TD = pq.pq_load_columns(ctx, pin(D, ("key", "seg")), mode=pq.PQ_STREAMING)
+    TM = pq.pq_load_columns(ctx, pin(M, ("key", "dref", "date")), mode=pq.PQ_STREAMING)
+    TF = pq.pq_load_columns(ctx, pin(F, ("mkey", "price", "disc", "date2")),
+                            mode=pq.PQ_STREAMING)
+    starts = datagen.f_starts(1, len(M["key"]), len(F["mkey"]))
+    rng = np.random.default_rng(77)
+    plans, specs = random_plans(rng, (TD, TM, TF), 40, len(M["key"]), len(F["mkey"]), starts)
+    tickets = [pq.pq_submit(ctx, p) for p in plans]
+    for i, t in enumerate(tickets):
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=120_000)
+        assert st == pq.PQ_OK
+        assert_same(res.as_dict(), oracle_plan(D, M, F, **specs[i]), f"served {i}")
+
+
 def test_streaming_fact_table_with_resident_dimensions(stream_ctx, stream, small):
     D, M, F = small
     ctx = stream_ctx
