@@ -605,7 +605,7 @@ def run_serve(args):
         th_plain = time.perf_counter() - t0
         h1 = hctx.stats()["h2d_bytes"]
         t0 = time.perf_counter()
-        bs = 64
+        bs = 256
         for a in range(0, nh, bs):
             sub = hplans[a:a + bs]
             arr = (pq.pq_plan * len(sub))(*sub)

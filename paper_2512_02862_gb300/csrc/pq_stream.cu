@@ -555,8 +555,13 @@ pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_resul
     i64 rows_per = (i64)((chunk_bytes - 4 * 256) / T.row_bytes) / 64 * 64;
     rows_per = std::max<i64>(rows_per, 64);
     if (T.packed) rows_per = std::max<i64>(rows_per / PQ_PACK_BLOCK, 1) * PQ_PACK_BLOCK;
-    for (i64 a = 0; a < urows[t]; a += rows_per)
-      chunks.push_back({t, a, std::min(rows_per, urows[t] - a)});
+    for (i64 a = 0; a < urows[t]; a += rows_per) {
+      const i64 A = lo + a, B = A + std::min(rows_per, urows[t] - a);
+      bool used = false;  // a chunk between the plans' row ranges is not read
+      for (int i = 0; i < n && !used; ++i)
+        used = prows(i, t) > 0 && prow0(i, t) < B && prow0(i, t) + prows(i, t) > A;
+      if (used) chunks.push_back({t, a, B - A});
+    }
   }
 
   // Workspace: the batch header, per plan the D and M key lists, a hit list
