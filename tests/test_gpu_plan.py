@@ -417,6 +417,28 @@ def test_streamed_batch_shares_one_ingest(stream_ctx, stream, small, source):
         assert_same(res[i].as_dict(), oracle_plan(D, M, F, **sp), f"{source} plan {i}")
 
 
+def test_streamed_batch_with_resident_dimensions(stream_ctx, stream, small):
+    """A batch whose D and M are resident and whose F is streamed (packed):
+    the resident tables are scanned in place, F once for all plans."""
+    D, M, F = small
+    ctx = stream_ctx
+    with torch.cuda.stream(stream):
+        d, m = to_dev(D), to_dev(M)
+        TD = pq.pq_load_columns(ctx, [d["key"], d["seg"]])
+        TM = pq.pq_load_columns(ctx, [m["key"], m["dref"], m["date"]])
+        TF = pq.pq_load_columns(ctx, [pq.pq_pack_column(F[c])
+                                      for c in ("mkey", "price", "disc", "date2")],
+                                mode=pq.PQ_STREAMING)
+        starts = datagen.f_starts(1, len(M["key"]), len(F["mkey"]))
+        rng = np.random.default_rng(91)
+        plans, specs = random_plans(rng, (TD, TM, TF), 16, len(M["key"]), len(F["mkey"]),
+                                    starts)
+        res = pq.pq_run_batch(ctx, plans, stream=stream)
+        ctx.sync(stream)
+    for i, sp in enumerate(specs):
+        assert_same(res[i].as_dict(), oracle_plan(D, M, F, **sp), f"plan {i}")
+
+
 def test_serving_over_streamed_tables(stream_ctx, stream, small):
     """Requests over host-resident (streamed) tables: served results equal
     the oracle's."""
