@@ -63,6 +63,8 @@ def _load():
         lib.oracle_run_plan.restype = i32
         lib.oracle_plan_groups.argtypes = plan + [vp, vp, i64]
         lib.oracle_plan_groups.restype = i64
+        lib.oracle_run_plan_aggfirst.argtypes = plan + [i64, i32, vp, vp, vp, vp]
+        lib.oracle_run_plan_aggfirst.restype = i32
         _lib = lib
     return _lib
 
@@ -155,6 +157,21 @@ def run_plan(D: dict, M: dict, F: dict, seg=1, m_date_lt=1200, f_date_gt=1200, k
     st = _load().oracle_run_plan(*_plan_args(D, M, F, d_op, seg, m_op, m_date_lt, f_op,
                                              f_date_gt), k, _p(ok), _p(os_),
                                  ctypes.addressof(n_out), ctypes.addressof(ng))
+    return dict(keys=ok[:n_out.value].copy(), sums=os_[:n_out.value].copy(),
+                ngroups=int(ng.value), status=int(st))
+
+
+def run_plan_aggfirst(D: dict, M: dict, F: dict, seg=1, m_date_lt=1200, f_date_gt=1200,
+                      having=-(1 << 63), k=10, d_op="==", m_op="<", f_op=">"):
+    """The aggregate-first plan: F grouped by mkey (date2 filter), groups with
+    sum > having whose key is in M' (semi-join), top-k."""
+    ok = np.empty(max(k, 1), dtype=np.int64)
+    os_ = np.empty(max(k, 1), dtype=np.int64)
+    n_out = ctypes.c_int64(0)
+    ng = ctypes.c_int64(0)
+    st = _load().oracle_run_plan_aggfirst(
+        *_plan_args(D, M, F, d_op, seg, m_op, m_date_lt, f_op, f_date_gt), int(having), k,
+        _p(ok), _p(os_), ctypes.addressof(n_out), ctypes.addressof(ng))
     return dict(keys=ok[:n_out.value].copy(), sums=os_[:n_out.value].copy(),
                 ngroups=int(ng.value), status=int(st))
 

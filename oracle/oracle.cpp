@@ -269,6 +269,47 @@ int oracle_run_plan(const int32_t* d_key, const int8_t* d_seg, int64_t n_d,
   return status;
 }
 
+/* The aggregate-first plan (a large materialised group-by filtered on its
+ * aggregate, the shape of the paper's Q18 remark, Sec. 6.3):
+ *   G  = for the F rows with f.date2 op_f c_f, grouped by f.mkey:
+ *        sum = sum of f.price * (100 - f.disc)      (every group, materialised)
+ *   M' = { m.key : m.date op_m c_m and m.dref in D' },  D' as above
+ *   result = the groups with sum > having and key in M' (a semi-join: a key
+ *            held by several M' rows counts once), top-k by sum desc, key asc,
+ *            and their number.
+ * Returns 0, or 7 if a group sum leaves int64. */
+int oracle_run_plan_aggfirst(const int32_t* d_key, const int8_t* d_seg, int64_t n_d,
+                             const int64_t* m_key, const int32_t* m_dref, const int32_t* m_date,
+                             int64_t n_m, const int64_t* f_mkey, const int64_t* f_price,
+                             const int8_t* f_disc, const int32_t* f_date2, int64_t n_f, int d_op,
+                             int64_t d_c, int m_op, int64_t m_c, int f_op, int64_t f_c,
+                             int64_t having, int k, int64_t* out_keys, int64_t* out_sums,
+                             int64_t* n_out, int64_t* ngroups) {
+  std::unordered_set<int64_t> d_pass;
+  for (int64_t i = 0; i < n_d; ++i)
+    if (pred(d_op, d_seg[i], d_c)) d_pass.insert(d_key[i]);
+  std::unordered_set<int64_t> m_keys;
+  for (int64_t i = 0; i < n_m; ++i)
+    if (pred(m_op, m_date[i], m_c) && d_pass.count(m_dref[i])) m_keys.insert(m_key[i]);
+  std::map<int64_t, __int128> g;
+  for (int64_t i = 0; i < n_f; ++i)
+    if (pred(f_op, f_date2[i], f_c))
+      g[f_mkey[i]] += static_cast<__int128>(f_price[i]) * (100 - f_disc[i]);
+  std::vector<int64_t> keys, vals;
+  int status = 0;
+  for (const auto& kv : g) {
+    if (!fits_int64(kv.second)) status = 7;
+    if (kv.second > having && m_keys.count(kv.first)) {
+      keys.push_back(kv.first);
+      vals.push_back(static_cast<int64_t>(kv.second));
+    }
+  }
+  *ngroups = static_cast<int64_t>(keys.size());
+  *n_out = oracle_topk(keys.data(), vals.data(), static_cast<int64_t>(keys.size()), k, out_keys,
+                       out_sums);
+  return status;
+}
+
 /* Every group of the plan (key, sum) sorted by key.  Returns the group
  * count; writes at most cap rows. */
 int64_t oracle_plan_groups(const int32_t* d_key, const int8_t* d_seg, int64_t n_d,
