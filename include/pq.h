@@ -321,7 +321,8 @@ enum pq_plan_flags {
   PQ_PLAN_CACHE_DSET = 2,   /* keep the filtered dimension key set resident and
                                reuse it for later plans with the same D table,
                                row range and predicate                         */
-  PQ_PLAN_NO_GRAPH = 4      /* never replay a captured CUDA graph              */
+  PQ_PLAN_NO_GRAPH = 4,     /* never replay a captured CUDA graph              */
+  PQ_PLAN_AGG_FIRST = 8     /* the aggregate-first plan (below)                */
 };
 
 /* The three-table plan (the running example's shape, Sec. 5.1):
@@ -334,7 +335,19 @@ enum pq_plan_flags {
  * Column order and types: D = [key int32, seg int8]; M = [key int64,
  * dref int32, date int32]; F = [mkey int64, price int64, disc int8,
  * date2 int32].  Each table may be restricted to the rows
- * [row0, row0 + rows) (rows < 0: to the end). */
+ * [row0, row0 + rows) (rows < 0: to the end).
+ *
+ * With PQ_PLAN_AGG_FIRST the plan aggregates first (a large materialised
+ * group-by filtered on its aggregate, the shape of Sec. 6.3's Q18 remark):
+ *   G = F rows with F.date2 op_f c_f grouped by F.mkey, sum = sum of
+ *       F.price * (100 - F.disc) over the group (every group materialised);
+ *   result = the groups with sum > `having` whose key is an M' key (a
+ *   semi-join: a key held by several M' rows counts once), top-k by sum
+ *   desc, key asc, and their number; `hits` = the F rows aggregated.
+ * It needs resident tables whose F keys span at most 4 * F rows + 4096
+ * values (PQ_ERR_INVALID_ARG otherwise).  Overflow is reported when the
+ * magnitudes of all summed revenues reach 2^62, the bound below which no
+ * group sum can leave int64. */
 typedef struct pq_plan {
   const pq_table* D;
   const pq_table* M;
@@ -346,6 +359,7 @@ typedef struct pq_plan {
   int32_t log2P;        /* <= 0: context default */
   float load_factor;    /* <= 0: context default */
   int32_t reserved;
+  int64_t having;       /* PQ_PLAN_AGG_FIRST: keep groups whose sum > having */
 } pq_plan;
 
 /* Result of one plan; the device writes it with one copy. */

@@ -70,7 +70,7 @@ class pq_plan(Structure):
                 ("d_op", c_int32), ("m_op", c_int32), ("f_op", c_int32), ("k", c_int32),
                 ("d_c", c_int64), ("m_c", c_int64), ("f_c", c_int64),
                 ("flags", c_int32), ("log2P", c_int32), ("load_factor", c_float),
-                ("reserved", c_int32)]
+                ("reserved", c_int32), ("having", c_int64)]
 
 
 class pq_result(Structure):
@@ -427,17 +427,25 @@ def pq_load_columns(ctx: Context, columns, mode: int = PQ_RESIDENT, stream=None)
 
 
 # ------------------------------------------------------------------- plans ----
+PQ_PLAN_AGG_FIRST = 8
+
+
 def make_plan(D: Table, M: Table, F: Table, seg=1, m_date_lt=1200, f_date_gt=1200, k=10,
               d_op="==", m_op="<", f_op=">", rows=None, flags=0, log2P=0,
-              load_factor=0.0) -> pq_plan:
+              load_factor=0.0, having=None) -> pq_plan:
     """The three-table plan: D.seg d_op seg, M.date m_op m_date_lt,
-    F.date2 f_op f_date_gt; ``rows`` = dict(d=(row0, n), m=..., f=...)."""
+    F.date2 f_op f_date_gt; ``rows`` = dict(d=(row0, n), m=..., f=...).
+    ``having`` given: the aggregate-first plan (groups of F by mkey with
+    sum > having whose key is in M')."""
     rows = rows or {}
     d0, dn = rows.get("d", (0, -1))
     m0, mn = rows.get("m", (0, -1))
     f0, fn = rows.get("f", (0, -1))
+    if having is not None:
+        flags |= PQ_PLAN_AGG_FIRST
     return pq_plan(D.h, M.h, F.h, d0, dn, m0, mn, f0, fn, CMP[d_op], CMP[m_op], CMP[f_op], k,
-                   seg, m_date_lt, f_date_gt, flags, log2P, load_factor, 0)
+                   seg, m_date_lt, f_date_gt, flags, log2P, load_factor, 0,
+                   int(having) if having is not None else 0)
 
 
 def pinned_results(n: int):

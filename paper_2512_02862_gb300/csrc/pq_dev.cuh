@@ -67,7 +67,7 @@ struct Pred32 {
   unsigned span;
   unsigned neg;
 };
-__device__ __forceinline__ Pred32 to32(const Pred& p) {
+__host__ __device__ __forceinline__ Pred32 to32(const Pred& p) {
   const i64 lo = p.lo < (i64)INT32_MIN ? (i64)INT32_MIN : p.lo;
   const i64 hi = p.hi > (i64)INT32_MAX ? (i64)INT32_MAX : p.hi;
   Pred32 r;

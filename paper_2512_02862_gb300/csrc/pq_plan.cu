@@ -51,7 +51,7 @@ __global__ void k_key_range(const void* col, int is64, i64 n, u64* out) {
 
 // The key range of column c of a resident table, measured once (one kernel
 // and a read-back on stream s) and kept with the column.
-static bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
+bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
   const Column& col = t->cols[c];
   if (col.has_range) return true;
   if (!col.dev || t->nrows <= 0) return false;
@@ -452,6 +452,16 @@ size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n) {
 pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
                              cudaStream_t s, bool allow_graph) {
   if (n <= 0 || !plans || !results) return fail(ctx, PQ_ERR_INVALID_ARG, "batch: bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (plans[i].flags & PQ_PLAN_AGG_FIRST) {  // aggregate-first plans run one by one
+      for (int j = 0; j < n; ++j) {
+        pq_status st = plans[j].flags & PQ_PLAN_AGG_FIRST
+                           ? run_plan_aggfirst(ctx, plans[j], &results[j], s)
+                           : run_batch_internal(ctx, &plans[j], 1, &results[j], s, false);
+        if (st != PQ_OK) return st;
+      }
+      return PQ_OK;
+    }
   std::vector<ResolvedPlan> R(n);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
@@ -727,6 +737,8 @@ extern "C" {
 
 pq_status pq_run_plan(pq_ctx* ctx, const pq_plan* plan, pq_result* result, void* stream) {
   if (!ctx || !plan || !result) return PQ_ERR_INVALID_ARG;
+  if (plan->flags & PQ_PLAN_AGG_FIRST)
+    return pqh::run_plan_aggfirst(ctx, *plan, result, pqh::S(stream));
   pqh::ResolvedPlan r;
   pq_status st = pqh::resolve_plan(ctx, *plan, r, false);
   if (st != PQ_OK) return st;

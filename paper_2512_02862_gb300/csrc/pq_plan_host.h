@@ -54,6 +54,14 @@ inline char* mtable_assign(char* p, int e, pqk::PlanDev& d) {
   return p + mtable_bytes(e);
 }
 
+// The key range of column c of a resident table (Column::umin/umax), measured
+// on first use by one kernel and a read-back on stream s; false if the column
+// is not on the device or the table is empty.
+bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s);
+
+// The aggregate-first plan (PQ_PLAN_AGG_FIRST; pq_agg.cu).
+pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result, cudaStream_t s);
+
 // Per-plan workspace bytes (excluding a cached D-set block).
 size_t plan_bytes(const ResolvedPlan& r);
 
