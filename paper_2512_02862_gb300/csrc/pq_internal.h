@@ -96,6 +96,9 @@ PackedRange packed_range(const PackedView& v, int64_t row0, int64_t n);
 cudaError_t unpack_launch(const PackBlock* dblk, const uint32_t* dwords, int64_t w0, int64_t row0,
                           int64_t n, int type, void* out, int num_sms, cudaStream_t s);
 
+// Descent positions kept per key column (see Column::desc).
+constexpr int kMaxDescents = 8;
+
 struct Column {
   int type = 0;           // pq_dtype
   bool packed = false;    // source is a packed column (PQ_SRC_PACKED)
@@ -109,6 +112,11 @@ struct Column {
   // ukey = key xor 2^63), measured on first use by a plan and kept.
   mutable bool has_range = false;
   mutable uint64_t umin = 0, umax = 0;
+  // Key order, measured with the range: the rows that start a new
+  // non-decreasing run of keys (ascending), ndesc of them, or ndesc = -1 when
+  // there are more than kMaxDescents.
+  mutable int ndesc = -1;
+  mutable int64_t desc[kMaxDescents] = {};
 };
 
 }  // namespace pqh

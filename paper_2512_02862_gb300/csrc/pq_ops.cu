@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   __shared__ bool s_last;
   __shared__ i64 s_scr[8][64];
   const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
-  const i64 per = (n + gridDim.x - 1) / gridDim.x;
+  // Only the first nb blocks take pairs (at least 2048 each), so that a
+  // small count read on the device leaves few lists to merge.
+  const int nb = (int)max((i64)1, min((i64)gridDim.x, (n + 2047) / 2048));
+  const i64 per = (n + nb - 1) / nb;
   const i64 lo = min(n, per * blockIdx.x), hi = min(n, lo + per);
   TopList L;
   L.bind(s_scr[threadIdx.x >> 5]);
@@ -446,18 +449,33 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
     if (lane == 0) s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x >= 32) return;
+  if (!s_last) return;
+  // The last block merges the blocks' lists: each warp offers 32 entries
+  // of the grid * K list slots per round; an entry, its slot's list count
+  // and its value are independent loads (L2, not L1: other blocks wrote
+  // them), so a round costs one memory latency.  Slots past a list's count
+  // are in the buffer but unused.
   __threadfence();
   L.clear();
-  const i64 total = (i64)gridDim.x * K;
-  for (i64 j = 0; j < total; j += 32) {
-    const i64 e = j + lane;
-    const bool v = e < total && (int)(e % K) < *(volatile int*)&part_c[e / K];
-    const i64 k = v ? *(volatile i64*)&part_k[e] : 0, s = v ? *(volatile i64*)&part_s[e] : 0;
+  const int total = nb * K;
+  for (int base = (threadIdx.x >> 5) * 32; base < total; base += blockDim.x) {
+    const int e = base + lane;
+    bool v = false;
+    i64 k = 0, s = 0;
+    if (e < total) {
+      const int b = e / K;
+      const int c = __ldcg(part_c + b);
+      k = __ldcg(part_k + e);
+      s = __ldcg(part_s + e);
+      v = e - b * K < c;
+    }
     L.offer(K, v, k, s);
   }
-  L.store(out_keys, out_sums);
-  if (lane == 0) *d_nout = L.cnt;
+  tk_block_merge(L, K, sk, ss, sc);
+  if (threadIdx.x < 32) {
+    L.store(out_keys, out_sums);
+    if (lane == 0) *d_nout = L.cnt;
+  }
 }
 
 template <typename T>

@@ -37,14 +37,24 @@ static bool check_types(const pq_table* t, std::initializer_list<int> types) {
 
 // Range of an int32 / int64 key column (order-preserving ukey): out[0] holds
 // ~min, out[1] the max, both zero-initialised and grown with atomicMax.
+// out[2] counts the descents (rows whose key is greater than the next row's;
+// counting stops soon after kMaxDescents) and out[3 + j] holds the row after
+// descent j for the first kMaxDescents of them, in no particular order.
 __global__ void k_key_range(const void* col, int is64, i64 n, u64* out) {
   u64 nmin = 0, umax = 0;
+  auto at = [&](i64 i) {
+    return is64 ? __ldg(reinterpret_cast<const i64*>(col) + i)
+                : (i64)__ldg(reinterpret_cast<const int*>(col) + i);
+  };
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
        i += (i64)gridDim.x * blockDim.x) {
-    const i64 k = is64 ? __ldg(reinterpret_cast<const i64*>(col) + i)
-                       : (i64)__ldg(reinterpret_cast<const int*>(col) + i);
+    const i64 k = at(i);
     nmin = max(nmin, ~ukey(k));
     umax = max(umax, ukey(k));
+    if (i + 1 < n && k > at(i + 1) && *(volatile u64*)(out + 2) <= (u64)kMaxDescents) {
+      const u64 j = atomicAdd(reinterpret_cast<unsigned long long*>(out + 2), 1ULL);
+      if (j < (u64)kMaxDescents) out[3 + j] = (u64)(i + 1);
+    }
   }
   range_commit(nmin, umax, out, out + 1);
 }
@@ -58,12 +68,13 @@ bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
   std::lock_guard<std::mutex> g(ctx->small_mu);
   u64* d = (u64*)ctx->arena.alloc(256);
   if (!d) return false;
-  bool ok = cudaMemsetAsync(d, 0, 16, s) == cudaSuccess;
+  bool ok = cudaMemsetAsync(d, 0, 24, s) == cudaSuccess;
+  constexpr size_t rb = 8 * (3 + kMaxDescents);
   if (ok) {
     const int grid = (int)std::min<i64>((t->nrows + 255) / 256, (i64)ctx->num_sms * 8);
     k_key_range<<<grid, 256, 0, s>>>(col.dev, col.type == PQ_INT64 ? 1 : 0, t->nrows, d);
     ok = cudaGetLastError() == cudaSuccess &&
-         cudaMemcpyAsync(ctx->h_small, d, 16, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+         cudaMemcpyAsync(ctx->h_small, d, rb, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
          cudaStreamSynchronize(s) == cudaSuccess;
     ctx->launches++;
   }
@@ -74,6 +85,10 @@ bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
   }
   col.umin = ~(u64)ctx->h_small[0];
   col.umax = (u64)ctx->h_small[1];
+  const int64_t nd = ctx->h_small[2];
+  col.ndesc = nd > kMaxDescents ? -1 : (int)nd;
+  for (int j = 0; j < col.ndesc; ++j) col.desc[j] = ctx->h_small[3 + j];
+  std::sort(col.desc, col.desc + std::max(col.ndesc, 0));
   col.has_range = true;
   return true;
 }

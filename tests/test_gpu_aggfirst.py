@@ -101,6 +101,84 @@ def test_repeated_keys_and_row_ranges(ctx, stream):
     cut = lambda t, r0, n: {c: v[r0:r0 + n] for c, v in t.items()}
     same(got, oracle.run_plan_aggfirst(D, cut(M, 50, 30_000), cut(F, 1000, 100_000), having=0,
                                        k=20), "rows")
+    # an odd first row: the scan's unaligned (scalar) path
+    rows = dict(f=(1001, 99_999), m=(3, 39_000))
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=1, k=64, having=I64_MIN, rows=rows))
+    same(got, oracle.run_plan_aggfirst(D, cut(M, 3, 39_000), cut(F, 1001, 99_999), seg=1,
+                                       having=I64_MIN, k=64), "odd rows")
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
+@pytest.mark.parametrize("having", [I64_MIN, 0, 10_000_000_000])
+def test_zipf_keys(ctx, stream, having):
+    """Keys in no order with heavy hitters: one group's rows fall in many
+    tiles and many runs."""
+    D, M, F = datagen.make(2000, 30_000, 300_000, seed=5, fk="zipf", zipf_s=1.1)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    for p in PREDS[:3]:
+        got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=p["seg"], m_date_lt=p["mc"],
+                                            f_date_gt=p["fc"], k=64, having=having))
+        same(got, oracle.run_plan_aggfirst(D, M, F, seg=p["seg"], m_date_lt=p["mc"],
+                                           f_date_gt=p["fc"], having=having, k=64),
+             f"zipf {p} {having}")
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
+def sorted_chunks(nseg, seed, narrow=False):
+    """F as nseg chunks, each in key order, over overlapping keys (nseg - 1
+    descents), with a few keys of hundreds of rows, so that runs span whole
+    128-row tiles and a key's rows fall in several chunks."""
+    rng = np.random.default_rng(seed)
+    R = 5000
+    D = dict(key=np.arange(1, 101, dtype=np.int32), seg=rng.integers(0, 5, 100).astype(np.int8))
+    M = dict(key=np.arange(R, dtype=np.int64) * 2, dref=rng.integers(1, 101, R).astype(np.int32),
+             date=rng.integers(0, 2406, R).astype(np.int32))
+    keys = []
+    for i in range(nseg):
+        if narrow and i > 0:        # later chunks over narrow key ranges
+            lo = 600 * (nseg - i)     # each lower than the last: a descent
+            k = np.concatenate([rng.integers(lo, lo + 500, 800), np.full(400, lo + 250)])
+        else:
+            k = rng.integers(0, 2 * R, 6000)
+            k = np.concatenate([k, np.full(700, rng.integers(0, 2 * R)), np.full(300, 2 * R - 2)])
+        keys.append(np.sort(k))
+    mk = np.concatenate(keys).astype(np.int64)
+    n = len(mk)
+    F = dict(mkey=mk, price=rng.integers(90_000, 10_500_000, n).astype(np.int64),
+             disc=rng.integers(0, 11, n).astype(np.int8),
+             date2=rng.integers(0, 2406, n).astype(np.int32))
+    return D, M, F
+
+
+@pytest.mark.parametrize("nseg,narrow", [(1, False), (2, False), (9, False), (10, False),
+                                         (3, True), (9, True)])
+def test_key_ordered_segments(ctx, stream, nseg, narrow):
+    """The scan of F in key-ordered segments (up to 8 descents) and the
+    reduction path beyond; row ranges that cut segments; later segments
+    over narrow key ranges (groups outside them are final at commit)."""
+    D, M, F = sorted_chunks(nseg, seed=nseg, narrow=narrow)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    cut = lambda t, r0, n: {c: v[r0:r0 + n] for c, v in t.items()}
+    n_f = len(F["mkey"])
+    for having in (I64_MIN, 0, 1_000_000_000, 20_000_000_000):
+        for p in PREDS[:2]:
+            got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=p["seg"], m_date_lt=p["mc"],
+                                                f_date_gt=p["fc"], k=64, having=having))
+            same(got, oracle.run_plan_aggfirst(D, M, F, seg=p["seg"], m_date_lt=p["mc"],
+                                               f_date_gt=p["fc"], having=having, k=64),
+                 f"{nseg} {p} {having}")
+        for r0, n in ((1, n_f - 1), (7001, n_f - 9000), (3, 6500)):
+            if 4 * n + 4096 < 10_000:    # too few rows for the keys' span: refused
+                continue
+            got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=1, m_date_lt=2000, f_date_gt=300,
+                                                k=64, having=having, rows=dict(f=(r0, n))))
+            same(got, oracle.run_plan_aggfirst(D, M, cut(F, r0, n), seg=1, m_date_lt=2000,
+                                               f_date_gt=300, having=having, k=64),
+                 f"{nseg} rows {r0} {n} {having}")
     for t in (TD, TM, TF):
         t.free(stream)
 
