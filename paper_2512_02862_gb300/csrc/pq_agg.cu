@@ -386,59 +386,108 @@ int resident_blocks(K k) {
 
 }  // namespace
 
+namespace {
+
+// Sizes of an aggregate-first plan's workspace, from the tables' key ranges
+// and key order (measured once per key column).
+struct AggShape {
+  u64 d_bits = 0, m_bits = 0, f_bits = 0;
+  size_t cap = 1;       // candidates: at most one per key of M' inside the F range
+  bool sorted = false;  // F scanned as its non-decreasing segments
+  std::vector<i64> seg;  // segment starts within the plan's F rows, then n_f
+  i64 ntiles = 0;        // tiles of the longest segment
+  size_t head = 0, sums_bytes = 0, zero = 0, edge_bytes = 0, cand_bytes = 0;
+};
+
+size_t words_bytes(u64 bits) { return (size_t)((bits + 31) / 32) * 4; }
+
+pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cudaStream_t s,
+                    AggShape& g) {
+  const pq_table* T[3] = {plan.D, plan.M, plan.F};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (s) cudaStreamIsCapturing(s, &cap);
+  for (int t = 0; t < 3; ++t) {
+    if (T[t]->nrows <= 0 || T[t]->cols[0].has_range) continue;
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(ctx, PQ_ERR_INVALID_ARG,
+                  "aggregate-first plan: run it once before capturing a stream (key ranges)");
+    if (!ensure_range(ctx, T[t], 0, s))
+      return fail(ctx, PQ_ERR_CUDA, "aggregate-first plan: key range of table %d", t);
+  }
+  auto span = [&](int t) -> u64 {
+    const Column& c = T[t]->cols[0];
+    return c.has_range && c.umax >= c.umin ? c.umax - c.umin + 1 : 0;
+  };
+  g.d_bits = span(0), g.m_bits = span(1), g.f_bits = span(2);
+  const u64 dense_cap = 4ULL * (u64)std::max<i64>(r.n_f, 1) + 4096;
+  if (g.f_bits > dense_cap || g.f_bits > kMaxBmBits || g.m_bits > kMaxBmBits ||
+      g.d_bits > kMaxBmBits)
+    return fail(ctx, PQ_ERR_INVALID_ARG,
+                "aggregate-first plan: F keys span %llu values for %lld rows (dense keys needed)",
+                (unsigned long long)g.f_bits, (long long)r.n_f);
+  g.cap = (size_t)std::max<u64>(std::min(g.f_bits, g.m_bits), 1);
+  // F as its non-decreasing segments of keys: in a segment each group is one
+  // run of rows, stored once, so the sum array needs no zeroing.  More than
+  // kMaxDescents segments: reductions into a zeroed array.
+  const Column& fk = T[2]->cols[0];
+  g.sorted = fk.ndesc >= 0;
+  g.seg.assign(1, 0);
+  if (g.sorted)
+    for (int j = 0; j < fk.ndesc; ++j)
+      if (fk.desc[j] > r.f_row0 && fk.desc[j] < r.f_row0 + r.n_f) g.seg.push_back(fk.desc[j] - r.f_row0);
+  g.seg.push_back(r.n_f);
+  for (size_t j = 0; j + 1 < g.seg.size(); ++j)
+    g.ntiles = std::max(g.ntiles, (g.seg[j + 1] - g.seg[j] + 127) / 128);
+  // Zeroed: counters, D' and M' bitmaps, hit flags (and the sums unless sorted).
+  g.head = 256 + al256(words_bytes(g.d_bits)) + al256(words_bytes(g.m_bits)) +
+           al256((size_t)(g.f_bits + 15) / 16 * 16);
+  g.sums_bytes = al256(8 * (size_t)std::max<u64>(g.f_bits, 1));
+  g.zero = g.head + (g.sorted ? 0 : g.sums_bytes);
+  g.edge_bytes = g.sorted ? al256(sizeof(TileEdge) * g.ntiles) + al256(g.ntiles) : 0;
+  g.cand_bytes = al256(16 * g.cap) + al256(16 * PQ_MAX_K) + 256 + sizeof(pq_result);
+  return PQ_OK;
+}
+
+}  // namespace
+
+pq_status aggfirst_bytes(pq_ctx* ctx, const pq_plan& plan, size_t* bytes) {
+  ResolvedPlan r;
+  AggShape g;
+  pq_status st = resolve_plan(ctx, plan, r, true);
+  if (st == PQ_OK) st = agg_shape(ctx, plan, r, nullptr, g);
+  if (st != PQ_OK) return st;
+  // The top-k operator's own scratch: lists of at most 2 blocks per SM.
+  const size_t topk = (size_t)ctx->num_sms * 2 * (16 * PQ_MAX_K + 4) + 512;
+  *bytes = g.head + g.sums_bytes + g.edge_bytes + al256(g.cand_bytes) + al256(topk) + 4 * 256;
+  return PQ_OK;
+}
+
 pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result, cudaStream_t s) {
   ResolvedPlan r;
   pq_status st = resolve_plan(ctx, plan, r, true);
   if (st != PQ_OK) return st;
   const PlanDev& d = r.dev;
-  // Key ranges of the whole tables, measured once per column.
   const pq_table* T[3] = {plan.D, plan.M, plan.F};
-  for (int t = 0; t < 3; ++t)
-    if (T[t]->nrows > 0 && !ensure_range(ctx, T[t], 0, s))
-      return fail(ctx, PQ_ERR_CUDA, "aggregate-first plan: key range of table %d", t);
-  auto span = [&](int t) -> u64 {
-    const Column& c = T[t]->cols[0];
-    return c.has_range && c.umax >= c.umin ? c.umax - c.umin + 1 : 0;
-  };
-  const u64 d_bits = span(0), m_bits = span(1), f_bits = span(2);
-  const u64 dense_cap = 4ULL * (u64)std::max<i64>(r.n_f, 1) + 4096;
-  if (f_bits > dense_cap || f_bits > kMaxBmBits || m_bits > kMaxBmBits || d_bits > kMaxBmBits)
-    return fail(ctx, PQ_ERR_INVALID_ARG,
-                "aggregate-first plan: F keys span %llu values for %lld rows (dense keys needed)",
-                (unsigned long long)f_bits, (long long)r.n_f);
-  // Candidates: at most one per key of M' inside the F range.
-  const size_t cap = (size_t)std::max<u64>(std::min(f_bits, m_bits), 1);
-  auto words = [](u64 bits) { return (size_t)((bits + 31) / 32) * 4; };
-  // F as its non-decreasing segments of keys (measured with its range): in a
-  // segment each group is one run of rows, stored once, so the sum array
-  // needs no zeroing.  More than kMaxDescents segments: reductions into a
-  // zeroed array.
-  const Column& fk = T[2]->cols[0];
-  const bool sorted = fk.ndesc >= 0;
-  std::vector<i64> seg{0};  // segment starts within the plan's F rows, then n_f
-  if (sorted)
-    for (int j = 0; j < fk.ndesc; ++j)
-      if (fk.desc[j] > r.f_row0 && fk.desc[j] < r.f_row0 + r.n_f) seg.push_back(fk.desc[j] - r.f_row0);
-  seg.push_back(r.n_f);
-  i64 ntiles = 0;
-  for (size_t j = 0; j + 1 < seg.size(); ++j) ntiles = std::max(ntiles, (seg[j + 1] - seg[j] + 127) / 128);
+  AggShape g;
+  st = agg_shape(ctx, plan, r, s, g);
+  if (st != PQ_OK) return st;
+  const u64 d_bits = g.d_bits, m_bits = g.m_bits, f_bits = g.f_bits;
+  const size_t cap = g.cap;
+  const bool sorted = g.sorted;
+  const std::vector<i64>& seg = g.seg;
+  const size_t head = g.head, sums_bytes = g.sums_bytes, zero = g.zero, edge_bytes = g.edge_bytes;
+  const i64 ntiles = g.ntiles;
   Scratch scr(ctx, s);
-  // Zeroed: counters, D' and M' bitmaps, hit flags (and the sums unless sorted).
-  const size_t head = 256 + al256(words(d_bits)) + al256(words(m_bits)) +
-                      al256((size_t)(f_bits + 15) / 16 * 16);
-  const size_t sums_bytes = al256(8 * (size_t)std::max<u64>(f_bits, 1));
-  const size_t zero = head + (sorted ? 0 : sums_bytes);
-  const size_t edge_bytes = sorted ? al256(sizeof(TileEdge) * ntiles) + al256(ntiles) : 0;
   char* z = (char*)scr.get(head + sums_bytes + edge_bytes);
-  char* c = (char*)scr.get(al256(16 * cap) + al256(16 * PQ_MAX_K) + 256 + sizeof(pq_result));
+  char* c = (char*)scr.get(g.cand_bytes);
   if (!z || !c)
     return fail(ctx, PQ_ERR_BUDGET, "aggregate-first plan: %zu bytes",
-                head + sums_bytes + edge_bytes + 16 * cap);
+                head + sums_bytes + edge_bytes + g.cand_bytes);
   AggPlan a{};
   a.ctr = (u64*)z;
   a.dbm = (u32*)(z + 256);
-  a.mbm = (u32*)((char*)a.dbm + al256(words(d_bits)));
-  a.hit = (unsigned char*)a.mbm + al256(words(m_bits));
+  a.mbm = (u32*)((char*)a.dbm + al256(words_bytes(d_bits)));
+  a.hit = (unsigned char*)a.mbm + al256(words_bytes(m_bits));
   a.sums = (i64*)(z + head);
   if (sorted) {
     a.edge = (TileEdge*)(z + head + sums_bytes);

@@ -61,6 +61,9 @@ bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s);
 
 // The aggregate-first plan (PQ_PLAN_AGG_FIRST; pq_agg.cu).
 pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result, cudaStream_t s);
+// Arena bytes an aggregate-first plan needs; an error if it cannot run
+// (tables not resident, keys not dense).  Measures the key ranges on first use.
+pq_status aggfirst_bytes(pq_ctx* ctx, const pq_plan& plan, size_t* bytes);
 
 // Per-plan workspace bytes (excluding a cached D-set block).
 size_t plan_bytes(const ResolvedPlan& r);

@@ -100,11 +100,14 @@ void Server::loop() {
       size_t budget = ctx->arena.largest_free();
       size_t used = batch_layout(kMaxBatch).end;
       std::vector<Request> take;
+      // An aggregate-first request forms a batch of its own.
+      auto agg = [](const Request& q) { return (q.plan.flags & PQ_PLAN_AGG_FIRST) != 0; };
       while (!pending.empty() && (int)take.size() < kMaxBatch &&
-             (take.empty() || used + pending.front().bytes <= budget)) {
+             (take.empty() || (used + pending.front().bytes <= budget && !agg(pending.front())))) {
         used += pending.front().bytes;
         take.push_back(pending.front());
         pending.pop_front();
+        if (agg(take.back())) break;
       }
       std::vector<pq_plan> plans;
       for (auto& r : take) plans.push_back(r.plan);
@@ -203,9 +206,14 @@ extern "C" {
 pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket) {
   if (!ctx || !plan || !ticket) return PQ_ERR_INVALID_ARG;
   ResolvedPlan r;
-  pq_status st = resolve_plan(ctx, *plan, r, false);
+  const bool agg = plan->flags & PQ_PLAN_AGG_FIRST;
+  pq_status st = resolve_plan(ctx, *plan, r, agg);
   if (st != PQ_OK) return st;
   const bool streamed = !r.resident[0] || !r.resident[1] || !r.resident[2];
+  // An aggregate-first plan is checked here (resident tables, dense keys) and
+  // later runs in a batch of its own.
+  size_t agg_bytes = 0;
+  if (agg && (st = aggfirst_bytes(ctx, *plan, &agg_bytes)) != PQ_OK) return st;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     st = server_start(ctx);
@@ -214,13 +222,14 @@ pq_status pq_submit(pq_ctx* ctx, const pq_plan* plan, uint64_t* ticket) {
   Server* srv = ctx->server;
   Request q;
   q.plan = *plan;
-  q.plan.flags |= PQ_PLAN_CACHE_DSET;
+  if (!agg) q.plan.flags |= PQ_PLAN_CACHE_DSET;
   // A batch of streamed plans also holds the chunk ring: a share of it per
   // request (a batch that still does not fit is retried when others finish).
-  q.bytes = plan_bytes(r) + 256 +
-            (streamed ? (size_t)std::max(2, ctx->opt.ring_slots) *
-                            (size_t)(2 * ctx->opt.chunk_bytes) / 8
-                      : 0);
+  q.bytes = agg ? agg_bytes
+                : plan_bytes(r) + 256 +
+                      (streamed ? (size_t)std::max(2, ctx->opt.ring_slots) *
+                                      (size_t)(2 * ctx->opt.chunk_bytes) / 8
+                                : 0);
   q.t0 = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> g(srv->mu);

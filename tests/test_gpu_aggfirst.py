@@ -183,6 +183,56 @@ def test_key_ordered_segments(ctx, stream, nseg, narrow):
         t.free(stream)
 
 
+def mixed_plans(tables):
+    """Aggregate-first and join-first plans over the same tables, with the
+    oracle call that gives each one's result."""
+    TD, TM, TF = tables
+    out = []
+    for i, p in enumerate(PREDS * 2):
+        q = dict(seg=p["seg"], m_date_lt=p["mc"], f_date_gt=p["fc"], k=[1, 10, 64][i % 3])
+        if i % 2 == 0:
+            h = [I64_MIN, 0, 2_000_000_000, 4_000_000_000][i % 4]
+            out.append((pq.make_plan(TD, TM, TF, having=h, **q),
+                        lambda D, M, F, q=q, h=h: oracle.run_plan_aggfirst(D, M, F, having=h, **q)))
+        else:
+            out.append((pq.make_plan(TD, TM, TF, **q),
+                        lambda D, M, F, q=q: oracle.run_plan(D, M, F, **q)))
+    return out
+
+
+def test_batch_mixing_plan_shapes(ctx, stream, small, small_tables):
+    plans = mixed_plans(small_tables[:3])
+    with torch.cuda.stream(stream):
+        res = pq.pq_run_batch(ctx, [p for p, _ in plans], stream=stream)
+        ctx.sync(stream)
+    for i, (_, want) in enumerate(plans):
+        same(res[i], want(*small), f"batch {i}")
+
+
+def test_serving_mixing_plan_shapes(ctx, small, small_tables):
+    """Served aggregate-first requests (each in a batch of its own) beside
+    batched join-first ones: every result equals the oracle's."""
+    plans = mixed_plans(small_tables[:3]) * 3
+    tickets = [pq.pq_submit(ctx, p) for p, _ in plans]
+    for i, t in enumerate(tickets):
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=120_000)
+        assert st == pq.PQ_OK and lat > 0
+        same(res, plans[i][1](*small), f"served {i}")
+
+
+def test_serving_refuses_aggfirst_over_streamed_tables(ctx, small):
+    D, M, F = small
+    pin = lambda t, names: [torch.from_numpy(np.ascontiguousarray(t[c])).pin_memory()
+                            for c in names]
+    TD = pq.pq_load_columns(ctx, pin(D, ("key", "seg")), mode=pq.PQ_STREAMING)
+    TM = pq.pq_load_columns(ctx, pin(M, ("key", "dref", "date")), mode=pq.PQ_STREAMING)
+    TF = pq.pq_load_columns(ctx, pin(F, ("mkey", "price", "disc", "date2")),
+                            mode=pq.PQ_STREAMING)
+    with pytest.raises(pq.PQError) as e:
+        pq.pq_submit(ctx, pq.make_plan(TD, TM, TF, having=0))
+    assert e.value.status == pq.PQ_ERR_INVALID_ARG
+
+
 def test_x100_workload(ctx, stream):
     D, M, F = datagen.workload("x100")
     having = 4_000_000_000
