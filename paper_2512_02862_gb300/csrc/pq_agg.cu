@@ -69,7 +69,8 @@ struct AggPlan {
   i64 having;
   i64* cand_k;
   i64* cand_s;
-  u64* ctr;  // [0] candidates, [1] sum of |revenue| (saturating at 2^62), [2] F rows, [3] status
+  u64* ctr;  // [0] candidates, [1] sum of |revenue| (saturating at 2^62), [2] F rows,
+             // [3] status; bytes 128-131: the top-k's ticket (all zeroed per run)
   DevStatus* st;  // the context's error latch (read by pq_sync)
 };
 
@@ -88,6 +89,7 @@ __device__ __forceinline__ void store_group(const AggPlan& a, u64 idx, u64 sum) 
 }
 
 __global__ void __launch_bounds__(256) k_agg_dbits(AggPlan a) {
+  chain_begin();
   const i64 stride = (i64)gridDim.x * blockDim.x;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_d; i += stride)
     if (pass(a.pd, a.d_seg[i])) bit_set(a.dbm, ukey((i64)a.d_key[i]) - a.d_base);
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(256) k_agg_dbits(AggPlan a) {
 // when aligned), so that each thread has 4 independent chains of loads in
 // flight: date -> D' bit -> key -> M' bit.
 __global__ void __launch_bounds__(256) k_agg_mbits(AggPlan a) {
+  chain_begin();
   const u64 keep = policy_keep(), pol = policy_stream();
   const i64 n4 = (a.n_m + 3) / 4;
   const i64 stride = (i64)gridDim.x * blockDim.x;
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(256) k_agg_mbits(AggPlan a) {
 // stay below 2^62 (otherwise the plan reports PQ_ERR_OVERFLOW).
 template <bool SORTED>
 __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
+  chain_begin();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 pol = policy_stream();
   const i64 nw = (i64)gridDim.x * (blockDim.x >> 5);
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
 // begun earlier) adds the next tiles' first-run parts while they are whole
 // tiles that go on, then the part where the run ends, and stores the total.
 __global__ void __launch_bounds__(256) k_agg_fixup(AggPlan a, i64 ntiles) {
+  chain_begin();
   const i64 stride = (i64)gridDim.x * blockDim.x;
   for (i64 g = (i64)blockIdx.x * blockDim.x + threadIdx.x; g < ntiles; g += stride) {
     const int f = a.eflag[g];
@@ -328,6 +333,7 @@ __global__ void __launch_bounds__(256) k_agg_fixup(AggPlan a, i64 ntiles) {
 // appended as a (key, sum) candidate.  M' is usually far smaller than the
 // group count, so only its groups read their flag and sum.
 __global__ void __launch_bounds__(256) k_agg_select(AggPlan a) {
+  chain_begin();
   const int lane = threadIdx.x & 31;
   const i64 words = (i64)((a.m_bits + 31) / 32);
   const i64 stride = (i64)gridDim.x * blockDim.x;
@@ -361,6 +367,7 @@ __global__ void __launch_bounds__(256) k_agg_select(AggPlan a) {
 
 __global__ void k_agg_result(const u64* ctr, const i64* keys, const i64* sums,
                              const i64* nout, int k, pq_result* out) {
+  chain_begin();
   const int t = threadIdx.x;
   const i64 n = *nout;
   if (t < k && t < n) out->keys[t] = keys[t], out->sums[t] = sums[t];
@@ -371,6 +378,22 @@ __global__ void k_agg_result(const u64* ctr, const i64* keys, const i64* sums,
     out->reserved = 0;
     out->hits = (i64)ctr[2];
   }
+}
+
+// Launch of a plan kernel; `chained`: programmatic dependent launch (the
+// kernel waits for its predecessor at entry, so only the launch overlaps).
+template <typename... P, typename... A>
+cudaError_t launch(void (*k)(P...), int grid, int block, cudaStream_t s, bool chained, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 // Blocks of 256 threads of kernel k resident per SM (at least 1).
@@ -444,7 +467,9 @@ pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cud
   g.sums_bytes = al256(8 * (size_t)std::max<u64>(g.f_bits, 1));
   g.zero = g.head + (g.sorted ? 0 : g.sums_bytes);
   g.edge_bytes = g.sorted ? al256(sizeof(TileEdge) * g.ntiles) + al256(g.ntiles) : 0;
-  g.cand_bytes = al256(16 * g.cap) + al256(16 * PQ_MAX_K) + 256 + sizeof(pq_result);
+  // Candidates, the top-k output and count, the result record, the top-k's lists.
+  g.cand_bytes = al256(16 * g.cap) + al256(16 * PQ_MAX_K) + 256 + al256(sizeof(pq_result)) +
+                 al256(topk_scratch_bytes(ctx, (int64_t)g.cap, PQ_MAX_K));
   return PQ_OK;
 }
 
@@ -456,9 +481,7 @@ pq_status aggfirst_bytes(pq_ctx* ctx, const pq_plan& plan, size_t* bytes) {
   pq_status st = resolve_plan(ctx, plan, r, true);
   if (st == PQ_OK) st = agg_shape(ctx, plan, r, nullptr, g);
   if (st != PQ_OK) return st;
-  // The top-k operator's own scratch: lists of at most 2 blocks per SM.
-  const size_t topk = (size_t)ctx->num_sms * 2 * (16 * PQ_MAX_K + 4) + 512;
-  *bytes = g.head + g.sums_bytes + g.edge_bytes + al256(g.cand_bytes) + al256(topk) + 4 * 256;
+  *bytes = g.head + g.sums_bytes + g.edge_bytes + al256(g.cand_bytes) + 2 * 256;
   return PQ_OK;
 }
 
@@ -499,6 +522,7 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
   i64* os = ok + PQ_MAX_K;
   i64* nout = (i64*)(c + al256(16 * cap) + al256(16 * PQ_MAX_K));
   pq_result* dres = (pq_result*)((char*)nout + 256);
+  void* lists = (char*)dres + al256(sizeof(pq_result));
   a.d_key = d.d_key, a.d_seg = d.d_seg, a.n_d = r.n_d, a.pd = d.pd;
   a.d_base = T[0]->cols[0].umin, a.d_bits = d_bits;
   a.m_key = d.m_key, a.m_dref = d.m_dref, a.m_date = d.m_date, a.n_m = r.n_m, a.pm = to32(d.pm);
@@ -521,10 +545,18 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
   };
   // A table with rows has a measured range, so every key of the plan's rows
   // indexes inside its bitmap or sum array.
-  if (d_bits) k_agg_dbits<<<grid(r.n_d, 256), 256, 0, s>>>(a);
-  if (d_bits && m_bits) k_agg_mbits<<<grid((r.n_m + 3) / 4, 256), 256, 0, s>>>(a);
+  // Kernels after the first are chained (programmatic dependent launch).
+  bool chained = false;
+  int launches = 0;
+  auto go = [&](cudaError_t e) {
+    chained = true;
+    ++launches;
+    return e;
+  };
+  if (d_bits) PQ_CUDA(ctx, go(launch(k_agg_dbits, grid(r.n_d, 256), 256, s, chained, a)));
+  if (d_bits && m_bits)
+    PQ_CUDA(ctx, go(launch(k_agg_mbits, grid((r.n_m + 3) / 4, 256), 256, s, chained, a)));
   if (f_bits) {
-    int launches = 0;
     for (size_t j = 0; j + 1 < seg.size(); ++j) {
       AggPlan b = a;
       const i64 off = seg[j];
@@ -536,24 +568,22 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
       if (b.n_f <= 0) continue;
       if (sorted) {
         const i64 nt = (b.n_f + 127) / 128;
-        k_agg_fscan<true><<<fgrid(b.n_f, true), 256, 0, s>>>(b);
-        k_agg_fixup<<<grid(nt, 256), 256, 0, s>>>(b, nt);
-        launches += 2;
+        PQ_CUDA(ctx, go(launch(k_agg_fscan<true>, fgrid(b.n_f, true), 256, s, chained, b)));
+        PQ_CUDA(ctx, go(launch(k_agg_fixup, grid(nt, 256), 256, s, chained, b, nt)));
       } else {
-        k_agg_fscan<false><<<fgrid(b.n_f, false), 256, 0, s>>>(b);
-        launches += 1;
+        PQ_CUDA(ctx, go(launch(k_agg_fscan<false>, fgrid(b.n_f, false), 256, s, chained, b)));
       }
     }
-    if (m_bits) k_agg_select<<<grid((i64)(m_bits + 31) / 32, 256), 256, 0, s>>>(a), ++launches;
-    ctx->launches += launches;
+    if (m_bits)
+      PQ_CUDA(ctx, go(launch(k_agg_select, grid((i64)(m_bits + 31) / 32, 256), 256, s, chained, a)));
   }
-  PQ_CUDA(ctx, cudaGetLastError());
-  ctx->launches += (d_bits ? 1 : 0) + (d_bits && m_bits ? 1 : 0);
-  st = pq_topk(ctx, (const int64_t*)a.cand_k, (const int64_t*)a.cand_s, (int64_t)cap,
-               (const int64_t*)a.ctr, d.k, (int64_t*)ok, (int64_t*)os, (int64_t*)nout, s);
-  if (st != PQ_OK) return st;
-  k_agg_result<<<1, 64, 0, s>>>(a.ctr, ok, os, nout, d.k, dres);
-  PQ_CUDA(ctx, cudaGetLastError());
+  ctx->launches += launches;
+  // Top-k of the candidates (ticket zeroed with the counters), then the record.
+  PQ_CUDA(ctx, topk_launch(ctx, (const int64_t*)a.cand_k, (const int64_t*)a.cand_s, (int64_t)cap,
+                           (const int64_t*)a.ctr, d.k, (int64_t*)ok, (int64_t*)os, (int64_t*)nout,
+                           (unsigned*)(z + 128), lists, chained, s));
+  PQ_CUDA(ctx, launch(k_agg_result, 1, 64, s, true, (const u64*)a.ctr, (const i64*)ok,
+                      (const i64*)os, (const i64*)nout, d.k, dres));
   ctx->launches += 1;
   ctx->plans++;
   return read_back(ctx, result, dres, 1, s);

@@ -195,6 +195,16 @@ __device__ __forceinline__ T ld_stream(const T* p) {
   return __ldcs(p);
 }
 
+// Programmatic dependent launch: every plan kernel is launched so that it may
+// start while the previous kernel of the chain finishes.  It first waits
+// until that kernel has completed and its writes are visible, then lets the
+// next kernel of the chain launch early in turn.  Launched without the
+// attribute, the wait returns at once.
+__device__ __forceinline__ void chain_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ u32 lanemask_lt() {
   u32 m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -243,6 +243,14 @@ struct Scratch {
 
 // Launchers implemented in pq_ops.cu, used by the plan paths.
 pq_status fill_i64(pq_ctx* ctx, pqk::i64* p, int64_t n, pqk::i64 v, cudaStream_t s);
+// The top-k operator's kernel on caller-provided scratch: `ticket` zeroed
+// before the launch, `lists` topk_scratch_bytes(ctx, n, k) bytes; it always
+// writes *d_nout (n >= 1).  `chained`: programmatic dependent launch.
+size_t topk_scratch_bytes(pq_ctx* ctx, int64_t n, int k);
+cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t n,
+                        const int64_t* d_n, int k, int64_t* out_keys, int64_t* out_sums,
+                        int64_t* d_nout, unsigned* ticket, void* lists, bool chained,
+                        cudaStream_t s);
 
 // Plan internals (pq_plan.cu) used by pq_serve.cu and pq_tune.cu.
 pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,

@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   __shared__ int sc[8];
   __shared__ bool s_last;
   __shared__ i64 s_scr[8][64];
+  chain_begin();
   const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
   // Only the first nb blocks take pairs (at least 2048 each), so that a
   // small count read on the device leaves few lists to merge.
@@ -505,6 +506,40 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 }  // namespace
 
 namespace pqh {
+namespace {
+int topk_grid(pq_ctx* ctx, i64 n) {
+  return (int)std::max<i64>(1, std::min<i64>((n + 2047) / 2048, (i64)ctx->num_sms * 2));
+}
+}  // namespace
+
+size_t topk_scratch_bytes(pq_ctx* ctx, int64_t n, int k) {
+  const int grid = topk_grid(ctx, n);
+  return (size_t)grid * k * 16 + (size_t)grid * 4;
+}
+
+cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t n,
+                        const int64_t* d_n, int k, int64_t* out_keys, int64_t* out_sums,
+                        int64_t* d_nout, unsigned* ticket, void* lists, bool chained,
+                        cudaStream_t s) {
+  const int grid = topk_grid(ctx, n);
+  i64* pk = (i64*)lists;
+  i64* ps = pk + (i64)grid * k;
+  int* pc = (int*)(ps + (i64)grid * k);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = chained ? 1 : 0;
+  ctx->launches++;
+  return cudaLaunchKernelEx(&cfg, k_topk, (const i64*)keys, (const i64*)sums, (i64)n,
+                            (const i64*)d_n, k, pk, ps, pc, (u32*)ticket, (i64*)out_keys,
+                            (i64*)out_sums, (i64*)d_nout);
+}
+
 pq_status fill_i64(pq_ctx* ctx, i64* p, int64_t n, i64 v, cudaStream_t s) {
   if (n <= 0) return PQ_OK;
   int grid = (int)std::min<i64>((n + 255) / 256, (i64)ctx->num_sms * 8);
@@ -733,18 +768,12 @@ pq_status pq_topk(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t
   cudaStream_t s = S(stream);
   PQ_CUDA(ctx, cudaMemsetAsync(d_nout, 0, sizeof(int64_t), s));
   if (n == 0) return PQ_OK;
-  const int grid = (int)std::max<i64>(1, std::min<i64>((n + 2047) / 2048, (i64)ctx->num_sms * 2));
   pqh::Scratch scr(ctx, s);
-  char* w = (char*)scr.get((size_t)grid * k * 16 + grid * 4 + 256);
+  char* w = (char*)scr.get(pqh::topk_scratch_bytes(ctx, n, k) + 256);
   if (!w) return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_topk: no scratch");
-  u32* ticket = (u32*)w;
-  i64* pk = (i64*)(w + 256);
-  i64* ps = pk + (i64)grid * k;
-  int* pc = (int*)(ps + (i64)grid * k);
   PQ_CUDA(ctx, cudaMemsetAsync(w, 0, 256, s));
-  k_topk<<<grid, 256, 0, s>>>((const i64*)keys, (const i64*)sums, n, (const i64*)d_n, k, pk, ps,
-                              pc, ticket, (i64*)out_keys, (i64*)out_sums, (i64*)d_nout);
-  PQ_LAUNCHED(ctx);
+  PQ_CUDA(ctx, pqh::topk_launch(ctx, keys, sums, n, d_n, k, out_keys, out_sums, d_nout,
+                                (unsigned*)w, w + 256, false, s));
   return PQ_OK;
 }
 

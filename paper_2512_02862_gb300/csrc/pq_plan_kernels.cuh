@@ -480,14 +480,6 @@ __device__ __forceinline__ void q_latch(QCtr* c, DevStatus* st, int code, i64 de
   latch(st, code, detail);
 }
 
-// Programmatic dependent launch: every plan kernel is launched so that it may
-// start while the previous kernel of the chain finishes.  It first waits
-// until that kernel has completed and its writes are visible, then lets the
-// next kernel of the chain launch early in turn.
-__device__ __forceinline__ void chain_begin() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Geometry of a bucketized table of 2^e slots: bucket mask and the shift that
 // takes a bucket index from the top of the Fibonacci product.
