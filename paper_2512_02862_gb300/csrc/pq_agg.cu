@@ -5,7 +5,8 @@
 //   D' bitmap  <- D rows with seg op_d c_d                  (k_agg_dbits)
 //   M' bitmap  <- M rows with date op_m c_m, dref in D'      (k_agg_mbits)
 //   G          <- F rows with date2 op_f c_f: sums[mkey] += price*(100-disc),
-//                 a group per set flag of the F key range    (k_agg_fscan)
+//                 a group per set flag of the F key range    (k_agg_fscan,
+//                                                             k_agg_fixup)
 //   candidates <- keys of M' whose group exists and has sum > having
 //                                                            (k_agg_select)
 //   result     <- top-k of the candidates (the top-k operator's kernel) and
@@ -14,10 +15,13 @@
 // The group sums live in a dense array over the F key range (8 bytes per key
 // of the range), so the plan needs keys whose range is at most a few times
 // the F row count.  Consecutive rows of the same group are added up inside
-// the warp first; each run's total is then one reduction nobody waits for.
-// int64 overflow: each revenue is formed in 128 bits; a group sum
-// can only leave int64 if the magnitudes of all summed revenues exceed 2^62,
-// which the plan tracks (one atomic per warp) and reports as PQ_ERR_OVERFLOW.
+// the warp first.  When F's keys come in a few non-decreasing segments
+// (measured once per key column), each segment is scanned by its own launch
+// and every group's total is stored once (k_agg_fixup finishes the runs that
+// tile edges cut); otherwise each run's total is one reduction into a zeroed
+// array.  int64 overflow: a group sum can only leave int64 if the magnitudes
+// of all summed revenues reach 2^62, which the plan tracks (one atomic per
+// warp) and reports as PQ_ERR_OVERFLOW; a single revenue is formed exactly.
 #include <algorithm>
 #include <vector>
 
@@ -135,12 +139,14 @@ __global__ void __launch_bounds__(256) k_agg_mbits(AggPlan a) {
 // (vector loads when the columns are 16-byte aligned).  F is typically
 // clustered by mkey, so the tile's rows form runs of equal keys: a segmented
 // scan over the warp adds up each run (rows that fail the filter count 0) and
-// the lane holding a run's last row commits it -- one reduction into the
-// group's sum and one plain byte store of its hit flag per run that holds a
-// passing row.  Runs cut by a tile boundary are committed in parts; the
-// reduction makes that exact for any key order.  Partial sums are formed in
-// wrapping 64-bit arithmetic, exact while the magnitudes of all revenues
-// stay below 2^62 (otherwise the plan reports PQ_ERR_OVERFLOW).
+// the lane holding a run's last row commits it, if the run holds a passing
+// row.  SORTED (one non-decreasing segment of F): a run is its group's only
+// writer, so the commit is a plain store of the sum and the hit flag; runs
+// that a tile edge cuts leave their parts in the tile's edge record for
+// k_agg_fixup.  Otherwise each run's total is reduced into the zeroed sum
+// array (exact for any key order) and its hit flag stored.  Partial sums are
+// formed in wrapping 64-bit arithmetic, exact while the magnitudes of all
+// revenues stay below 2^62 (otherwise the plan reports PQ_ERR_OVERFLOW).
 template <bool SORTED>
 __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
   chain_begin();
@@ -227,9 +233,8 @@ __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
       fl |= ((pm >> j) & 1u) << 1;
     }
     // Segmented inclusive scan over lanes: the lane's last run summed back
-    // to the lane where it starts.
-    // It ends as soon as every lane has reached its run's start (runs span
-    // few lanes, so usually after one or two steps).
+    // to the lane where it starts.  It ends as soon as every lane has reached
+    // its run's start (runs span few lanes: usually one or two steps).
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       if (__all_sync(kFull, fl & 1u)) break;
