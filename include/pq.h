@@ -344,8 +344,8 @@ enum pq_plan_flags {
  *   result = the groups with sum > `having` whose key is an M' key (a
  *   semi-join: a key held by several M' rows counts once), top-k by sum
  *   desc, key asc, and their number; `hits` = the F rows aggregated.
- * It needs resident tables whose F keys span at most 4 * F rows + 4096
- * values (PQ_ERR_INVALID_ARG otherwise).  Overflow is reported when the
+ * It needs resident tables whose F keys span at most 4 * (rows of the F
+ * table) + 4096 values (PQ_ERR_INVALID_ARG otherwise).  Overflow is reported when the
  * magnitudes of all summed revenues reach 2^62, the bound below which no
  * group sum can leave int64. */
 typedef struct pq_plan {

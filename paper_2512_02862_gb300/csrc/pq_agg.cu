@@ -446,13 +446,15 @@ pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cud
     const Column& c = T[t]->cols[0];
     return c.has_range && c.umax >= c.umin ? c.umax - c.umin + 1 : 0;
   };
-  g.d_bits = span(0), g.m_bits = span(1), g.f_bits = span(2);
-  const u64 dense_cap = 4ULL * (u64)std::max<i64>(r.n_f, 1) + 4096;
+  g.d_bits = span(0), g.m_bits = span(1);
+  g.f_bits = r.n_f > 0 ? span(2) : 0;  // no F rows: no group, nothing to scan
+  // The sum array spans the F table's key range: dense keys are required.
+  const u64 dense_cap = 4ULL * (u64)std::max<i64>(T[2]->nrows, 1) + 4096;
   if (g.f_bits > dense_cap || g.f_bits > kMaxBmBits || g.m_bits > kMaxBmBits ||
       g.d_bits > kMaxBmBits)
     return fail(ctx, PQ_ERR_INVALID_ARG,
                 "aggregate-first plan: F keys span %llu values for %lld rows (dense keys needed)",
-                (unsigned long long)g.f_bits, (long long)r.n_f);
+                (unsigned long long)g.f_bits, (long long)T[2]->nrows);
   g.cap = (size_t)std::max<u64>(std::min(g.f_bits, g.m_bits), 1);
   // F as its non-decreasing segments of keys: in a segment each group is one
   // run of rows, stored once, so the sum array needs no zeroing.  More than

@@ -171,8 +171,8 @@ def test_key_ordered_segments(ctx, stream, nseg, narrow):
             same(got, oracle.run_plan_aggfirst(D, M, F, seg=p["seg"], m_date_lt=p["mc"],
                                                f_date_gt=p["fc"], having=having, k=64),
                  f"{nseg} {p} {having}")
-        for r0, n in ((1, n_f - 1), (7001, n_f - 9000), (3, 6500)):
-            if 4 * n + 4096 < 10_000:    # too few rows for the keys' span: refused
+        for r0, n in ((1, n_f - 1), (7001, n_f - 9000), (3, 6500), (4999, 1)):
+            if n <= 0:
                 continue
             got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=1, m_date_lt=2000, f_date_gt=300,
                                                 k=64, having=having, rows=dict(f=(r0, n))))
@@ -231,6 +231,24 @@ def test_serving_refuses_aggfirst_over_streamed_tables(ctx, small):
     with pytest.raises(pq.PQError) as e:
         pq.pq_submit(ctx, pq.make_plan(TD, TM, TF, having=0))
     assert e.value.status == pq.PQ_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("rows", [dict(f=(5, 0)), dict(m=(0, 0)), dict(d=(7, 0)),
+                                  dict(f=(599_999, 1)), dict(m=(0, 800), f=(0, 3000)),
+                                  dict(m=(0, 1), f=(0, 9))],
+                         ids=["no-F", "no-M", "no-D", "one-F", "few", "one-M"])
+def test_empty_and_tiny_ranges(ctx, stream, small, small_tables, rows):
+    """Empty row ranges and ranges of a few rows, with every predicate
+    passing (so that the few rows form groups)."""
+    TD, TM, TF, _ = small_tables
+    D, M, F = small
+    cut = lambda t, key: ({c: v[rows[key][0]:rows[key][0] + rows[key][1]] for c, v in t.items()}
+                          if key in rows else t)
+    q = dict(d_op="all", m_op="all", f_op="all", k=64)
+    for having in (I64_MIN, 0, 500_000_000):
+        got = run(ctx, stream, pq.make_plan(TD, TM, TF, having=having, rows=rows, **q))
+        same(got, oracle.run_plan_aggfirst(cut(D, "d"), cut(M, "m"), cut(F, "f"), having=having,
+                                           **q), f"{rows} {having}")
 
 
 def test_x100_workload(ctx, stream):
