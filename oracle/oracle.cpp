@@ -288,20 +288,24 @@ int oracle_run_plan_aggfirst(const int32_t* d_key, const int8_t* d_seg, int64_t 
   std::unordered_set<int64_t> d_pass;
   for (int64_t i = 0; i < n_d; ++i)
     if (pred(d_op, d_seg[i], d_c)) d_pass.insert(d_key[i]);
-  std::unordered_set<int64_t> m_keys;
+  std::unordered_map<int64_t, int64_t> m_keys;  // key -> M' rows holding it
   for (int64_t i = 0; i < n_m; ++i)
-    if (pred(m_op, m_date[i], m_c) && d_pass.count(m_dref[i])) m_keys.insert(m_key[i]);
+    if (pred(m_op, m_date[i], m_c) && (g_plant == 11 || d_pass.count(m_dref[i])))
+      ++m_keys[m_key[i]];
   std::map<int64_t, __int128> g;
   for (int64_t i = 0; i < n_f; ++i)
-    if (pred(f_op, f_date2[i], f_c))
+    if (g_plant == 12 || pred(f_op, f_date2[i], f_c))
       g[f_mkey[i]] += static_cast<__int128>(f_price[i]) * (100 - f_disc[i]);
   std::vector<int64_t> keys, vals;
   int status = 0;
   for (const auto& kv : g) {
     if (!fits_int64(kv.second)) status = 7;
-    if (kv.second > having && m_keys.count(kv.first)) {
+    const auto m = m_keys.find(kv.first);
+    const __int128 sum = g_plant == 9 && m != m_keys.end() ? kv.second * m->second : kv.second;
+    const bool above = g_plant == 10 ? sum >= having : sum > having;
+    if (above && m != m_keys.end()) {
       keys.push_back(kv.first);
-      vals.push_back(static_cast<int64_t>(kv.second));
+      vals.push_back(static_cast<int64_t>(sum));
     }
   }
   *ngroups = static_cast<int64_t>(keys.size());

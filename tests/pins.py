@@ -229,7 +229,54 @@ def pin_plan_pass_all_closed_form():
     assert int(r["sums"][-1]) >= int(np.sort(sums)[-6])
 
 
+def brute_aggfirst(D, M, F, seg, mc, fc, having):
+    """Aggregate-first plan by definition: every group of F (date2 filter),
+    kept when sum > having and its key is held by at least one M' row."""
+    dset = {int(D["key"][i]) for i in range(len(D["key"])) if int(D["seg"][i]) == seg}
+    mkeys = {int(M["key"][j]) for j in range(len(M["key"]))
+             if int(M["date"][j]) < mc and int(M["dref"][j]) in dset}
+    g = {}
+    for i in range(len(F["mkey"])):
+        if int(F["date2"][i]) > fc:
+            mk = int(F["mkey"][i])
+            g[mk] = g.get(mk, 0) + int(F["price"][i]) * (100 - int(F["disc"][i]))
+    return {k: v for k, v in g.items() if v > having and k in mkeys}
+
+
+def pin_aggfirst_bruteforce(seed: int = 12):
+    """Brute force with M keys held by several rows and D rows that fail."""
+    for trial in range(3):
+        D, M, F = datagen.make(40, 300, 1200, seed=200 + seed + trial)
+        M = dict(M)
+        M["key"] = M["key"].copy()
+        M["key"][1::7] = M["key"][0:-1:7][:len(M["key"][1::7])]      # repeated keys
+        for (seg, mc, fc) in ((1, 1200, 1200), (0, 2000, 300)):
+            for having in (-(1 << 63), 0, 2_000_000_000):
+                want = brute_aggfirst(D, M, F, seg, mc, fc, having)
+                r = oracle.run_plan_aggfirst(D, M, F, seg=seg, m_date_lt=mc, f_date_gt=fc,
+                                             having=having, k=20)
+                order = sorted(want, key=lambda x: (-want[x], x))[:20]
+                assert r["ngroups"] == len(want) and r["status"] == 0
+                assert r["keys"].tolist() == order
+                assert r["sums"].tolist() == [want[x] for x in order]
+
+
+def pin_aggfirst_threshold_is_strict():
+    """A group whose sum equals the threshold is left out; one unit lower
+    keeps it (hand-computed: groups 7 -> 1000, 8 -> 2500)."""
+    D = dict(key=np.array([1], np.int32), seg=np.array([1], np.int8))
+    M = dict(key=np.array([7, 8], np.int64), dref=np.array([1, 1], np.int32),
+             date=np.array([0, 0], np.int32))
+    F = dict(mkey=np.array([7, 8, 8], np.int64), price=np.array([10, 20, 10], np.int64),
+             disc=np.array([0, 0, 50], np.int8), date2=np.array([9, 9, 9], np.int32))
+    r = oracle.run_plan_aggfirst(D, M, F, seg=1, m_date_lt=10, f_date_gt=0, having=1000, k=5)
+    assert r["keys"].tolist() == [8] and r["sums"].tolist() == [2500] and r["ngroups"] == 1
+    r = oracle.run_plan_aggfirst(D, M, F, seg=1, m_date_lt=10, f_date_gt=0, having=999, k=5)
+    assert r["keys"].tolist() == [8, 7] and r["sums"].tolist() == [2500, 1000]
+
+
 ALL_PINS = [pin_filter_bruteforce, pin_filter_known, pin_partition_constant_and_known_buckets,
             pin_partition_invariants, pin_join_bruteforce, pin_groupby_bruteforce,
             pin_topk_bruteforce, pin_plan_golden, pin_plan_bruteforce,
-            pin_plan_duplicate_build_keys, pin_plan_pass_all_closed_form]
+            pin_plan_duplicate_build_keys, pin_plan_pass_all_closed_form,
+            pin_aggfirst_bruteforce, pin_aggfirst_threshold_is_strict]

@@ -1,6 +1,8 @@
 """Each planted mistake in the oracle (an off-by-one predicate, the wrong hash
 bits, a dropped or sign-flipped term, a reversed tie-break, a wrong join
-index, transposed operands) must trip at least one pin."""
+index, transposed operands, and in the aggregate-first plan a semi-join
+taken as a join, a non-strict threshold, a dropped D' or date filter) must
+trip at least one pin."""
 import pytest
 
 import oracle
@@ -15,6 +17,10 @@ PLANTS = {
     6: "M.dref looked up off by one",
     7: "group-by with key and value transposed",
     8: "join pair with probe row and build value swapped",
+    9: "aggregate-first semi-join counts a key once per M' row",
+    10: "aggregate-first threshold compared with >=",
+    11: "aggregate-first M' ignores D'",
+    12: "aggregate-first aggregation drops the F date filter",
 }
 
 
