@@ -8,7 +8,9 @@ shares no code with the CUDA library.
 Parity status of each function (the pins live in ``tests/test_oracle_pins.py``):
   filter, partition, join, groupby_sum, topk, run_plan, plan_groups -- pinned
   by brute force on tiny inputs, closed forms, invariants, a hand-worked
-  example (``tests/golden/``) and planted-mistake checks.
+  example (``tests/golden/``); ``tests/test_oracle_mutations.py`` compiles
+  copies of oracle.cpp with one deliberate mistake each and checks that the
+  pins catch every one.
 """
 from __future__ import annotations
 
@@ -41,13 +43,10 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
-        i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-        lib.oracle_set_plant.argtypes = [i32]
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    if True:  # argument types of every exported routine
         lib.oracle_filter.argtypes = [vp, i32, i64, i32, i64, vp, i64, vp]
         lib.oracle_filter.restype = i64
         lib.oracle_partition.argtypes = [vp, i32, i64, i32, i32, vp, vp, vp, vp, vp]
@@ -65,8 +64,35 @@ def _load():
         lib.oracle_plan_groups.restype = i64
         lib.oracle_run_plan_aggfirst.argtypes = plan + [i64, i32, vp, vp, vp, vp]
         lib.oracle_run_plan_aggfirst.restype = i32
-        _lib = lib
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = _bind(_LIB)
     return _lib
+
+
+class variant:
+    """Context manager for the mutation tests: while it is active, every
+    function of this module calls the library compiled at ``path`` (a copy
+    of oracle.cpp with one deliberate mistake) instead of the oracle."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _bind(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _p(a):
@@ -74,11 +100,6 @@ def _p(a):
         return None
     assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"], type(a)
     return a.ctypes.data
-
-
-def set_plant(p: int) -> None:
-    """Plant deliberate mistake ``p`` (0 restores the correct oracle)."""
-    _load().oracle_set_plant(int(p))
 
 
 def filter(col: np.ndarray, op: str, c: int, sel_in: np.ndarray | None = None) -> np.ndarray:

@@ -30,11 +30,6 @@
 
 namespace {
 
-/* Deliberate-mistake switch for the mutation tests (0 = correct oracle).
- * Each non-zero value plants one plausible error so that the tests can show
- * that the pins catch it. */
-int g_plant = 0;
-
 int64_t load(const void* col, int type, int64_t i) {
   switch (type) {
     case 1: return static_cast<const int8_t*>(col)[i];
@@ -56,7 +51,7 @@ void store(void* col, int type, int64_t i, int64_t v) {
  * pushed-down filter, Sec. 4 and Sec. 6.1). */
 bool pred(int op, int64_t v, int64_t c) {
   switch (op) {
-    case 0: return g_plant == 1 ? v <= c : v < c;
+    case 0: return v < c;
     case 1: return v <= c;
     case 2: return v > c;
     case 3: return v >= c;
@@ -80,22 +75,18 @@ uint64_t bucket_of(int64_t key, int log2P) {
   if (log2P == 0) return 0;
   const uint64_t golden = 11400714819323198485ULL;
   uint64_t h = static_cast<uint64_t>(key) * golden;
-  if (g_plant == 2) return h & ((1ULL << log2P) - 1);
   return h >> (64 - log2P);
 }
 
 bool before(int64_t ka, int64_t sa, int64_t kb, int64_t sb) {
   /* Top-k order: larger sum first, ties broken by smaller key. */
   if (sa != sb) return sa > sb;
-  if (g_plant == 5) return ka > kb;
   return ka < kb;
 }
 
 }  // namespace
 
 extern "C" {
-
-void oracle_set_plant(int p) { g_plant = p; }
 
 /* Selection (filter pushdown into the scan, Sec. 4 / Sec. 6.1): the row ids
  * whose value satisfies the predicate, in ascending row order.  With a
@@ -152,10 +143,7 @@ int64_t oracle_join(const void* bkey, int bktype, const int64_t* bval, int64_t n
   std::vector<std::pair<int64_t, int64_t>> pairs;
   for (int64_t i = 0; i < np; ++i) {
     auto range = table.equal_range(load(pkey, pktype, i));
-    for (auto it = range.first; it != range.second; ++it) {
-      if (g_plant == 8) pairs.emplace_back(it->second, i);
-      else pairs.emplace_back(i, it->second);
-    }
+    for (auto it = range.first; it != range.second; ++it) pairs.emplace_back(i, it->second);
   }
   std::sort(pairs.begin(), pairs.end());
   int64_t total = static_cast<int64_t>(pairs.size());
@@ -172,10 +160,7 @@ int64_t oracle_join(const void* bkey, int bktype, const int64_t* bval, int64_t n
 int64_t oracle_groupby_sum(const void* key, int ktype, const int64_t* val, int64_t n,
                            int64_t* out_keys, int64_t* out_sums, int64_t cap, int* overflow) {
   std::map<int64_t, __int128> groups;
-  for (int64_t i = 0; i < n; ++i) {
-    if (g_plant == 7) groups[val[i]] += load(key, ktype, i);
-    else groups[load(key, ktype, i)] += val[i];
-  }
+  for (int64_t i = 0; i < n; ++i) groups[load(key, ktype, i)] += val[i];
   int ovf = 0;
   int64_t g = 0;
   for (const auto& kv : groups) {
@@ -225,7 +210,7 @@ static std::map<int64_t, __int128> plan_groups(
 
   std::unordered_multimap<int64_t, int64_t> m_pass;  // M.key -> M row
   for (int64_t i = 0; i < n_m; ++i) {
-    int64_t ref = g_plant == 6 ? int64_t{m_dref[i]} + 1 : int64_t{m_dref[i]};
+    const int64_t ref = m_dref[i];
     if (pred(m_op, m_date[i], m_c) && d_pass.count(ref)) m_pass.emplace(m_key[i], i);
   }
 
@@ -234,10 +219,7 @@ static std::map<int64_t, __int128> plan_groups(
     if (!pred(f_op, f_date2[i], f_c)) continue;
     auto range = m_pass.equal_range(f_mkey[i]);
     for (auto it = range.first; it != range.second; ++it) {
-      __int128 revenue;
-      if (g_plant == 3) revenue = static_cast<__int128>(f_price[i]);
-      else if (g_plant == 4) revenue = static_cast<__int128>(f_price[i]) * (100 + f_disc[i]);
-      else revenue = static_cast<__int128>(f_price[i]) * (100 - f_disc[i]);
+      const __int128 revenue = static_cast<__int128>(f_price[i]) * (100 - f_disc[i]);
       sums[it->first] += revenue;
     }
   }
@@ -290,20 +272,18 @@ int oracle_run_plan_aggfirst(const int32_t* d_key, const int8_t* d_seg, int64_t 
     if (pred(d_op, d_seg[i], d_c)) d_pass.insert(d_key[i]);
   std::unordered_map<int64_t, int64_t> m_keys;  // key -> M' rows holding it
   for (int64_t i = 0; i < n_m; ++i)
-    if (pred(m_op, m_date[i], m_c) && (g_plant == 11 || d_pass.count(m_dref[i])))
-      ++m_keys[m_key[i]];
+    if (pred(m_op, m_date[i], m_c) && d_pass.count(m_dref[i])) ++m_keys[m_key[i]];
   std::map<int64_t, __int128> g;
   for (int64_t i = 0; i < n_f; ++i)
-    if (g_plant == 12 || pred(f_op, f_date2[i], f_c))
+    if (pred(f_op, f_date2[i], f_c))
       g[f_mkey[i]] += static_cast<__int128>(f_price[i]) * (100 - f_disc[i]);
   std::vector<int64_t> keys, vals;
   int status = 0;
   for (const auto& kv : g) {
     if (!fits_int64(kv.second)) status = 7;
     const auto m = m_keys.find(kv.first);
-    const __int128 sum = g_plant == 9 && m != m_keys.end() ? kv.second * m->second : kv.second;
-    const bool above = g_plant == 10 ? sum >= having : sum > having;
-    if (above && m != m_keys.end()) {
+    const __int128 sum = kv.second;
+    if (sum > having && m != m_keys.end()) {
       keys.push_back(kv.first);
       vals.push_back(static_cast<int64_t>(sum));
     }

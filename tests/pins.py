@@ -275,8 +275,44 @@ def pin_aggfirst_threshold_is_strict():
     assert r["keys"].tolist() == [8, 7] and r["sums"].tolist() == [2500, 1000]
 
 
+def _overflow_tables(prices, discs):
+    """One D row, one M row (key 5) and F rows of key 5 that all pass."""
+    D = dict(key=np.array([1], np.int32), seg=np.array([1], np.int8))
+    M = dict(key=np.array([5], np.int64), dref=np.array([1], np.int32),
+             date=np.array([0], np.int32))
+    n = len(prices)
+    F = dict(mkey=np.full(n, 5, np.int64), price=np.array(prices, np.int64),
+             disc=np.array(discs, np.int8), date2=np.full(n, 2000, np.int32))
+    return D, M, F
+
+
+def pin_plan_overflow_status():
+    """Status 7 exactly when a group sum leaves int64 (hand-computed edges:
+    2^63 - 1 = 73 * 126347562148695559, -2^63 = 64 * -2^57)."""
+    top = 126347562148695559          # * (100 - 27) = 2^63 - 1
+    cases = [([top], [27], 0, 2**63 - 1),                   # exactly INT64_MAX: fits
+             ([top, 1], [27, 99], 7, None),                  # INT64_MAX + 1
+             ([-(2**57)], [36], 0, -(2**63)),                # exactly INT64_MIN: fits
+             ([-(2**57), -1], [36, 99], 7, None),            # INT64_MIN - 1
+             ([2**56, 2**56], [0, 0], 7, None),              # 2 * 100 * 2^56 > 2^63
+             ([top, -5], [27, 0], 0, 2**63 - 1 - 500)]       # back inside by a negative row
+    for prices, discs, status, total in cases:
+        D, M, F = _overflow_tables(prices, discs)
+        for agg in (False, True):
+            run = oracle.run_plan_aggfirst if agg else oracle.run_plan
+            r = run(D, M, F, seg=1, m_date_lt=10, f_date_gt=0)
+            assert r["status"] == status, (prices, discs, r["status"])
+            if total is None:
+                continue
+            # the aggregate-first plan keeps sums > having (INT64_MIN by default)
+            kept = not agg or total > -(2**63)
+            assert r["keys"].tolist() == ([5] if kept else []), (agg, prices)
+            assert r["sums"].tolist() == ([total] if kept else [])
+
+
 ALL_PINS = [pin_filter_bruteforce, pin_filter_known, pin_partition_constant_and_known_buckets,
             pin_partition_invariants, pin_join_bruteforce, pin_groupby_bruteforce,
             pin_topk_bruteforce, pin_plan_golden, pin_plan_bruteforce,
             pin_plan_duplicate_build_keys, pin_plan_pass_all_closed_form,
-            pin_aggfirst_bruteforce, pin_aggfirst_threshold_is_strict]
+            pin_aggfirst_bruteforce, pin_aggfirst_threshold_is_strict,
+            pin_plan_overflow_status]
