@@ -121,7 +121,11 @@ pq_status pq_default_options(pq_options* opt);
 pq_status pq_create(const pq_options* opt, void* arena, size_t arena_bytes, pq_ctx** out);
 
 /* Stop the serving loop, wait for the device, release everything the context
- * holds (the arena itself stays with the caller). */
+ * holds (the arena itself stays with the caller).  Requests still queued in
+ * the serving loop complete with PQ_ERR_TIMEOUT without running; batches
+ * already on the GPU get 30 s to finish.  If one does not, nothing is
+ * released (its memory may still be in use), the context must not be used
+ * again, and the call returns PQ_ERR_TIMEOUT instead of waiting without end. */
 pq_status pq_destroy(pq_ctx* ctx);
 
 /* Wait for `stream`, then return (and clear) the first device-latched error

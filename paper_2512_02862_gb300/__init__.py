@@ -189,6 +189,10 @@ def _stream(stream):
     return c_void_p(s.cuda_stream)
 
 
+# Arenas of contexts that pq_destroy could not release (kept until exit).
+_KEPT_ALIVE: list = []
+
+
 class Context:
     """A libpq context over a device arena of ``arena_bytes`` (the budget)."""
 
@@ -218,9 +222,15 @@ class Context:
         self._check(st, self.h)
 
     def close(self):
+        """pq_destroy.  If a served batch did not finish in time the library
+        keeps the context (its memory may still be in use on the device), so
+        the arena is kept alive too and PQError(PQ_ERR_TIMEOUT) is raised."""
         if getattr(self, "h", None):
-            library().pq_destroy(self.h)
+            st = library().pq_destroy(self.h)
             self.h = None
+            if st != PQ_OK:
+                _KEPT_ALIVE.append(self.arena)
+                raise PQError(st, "pq_destroy: a served batch did not complete")
 
     def __del__(self):
         try:

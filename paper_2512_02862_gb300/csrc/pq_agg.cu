@@ -435,7 +435,7 @@ pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cud
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (s) cudaStreamIsCapturing(s, &cap);
   for (int t = 0; t < 3; ++t) {
-    if (T[t]->nrows <= 0 || T[t]->cols[0].has_range) continue;
+    if (T[t]->nrows <= 0 || T[t]->cols[0].range.known()) continue;
     if (cap != cudaStreamCaptureStatusNone)
       return fail(ctx, PQ_ERR_INVALID_ARG,
                   "aggregate-first plan: run it once before capturing a stream (key ranges)");
@@ -443,8 +443,8 @@ pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cud
       return fail(ctx, PQ_ERR_CUDA, "aggregate-first plan: key range of table %d", t);
   }
   auto span = [&](int t) -> u64 {
-    const Column& c = T[t]->cols[0];
-    return c.has_range && c.umax >= c.umin ? c.umax - c.umin + 1 : 0;
+    const KeyRange& c = T[t]->cols[0].range;
+    return c.known() && c.umax >= c.umin ? c.umax - c.umin + 1 : 0;
   };
   g.d_bits = span(0), g.m_bits = span(1);
   g.f_bits = r.n_f > 0 ? span(2) : 0;  // no F rows: no group, nothing to scan
@@ -459,7 +459,7 @@ pq_status agg_shape(pq_ctx* ctx, const pq_plan& plan, const ResolvedPlan& r, cud
   // F as its non-decreasing segments of keys: in a segment each group is one
   // run of rows, stored once, so the sum array needs no zeroing.  More than
   // kMaxDescents segments: reductions into a zeroed array.
-  const Column& fk = T[2]->cols[0];
+  const KeyRange& fk = T[2]->cols[0].range;
   g.sorted = fk.ndesc >= 0;
   g.seg.assign(1, 0);
   if (g.sorted)
@@ -531,13 +531,13 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
   pq_result* dres = (pq_result*)((char*)nout + 256);
   void* lists = (char*)dres + al256(sizeof(pq_result));
   a.d_key = d.d_key, a.d_seg = d.d_seg, a.n_d = r.n_d, a.pd = d.pd;
-  a.d_base = T[0]->cols[0].umin, a.d_bits = d_bits;
+  a.d_base = T[0]->cols[0].range.umin, a.d_bits = d_bits;
   a.m_key = d.m_key, a.m_dref = d.m_dref, a.m_date = d.m_date, a.n_m = r.n_m, a.pm = to32(d.pm);
-  a.m_base = T[1]->cols[0].umin, a.m_bits = m_bits;
+  a.m_base = T[1]->cols[0].range.umin, a.m_bits = m_bits;
   a.f_mkey = d.f_mkey, a.f_price = d.f_price, a.f_disc = d.f_disc, a.f_date = d.f_date;
   a.n_f = r.n_f, a.pf = to32(d.pf);
   a.mvec = (uintptr_t)a.m_date % 16 == 0 && (uintptr_t)a.m_dref % 16 == 0;
-  a.f_base = T[2]->cols[0].umin, a.f_bits = f_bits;
+  a.f_base = T[2]->cols[0].range.umin, a.f_bits = f_bits;
   a.having = plan.having;
   a.st = ctx->d_status;
   PQ_CUDA(ctx, cudaMemsetAsync(z, 0, zero, s));

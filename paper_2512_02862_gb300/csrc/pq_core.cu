@@ -193,6 +193,29 @@ pq_status fail(pq_ctx* ctx, pq_status st, const char* fmt, ...) {
   return st;
 }
 
+SmallPinned::SmallPinned(pq_ctx* c) : ctx(c) {
+  {
+    std::lock_guard<std::mutex> g(ctx->small_mu);
+    if (!ctx->small_free.empty()) {
+      p = ctx->small_free.back();
+      ctx->small_free.pop_back();
+      return;
+    }
+  }
+  own = cudaHostAlloc((void**)&p, kSmallBytes, 0) == cudaSuccess;
+  if (!own) p = nullptr, cudaGetLastError();
+}
+
+SmallPinned::~SmallPinned() {
+  if (!p) return;
+  if (own) {
+    cudaFreeHost(p);
+    return;
+  }
+  std::lock_guard<std::mutex> g(ctx->small_mu);
+  ctx->small_free.push_back(p);
+}
+
 pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, PQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -357,9 +380,12 @@ pq_status pq_create(const pq_options* opt, void* arena, size_t arena_bytes, pq_c
   ctx->d_status = (pqk::DevStatus*)ctx->arena.alloc(2 * sizeof(pqk::DevStatus));
   bool ok = ctx->d_status &&
             cudaHostAlloc((void**)&ctx->h_status, sizeof(pqk::DevStatus), 0) == cudaSuccess &&
-            cudaHostAlloc((void**)&ctx->h_small, 4096, 0) == cudaSuccess &&
+            cudaHostAlloc((void**)&ctx->h_small, kSmallBytes * kSmallBufs, 0) == cudaSuccess &&
             cudaMemset(ctx->d_status, 0, 2 * sizeof(pqk::DevStatus)) == cudaSuccess &&
             ctx->ring.init(64 << 10, 32) && pqh::plan_kernels_init(ctx) == PQ_OK;
+  for (int i = 0; ok && i < kSmallBufs; ++i)
+    ctx->small_free.push_back(ctx->h_small + i * (kSmallBytes / 8));
+  ok = ok && cudaStreamCreateWithFlags(&ctx->util_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (int i = 0; ok && i < o.copy_streams; ++i) {
     cudaStream_t s;
     ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
@@ -375,10 +401,13 @@ pq_status pq_create(const pq_options* opt, void* arena, size_t arena_bytes, pq_c
 
 pq_status pq_destroy(pq_ctx* ctx) {
   if (!ctx) return PQ_ERR_INVALID_ARG;
-  server_stop(ctx);
+  // A served batch that never completes leaves the context allocated: its
+  // memory may still be in use on the device.
+  if (server_stop(ctx) != PQ_OK) return PQ_ERR_TIMEOUT;
   cudaDeviceSynchronize();
   plan_cache_destroy(ctx);
   for (auto s : ctx->copy_streams) cudaStreamDestroy(s);
+  if (ctx->util_stream) cudaStreamDestroy(ctx->util_stream);
   for (auto& kv : ctx->prof)
     for (auto& pr : kv.second.pairs) cudaEventDestroy(pr.first), cudaEventDestroy(pr.second);
   ctx->ring.shutdown();
@@ -550,16 +579,7 @@ const void* pq_table_column(const pq_table* t, int col) {
 
 pq_status pq_table_free(pq_ctx* ctx, pq_table* t, void* stream) {
   if (!ctx || !t) return PQ_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> g(ctx->mu);
   cudaStream_t s = S(stream);
-  for (auto it = ctx->dsets.begin(); it != ctx->dsets.end();) {
-    if (it->table_id == t->id) {
-      ctx->arena.release(it->block, s);
-      it = ctx->dsets.erase(it);
-    } else {
-      ++it;
-    }
-  }
   forget_table(ctx, t->id, s);
   for (auto& c : t->cols) ctx->arena.release(c.owned, s);
   delete t;

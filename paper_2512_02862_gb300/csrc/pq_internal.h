@@ -96,8 +96,30 @@ PackedRange packed_range(const PackedView& v, int64_t row0, int64_t n);
 cudaError_t unpack_launch(const PackBlock* dblk, const uint32_t* dwords, int64_t w0, int64_t row0,
                           int64_t n, int type, void* out, int num_sms, cudaStream_t s);
 
-// Descent positions kept per key column (see Column::desc).
+// Descent positions kept per key column (see KeyRange::desc).
 constexpr int kMaxDescents = 8;
+
+// Range of an integer key column (order-preserving ukey = key xor 2^63) and
+// its key order: the rows that start a new non-decreasing run of keys
+// (ascending), ndesc of them, or ndesc = -1 when there are more than
+// kMaxDescents.  The fields are written once, before `ready` is set with
+// release order; a reader that sees `ready` (acquire) reads them without a
+// lock, since they never change afterwards.
+struct KeyRange {
+  std::atomic<bool> ready{false};
+  uint64_t umin = 0, umax = 0;
+  int ndesc = -1;
+  int64_t desc[kMaxDescents] = {};
+  KeyRange() = default;
+  KeyRange(const KeyRange& o) { *this = o; }
+  KeyRange& operator=(const KeyRange& o) {
+    umin = o.umin, umax = o.umax, ndesc = o.ndesc;
+    for (int j = 0; j < kMaxDescents; ++j) desc[j] = o.desc[j];
+    ready.store(o.ready.load(std::memory_order_acquire), std::memory_order_release);
+    return *this;
+  }
+  bool known() const { return ready.load(std::memory_order_acquire); }
+};
 
 struct Column {
   int type = 0;           // pq_dtype
@@ -108,15 +130,9 @@ struct Column {
   bool pinned = false;    // host source is page-locked
   void* owned = nullptr;  // arena block owned by the table
   std::string path;
-  // Range of an integer key column of a resident table (order-preserving
-  // ukey = key xor 2^63), measured on first use by a plan and kept.
-  mutable bool has_range = false;
-  mutable uint64_t umin = 0, umax = 0;
-  // Key order, measured with the range: the rows that start a new
-  // non-decreasing run of keys (ascending), ndesc of them, or ndesc = -1 when
-  // there are more than kMaxDescents.
-  mutable int ndesc = -1;
-  mutable int64_t desc[kMaxDescents] = {};
+  // Range and key order of an integer key column of a resident table,
+  // measured on first use by a plan and kept (see KeyRange).
+  mutable KeyRange range;
 };
 
 }  // namespace pqh
@@ -160,6 +176,13 @@ struct DsetEntry {
   bool bm;            // built as a static key bitmap
   cudaEvent_t ready;  // recorded after the set is built
   uint64_t last_use;
+  // Batches between their look-up of the entry and the record of their
+  // completion event: an entry with pins is never released.
+  int pins;
+  bool dead;          // its table was freed while pinned: erased at unpin
+  // Completion events of the batches that read the entry; a release of the
+  // block is ordered after all of them.
+  std::vector<cudaEvent_t> users;
 };
 
 }  // namespace pqh
@@ -172,14 +195,17 @@ struct pq_ctx {
   pqh::PinnedRing ring;
   pqk::DevStatus* d_status = nullptr;
   pqk::DevStatus* h_status = nullptr;   // pinned mirror
-  int64_t* h_small = nullptr;            // pinned scratch for count read-backs
-  std::mutex small_mu;
+  int64_t* h_small = nullptr;            // pinned read-back buffers (SmallPinned)
+  std::vector<int64_t*> small_free;      // free buffers of h_small
+  std::mutex small_mu;                   // guards small_free only
+  std::mutex range_mu;                   // serialises writers of KeyRange
   std::mutex mu;                         // serialises API calls that touch state
   std::string last_error;
   std::atomic<int64_t> launches{0}, h2d{0}, d2h{0}, chunks{0}, plans{0}, replays{0};
   std::atomic<uint64_t> next_table_id{1};
   std::map<std::string, pqh::Profile> prof;
   std::vector<cudaStream_t> copy_streams;
+  cudaStream_t util_stream = nullptr;    // key-range measurements
   std::list<pqh::DsetEntry> dsets;   // stable addresses
   uint64_t dset_tick = 0;
   pqh::PlanCache* plan_cache = nullptr;   // owned; freed by plan_cache_destroy
@@ -225,6 +251,19 @@ void prof_begin(pq_ctx* ctx, const char* name, cudaStream_t s, cudaEvent_t* stop
 void prof_end(cudaEvent_t stop, cudaStream_t s);
 void prof_collect(pq_ctx* ctx);
 
+// A pinned read-back buffer of kSmallBytes from the context's pool, returned
+// at scope exit.  The pool's lock is held only to take and return a buffer,
+// never across a wait on the GPU.
+constexpr size_t kSmallBytes = 512;
+constexpr int kSmallBufs = 64;
+struct SmallPinned {
+  pq_ctx* ctx;
+  int64_t* p = nullptr;
+  bool own = false;  // allocated because the pool was empty
+  explicit SmallPinned(pq_ctx* c);
+  ~SmallPinned();
+};
+
 // Scoped arena scratch released on a stream at scope exit.
 struct Scratch {
   pq_ctx* ctx;
@@ -268,8 +307,10 @@ pq_status read_back(pq_ctx* ctx, pq_result* results, const pq_result* dev, int n
                     cudaStream_t s);
 bool is_pinned(const void* p);
 void plan_cache_destroy(pq_ctx* ctx);
-// Drop cached graphs that reference table `id`.
+// Drop cached graphs and D-sets that reference table `id`; their memory is
+// released in the order of stream `s`.  Takes ctx->mu itself.
 void forget_table(pq_ctx* ctx, uint64_t id, cudaStream_t s);
-void server_stop(pq_ctx* ctx);
+// Stop the serving loop; PQ_ERR_TIMEOUT if a batch did not complete in time.
+pq_status server_stop(pq_ctx* ctx);
 
 }  // namespace pqh

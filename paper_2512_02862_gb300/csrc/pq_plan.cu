@@ -59,37 +59,51 @@ __global__ void k_key_range(const void* col, int is64, i64 n, u64* out) {
   range_commit(nmin, umax, out, out + 1);
 }
 
-// The key range of column c of a resident table, measured once (one kernel
-// and a read-back on stream s) and kept with the column.
+// The key range of column c of a resident table, measured once and kept with
+// the column.  The measurement (one kernel and a read-back) runs on the
+// context's utility stream, ordered after the work queued so far on `s` (the
+// legacy default stream when `s` is null), and the host waits for it with no
+// lock held.  Two threads may measure the same column at once: both find the
+// same range and the first to publish it wins.
 bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
   const Column& col = t->cols[c];
-  if (col.has_range) return true;
+  if (col.range.known()) return true;
   if (!col.dev || t->nrows <= 0) return false;
-  std::lock_guard<std::mutex> g(ctx->small_mu);
+  cudaStream_t u = ctx->util_stream;
+  SmallPinned h(ctx);
   u64* d = (u64*)ctx->arena.alloc(256);
-  if (!d) return false;
-  bool ok = cudaMemsetAsync(d, 0, 24, s) == cudaSuccess;
+  cudaEvent_t after = nullptr;
+  bool ok = h.p && d &&
+            cudaEventCreateWithFlags(&after, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventRecord(after, s ? s : cudaStreamLegacy) == cudaSuccess &&
+            cudaStreamWaitEvent(u, after, 0) == cudaSuccess &&
+            cudaMemsetAsync(d, 0, 24, u) == cudaSuccess;
   constexpr size_t rb = 8 * (3 + kMaxDescents);
+  static_assert(rb <= kSmallBytes, "read-back buffer");
   if (ok) {
     const int grid = (int)std::min<i64>((t->nrows + 255) / 256, (i64)ctx->num_sms * 8);
-    k_key_range<<<grid, 256, 0, s>>>(col.dev, col.type == PQ_INT64 ? 1 : 0, t->nrows, d);
+    k_key_range<<<grid, 256, 0, u>>>(col.dev, col.type == PQ_INT64 ? 1 : 0, t->nrows, d);
     ok = cudaGetLastError() == cudaSuccess &&
-         cudaMemcpyAsync(ctx->h_small, d, rb, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-         cudaStreamSynchronize(s) == cudaSuccess;
+         cudaMemcpyAsync(h.p, d, rb, cudaMemcpyDeviceToHost, u) == cudaSuccess &&
+         cudaStreamSynchronize(u) == cudaSuccess;
     ctx->launches++;
   }
-  ctx->arena.release(d, s);
+  if (after) cudaEventDestroy(after);
+  if (d) ctx->arena.release(d, u);
   if (!ok) {
     cudaGetLastError();
     return false;
   }
-  col.umin = ~(u64)ctx->h_small[0];
-  col.umax = (u64)ctx->h_small[1];
-  const int64_t nd = ctx->h_small[2];
-  col.ndesc = nd > kMaxDescents ? -1 : (int)nd;
-  for (int j = 0; j < col.ndesc; ++j) col.desc[j] = ctx->h_small[3 + j];
-  std::sort(col.desc, col.desc + std::max(col.ndesc, 0));
-  col.has_range = true;
+  std::lock_guard<std::mutex> g(ctx->range_mu);
+  if (col.range.known()) return true;
+  KeyRange& kr = col.range;
+  kr.umin = ~(u64)h.p[0];
+  kr.umax = (u64)h.p[1];
+  const int64_t nd = h.p[2];
+  kr.ndesc = nd > kMaxDescents ? -1 : (int)nd;
+  for (int j = 0; j < kr.ndesc; ++j) kr.desc[j] = h.p[3 + j];
+  std::sort(kr.desc, kr.desc + std::max(kr.ndesc, 0));
+  kr.ready.store(true, std::memory_order_release);
   return true;
 }
 
@@ -103,8 +117,8 @@ static void plan_static(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, cudaStre
   d.d_e = r.e_d;
   d.m_e = r.e_m;
   auto fits = [&](const pq_table* t, int e, u64* su, u64* sb) -> bool {
-    const Column& c = t->cols[0];
-    if (!c.has_range && (capturing || !ensure_range(ctx, t, 0, s))) return false;
+    const KeyRange& c = t->cols[0].range;
+    if (!c.known() && (capturing || !ensure_range(ctx, t, 0, s))) return false;
     const u64 span = c.umax - c.umin;  // bits - 1
     if (c.umax < c.umin || span >= (32ULL << e) || span >= kMaxBmBits) return false;
     *su = c.umin;
@@ -397,6 +411,7 @@ void plan_cache_destroy(pq_ctx* ctx) {
   }
   for (auto& d : ctx->dsets) {
     if (d.ready) cudaEventDestroy(d.ready);
+    for (auto ev : d.users) cudaEventDestroy(ev);
     ctx->arena.release_now(d.block);
   }
   ctx->dsets.clear();
@@ -412,20 +427,53 @@ static std::string plan_key(pq_ctx* ctx, const pq_plan& p) {
   return k;
 }
 
-// Drop cached graphs and D-sets that reference table `id` (called on free).
+// Release a cached graph's workspace once `s` has passed its last replay;
+// the executable graph itself is freed by CUDA when it is no longer running.
+static void graph_release(pq_ctx* ctx, GraphEntry& e, cudaStream_t s) {
+  if (e.done) cudaStreamWaitEvent(s, e.done, 0), cudaEventDestroy(e.done);
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  ctx->arena.release(e.ws, s);
+}
+
+// Release a cached D-set's block once `s` has passed its build and every
+// batch that read it (their completion events).  No host wait.
+static void dset_release(pq_ctx* ctx, DsetEntry& e, cudaStream_t s) {
+  for (auto ev : e.users) cudaStreamWaitEvent(s, ev, 0), cudaEventDestroy(ev);
+  e.users.clear();
+  if (e.ready) cudaStreamWaitEvent(s, e.ready, 0), cudaEventDestroy(e.ready);
+  e.ready = nullptr;
+  ctx->arena.release(e.block, s);
+}
+
+// Drop cached graphs and D-sets that reference table `id` (called on free),
+// their memory released in the order of stream `s`.  Takes ctx->mu itself.
 void forget_table(pq_ctx* ctx, uint64_t id, cudaStream_t s) {
-  if (!ctx->plan_cache) return;
-  auto& v = ctx->plan_cache->entries;
-  for (auto it = v.begin(); it != v.end();) {
-    if (it->tids[0] == id || it->tids[1] == id || it->tids[2] == id) {
-      if (it->done) cudaEventSynchronize(it->done), cudaEventDestroy(it->done);
-      if (it->exec) cudaGraphExecDestroy(it->exec);
-      ctx->arena.release(it->ws, s);
-      it = v.erase(it);
-    } else {
-      ++it;
+  std::vector<GraphEntry> graphs;
+  std::list<DsetEntry> sets;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->plan_cache) {
+      auto& v = ctx->plan_cache->entries;
+      for (auto it = v.begin(); it != v.end();) {
+        if (it->tids[0] == id || it->tids[1] == id || it->tids[2] == id) {
+          graphs.push_back(*it);
+          it = v.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (auto it = ctx->dsets.begin(); it != ctx->dsets.end();) {
+      auto nx = std::next(it);
+      if (it->table_id == id) {
+        if (it->pins > 0) it->dead = true;  // released by its last user
+        else sets.splice(sets.end(), ctx->dsets, it);
+      }
+      it = nx;
     }
   }
+  for (auto& e : graphs) graph_release(ctx, e, s);
+  for (auto& e : sets) dset_release(ctx, e, s);
 }
 
 // ------------------------------------------------------------------ batch ----
@@ -509,68 +557,135 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     }
   }
 
-  // D-set sharing inside the batch and across batches (cache).
-  std::unique_lock<std::mutex> lk(ctx->mu);
+  // D-set sharing inside the batch and across batches (cache).  Cached
+  // entries found here are pinned until this batch has recorded its
+  // completion on them; new entries are built into blocks of their own and
+  // join the cache only once their build is queued.  No host wait happens
+  // under ctx->mu.
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   std::vector<cudaEvent_t> waits;
-  for (int i = 0; i < n; ++i) {
-    ResolvedPlan& r = R[i];
-    for (int j = 0; j < i; ++j)
-      if (R[j].builds && same_dset(R[j], plans[j], r, plans[i])) {
-        r.builds = false;
-        r.dset_from = j;
-        break;
-      }
-    if (!r.builds || !(plans[i].flags & PQ_PLAN_CACHE_DSET)) continue;
-    for (auto& e : ctx->dsets) {
-      if (e.table_id == plans[i].D->id && e.row0 == r.d_row0 && e.rows == r.n_d &&
-          e.pred.lo == r.dev.pd.lo && e.pred.hi == r.dev.pd.hi && e.pred.neg == r.dev.pd.neg &&
-          e.lf1024 == r.dev.lf1024) {
-        r.builds = false;
-        r.dset_from = -2;
-        r.cache = &e;
-        e.last_use = ++ctx->dset_tick;
-        waits.push_back(e.ready);
-        break;
-      }
-    }
-    if (r.builds) {
-      DsetEntry e{};
-      e.table_id = plans[i].D->id;
-      e.row0 = r.d_row0;
-      e.rows = r.n_d;
-      e.pred = r.dev.pd;
-      e.lf1024 = r.dev.lf1024;
-      e.log2max = r.e_d;
-      e.bm = r.dev.d_static != 0;  // built from the static range
-      e.block = ctx->arena.alloc(dset_block_bytes(r.e_d));
-      if (!e.block) continue;  // no room to cache: build in the workspace
-      if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
-        ctx->arena.release_now(e.block);
-        continue;
-      }
-      e.keys = nullptr;  // laid out by dset_block_assign
-      if (ctx->dsets.size() >= 64) {
-        // Evict the least recently used set that this batch does not use.
-        auto old = ctx->dsets.end();
-        for (auto it = ctx->dsets.begin(); it != ctx->dsets.end(); ++it) {
-          bool used = false;
-          for (int j = 0; j < i; ++j) used = used || R[j].cache == &*it;
-          if (!used && (old == ctx->dsets.end() || it->last_use < old->last_use)) old = it;
+  std::vector<DsetEntry*> pinned;   // cached entries this batch reads
+  std::list<DsetEntry> fresh;       // entries this batch builds
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (int i = 0; i < n; ++i) {
+      ResolvedPlan& r = R[i];
+      for (int j = 0; j < i; ++j)
+        if (R[j].builds && same_dset(R[j], plans[j], r, plans[i])) {
+          r.builds = false;
+          r.dset_from = j;
+          break;
         }
-        if (old != ctx->dsets.end()) {
-          cudaEventSynchronize(old->ready);
-          cudaEventDestroy(old->ready);
-          ctx->arena.release(old->block, s);
-          ctx->dsets.erase(old);
+      if (!r.builds || !(plans[i].flags & PQ_PLAN_CACHE_DSET) || capturing) continue;
+      for (auto& e : ctx->dsets) {
+        if (!e.dead && e.table_id == plans[i].D->id && e.row0 == r.d_row0 && e.rows == r.n_d &&
+            e.pred.lo == r.dev.pd.lo && e.pred.hi == r.dev.pd.hi && e.pred.neg == r.dev.pd.neg &&
+            e.lf1024 == r.dev.lf1024) {
+          r.builds = false;
+          r.dset_from = -2;
+          r.cache = &e;
+          e.last_use = ++ctx->dset_tick;
+          // Completed readers need no ordering any more.
+          for (auto it = e.users.begin(); it != e.users.end();) {
+            if (cudaEventQuery(*it) == cudaSuccess) cudaEventDestroy(*it), it = e.users.erase(it);
+            else ++it;
+          }
+          cudaGetLastError();
+          if (e.pins++ == 0 || std::find(pinned.begin(), pinned.end(), &e) == pinned.end())
+            pinned.push_back(&e);
+          else
+            e.pins--;  // already pinned by this batch
+          waits.push_back(e.ready);
+          break;
         }
       }
-      e.last_use = ++ctx->dset_tick;
-      ctx->dsets.push_back(e);
-      r.cache = &ctx->dsets.back();
-      r.cache_new = true;
-      r.dset_from = -3;  // builds into a new cache block
     }
   }
+  for (int i = 0; i < n; ++i) {
+    ResolvedPlan& r = R[i];
+    if (!r.builds || !(plans[i].flags & PQ_PLAN_CACHE_DSET) || capturing) continue;
+    DsetEntry e{};
+    e.table_id = plans[i].D->id;
+    e.row0 = r.d_row0;
+    e.rows = r.n_d;
+    e.pred = r.dev.pd;
+    e.lf1024 = r.dev.lf1024;
+    e.log2max = r.e_d;
+    e.bm = r.dev.d_static != 0;  // built from the static range
+    e.block = ctx->arena.alloc(dset_block_bytes(r.e_d));
+    if (!e.block) continue;  // no room to cache: build in the workspace
+    if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->arena.release_now(e.block);
+      continue;
+    }
+    e.keys = nullptr;  // laid out by dset_block_assign
+    fresh.push_back(e);
+    r.cache = &fresh.back();
+    r.cache_new = true;
+    r.dset_from = -3;  // builds into a new cache block
+  }
+  // Undo the cache bookkeeping of a batch that does not run.
+  auto unwind = [&]() {
+    std::list<DsetEntry> drop;
+    {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      for (DsetEntry* e : pinned)
+        if (--e->pins == 0 && e->dead)
+          for (auto it = ctx->dsets.begin(); it != ctx->dsets.end(); ++it)
+            if (&*it == e) {
+              drop.splice(drop.end(), ctx->dsets, it);
+              break;
+            }
+    }
+    for (auto& e : drop) dset_release(ctx, e, s);
+    for (auto& e : fresh) {
+      if (e.ready) cudaEventDestroy(e.ready), e.ready = nullptr;
+      ctx->arena.release(e.block, s);
+    }
+    pinned.clear();
+    fresh.clear();
+  };
+  // After the chain is queued: the new sets are ready after it, every entry
+  // the batch touched records the batch's completion, the new entries join
+  // the cache, and the least recently used unpinned entries beyond 64 leave it.
+  auto commit = [&]() {
+    for (auto& e : fresh) cudaEventRecord(e.ready, s);
+    std::vector<std::pair<DsetEntry*, cudaEvent_t>> marks;
+    auto mark = [&](DsetEntry* e) {
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventRecord(ev, s) == cudaSuccess)
+        marks.push_back({e, ev});
+      else if (ev)
+        cudaEventDestroy(ev);
+      cudaGetLastError();
+    };
+    for (DsetEntry* e : pinned) mark(e);
+    for (auto& e : fresh) mark(&e);
+    std::list<DsetEntry> drop;
+    {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      for (auto& m : marks) m.first->users.push_back(m.second);
+      for (auto& e : fresh) e.last_use = ++ctx->dset_tick;
+      ctx->dsets.splice(ctx->dsets.end(), fresh);
+      for (DsetEntry* e : pinned) e->pins--;
+      for (auto it = ctx->dsets.begin(); it != ctx->dsets.end();) {
+        auto nx = std::next(it);
+        if (it->dead && it->pins == 0) drop.splice(drop.end(), ctx->dsets, it);
+        it = nx;
+      }
+      while (ctx->dsets.size() > 64) {
+        auto old = ctx->dsets.end();
+        for (auto it = ctx->dsets.begin(); it != ctx->dsets.end(); ++it)
+          if (it->pins == 0 && (old == ctx->dsets.end() || it->last_use < old->last_use)) old = it;
+        if (old == ctx->dsets.end()) break;
+        drop.splice(drop.end(), ctx->dsets, old);
+      }
+    }
+    for (auto& e : drop) dset_release(ctx, e, s);
+    pinned.clear();
+  };
 
   const BatchLayout L = batch_layout(n);
   size_t total = L.end;
@@ -581,6 +696,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   }
   char* ws = (char*)ctx->arena.alloc(total);
   if (!ws) {
+    unwind();
     return fail(ctx, PQ_ERR_BUDGET, "batch of %d plans needs %zu bytes (largest free %zu)", n,
                 total, ctx->arena.largest_free());
   }
@@ -639,7 +755,6 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     tmax[kPhaseMdup] += (r.n_m + kTB - 1) / kTB;
     tmax[kPhaseTopk] += topk_parts(r.e_m);
   }
-  lk.unlock();
   tmax[kPhaseD] = tD[n];
   tmax[kPhaseM] = tM[n];
   tmax[kPhaseFscan] = tF[n];
@@ -647,8 +762,15 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   for (int i = 0; i < n; ++i) tmax[kPhaseF] += (R[i].n_f + 63) / 64;
   tmax[kPhaseTopk2] = tmax[kPhaseTopk];
 
-  for (auto ev : waits) PQ_CUDA(ctx, cudaStreamWaitEvent(s, ev, 0));
-  PQ_CUDA(ctx, ctx->ring.upload(ws + L.desc, host.data(), host.size(), s));
+  cudaError_t ue = cudaSuccess;
+  for (auto ev : waits)
+    if (ue == cudaSuccess) ue = cudaStreamWaitEvent(s, ev, 0);
+  if (ue == cudaSuccess) ue = ctx->ring.upload(ws + L.desc, host.data(), host.size(), s);
+  if (ue != cudaSuccess) {
+    unwind();
+    ctx->arena.release(ws, s);
+    return cuda_fail(ctx, ue, "batch set-up");
+  }
   Batch b = make_batch(ctx, ws, n, L);
   b.clear_m = any_build ? 1 : 0;  // else no D scan runs: the memsets clear them
   if (!any_build) clears.insert(clears.end(), m_clears.begin(), m_clears.end());
@@ -713,21 +835,22 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       PQ_CUDA(ctx, cudaGraphLaunch(exec, s));
       PQ_CUDA(ctx, cudaEventRecord(e.done, s));
       ctx->plans++;
-      std::lock_guard<std::mutex> g(ctx->mu);
-      auto& v = ctx->plan_cache->entries;
-      if (v.size() >= 16) {
-        auto old = std::min_element(v.begin(), v.end(), [](const GraphEntry& a,
-                                                            const GraphEntry& c) {
-          return a.last_use < c.last_use;
-        });
-        cudaEventSynchronize(old->done);
-        cudaEventDestroy(old->done);
-        cudaGraphExecDestroy(old->exec);
-        ctx->arena.release(old->ws, s);
-        v.erase(old);
+      std::vector<GraphEntry> evicted;  // least recently used beyond 16 graphs
+      {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto& v = ctx->plan_cache->entries;
+        if (v.size() >= 16) {
+          auto old = std::min_element(v.begin(), v.end(), [](const GraphEntry& a,
+                                                              const GraphEntry& c) {
+            return a.last_use < c.last_use;
+          });
+          evicted.push_back(*old);
+          v.erase(old);
+        }
+        e.last_use = ++ctx->plan_cache->tick;
+        v.push_back(e);
       }
-      e.last_use = ++ctx->plan_cache->tick;
-      v.push_back(e);
+      for (auto& o : evicted) graph_release(ctx, o, s);
       return read_back(ctx, results, out, 1, s);
     }
     if (st != PQ_OK) {
@@ -737,10 +860,11 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   }
   st = chain(nullptr, nullptr, nullptr);
   if (st == PQ_OK) {
-    for (int i = 0; i < n; ++i)
-      if (R[i].cache_new && R[i].cache) cudaEventRecord(R[i].cache->ready, s);
+    commit();
     st = read_back(ctx, results, out, n, s);
     ctx->plans += n;
+  } else {
+    unwind();
   }
   ctx->arena.release(ws, s);
   return st;

@@ -39,9 +39,12 @@ struct ServeSlot {
   cudaStream_t s = nullptr;
   pq_result* results = nullptr;  // pinned, kMaxBatch entries
   std::vector<Request> reqs;
+  // busy: the slot holds a batch; it is set, together with reqs, under the
+  // server's lock BEFORE the batch is enqueued, and the completion callback
+  // only ever sets `completed`, so a batch that finishes before the server
+  // thread re-takes the lock is still delivered.
   bool busy = false;
   bool completed = false;
-  pq_status st = PQ_OK;
   struct Server* srv = nullptr;
 };
 
@@ -55,10 +58,13 @@ struct Server {
   std::vector<ServeSlot> slots;
   std::thread th;
   bool stop = false;
+  Clock::time_point stop_by;        // deadline for the batches in flight at stop
+  bool abandoned = false;           // a batch was still in flight at the deadline
+  bool budget_wait = false;         // admission waits for a batch to complete
   uint64_t next_ticket = 1;
-  double last_latency_us = 0;
 
   void loop();
+  void finish(const std::vector<Request>& reqs, pq_status st);
 };
 
 static void CUDART_CB on_batch_done(void* arg) {
@@ -68,6 +74,19 @@ static void CUDART_CB on_batch_done(void* arg) {
     sl->completed = true;
   }
   sl->srv->cv.notify_all();
+}
+
+// Requests that will not run: their tickets complete with status `st`.
+// Called with `mu` held.
+void Server::finish(const std::vector<Request>& reqs, pq_status st) {
+  for (auto& r : reqs) {
+    Finished f;
+    memset(&f.res, 0, sizeof f.res);
+    f.res.status = st;
+    f.latency_us = 0;
+    done[r.ticket] = f;
+  }
+  cv_done.notify_all();
 }
 
 void Server::loop() {
@@ -80,96 +99,135 @@ void Server::loop() {
       for (size_t i = 0; i < sl.reqs.size(); ++i) {
         Finished f;
         f.res = sl.results[i];
-        if (sl.st != PQ_OK) f.res.status = sl.st;
         f.latency_us = std::chrono::duration<double, std::micro>(now - sl.reqs[i].t0).count();
         done[sl.reqs[i].ticket] = f;
       }
       sl.reqs.clear();
       sl.busy = sl.completed = false;
+      budget_wait = false;
       cv_done.notify_all();
     }
     if (stop) {
+      // Requests not yet admitted never run; batches in flight get until
+      // the deadline.
+      if (!pending.empty()) {
+        finish(std::vector<Request>(pending.begin(), pending.end()), PQ_ERR_TIMEOUT);
+        pending.clear();
+      }
       bool any = false;
       for (auto& sl : slots) any = any || sl.busy;
       if (!any) return;
-    }
-    // Admit queued requests into free slots.
-    bool progressed = false;
-    for (auto& sl : slots) {
-      if (sl.busy || pending.empty() || stop) continue;
-      size_t budget = ctx->arena.largest_free();
-      size_t used = batch_layout(kMaxBatch).end;
-      std::vector<Request> take;
-      // An aggregate-first request forms a batch of its own.
-      auto agg = [](const Request& q) { return (q.plan.flags & PQ_PLAN_AGG_FIRST) != 0; };
-      while (!pending.empty() && (int)take.size() < kMaxBatch &&
-             (take.empty() || (used + pending.front().bytes <= budget && !agg(pending.front())))) {
-        used += pending.front().bytes;
-        take.push_back(pending.front());
-        pending.pop_front();
-        if (agg(take.back())) break;
+      if (Clock::now() >= stop_by) {
+        abandoned = true;
+        return;
       }
-      std::vector<pq_plan> plans;
-      for (auto& r : take) plans.push_back(r.plan);
-      lk.unlock();
-      pq_status st = run_batch_internal(ctx, plans.data(), (int)plans.size(), sl.results, sl.s,
-                                        false);
-      if (st == PQ_OK) st = cudaLaunchHostFunc(sl.s, on_batch_done, &sl) == cudaSuccess
-                                ? PQ_OK
-                                : PQ_ERR_CUDA;
-      lk.lock();
-      bool others_busy = false;
-      for (auto& o : slots) others_busy = others_busy || o.busy;
-      if (st == PQ_ERR_BUDGET && others_busy) {
-        // Not enough memory while other batches hold it: requeue and wait.
-        for (auto it = take.rbegin(); it != take.rend(); ++it) pending.push_front(*it);
+      cv.wait_until(lk, stop_by);
+      continue;
+    }
+    ServeSlot* free_slot = nullptr;
+    for (auto& sl : slots)
+      if (!sl.busy) {
+        free_slot = &sl;
         break;
       }
-      if (st != PQ_OK) {
-        for (auto& r : take) {
-          Finished f;
-          memset(&f.res, 0, sizeof f.res);
-          f.res.status = st;
-          f.latency_us = 0;
-          done[r.ticket] = f;
+    if (!free_slot || pending.empty() || budget_wait) {
+      cv.wait(lk, [&] {
+        if (stop) return true;
+        bool any_free = false;
+        for (auto& sl : slots) {
+          if (sl.busy && sl.completed) return true;
+          any_free = any_free || !sl.busy;
         }
-        cv_done.notify_all();
-        continue;
-      }
-      sl.reqs = std::move(take);
-      sl.busy = true;
-      sl.completed = false;
-      sl.st = PQ_OK;
-      progressed = true;
+        return any_free && !pending.empty() && !budget_wait;
+      });
+      continue;
     }
-    if (progressed) continue;
-    cv.wait(lk, [&] {
-      if (stop) return true;
-      bool free_slot = false;
-      for (auto& sl : slots) {
-        if (sl.busy && sl.completed) return true;
-        free_slot = free_slot || !sl.busy;
-      }
-      return free_slot && !pending.empty();
-    });
+    // The arena's free space is read without the server's lock: the arena
+    // may wait for the GPU, and the completion callbacks need this lock.
+    lk.unlock();
+    const size_t budget = ctx->arena.largest_free();
+    lk.lock();
+    if (stop || pending.empty()) continue;
+    ServeSlot& sl = *free_slot;
+    size_t used = batch_layout(kMaxBatch).end;
+    std::vector<Request> take;
+    // An aggregate-first request forms a batch of its own.
+    auto agg = [](const Request& q) { return (q.plan.flags & PQ_PLAN_AGG_FIRST) != 0; };
+    while (!pending.empty() && (int)take.size() < kMaxBatch &&
+           (take.empty() || (used + pending.front().bytes <= budget && !agg(pending.front())))) {
+      used += pending.front().bytes;
+      take.push_back(pending.front());
+      pending.pop_front();
+      if (agg(take.back())) break;
+    }
+    std::vector<pq_plan> plans;
+    for (auto& r : take) plans.push_back(r.plan);
+    sl.reqs = std::move(take);
+    sl.busy = true;
+    sl.completed = false;
+    lk.unlock();
+    pq_status st = run_batch_internal(ctx, plans.data(), (int)plans.size(), sl.results, sl.s,
+                                      false);
+    bool callback = false;
+    if (st == PQ_OK) {
+      callback = cudaLaunchHostFunc(sl.s, on_batch_done, &sl) == cudaSuccess;
+      if (!callback) st = PQ_ERR_CUDA;
+    }
+    lk.lock();
+    if (callback) continue;  // the callback completes the slot
+    // No callback will come: the slot is free again at once (its stream
+    // keeps any work already queued in order before the next batch).
+    std::vector<Request> reqs = std::move(sl.reqs);
+    sl.reqs.clear();
+    sl.busy = sl.completed = false;
+    bool others_busy = false;
+    for (auto& o : slots) others_busy = others_busy || o.busy;
+    if (st == PQ_ERR_BUDGET && others_busy) {
+      // Not enough memory while other batches hold it: requeue and admit
+      // again once one of them completes.
+      for (auto it = reqs.rbegin(); it != reqs.rend(); ++it) pending.push_front(*it);
+      budget_wait = true;
+      continue;
+    }
+    finish(reqs, st);
   }
 }
 
-void server_stop(pq_ctx* ctx) {
+// Stop the serving loop.  Batches in flight get kStopWaitMs to complete;
+// if one does not, the server (its streams, pinned buffers and thread state,
+// which a late completion callback would still touch) is left allocated and
+// PQ_ERR_TIMEOUT returned, instead of waiting without end.
+constexpr int kStopWaitMs = 30000;
+
+pq_status server_stop(pq_ctx* ctx) {
   Server* srv = ctx->server;
-  if (!srv) return;
+  if (!srv) return PQ_OK;
+  const auto deadline = Clock::now() + std::chrono::milliseconds(kStopWaitMs);
   {
     std::lock_guard<std::mutex> g(srv->mu);
     srv->stop = true;
+    srv->stop_by = deadline;
   }
   srv->cv.notify_all();
   if (srv->th.joinable()) srv->th.join();
+  ctx->server = nullptr;
+  bool idle = !srv->abandoned;
   for (auto& sl : srv->slots) {
-    if (sl.s) cudaStreamSynchronize(sl.s), cudaStreamDestroy(sl.s);
+    while (idle && sl.s && cudaStreamQuery(sl.s) == cudaErrorNotReady) {
+      if (Clock::now() >= deadline) idle = false;
+      else std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+  }
+  cudaGetLastError();
+  if (!idle)
+    return fail(ctx, PQ_ERR_TIMEOUT, "serving loop: a batch did not complete within %d ms",
+                kStopWaitMs);
+  for (auto& sl : srv->slots) {
+    if (sl.s) cudaStreamDestroy(sl.s);
     if (sl.results) cudaFreeHost(sl.results);
   }
   delete srv;
-  ctx->server = nullptr;
+  return PQ_OK;
 }
 
 static pq_status server_start(pq_ctx* ctx) {

@@ -421,13 +421,13 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     if (st != PQ_OK) return st;
     i64 count = 0;
     {
-      std::lock_guard<std::mutex> g(ctx->small_mu);
-      cudaError_t e = cudaMemcpyAsync(ctx->h_small, t == 0 ? (void*)&ctr->dcount
-                                                           : (void*)&ctr->mcount,
-                                      8, cudaMemcpyDeviceToHost, s);
+      SmallPinned h(ctx);
+      if (!h.p) return fail(ctx, PQ_ERR_CUDA, "streaming plan: pinned read-back buffer");
+      cudaError_t e = cudaMemcpyAsync(h.p, t == 0 ? (void*)&ctr->dcount : (void*)&ctr->mcount, 8,
+                                      cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming plan: count read-back");
-      count = ctx->h_small[0];
+      count = h.p[0];
     }
     const int e = cap_log2(count, d.lf1024);
     if (t == 0) {

@@ -455,7 +455,7 @@ def test_serving_over_streamed_tables(stream_ctx, stream, small):
     plans, specs = random_plans(rng, (TD, TM, TF), 40, len(M["key"]), len(F["mkey"]), starts)
     tickets = [pq.pq_submit(ctx, p) for p in plans]
     for i, t in enumerate(tickets):
-        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=120_000)
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=15_000)
         assert st == pq.PQ_OK
         assert_same(res.as_dict(), oracle_plan(D, M, F, **specs[i]), f"served {i}")
 
@@ -484,12 +484,46 @@ def test_serving_results_same_alone_and_in_the_mix(ctx, stream, small, small_tab
                                 starts)
     tickets = [pq.pq_submit(ctx, p) for p in plans]
     for i, t in enumerate(tickets):
-        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=60_000)
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=15_000)
         assert st == pq.PQ_OK and lat > 0
         want = oracle_plan(D, M, F, **specs[i])
         assert_same(res.as_dict(), want, f"served {i}")
         if i % 37 == 0:
             assert run(ctx, stream, plans[i]) == res.as_dict()   # alone
+
+
+def test_serving_tiny_requests_one_by_one(ctx, small, small_tables):
+    """Requests submitted and polled one at a time: each batch is a single
+    tiny plan that can finish before the serving thread has finished queuing
+    it, which must still complete its ticket."""
+    D, M, F = small
+    TD, TM, TF, _ = small_tables
+    for i in range(300):
+        rows = dict(m=(16 * i, 16), f=(64 * i, 64))
+        t = pq.pq_submit(ctx, pq.make_plan(TD, TM, TF, d_op="all", m_op="all", f_op="all",
+                                           rows=rows, k=4))
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=15_000)
+        assert st == pq.PQ_OK, (i, st)
+        if i % 50 == 0:
+            assert_same(res.as_dict(), oracle_plan(D, M, F, d_op="all", m_op="all", f_op="all",
+                                                   rows=rows, k=4), f"request {i}")
+
+
+def test_close_with_requests_in_flight(stream, small):
+    """Closing a context while requests are queued and batches run: the
+    batches on the GPU finish, the queued requests are dropped, and close
+    returns (bounded) without error."""
+    import time
+    D, M, F = small
+    c = pq.Context(arena_bytes=1 << 30)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, c, D, M, F, stream=stream)
+        torch.cuda.current_stream().synchronize()
+    for i in range(400):
+        pq.pq_submit(c, pq.make_plan(TD, TM, TF, seg=i % 5, k=10))
+    t0 = time.monotonic()
+    c.close()
+    assert time.monotonic() - t0 < 35
 
 
 def test_autotune_keeps_results(ctx, stream, small, small_tables):

@@ -215,7 +215,7 @@ def test_serving_mixing_plan_shapes(ctx, small, small_tables):
     plans = mixed_plans(small_tables[:3]) * 3
     tickets = [pq.pq_submit(ctx, p) for p, _ in plans]
     for i, t in enumerate(tickets):
-        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=120_000)
+        st, res, lat = pq.pq_poll(ctx, t, timeout_ms=15_000)
         assert st == pq.PQ_OK and lat > 0
         same(res, plans[i][1](*small), f"served {i}")
 
