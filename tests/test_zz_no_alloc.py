@@ -3,14 +3,17 @@
 pq_filter_noalloc serves callers that cannot allocate device memory (code
 running during a CUDA graph capture, or inside a runtime that owns every
 allocation): it takes no context and keeps its scratch in a static device
-array of the library.  Its output must equal pq_filter's, exactly (row ids
-are integers), on two calls in a row that reuse the same static scratch.
+array of the library.  Its output must equal pq_filter's and the CPU
+oracle's, exactly (row ids are integers), on two calls in a row that reuse
+the same static scratch.
 This file is collected last so that a failure here never hides another test.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +56,7 @@ def test_noalloc_filter_matches_pq_filter_on_two_calls(pq):
         k = int(wcnt.item())
         assert int(cnt.item()) == k and int(err.item()) == 0, (op, c)
         assert torch.equal(out[:k], want[:k]), (op, c)
+        assert np.array_equal(out[:k].cpu().numpy(), oracle.filter(a, op, c)), (op, c)
     ctx.close()
 
 
@@ -76,6 +80,8 @@ def test_noalloc_filter_with_selection_vector(pq):
     k = int(wcnt.item())
     assert int(cnt.item()) == k and int(err.item()) == 0
     assert torch.equal(out[:k], want[:k])
+    want_cpu = oracle.filter(a, "!=", 5, sel_in=oracle.filter(a, ">", -200))
+    assert np.array_equal(out[:k].cpu().numpy(), want_cpu)
     ctx.close()
 
 
