@@ -127,6 +127,20 @@ static void plan_static(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, cudaStre
   };
   d.d_static = r.resident[0] && fits(p.D, r.e_d, &d.d_su, &d.d_sb) ? 1 : 0;
   d.m_static = r.resident[1] && fits(p.M, r.e_m, &d.m_su, &d.m_sb) ? 1 : 0;
+  // Bound of one row's revenue |price * (100 - disc)|: the price column's
+  // measured range times the largest |100 - disc| of an int8 (228).
+  d.rev_max = 0;
+  if (r.resident[2] && p.F->nrows > 0) {
+    const KeyRange& pr = p.F->cols[1].range;
+    if (pr.known() || (!capturing && ensure_range(ctx, p.F, 1, s))) {
+      const i64 lo = (i64)(pr.umin ^ (1ULL << 63)), hi = (i64)(pr.umax ^ (1ULL << 63));
+      const unsigned __int128 amax =
+          std::max(lo < 0 ? (unsigned __int128)(-(__int128)lo) : (unsigned __int128)lo,
+                   hi < 0 ? (unsigned __int128)(-(__int128)hi) : (unsigned __int128)hi);
+      const unsigned __int128 rev = amax * 228;
+      if (rev < ((unsigned __int128)1 << 63)) d.rev_max = (u64)rev;
+    }
+  }
 }
 
 pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need_resident) {
@@ -188,6 +202,17 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
   for (auto q : ptrs) d.vec &= (((uintptr_t)q) & 15) == 0;
   d.m_pair = p.M->mode == PQ_MAPPED ? 1 : 0;
   d.f_pair = p.F->mode == PQ_MAPPED ? 1 : 0;
+  d.part_log2 = 0;
+  if (p.flags & PQ_PLAN_PARTITIONED) {
+    if (p.flags & PQ_PLAN_AGG_FIRST)
+      return fail(ctx, PQ_ERR_INVALID_ARG,
+                  "plan: PQ_PLAN_PARTITIONED applies to the join-first plan only");
+    const int lp = p.log2P > 0 ? p.log2P : ctx->opt.log2P;
+    if (lp < 1 || lp > kMaxPartLog2)
+      return fail(ctx, PQ_ERR_INVALID_ARG, "plan: partitioned fan-out 2^%d (1 .. 2^%d)", lp,
+                  kMaxPartLog2);
+    d.part_log2 = lp;
+  }
   return PQ_OK;
 }
 
@@ -206,6 +231,8 @@ size_t plan_bytes(const ResolvedPlan& r) {
   b += al(r.parts * 8) * 2 + al(r.parts * 4);                  // top-k tile maxima
   b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k candidates
   b += al(r.n_f * 4);                                           // F hit list
+  if (r.dev.part_log2)                                          // partitioned hits
+    b += al(((1 << r.dev.part_log2) + 1) * 8) + al(r.n_f * 8) + al(r.n_f * 4) + al(r.n_f * 8);
   return b;
 }
 
@@ -228,6 +255,13 @@ void plan_assign(ResolvedPlan& r, char* base) {
   d.cand_k = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
   d.cand_s = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
   d.hlist = (u32*)take(r.n_f * 4);
+  d.part = nullptr, d.pval0 = nullptr, d.pslot = nullptr, d.pval = nullptr;
+  if (d.part_log2) {
+    d.part = (u64*)take(((1 << d.part_log2) + 1) * 8);
+    d.pval0 = (i64*)take(r.n_f * 8);
+    d.pslot = (u32*)take(r.n_f * 4);
+    d.pval = (i64*)take(r.n_f * 8);
+  }
 }
 
 BatchLayout batch_layout(int nq) {
@@ -243,7 +277,7 @@ BatchLayout batch_layout(int nq) {
   L.tF = o;
   o += 8 * (nq + 1);
   L.dyn = al(o);
-  o = L.dyn + 8 * 8 * (nq + 1);
+  o = L.dyn + 11 * 8 * (nq + 1);
   L.work = al(o);
   o = L.work + 256;
   L.ctr = o;
@@ -271,10 +305,12 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
 
 static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "plan_mscan",
                                    "plan_mfill", "plan_mbuild", "plan_mrank",  "plan_mdup",
-                                   "plan_fscan", "plan_fprobe", "plan_topk",   "plan_topk2"};
+                                   "plan_fscan", "plan_fpart",  "plan_fscatter", "plan_fagg",
+                                   "plan_fprobe", "plan_topk",  "plan_topk2"};
+static_assert(sizeof(kPhaseName) / sizeof(kPhaseName[0]) == kPhaseTopk2 + 1, "phase names");
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[18] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
+  const void* fn[21] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
                         (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true, true>,
                         (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
                         (const void*)k_plan_fscan<false>, (const void*)k_plan_topk,
@@ -284,8 +320,11 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
                         (const void*)k_plan_mscan<true, false>,
                         (const void*)k_plan_mscan<false, false>,
                         (const void*)k_plan_mscan_bm<true>,
-                        (const void*)k_plan_mscan_bm<false>};
-  for (int i = 0; i < 18; ++i) {
+                        (const void*)k_plan_mscan_bm<false>,
+                        (const void*)k_plan_fpart,
+                        (const void*)k_plan_fscatter,
+                        (const void*)k_plan_fagg};
+  for (int i = 0; i < 21; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -370,6 +409,11 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
       e = vec ? launch_chained(k_plan_fscan<true>, plan_grid(ctx, 8), 256, s, b)
               : launch_chained(k_plan_fscan<false>, plan_grid(ctx, 6), 256, s, b);
       break;
+    case kPhaseFpart: e = launch_chained(k_plan_fpart, plan_grid(ctx, 18, 1), 256, s, b); break;
+    case kPhaseFscatter:
+      e = launch_chained(k_plan_fscatter, plan_grid(ctx, 19, 1), 256, s, b);
+      break;
+    case kPhaseFagg: e = launch_chained(k_plan_fagg, plan_grid(ctx, 20), 256, s, b); break;
     case kPhaseF: e = launch_chained(k_plan_fprobe, plan_grid(ctx, 13), 256, s, b); break;
     case kPhaseTopk: e = launch_chained(k_plan_topk, plan_grid(ctx, 7, 1), kTKW * 32, s, b); break;
     case kPhaseTopk2:
@@ -701,6 +745,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
                 total, ctx->arena.largest_free());
   }
   bool any_build = false, vec = true, list_d = false, list_m = false, bm_dm = true;
+  bool any_part = false;
   std::vector<std::pair<void*, size_t>> clears;  // static D bitmaps to zero first
   std::vector<std::pair<void*, size_t>> m_clears;  // static M bitmaps: the D scan clears them
   i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
@@ -731,6 +776,13 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       clears.push_back({(char*)d.dset_tag + table_layout(r.e_d, false).keybm,
                         (size_t)((d.d_sb + 127) / 128 * 16)});
     if (d.m_static) m_clears.push_back({(void*)d.ht_tag, (size_t)dense_layout(0, d.m_sb).tdir});
+    if (d.part_log2) {
+      any_part = true;
+      clears.push_back({(void*)d.part, (size_t)((1 << d.part_log2) + 1) * 8});
+      tmax[kPhaseFpart] += (r.n_f + kPT - 1) / kPT;
+      tmax[kPhaseFscatter] += (r.n_f + kPT - 1) / kPT;
+      tmax[kPhaseFagg] += (r.n_f + kAT - 1) / kAT;
+    }
     list_d = list_d || (r.builds && !d.d_static);
     list_m = list_m || !d.m_static;
     // The D-set is a bitmap for certain when it is built here from a static
@@ -781,17 +833,20 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   auto chain = [&](cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) -> pq_status {
     PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
     for (auto& c : clears) PQ_CUDA(ctx, cudaMemsetAsync(c.first, 0, c.second, s));
+    // The first phase that reads the M dictionary's directories.
+    const int first_probe = any_part ? kPhaseFpart : kPhaseF;
     for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
       // Phases only plans with key lists need.
       if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
       if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;
+      if (!any_part && part_phase(ph)) continue;
       cudaStream_t on = s;
       if (side && ph == kPhaseMrank) {
         PQ_CUDA(ctx, cudaEventRecord(fork, s));
         PQ_CUDA(ctx, cudaStreamWaitEvent(side, fork, 0));
       }
       if (side && (ph == kPhaseMrank || ph == kPhaseMdup)) on = side;
-      if (side && ph == kPhaseF) PQ_CUDA(ctx, cudaStreamWaitEvent(s, join, 0));
+      if (side && ph == first_probe) PQ_CUDA(ctx, cudaStreamWaitEvent(s, join, 0));
       pq_status st = launch_phase(ctx, ph, b, vec, on, tmax[ph], list_m, bm_dm);
       if (st != PQ_OK) return st;
       if (side && ph == kPhaseMdup) PQ_CUDA(ctx, cudaEventRecord(join, side));

@@ -92,7 +92,14 @@ pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
 pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s,
                        i64 tiles_max = -1, bool list_m = true, bool bm_dm = false);
 
+// Phases in chain order.  Fpart, Fscatter and Fagg run only for batches
+// with a partitioned plan; the F probe (kPhaseF) always runs, for the plans
+// that are not partitioned, and its last block sizes the top-k for all.
 enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseMrank,
-       kPhaseMdup, kPhaseFscan, kPhaseF, kPhaseTopk, kPhaseTopk2 };
+       kPhaseMdup, kPhaseFscan, kPhaseFpart, kPhaseFscatter, kPhaseFagg, kPhaseF, kPhaseTopk,
+       kPhaseTopk2 };
+inline bool part_phase(int ph) {
+  return ph == kPhaseFpart || ph == kPhaseFscatter || ph == kPhaseFagg;
+}
 
 }  // namespace pqh

@@ -152,13 +152,14 @@ __host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
 // is not a hash table: a group's slot is the rank of its key among the
 // distinct M' keys (the set bits before its bit), read from a two-level
 // directory (set bits before each tile of kRankTile 512-bit blocks, and
-// before each block within its tile) plus the block's words.  Slots follow
-// key order.  Layout in the M table's region, for c entries in the M list
-// (members of M') and `bits` bitmap bits (byte offsets; the bitmap comes
-// first so that its place does not depend on c):
+// before each 32-bit word within its tile) plus the key's word: three loads
+// and one popcount.  Slots follow key order.  Layout in the M table's
+// region, for c entries in the M list (members of M') and `bits` bitmap bits
+// (byte offsets; the bitmap comes first so that its place does not depend
+// on c):
 //   bm    the key-range bitmap                64 B per 512-bit block
 //   tdir  u32 set bits before each tile, then the total
-//   bdir  u16 set bits before each block within its tile
+//   wdir  u16 set bits before each word within its tile (2 B per word)
 //   hit   first-hit bit per slot              c/8 B
 //   sums  i64 sum per slot                    8c B
 //   cnt   u32 copies of the key per slot      4c B (written only when the
@@ -167,7 +168,7 @@ __host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
 // fill); the rank pass writes the directories and clears hit, sums, cnt.
 constexpr int kRankTile = 64;   // bitmap blocks per tile (at most 32768 bits)
 struct DenseLayout {
-  u64 bm, tdir, bdir, hit, sums, cnt, total;
+  u64 bm, tdir, wdir, hit, sums, cnt, total;
 };
 __host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
   auto a = [](u64 x) { return (x + 255) & ~255ULL; };
@@ -175,8 +176,8 @@ __host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
   DenseLayout L;
   L.bm = 0;
   L.tdir = a(64 * blocks);
-  L.bdir = L.tdir + a(4 * (tiles + 1));
-  L.hit = L.bdir + a(2 * blocks);
+  L.wdir = L.tdir + a(4 * (tiles + 1));
+  L.hit = L.wdir + a(32 * blocks);
   L.sums = L.hit + a(((u64)c + 7) / 8);
   L.cnt = L.sums + a(8 * (u64)c);
   L.total = L.cnt + a(4 * (u64)c);
@@ -311,6 +312,23 @@ struct PlanDev {
   i64* cand_k;  // top-k candidates (topk_cand_cap entries)
   i64* cand_s;
   u32* hlist;   // F rows that hit (n_f entries, rows of the plan)
+  // Partitioned F phase (PQ_PLAN_PARTITIONED): the hits are radix-
+  // partitioned by group slot into 2^part_log2 buckets (part_shift) before
+  // they are aggregated, so that each bucket's slice of the group arrays is
+  // small enough to stay in L2 while its hits are added.  0: not partitioned.
+  // Upper bound of |price * (100 - disc)| over the F table's rows (from the
+  // measured range of its price column), or 0 when unknown.  When the hits
+  // times this bound times the largest multiplicity stay below 2^63, no
+  // group sum or partial sum can leave int64, and the probe commits with
+  // fire-and-forget reductions and no overflow checks (fast_commit).
+  u64 rev_max;
+  int part_log2;
+  u64* part;    // [2^part_log2 + 1]: matched hits per bucket, then the
+                // buckets' write cursors (their offsets in pslot / pval)
+  i64* pval0;   // revenue of each hit in hit order (n_f entries; the slot
+                // replaces the row in hlist)
+  u32* pslot;   // partitioned hits (n_f entries): group slot
+  i64* pval;    //                                 revenue times multiplicity
   QCtr* ctr;
   pq_result* out;
 };
@@ -342,7 +360,26 @@ struct Batch {
 };
 
 enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk,
-       kPhTopk2, kPhMrank, kPhMdup, kPhFscan };
+       kPhTopk2, kPhMrank, kPhMdup, kPhFscan, kPhFpart, kPhFagg, kPhFscatter };
+
+// Largest fan-out of a partitioned plan (buckets 2^kMaxPartLog2), hits per
+// block tile of its partition and scatter passes, records per warp tile of
+// its aggregation pass.
+constexpr int kMaxPartLog2 = 10;
+constexpr int kPT = 2048;
+constexpr int kAT = 1024;
+
+// Bucket of a hit in a partitioned plan with 2^log2P buckets: the top bits
+// of its group slot among the plan's n slots, bucket = slot >> part_shift(n,
+// log2P).  Dense M dictionary: slots are ranks in key order, so a bucket is
+// a key range; hash table: a slot's top bits are its key's home bucket, the
+// top bits of the key's Fibonacci product (a radix hash partition).  Either
+// way a bucket's groups occupy one contiguous range of the group arrays.
+__host__ __device__ __forceinline__ int part_shift(u64 n, int log2P) {
+  int len = 0;  // bits needed for the largest slot, n - 1
+  for (u64 x = n > 0 ? n - 1 : 0; x; x >>= 1) ++len;
+  return len > log2P ? len - log2P : 0;
+}
 
 // The kernels below are defined in exactly one translation unit (pq_plan.cu),
 // which defines PQ_DEFINE_PLAN_KERNELS before including this header.
@@ -1158,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_plan_mbuild(Batch b) {
 struct DenseView {
   const u32* bm;
   const u32* tdir;
-  const unsigned short* bdir;
+  const unsigned short* wdir;
   u64 blocks;
 };
 __device__ __forceinline__ DenseView dense_view(const void* region, i64 c, u64 bits) {
@@ -1167,32 +1204,21 @@ __device__ __forceinline__ DenseView dense_view(const void* region, i64 c, u64 b
   DenseView v;
   v.bm = reinterpret_cast<const u32*>(base + L.bm);
   v.tdir = reinterpret_cast<const u32*>(base + L.tdir);
-  v.bdir = reinterpret_cast<const unsigned short*>(base + L.bdir);
+  v.wdir = reinterpret_cast<const unsigned short*>(base + L.wdir);
   v.blocks = (bits + 511) / 512;
   return v;
 }
 
-// Rank of bitmap bit idx (which is set): set bits before it.
+// Rank of bitmap bit idx (which is set): set bits before it -- the tile's
+// prefix, the word's prefix within the tile, the bits below it in its word.
 __device__ __forceinline__ u64 dense_rank(const DenseView& d, u64 idx, u64 keep) {
-  const u64 blk = idx >> 9;
-  const int wi = (int)((idx >> 5) & 15);
-  const u32 below = (1u << (idx & 31)) - 1u;
-  const uint4* w4 = reinterpret_cast<const uint4*>(d.bm + blk * 16);
-  u32 r;
+  const u64 wi = idx >> 5;
+  u32 t, w;
   asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;"
-      : "=r"(r) : "l"(d.tdir + blk / kRankTile), "l"(keep));
-  r += ld_keep_u16(d.bdir + blk, keep);
-#pragma unroll
-  for (int qd = 0; qd < 4; ++qd) {
-    const uint4 v = ld_keep_v4u(w4 + qd, keep);
-    const u32 w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int x = qd * 4 + j;
-      r += x < wi ? __popc(w[j]) : x == wi ? __popc(w[j] & below) : 0u;
-    }
-  }
-  return r;
+      : "=r"(t) : "l"(d.tdir + (idx >> 15)), "l"(keep));
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(w) : "l"(d.bm + wi), "l"(keep));
+  const u32 wp = ld_keep_u16(d.wdir + wi, keep);
+  return (u64)t + wp + __popc(w & ((1u << (idx & 31)) - 1u));
 }
 
 // Key of dense slot `rank` (< distinct keys): the rank-th set bit.
@@ -1205,25 +1231,18 @@ __device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank)
     else hi = mid;
   }
   u32 r = (u32)(rank - d.tdir[lo]);
-  u64 b0 = lo * kRankTile, b1 = min(d.blocks, b0 + kRankTile);
-  while (b1 - b0 > 1) {  // last block of the tile with bdir <= r
-    const u64 mid = (b0 + b1) >> 1;
-    if (d.bdir[mid] <= r) b0 = mid;
-    else b1 = mid;
+  const u64 words = d.blocks * 16;
+  u64 w0 = lo * kRankTile * 16, w1 = min(words, w0 + kRankTile * 16);
+  while (w1 - w0 > 1) {  // last word of the tile with wdir <= r
+    const u64 mid = (w0 + w1) >> 1;
+    if (d.wdir[mid] <= r) w0 = mid;
+    else w1 = mid;
   }
-  r -= d.bdir[b0];
-  const u32* w = d.bm + b0 * 16;
-  for (int i = 0; i < 16; ++i) {
-    const u32 c = __popc(w[i]);
-    if (r < c) {
-      u32 x = w[i];
-      for (; r; --r) x &= x - 1;
-      const u64 u = umin + b0 * 512 + (u64)i * 32 + (u64)(__ffs(x) - 1);
-      return (i64)(u ^ (1ULL << 63));
-    }
-    r -= c;
-  }
-  return 0;  // not reached: rank < total
+  r -= d.wdir[w0];
+  u32 x = d.bm[w0];
+  for (; r; --r) x &= x - 1;
+  const u64 u = umin + w0 * 32 + (u64)(__ffs(x) - 1);
+  return (i64)(u ^ (1ULL << 63));
 }
 
 // Rank pass: one warp per tile of kRankTile blocks writes each block's set
@@ -1247,7 +1266,7 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
     char* base = reinterpret_cast<char*>(q.ht_tag);
     const uint4* bm = reinterpret_cast<const uint4*>(base + L.bm);
     u32* tdir = reinterpret_cast<u32*>(base + L.tdir);
-    unsigned short* bdir = reinterpret_cast<unsigned short*>(base + L.bdir);
+    unsigned short* wdir = reinterpret_cast<unsigned short*>(base + L.wdir);
     const u64 blocks = (bits + 511) / 512;
     const i64 lt = t - pre[qi];
     const u64 b0 = (u64)lt * kRankTile, b1 = min(blocks, b0 + kRankTile);
@@ -1259,14 +1278,15 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
     }
     u32 run = 0;
     for (u64 j0 = b0; j0 < b1; j0 += 32) {
-      const u64 j = j0 + lane;
+      const u64 j = j0 + lane;  // the lane's block: 16 words
+      u32 c[16];
       u32 p = 0;
-      if (j < b1) {
 #pragma unroll
-        for (int qd = 0; qd < 4; ++qd) {
-          const uint4 v = __ldcg(bm + j * 4 + qd);
-          p += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        }
+      for (int qd = 0; qd < 4; ++qd) {
+        const uint4 v = j < b1 ? __ldcg(bm + j * 4 + qd) : make_uint4(0, 0, 0, 0);
+        c[qd * 4] = __popc(v.x), c[qd * 4 + 1] = __popc(v.y);
+        c[qd * 4 + 2] = __popc(v.z), c[qd * 4 + 3] = __popc(v.w);
+        p += c[qd * 4] + c[qd * 4 + 1] + c[qd * 4 + 2] + c[qd * 4 + 3];
       }
       u32 incl = p;
 #pragma unroll
@@ -1274,7 +1294,20 @@ __global__ void __launch_bounds__(256) k_plan_mrank(Batch b) {
         const u32 y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
       }
-      if (j < b1) bdir[j] = (unsigned short)(run + incl - p);
+      if (j < b1) {  // the block's 16 word prefixes, two 16-byte stores
+        u32 pre = run + incl - p;
+        u32 h[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const u32 lo = pre;
+          pre += c[2 * x];
+          h[x] = lo | (pre << 16);
+          pre += c[2 * x + 1];
+        }
+        uint4* dst = reinterpret_cast<uint4*>(wdir + j * 16);
+        dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+      }
       run += __shfl_sync(kFull, incl, 31);
     }
     if (lane == 0) tdir[lt] = run;  // the tile's total, a prefix after the scan
@@ -1391,6 +1424,21 @@ struct ProbeCtx {
   int qi;  // plan index in the batch
 };
 
+// The fast commit of a plan (see PlanDev::rev_max), for `hits` hits.
+__device__ __forceinline__ bool fast_commit(const PlanDev& q, u64 hits) {
+  if (!q.rev_max) return false;
+  // Largest multiplicity: 1 for a dense dictionary of distinct keys, else
+  // the plan's M rows (a hash table may hold a key in many slots).
+  const unsigned __int128 mult = q.ctr->m_bits && !q.ctr->dup ? 1 : (u64)max(q.n_m, (i64)1);
+  return (unsigned __int128)hits * q.rev_max * mult < ((unsigned __int128)1 << 63);
+}
+__device__ __forceinline__ void red_add(i64* p, i64 v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(u32* p, u32 v) {
+  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool add_overflows(i64 old, i64 v) {
   return (v > 0 && old > INT64_MAX - v) || (v < 0 && old < INT64_MIN - v);
 }
@@ -1461,7 +1509,8 @@ __device__ __forceinline__ Hit probe_row(const Batch& bt_, const ProbeCtx& c, u3
 // kernel, so the repeated hits of hot groups (skewed data) stay on chip.
 // False when the entry belongs to another key.  (Measured on Zipf data: a
 // 2048-entry table with 4-way probing was slower than this one.)
-__device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, bool& ovf) {
+__device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, bool& ovf,
+                                        bool exact) {
   const u32 h = (u32)((ak * 0x9E3779B97F4A7C15ULL) >> (64 - kAggLog2));
   u64 cur = *(volatile u64*)&akey[h];
   if (cur == 0) {
@@ -1469,8 +1518,12 @@ __device__ __forceinline__ bool agg_try(u64* akey, i64* asum, u64 ak, i64 v, boo
     if (cur == 0) cur = ak;
   }
   if (cur != ak) return false;
-  const i64 old = (i64)atomicAdd((unsigned long long*)&asum[h], (unsigned long long)v);
-  ovf = ovf || add_overflows(old, v);
+  if (exact) {
+    const i64 old = (i64)atomicAdd((unsigned long long*)&asum[h], (unsigned long long)v);
+    ovf = ovf || add_overflows(old, v);
+  } else {
+    atomicAdd((unsigned long long*)&asum[h], (unsigned long long)v);
+  }
   return true;
 }
 
@@ -1505,8 +1558,19 @@ __device__ __forceinline__ GroupStore group_store(const PlanDev& q) {
 // else to the M table and sets the slot's first-hit bit (a reduction nobody
 // waits for).  The groups are read from the first-hit bits by the top-k
 // phase.  sc: the warp's 32-entry scratch.
+__device__ __forceinline__ void commit_hits_g(const Batch& b, i64* sc, u64* akey, i64* asum,
+                                              bool act, int qi, u64 s, i64 v,
+                                              const GroupStore* gs, bool exact);
 __device__ __forceinline__ void commit_hits(const Batch& b, i64* sc, u64* akey, i64* asum,
                                             bool act, int qi, u64 s, i64 v) {
+  commit_hits_g(b, sc, akey, asum, act, qi, s, v, nullptr, true);
+}
+// As commit_hits, with the plan's group store already resolved (gs, for
+// callers whose batch of 32 belongs to one plan; nullptr: look it up).
+// exact = false (fast_commit holds): reductions with no overflow checks.
+__device__ __forceinline__ void commit_hits_g(const Batch& b, i64* sc, u64* akey, i64* asum,
+                                              bool act, int qi, u64 s, i64 v,
+                                              const GroupStore* gs, bool exact) {
   const int lane = threadIdx.x & 31;
   const u64 ak = act ? ((u64)qi << 40) + s + 1 : 0;
   const u32 peers = __match_any_sync(kFull, ak);
@@ -1519,16 +1583,20 @@ __device__ __forceinline__ void commit_hits(const Batch& b, i64* sc, u64* akey, 
     __int128 acc = 0;
     for (u32 m = peers; m; m &= m - 1) acc += sc[__ffs(m) - 1];
     tot = (i64)acc;
-    ovf = acc != (__int128)tot;
+    ovf = exact && acc != (__int128)tot;
   }
   __syncwarp();
   if (lead) {
     const PlanDev& q = b.q[qi];
-    if (!(akey && agg_try(akey, asum, ak, tot, ovf))) {
-      const GroupStore g = group_store(q);
-      atomicOr(g.hit + (s >> 5), 1u << (s & 31));
-      const i64 old = (i64)atomicAdd((u64*)(g.sums + s * g.stride), (u64)tot);
-      ovf = ovf || add_overflows(old, tot);
+    if (!(akey && agg_try(akey, asum, ak, tot, ovf, exact))) {
+      const GroupStore g = gs ? *gs : group_store(q);
+      red_or(g.hit + (s >> 5), 1u << (s & 31));
+      if (exact) {
+        const i64 old = (i64)atomicAdd((u64*)(g.sums + s * g.stride), (u64)tot);
+        ovf = ovf || add_overflows(old, tot);
+      } else {
+        red_add(g.sums + s * g.stride, tot);
+      }
     }
     if (ovf) q_latch(q.ctr, b.st, PQ_ERR_OVERFLOW, (i64)s);
   }
@@ -1542,8 +1610,9 @@ __device__ __forceinline__ i64 topk_words(const PlanDev& q) {
 
 // End of an F-probe kernel: flush the block's aggregated sums to the plans'
 // tables; the block that finishes last sizes the top-k phase.
-__device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_akey,
-                                                const i64* s_asum, i64* sc) {
+// Flush a block's shared aggregation table into the plans' groups.
+__device__ __forceinline__ void agg_flush(const Batch& b, const u64* s_akey, const i64* s_asum,
+                                          i64* sc) {
   __syncthreads();
   int used = 0;
   for (int i = threadIdx.x; i < kAgg; i += blockDim.x) used |= s_akey[i] != 0;
@@ -1553,6 +1622,11 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
     commit_hits(b, sc, nullptr, nullptr, ak != 0, ak ? (int)((ak - 1) >> 40) : 0,
                 (ak - 1) & ((1ULL << 40) - 1), ak ? s_asum[i] : 0);
   }
+}
+
+__device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_akey,
+                                                const i64* s_asum, i64* sc) {
+  agg_flush(b, s_akey, s_asum, sc);
   if (finish(b.work, kPhFprobe)) {
     block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
@@ -1565,6 +1639,42 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_ake
       return max((i64)1, (w + topk_tile_words_w(w) - 1) / topk_tile_words_w(w));
     });
   }
+}
+
+// Partitioned plans, in the last block of the partition pass: each bucket's
+// count becomes its write cursor (exclusive scan, part[P] = total matched
+// hits), and the tile counts of the scatter pass (kPT hits per block tile)
+// and of the aggregation pass (kAT records per warp tile) go to their
+// prefixes.
+__device__ __forceinline__ void part_sizes(const Batch& b) {
+  __shared__ u64 s_carry;
+  for (int qi = 0; qi < b.nq; ++qi) {
+    const PlanDev& q = b.q[qi];
+    if (!q.part_log2) continue;
+    const int P = 1 << q.part_log2;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int p0 = 0; p0 < P; p0 += (int)blockDim.x) {
+      const int p = p0 + (int)threadIdx.x;
+      const u64 v = p < P ? __ldcg(q.part + p) : 0;
+      const u32 ex = block_exclusive_sum((u32)v);  // a plan holds < 2^32 hits
+      const u64 base = s_carry;
+      if (p < P) q.part[p] = base + ex;
+      __syncthreads();
+      if (threadIdx.x == blockDim.x - 1) s_carry = base + ex + v;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) q.part[P] = s_carry;
+    __syncthreads();
+  }
+  block_prefix(b.dyn + 9 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+    const PlanDev& q = b.q[qi];
+    return q.part_log2 ? (ld_count(&q.ctr->hcount) + kPT - 1) / kPT : 0;
+  });
+  block_prefix(b.dyn + 10 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+    const PlanDev& q = b.q[qi];
+    return q.part_log2 ? (i64)(__ldcg(q.part + (1 << q.part_log2)) + kAT - 1) / kAT : 0;
+  });
 }
 
 // F scan: warp tiles of F rows (up to 2048), 128 per step (lane l: rows
@@ -1718,7 +1828,11 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
       i64 tl = (h / (2 * warps) + 31) / 32 * 32;
       tl = tl < 64 ? 64 : tl > 4096 ? 4096 : tl;
       c->hp_tile = tl;
-      return (h + tl - 1) / tl;
+      return b.q[qi].part_log2 ? 0 : (h + tl - 1) / tl;  // partitioned: fpart .. fagg
+    });
+    block_prefix(b.dyn + 8 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
+      const PlanDev& q = b.q[qi];
+      return q.part_log2 ? (ld_count(&q.ctr->hcount) + kPT - 1) / kPT : 0;
     });
   }
 }
@@ -1757,17 +1871,313 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
     pc.base = 0;
     pc.keep = keep;
     pc.qi = qi;
-    const i64 tl = q.ctr->hp_tile, h = (i64)q.ctr->hcount;
+    QCtr* const c = q.ctr;
+    const i64 tl = c->hp_tile, h = (i64)c->hcount;
     const i64 i0 = (t - pre[qi]) * tl, i1 = min(h, i0 + tl);
-    const bool agg = (u64)h >= agg_min;
+    u64* const akey = (u64)h >= agg_min ? s_akey : nullptr;
+    const u64 m_bits = c->m_bits;
+    if (m_bits) {
+      // Dense dictionary, with the plan's constants held in registers for
+      // the whole tile: slot = rank of the key's bit (three loads), the
+      // multiplicity only when the members repeat keys.
+      const i64 mc = (i64)c->mcount;
+      const DenseView dv = dense_view(q.ht_tag, mc, m_bits);
+      const DenseLayout L = dense_layout(mc, m_bits);
+      char* const gb = reinterpret_cast<char*>(q.ht_tag);
+      const u32* const cnt = c->dup ? reinterpret_cast<const u32*>(gb + L.cnt) : nullptr;
+      GroupStore g;
+      g.hit = reinterpret_cast<u32*>(gb + L.hit);
+      g.sums = reinterpret_cast<i64*>(gb + L.sums);
+      g.stride = 1;
+      const u64 umin = c->m_umin;
+      const bool exact = !fast_commit(q, (u64)h);
+      for (i64 i = i0; i < i1; i += 32) {
+        const bool act = i + lane < i1;
+        u64 slot = 0;
+        i64 v = 0;
+        if (act) {
+          const i64 row = __ldg(q.hlist + i + lane);
+          const i64 k = __ldg(pc.mkey + row);
+          const i64 price = __ldg(pc.price + row);
+          const i64 disc = __ldg(pc.disc + row);
+          slot = dense_rank(dv, ukey(k) - umin, keep);
+          const i64 mult = cnt ? (i64)__ldg(cnt + slot) : 1;
+          if (exact) {
+            const __int128 v128 = (__int128)mult * ((__int128)price * (100 - disc));
+            v = (i64)v128;
+            if (v128 != (__int128)v) q_latch(c, b.st, PQ_ERR_OVERFLOW, k);
+          } else {
+            v = mult * (price * (100 - disc));  // fits: fast_commit's bound
+          }
+        }
+        commit_hits_g(b, sc, akey, s_asum, act, qi, slot, v, &g, exact);
+      }
+      continue;
+    }
+    const bool exact = !fast_commit(q, (u64)h);
     for (i64 i = i0; i < i1; i += 32) {
       const bool act = i + lane < i1;
       Hit x = {false, 0, 0};
       if (act) x = probe_row(b, pc, __ldg(q.hlist + i + lane));
-      commit_hits(b, sc, agg ? s_akey : nullptr, s_asum, x.act, qi, x.slot, x.v);
+      commit_hits_g(b, sc, akey, s_asum, x.act, qi, x.slot, x.v, nullptr, exact);
     }
   }
   fprobe_epilogue(b, s_akey, s_asum, sc);
+}
+
+// Probe of one hit against a dense dictionary, with the plan's constants in
+// registers: slot = rank of the key's bit, revenue times the key's copies in
+// M' (cnt: copy counts, or null when the members do not repeat keys), formed
+// in 128 bits (an int64 overflow is latched).
+struct DenseProbe {
+  DenseView dv;
+  const u32* cnt;
+  u64 umin;
+};
+__device__ __forceinline__ DenseProbe dense_probe(const PlanDev& q) {
+  const QCtr* c = q.ctr;
+  const i64 mc = (i64)c->mcount;
+  DenseProbe p;
+  p.dv = dense_view(q.ht_tag, mc, c->m_bits);
+  p.cnt = c->dup ? reinterpret_cast<const u32*>(reinterpret_cast<const char*>(q.ht_tag) +
+                                                dense_layout(mc, c->m_bits).cnt)
+                 : nullptr;
+  p.umin = c->m_umin;
+  return p;
+}
+__device__ __forceinline__ i64 dense_hit(const DenseProbe& p, const ProbeCtx& pc, const Batch& b,
+                                         QCtr* ctr, i64 row, u64* slot) {
+  const i64 k = __ldg(pc.mkey + row);
+  const i64 price = __ldg(pc.price + row);
+  const i64 disc = __ldg(pc.disc + row);
+  *slot = dense_rank(p.dv, ukey(k) - p.umin, pc.keep);
+  const i64 mult = p.cnt ? (i64)__ldg(p.cnt + *slot) : 1;
+  const __int128 v128 = (__int128)mult * ((__int128)price * (100 - disc));
+  const i64 v = (i64)v128;
+  if (v128 != (__int128)v) q_latch(ctr, b.st, PQ_ERR_OVERFLOW, k);
+  return v;
+}
+
+// Group slots of a plan: dense dictionary members, or hash-table slots.
+__device__ __forceinline__ u64 plan_slots(const QCtr* c) {
+  return c->m_bits ? c->mcount : (1ULL << c->mlog2);
+}
+
+// Partition pass of a partitioned plan (the radix partition ahead of the
+// exchange, Sec. 3.1, kept on one GPU), 1 of 2: block tiles of kPT hits.
+// Every hit is probed once (group slot and revenue, as in the F probe); the
+// slot replaces the row in the hit list and the revenue goes to pval0, both
+// in hit order (coalesced), a hit that misses the hash table gets slot ~0;
+// each matched hit is counted into its bucket (slot >> shift) in a block
+// histogram in shared memory, flushed to the plan's bucket counters when
+// the block moves to another plan and at the end.  The last block turns the
+// counts into bucket cursors (part_sizes).
+__global__ void __launch_bounds__(256) k_plan_fpart(Batch b) {
+  chain_begin();
+  constexpr int kPmax = 1 << kMaxPartLog2;
+  __shared__ u32 s_hist[kPmax];
+  __shared__ i64 s_t;
+  const u64 keep = policy_keep();
+  const bool ov = b.ov.table == 3;
+  const i64* pre = b.dyn + 8 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  for (int p = threadIdx.x; p < kPmax; p += blockDim.x) s_hist[p] = 0;
+  __syncthreads();
+  int cq = -1;  // plan whose counts s_hist holds
+  auto flush = [&]() {
+    __syncthreads();
+    if (cq >= 0) {
+      const PlanDev& q = b.q[cq];
+      for (int p = threadIdx.x; p < (1 << q.part_log2); p += blockDim.x) {
+        const u32 c = s_hist[p];
+        if (c) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(q.part + p), (unsigned long long)c);
+          s_hist[p] = 0;
+        }
+      }
+    }
+    __syncthreads();
+  };
+  BlockClaim bc;
+  while (true) {
+    const i64 t = bc.next(b.work, kPhFpart, &s_t);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    if (qi != cq) flush(), cq = qi;  // block-uniform
+    const PlanDev& q = b.q[qi];
+    QCtr* const c = q.ctr;
+    const int shift = part_shift(plan_slots(c), q.part_log2);
+    ProbeCtx pc;
+    pc.mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
+    pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
+    pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+    pc.base = 0;
+    pc.keep = keep;
+    pc.qi = qi;
+    const i64 i0 = (t - pre[qi]) * kPT, i1 = min((i64)c->hcount, i0 + kPT);
+    if (c->m_bits) {
+      const DenseProbe dp = dense_probe(q);
+      for (i64 i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        u64 slot;
+        const i64 v = dense_hit(dp, pc, b, c, __ldcg(q.hlist + i), &slot);
+        q.hlist[i] = (u32)slot;
+        q.pval0[i] = v;
+        atomicAdd(&s_hist[slot >> shift], 1u);
+      }
+    } else {
+      for (i64 i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const Hit x = probe_row(b, pc, __ldcg(q.hlist + i));
+        q.hlist[i] = x.act ? (u32)x.slot : ~0u;
+        q.pval0[i] = x.v;
+        if (x.act) atomicAdd(&s_hist[x.slot >> shift], 1u);
+      }
+    }
+  }
+  flush();
+  if (finish(b.work, kPhFpart)) part_sizes(b);
+}
+
+// Partition pass, 2 of 2: block tiles of kPT hits in hit order.  The block
+// counts its matched hits per bucket in shared memory, claims one run per
+// bucket from the bucket's cursor, orders the tile's records by bucket in
+// shared memory and writes every run with consecutive threads on
+// consecutive records.  Record order inside a bucket is unspecified (the
+// sums are exact in any order).
+__global__ void __launch_bounds__(256) k_plan_fscatter(Batch b) {
+  chain_begin();
+  constexpr int kPmax = 1 << kMaxPartLog2;
+  constexpr int kPer = kPT / 256;
+  __shared__ u32 s_cnt[kPmax];  // the tile's records per bucket, then their offsets
+  __shared__ u64 s_go[kPmax];   // global position of the tile's run of each bucket
+  __shared__ u32 s_slot[kPT];
+  __shared__ i64 s_val[kPT];
+  __shared__ unsigned short s_bk[kPT];
+  __shared__ i64 s_t;
+  const i64* pre = b.dyn + 9 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  BlockClaim bc;
+  while (true) {
+    const i64 t = bc.next(b.work, kPhFscatter, &s_t);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    QCtr* const c = q.ctr;
+    const int P = 1 << q.part_log2;
+    const int shift = part_shift(plan_slots(c), q.part_log2);
+    const i64 i0 = (t - pre[qi]) * kPT;
+    const int n = (int)min((i64)kPT, (i64)c->hcount - i0);
+    for (int p = threadIdx.x; p < P; p += blockDim.x) s_cnt[p] = 0;
+    __syncthreads();
+    u32 slot[kPer], bl[kPer];  // bl: bucket << 16 | rank within the bucket's run
+    i64 val[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int idx = j * 256 + (int)threadIdx.x;
+      slot[j] = idx < n ? __ldcs(q.hlist + i0 + idx) : ~0u;
+      val[j] = idx < n ? __ldcs(q.pval0 + i0 + idx) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const u32 bk = slot[j] != ~0u ? slot[j] >> shift : 0u;
+      bl[j] = slot[j] != ~0u ? bk << 16 | atomicAdd(&s_cnt[bk], 1u) : ~0u;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+      const u32 cn = s_cnt[p];
+      s_go[p] = cn ? atomicAdd(reinterpret_cast<unsigned long long*>(q.part + p),
+                               (unsigned long long)cn)
+                   : 0;
+    }
+    u32 m = 0;  // matched records of the tile
+    {           // exclusive scan of the tile's bucket counts (P <= 4 * 256)
+      u32 v[4], sum = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = (int)threadIdx.x * 4 + j;
+        v[j] = p < P ? s_cnt[p] : 0u;
+        sum += v[j];
+      }
+      u32 run = block_exclusive_sum(sum);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = (int)threadIdx.x * 4 + j;
+        if (p < P) s_cnt[p] = run;
+        run += v[j];
+      }
+      __shared__ u32 s_m;
+      if (threadIdx.x == blockDim.x - 1) s_m = run;
+      __syncthreads();
+      m = s_m;
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (bl[j] != ~0u) {
+        const u32 bk = bl[j] >> 16, at = s_cnt[bk] + (bl[j] & 0xFFFFu);
+        s_slot[at] = slot[j];
+        s_val[at] = val[j];
+        s_bk[at] = (unsigned short)bk;
+      }
+    }
+    __syncthreads();
+    const u64 end = q.part[P];  // matched hits of the plan: the records' end
+    for (int i = threadIdx.x; i < (int)m; i += blockDim.x) {
+      const u32 bk = s_bk[i];
+      const u64 g = s_go[bk] + (u64)(i - (int)s_cnt[bk]);
+      if (g < end) {
+        q.pslot[g] = s_slot[i];
+        q.pval[g] = s_val[i];
+      } else {  // bucket sizes disagree with the counts: never written out of bounds
+        q_latch(c, b.st, PQ_ERR_CAPACITY, (i64)g);
+      }
+    }
+    __syncthreads();
+  }
+  finish(b.work, kPhFscatter);
+}
+
+// Aggregation pass of a partitioned plan: warp tiles of kAT partitioned
+// records, claimed in order, so that the GPU sweeps the buckets one after
+// another and the group sums of the buckets in work stay in L2 (a bucket's
+// groups are one range of the group arrays).  Records of
+// the same group in a batch of 32 combine first; hit-heavy plans go through
+// the block's shared aggregation table, as in the F probe.
+__global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
+  chain_begin();
+  __shared__ u64 s_akey[kAgg];
+  __shared__ i64 s_asum[kAgg];
+  __shared__ i64 s_sc[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  i64* sc = s_sc[warp];
+  for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
+  __syncthreads();
+  const u64 agg_min = (u64)gridDim.x * 2048;
+  const i64* pre = b.dyn + 10 * (b.nq + 1);
+  const i64 total = pre[b.nq];
+  WarpClaim wc;
+  while (true) {
+    const i64 t = wc.next(b.work, kPhFagg);
+    if (t >= total) break;
+    const int qi = find_q(pre, b.nq, t);
+    const PlanDev& q = b.q[qi];
+    const i64 h = (i64)q.part[1 << q.part_log2];  // matched hits (part_sizes)
+    const i64 i0 = (t - pre[qi]) * kAT, i1 = min(h, i0 + kAT);
+    const bool agg = (u64)h >= agg_min;
+    // Slots of the plan's group arrays: a record outside them (which the
+    // partition pass never writes) is reported, not added.
+    const u64 nslots = plan_slots(q.ctr);
+    const GroupStore g = group_store(q);
+    const bool exact = !fast_commit(q, (u64)q.ctr->hcount);
+    for (i64 i = i0; i < i1; i += 32) {
+      const i64 idx = i + lane;
+      const u32 sl = idx < i1 ? __ldcs(q.pslot + idx) : ~0u;
+      const i64 v = idx < i1 ? __ldcs(q.pval + idx) : 0;
+      const bool ok = sl != ~0u && (u64)sl < nslots;
+      if (sl != ~0u && !ok) q_latch(q.ctr, b.st, PQ_ERR_CAPACITY, (i64)sl);
+      commit_hits_g(b, sc, agg ? s_akey : nullptr, s_asum, ok, qi, sl, v, &g, exact);
+    }
+  }
+  agg_flush(b, s_akey, s_asum, sc);
+  finish(b.work, kPhFagg);
 }
 
 // ------------------------------------------------------------------- topk ----

@@ -237,6 +237,12 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   for (const Chunk& ch : chunks)
     if (ch.table == 2) f_hits = std::max(f_hits, ch.rows);
   char* ws = (char*)scr.get(L.end + al(r.n_d * 8) + al(r.n_m * 8) + al(f_hits * 4 + 4));
+  // Partitioned plan: bucket counters and the partitioned hits of one chunk.
+  const int plog = r.dev.part_log2;
+  char* pws = plog ? (char*)scr.get(al(((1 << plog) + 1) * 8) + al(f_hits * 8 + 8) +
+                                    al(f_hits * 4 + 4) + al(f_hits * 8 + 8))
+                   : nullptr;
+  if (plog && !pws) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: partitioned hits");
   // A slot holds a chunk's plain columns and, for packed columns, their
   // packed bytes behind them (never more than the plain bytes plus the block
   // tables and padding).
@@ -252,6 +258,16 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   d.dlist = (i64*)(ws + L.end);
   d.mlist = (i64*)(ws + L.end + al(r.n_d * 8));
   d.hlist = (u32*)(ws + L.end + al(r.n_d * 8) + al(r.n_m * 8));
+  if (plog) {
+    char* q = pws;
+    d.part = (u64*)q;
+    q += al(((1 << plog) + 1) * 8);
+    d.pval0 = (i64*)q;
+    q += al(f_hits * 8 + 8);
+    d.pslot = (u32*)q;
+    q += al(f_hits * 4 + 4);
+    d.pval = (i64*)q;
+  }
   QCtr* ctr = (QCtr*)(ws + L.ctr);
   d.ctr = ctr;
   d.out = (pq_result*)(ws + L.out);
@@ -370,11 +386,16 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     }
     return PQ_OK;
   };
-  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseFscan};
-  // The F table's phase is the scan and the probe of its hits.
+  // The F table's phase is the scan and the probe of its hits (for a
+  // partitioned plan: the scan counting buckets, the partition pass, the
+  // aggregation pass, then the probe kernel's epilogue), chunk by chunk.
   auto launch_table = [&](int t, const Batch& bt, bool v) -> pq_status {
-    pq_status e = launch_phase(ctx, phase_of[t], bt, v, s);
-    if (e == PQ_OK && t == 2) e = launch_phase(ctx, kPhaseF, bt, v, s);
+    if (t < 2) return launch_phase(ctx, t == 0 ? kPhaseD : kPhaseM, bt, v, s);
+    if (plog) PQ_CUDA(ctx, cudaMemsetAsync(d.part, 0, ((1 << plog) + 1) * 8, s));
+    pq_status e = launch_phase(ctx, kPhaseFscan, bt, v, s);
+    for (int ph : {kPhaseFpart, kPhaseFscatter, kPhaseFagg})
+      if (e == PQ_OK && plog) e = launch_phase(ctx, ph, bt, v, s);
+    if (e == PQ_OK) e = launch_phase(ctx, kPhaseF, bt, v, s);
     return e;
   };
   size_t c = 0;
@@ -584,18 +605,33 @@ pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_resul
   pq_result* out = (pq_result*)(ws + L.out);
   std::vector<PlanDev> base(n);
   std::vector<char*> dset_ph(n);
+  std::vector<std::pair<void*, size_t>> part_clears;  // bucket counters, per F launch
   for (int i = 0; i < n; ++i) {
     PlanDev& d = R[i].dev;
     d.build_dset = 1;
     const i64 hl = streamed[2] ? std::min(R[i].n_f, f_chunk) : R[i].n_f;
+    const int plog = d.part_log2;
+    const size_t pbytes =
+        plog ? al(((1 << plog) + 1) * 8) + al(hl * 8 + 8) + al(hl * 4 + 4) + al(hl * 8 + 8) : 0;
     char* p = (char*)scr.get(al(R[i].n_d * 8) + al(R[i].n_m * 8) + al(hl * 4 + 4) +
-                             dset_block_bytes(6));
+                             dset_block_bytes(6) + pbytes);
     if (!p) return fail(ctx, PQ_ERR_BUDGET, "streaming batch: lists of plan %d", i);
     d.dlist = (i64*)p;
     d.mlist = (i64*)(p + al(R[i].n_d * 8));
     d.hlist = (u32*)(p + al(R[i].n_d * 8) + al(R[i].n_m * 8));
     dset_ph[i] = p + al(R[i].n_d * 8) + al(R[i].n_m * 8) + al(hl * 4 + 4);
     dset_block_assign(dset_ph[i], 6, d);
+    if (plog) {
+      char* q = dset_ph[i] + dset_block_bytes(6);
+      d.part = (u64*)q;
+      q += al(((1 << plog) + 1) * 8);
+      d.pval0 = (i64*)q;
+      q += al(hl * 8 + 8);
+      d.pslot = (u32*)q;
+      q += al(hl * 4 + 4);
+      d.pval = (i64*)q;
+      part_clears.push_back({d.part, (size_t)((1 << plog) + 1) * 8});
+    }
     d.ctr = ctr + i;
     d.out = out + i;
     base[i] = d;
@@ -735,10 +771,14 @@ pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_resul
   if (st != PQ_OK) return st;
   PQ_CUDA(ctx, cudaMemsetAsync(ws + L.work, 0, L.zero_bytes(), s));
   const Batch b = make_batch(ctx, ws, n, L);
-  const int phase_of[3] = {kPhaseD, kPhaseM, kPhaseFscan};
   auto launch_table = [&](int t, bool v) -> pq_status {
-    pq_status e = launch_phase(ctx, phase_of[t], b, v, s);
-    if (e == PQ_OK && t == 2) e = launch_phase(ctx, kPhaseF, b, v, s);
+    if (t < 2) return launch_phase(ctx, t == 0 ? kPhaseD : kPhaseM, b, v, s);
+    const bool part = !part_clears.empty();
+    for (auto& c : part_clears) PQ_CUDA(ctx, cudaMemsetAsync(c.first, 0, c.second, s));
+    pq_status e = launch_phase(ctx, kPhaseFscan, b, v, s);
+    for (int ph : {kPhaseFpart, kPhaseFscatter, kPhaseFagg})
+      if (e == PQ_OK && part) e = launch_phase(ctx, ph, b, v, s);
+    if (e == PQ_OK) e = launch_phase(ctx, kPhaseF, b, v, s);
     return e;
   };
   std::vector<QCtr> hctr(n);

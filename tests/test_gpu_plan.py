@@ -534,6 +534,30 @@ def test_autotune_keeps_results(ctx, stream, small, small_tables):
     assert_same(run(ctx, stream, plan), oracle_plan(*small))
 
 
+@pytest.mark.parametrize("flags,log2P", [(0, 0), (pq.PQ_PLAN_PARTITIONED, 5)],
+                         ids=["plain", "partitioned"])
+def test_exact_commit_path(ctx, stream, small, flags, log2P):
+    """One F row with a price of 2^55 that the date filter drops: the bound
+    on the revenues (hits x max |price| x 228) no longer excludes an int64
+    overflow, so the probe commits with checked atomics; no group overflows
+    and the result equals the oracle's."""
+    D, M, F = small
+    F = dict(F)
+    F["price"] = F["price"].copy()
+    F["date2"] = F["date2"].copy()
+    F["price"][0], F["date2"][0] = 2**55, 0
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    for p in (dict(seg=1, mc=1200, fc=1200), dict(seg=0, mc=0, fc=0, d_op="all", m_op="all")):
+        kw = dict(seg=p["seg"], m_date_lt=p["mc"], f_date_gt=p["fc"], k=10,
+                  d_op=p.get("d_op", "=="), m_op=p.get("m_op", "<"))
+        got = run(ctx, stream, pq.make_plan(TD, TM, TF, flags=flags, log2P=log2P, **kw))
+        assert_same(got, oracle_plan(D, M, F, seg=p["seg"], mc=p["mc"], fc=p["fc"], k=10,
+                                     d_op=kw["d_op"], m_op=kw["m_op"]), str(p))
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
 @pytest.mark.parametrize("price", [2**56, 2**60], ids=["sum-overflows", "product-overflows"])
 def test_overflow_is_reported(ctx, stream, price):
     D = dict(key=np.array([1], np.int32), seg=np.array([1], np.int8))
