@@ -44,11 +44,32 @@ WORKLOAD_TEXT = {
 }
 QUERY_TEXT = ("D.seg == 1, M.date < 1200, F.date2 > 1200; join F-M-D; group by M.key "
               "SUM(price*(100-disc)) int64; top-10")
+SKEW_QUERY_TEXT = ("pass-all predicates; join F-M-D; group by M.key SUM(price*(100-disc)) "
+                   "int64; top-10")
 
 
 def table_bytes(n_d, n_m, n_f):
     """Algorithmic bytes of a plan: every referenced column read once."""
     return 5 * n_d + 16 * n_m + 21 * n_f
+
+
+def moved_bytes(n_d, n_m, n_f, hits):
+    """Bytes the plan's kernels load from the tables (an upper bound): the D
+    and M columns in full, date2 and mkey of every F row, price and disc
+    only for the F rows that joined."""
+    return 5 * n_d + 16 * n_m + 12 * n_f + 9 * hits
+
+
+def bench_config(workload: str, n_gpus: int) -> dict:
+    """The `config` both arms print (identical, so the arms are comparable)."""
+    import datagen
+    w = datagen.WORKLOADS[workload]
+    nbytes = table_bytes(w["n_d"], w["n_m"], w["n_f"])
+    return {"workload": WORKLOAD_TEXT[workload],
+            "query": SKEW_QUERY_TEXT if workload == "skew" else QUERY_TEXT,
+            "l2": f"inputs ({nbytes / 1e9:.2f} GB) larger than L2 (129 MB); no flush between "
+                  "steps",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
 
 
 def query(name):
@@ -190,17 +211,25 @@ def job_rate(units_per_rank: int, steps: int, t_max_s: float, world: int) -> flo
 
 # -------------------------------------------------------------- CPU side ----
 def cpu_oracle_rate(D, M, F, q, budget_s=20.0, max_runs=3):
-    """Oracle (single-threaded) on the workload: F rows per second."""
+    """Oracle (single-threaded) on the workload: F rows per second, runs,
+    seconds, and the result of the last run (for the parity check)."""
     import oracle
     oracle.build()
     runs, t_total = 0, 0.0
     n_f = len(F["mkey"])
+    want = None
     while runs < max_runs and t_total < budget_s:
         t0 = time.perf_counter()
-        oracle.run_plan(D, M, F, **q)
+        want = oracle.run_plan(D, M, F, **q)
         t_total += time.perf_counter() - t0
         runs += 1
-    return n_f * runs / t_total, runs, t_total
+    return n_f * runs / t_total, runs, t_total, want
+
+
+def same_as_oracle(got: dict, want: dict) -> bool:
+    return (got["status"] == want["status"] and got["ngroups"] == want["ngroups"]
+            and got["keys"] == [int(x) for x in want["keys"]]
+            and got["sums"] == [int(x) for x in want["sums"]])
 
 
 def run_reference(args):
@@ -212,27 +241,43 @@ def run_reference(args):
     oracle.build()
     D, M, F = datagen.workload(args.workload)
     q = query(args.workload)
-    # Each step runs the oracle on a bounded F prefix (D and M whole) so that
-    # warm-up plus timed steps end within a few minutes: at most
-    # --ref-f-rows per step and about 200M F rows over the whole run.
-    f_sample = min(len(F["mkey"]), args.ref_f_rows,
-                   max(100_000, 200_000_000 // max(1, args.steps + args.warmup)))
-    Fs = {k: v[:f_sample] for k, v in F.items()}
-    for _ in range(args.warmup):
-        oracle.run_plan(D, M, Fs, **q)
+    # Each step runs the oracle on the whole workload when the warm-up and
+    # timed steps fit in --ref-budget-s; otherwise on a self-consistent slice
+    # of it (the first rows of M and exactly their F rows, F being grouped by
+    # M key, with D whole), sized so that they do.
+    t0 = time.perf_counter()
+    oracle.run_plan(D, M, F, **q)
+    t_full = time.perf_counter() - t0
+    n_m, n_f = len(M["key"]), len(F["mkey"])
+    frac = min(1.0, args.ref_budget_s / max(1e-9, t_full * (args.steps + args.warmup)))
+    if frac < 1.0 and args.workload != "skew":
+        w = datagen.WORKLOADS[args.workload]
+        starts = datagen.f_starts(w["seed"], n_m, n_f)
+        m_rows = max(16, int(n_m * frac))
+        f_rows = int(starts[m_rows]) if m_rows < n_m else n_f
+        Ms = {k: v[:m_rows] for k, v in M.items()}
+        Fs = {k: v[:f_rows] for k, v in F.items()}
+        sample = (f"M rows [0, {m_rows}) and their F rows [0, {f_rows}) with D whole, per step "
+                  f"(the whole workload takes {t_full:.1f} s per run)")
+    else:
+        Ms, Fs, f_rows = M, F, n_f
+        sample = f"the whole workload ({n_f} F rows) per step"
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.run_plan(D, Ms, Fs, **q)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run_plan(D, M, Fs, **q)
+        oracle.run_plan(D, Ms, Fs, **q)
     t = time.perf_counter() - t0
-    value = f_sample * args.steps / t
+    value = f_rows * args.steps / t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "query": QUERY_TEXT},
+        "config": bench_config(args.workload, args.gpus),
         "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"F rows [0, {f_sample}) with D and M whole, per step"},
+                         "sample": sample, "f_rows_per_step": int(f_rows),
+                         "whole_workload": bool(f_rows == n_f)},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -241,6 +286,195 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU side ----
+def _events_ms(torch, s, fn, reps):
+    """Mean milliseconds of fn() over reps runs, CUDA events on stream s."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        a.record(s)
+        for _ in range(reps):
+            fn()
+        b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def skew_sub(pq, torch, s, hbm, reps=20):
+    """The skewed workload (F 200M rows, Zipf(1.0) foreign keys into M 40M,
+    pass-all predicates, ~20M groups) timed at full size, plain and
+    partitioned (2^8 buckets), with parity against the oracle checked at
+    1/20 scale through the same kernels (the oracle needs minutes at full
+    size)."""
+    import datagen
+    import oracle
+    q = query("skew")
+    w = datagen.WORKLOADS["skew"]
+    out = {"workload": WORKLOAD_TEXT["skew"], "query": SKEW_QUERY_TEXT}
+
+    def tables(ctx, D, M, F):
+        dev = {k: {c: torch.from_numpy(v).cuda() for c, v in t.items()}
+               for k, t in (("D", D), ("M", M), ("F", F))}
+        with torch.cuda.stream(s):
+            TD = pq.pq_load_columns(ctx, [dev["D"]["key"], dev["D"]["seg"]], stream=s)
+            TM = pq.pq_load_columns(ctx, [dev["M"][c] for c in ("key", "dref", "date")], stream=s)
+            TF = pq.pq_load_columns(ctx, [dev["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                                    stream=s)
+        return TD, TM, TF, dev
+
+    # parity at 1/20 scale
+    D, M, F = datagen.make(w["n_d"] // 20, w["n_m"] // 20, w["n_f"] // 20, seed=w["seed"],
+                           fk="zipf", zipf_s=w["zipf_s"])
+    t0 = time.perf_counter()
+    want = oracle.run_plan(D, M, F, **q)
+    t_oracle = time.perf_counter() - t0
+    ctx = pq.Context(arena_bytes=4 << 30)
+    TD, TM, TF, keep = tables(ctx, D, M, F)
+    res = pq.pinned_results(1)
+    ok = True
+    for flags, lp in ((0, 0), (pq.PQ_PLAN_PARTITIONED, 8)):
+        with torch.cuda.stream(s):
+            pq.pq_run_plan(ctx, pq.make_plan(TD, TM, TF, flags=flags, log2P=lp, **q), res[0],
+                           stream=s)
+            ctx.sync(s)
+        ok = ok and same_as_oracle(res[0].as_dict(), want)
+    ctx.close()
+    del keep
+    out["parity"] = {"oracle": ok, "scale": "1/20 (F 10M rows)", "groups": want["ngroups"],
+                     "oracle_s": round(t_oracle, 1)}
+    # full size
+    D, M, F = datagen.workload("skew")
+    n_d, n_m, n_f = w["n_d"], w["n_m"], w["n_f"]
+    ctx = pq.Context(arena_bytes=16 << 30)
+    TD, TM, TF, keep = tables(ctx, D, M, F)
+    nbytes = table_bytes(n_d, n_m, n_f)
+    legs, first = {}, None
+    for name, flags, lp in (("plain", 0, 0), ("partitioned_2^8", pq.PQ_PLAN_PARTITIONED, 8)):
+        plan = pq.make_plan(TD, TM, TF, flags=flags, log2P=lp, **q)
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                pq.pq_run_plan(ctx, plan, res[0], stream=s)
+            ctx.sync(s)
+        r = res[0].as_dict()
+        first = first or r
+        ms = _events_ms(torch, s, lambda: pq.pq_run_plan(ctx, plan, res[0], stream=s), reps)
+        ctx.sync(s)
+        legs[name] = {"ms_per_plan": round(ms, 4), "rows_per_s": n_f / (ms / 1e3),
+                      "gb_per_s": round(nbytes / (ms / 1e3) / 1e9, 1),
+                      "frac_of_hbm": round(nbytes / (ms / 1e3) / 1e9 / hbm, 4),
+                      "same_result_as_plain": r == first}
+    out.update({"legs": legs, "groups": first["ngroups"], "algorithmic_bytes": nbytes,
+                "timing": f"CUDA events over {reps} plans after 3 warm-ups (graph replay)"})
+    ctx.close()
+    return out
+
+
+def serve_sub(pq, torch, ctx, s, tables, data, n_queries=500, rate=500.0, sample=8):
+    """Serving on the resident x100 tables: n_queries queries of the serving
+    workload (lognormal F slices, randomised predicates, Poisson arrivals at
+    `rate`), plain one-at-a-time vs batched vs served, closed loop, and the
+    open-loop p50/p99 latency; results identical across the three paths and
+    equal to the oracle's on a sample of the queries."""
+    import datagen
+    import oracle
+    TD, TM, TF = tables
+    D, M, F = data
+    w = datagen.WORKLOADS["x100"]
+    starts = datagen.f_starts(w["seed"], w["n_m"], w["n_f"])
+    qs = datagen.query_stream(5, n_queries, w["n_m"], starts, rate_qps=rate)
+
+    def mk(q, flags):
+        return pq.make_plan(TD, TM, TF, seg=q["seg"], m_date_lt=q["c"], f_date_gt=q["c"], k=10,
+                            rows=dict(m=(q["m_row0"], q["m_rows"]), f=(q["f_row0"], q["f_rows"])),
+                            flags=flags)
+
+    plain_plans = [mk(q, pq.PQ_PLAN_NO_GRAPH) for q in qs]
+    serve_plans = [mk(q, 0) for q in qs]
+    n = len(qs)
+    rp, rb = pq.pinned_results(n), pq.pinned_results(n)
+
+    def plain():
+        with torch.cuda.stream(s):
+            for i, p in enumerate(plain_plans):
+                pq.pq_run_plan(ctx, p, rp[i], stream=s)
+                ctx.sync(s)
+
+    def batched():
+        with torch.cuda.stream(s):
+            for a in range(0, n, 512):
+                sub = serve_plans[a:a + 512]
+                arr = (pq.pq_plan * len(sub))(*sub)
+                dst = pq.ctypes.cast(pq.ctypes.addressof(rb) + a * pq.ctypes.sizeof(pq.pq_result),
+                                     pq.ctypes.POINTER(pq.pq_result))
+                ctx.check(pq.library().pq_run_batch(ctx.h, arr, len(sub), dst, pq._stream(s)))
+            ctx.sync(s)
+
+    def served():
+        tickets = [pq.pq_submit(ctx, p) for p in serve_plans]
+        res = []
+        for t in tickets:
+            st, r, lat = pq.pq_poll(ctx, t, timeout_ms=60_000)
+            assert st == pq.PQ_OK, st
+            res.append(r.as_dict())
+        return res
+
+    plain(); batched(); served()      # warm-up: code, caches, resident D-sets
+    t0 = time.perf_counter(); plain(); t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter(); batched(); t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter(); sres = served(); t_serve = time.perf_counter() - t0
+    pres = [rp[i].as_dict() for i in range(n)]
+    bres = [rb[i].as_dict() for i in range(n)]
+    identical = pres == bres == sres
+    pick = np.linspace(0, n - 1, sample).astype(int)
+    cut = lambda t, r0, nn: {c: v[r0:r0 + nn] for c, v in t.items()}
+    oracle_ok = all(same_as_oracle(pres[i], oracle.run_plan(
+        D, cut(M, qs[i]["m_row0"], qs[i]["m_rows"]), cut(F, qs[i]["f_row0"], qs[i]["f_rows"]),
+        seg=qs[i]["seg"], m_date_lt=qs[i]["c"], f_date_gt=qs[i]["c"], k=10)) for i in pick)
+    # open loop: arrivals on the Poisson schedule
+    arrive = np.array([q["arrive_s"] for q in qs])
+    lat_plain = []
+    t_start = time.perf_counter()
+    with torch.cuda.stream(s):
+        for i, p in enumerate(plain_plans):
+            now = time.perf_counter() - t_start
+            if now < arrive[i]:
+                time.sleep(arrive[i] - now)
+            pq.pq_run_plan(ctx, p, rp[i], stream=s)
+            ctx.sync(s)
+            lat_plain.append(time.perf_counter() - t_start - arrive[i])
+    tickets = [None] * n
+
+    def feeder():
+        t_s = time.perf_counter()
+        for i, p in enumerate(serve_plans):
+            now = time.perf_counter() - t_s
+            if now < arrive[i]:
+                time.sleep(arrive[i] - now)
+            tickets[i] = pq.pq_submit(ctx, p)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    lat_serve = []
+    for i in range(n):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        st, r, lat = pq.pq_poll(ctx, tickets[i], timeout_ms=60_000)
+        identical = identical and st == pq.PQ_OK and r.as_dict() == pres[i]
+        lat_serve.append(lat / 1e6)
+    th.join()
+    pct = lambda a, p: round(1e3 * float(np.percentile(a, p)), 3)
+    return {"workload": f"{n} queries on slices of x100 (F rows lognormal, median 500k, "
+                        f"sigma 1.5), randomised seg and date constants, Poisson {rate} q/s",
+            "closed_loop_qps": {"plain": n / t_plain, "batched": n / t_batch,
+                                "served": n / t_serve},
+            "speedup_vs_plain": {"batched": round(t_plain / t_batch, 2),
+                                 "served": round(t_plain / t_serve, 2)},
+            "open_loop_latency_ms": {"plain": {"p50": pct(lat_plain, 50),
+                                               "p99": pct(lat_plain, 99)},
+                                     "served": {"p50": pct(lat_serve, 50),
+                                                "p99": pct(lat_serve, 99)}},
+            "parity": {"identical_across_paths": bool(identical), "oracle": bool(oracle_ok),
+                       "oracle_sample": f"{sample} of the {n} queries"}}
+
+
 def run_ours(args):
     import torch
 
@@ -334,6 +568,7 @@ def run_ours(args):
 
     value = job_rate(n_f, args.steps, t_ms / 1e3, world)
     plan_bytes = table_bytes(n_d, n_m, n_f)
+    moved = moved_bytes(n_d, n_m, n_f, int(res[0].hits))
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     # Dominant kernel: the F scan.  Algorithmic bytes per launch: date2 and
@@ -402,11 +637,23 @@ def run_ours(args):
                   for tn, cols in host.items()}
         t_pack = time.perf_counter() - t0
         packed_bytes = sum(p.nbytes for cols in packed.values() for p in cols.values())
+
+        def with_link(leg):
+            leg["_link"] = True  # filled in after the legs (measure_h2d allocates 2 GiB)
+            return leg
+
+        def fill_link(leg, link):
+            del leg["_link"]
+            gbs = leg["h2d_bytes_per_step"] / (leg["ms_per_step"] / 1e3) / 1e9
+            leg["link"] = {"gb_per_s": round(gbs, 1), "peak_gb_per_s": round(link, 1),
+                           "frac": round(gbs / link, 4),
+                           "peak": "measured here: pinned cudaMemcpyAsync host to device, "
+                                   "1 GiB, best of 5"}
         # 256 MB chunks (of plain rows) on three copy streams: measured 2.78 ms
         # per plan against 3.03 ms with the default 128 MB on two.
         ctx2 = pq.Context(arena_bytes=args.arena_gb << 30, chunk_bytes=256 << 20, ring_slots=6,
                           copy_streams=3)
-        e2e = host_plan_rate(ctx2, pq.PQ_STREAMING, packed)
+        e2e = with_link(host_plan_rate(ctx2, pq.PQ_STREAMING, packed))
         e2e["path"] = ("pq_run_plan on PQ_STREAMING tables of packed columns in pinned host "
                        "memory: chunked copies of the packed bytes, decoded on the device")
         e2e["packed"] = {"bytes": packed_bytes, "plain_bytes": plan_bytes,
@@ -415,35 +662,48 @@ def run_ours(args):
                          "ring_slots": 6, "copy_streams": 3}
         ctx2.close()
         ctx3 = pq.Context(arena_bytes=args.arena_gb << 30)
-        e2e["mapped"] = host_plan_rate(ctx3, pq.PQ_MAPPED)
+        e2e["mapped"] = with_link(host_plan_rate(ctx3, pq.PQ_MAPPED))
         e2e["mapped"]["path"] = ("pq_run_plan on PQ_MAPPED tables in pinned host memory: the "
                                  "plan kernels read the plain columns in place")
         ctx3.close()
         ctx4 = pq.Context(arena_bytes=args.arena_gb << 30)
-        e2e["streaming"] = host_plan_rate(ctx4, pq.PQ_STREAMING)
+        e2e["streaming"] = with_link(host_plan_rate(ctx4, pq.PQ_STREAMING))
         e2e["streaming"]["path"] = ("pq_run_plan on PQ_STREAMING tables of plain columns in "
                                     "pinned host memory (chunked host-to-device copies)")
         ctx4.close()
         del packed
+        link = measure_h2d()  # pinned host-to-device copy bandwidth, GB/s
+        for leg in (e2e, e2e["mapped"], e2e["streaming"]):
+            fill_link(leg, link)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        rate, runs, secs = cpu_oracle_rate(D, M, F, q)
-        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
-               "sample": f"{runs} full run(s) of the plan on the same workload "
-                         f"({secs:.1f} s, single thread)"}
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        rate, runs, secs, want = cpu_oracle_rate(D, M, F, q,
+                                                 max_runs=3 if world == 1 else 1)
+        parity = {"oracle": same_as_oracle(check, want),
+                  "what": "the timed plan's result (top-k keys and sums, group count, status) "
+                          "against the CPU oracle's on the same full workload"}
+        if world == 1:
+            cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{runs} full run(s) of the plan on the same workload "
+                             f"({secs:.1f} s, single thread)"}
+    subs = {}
+    if rank == 0 and world == 1 and args.workload == "x100" and not args.no_subs:
+        subs["serve"] = serve_sub(pq, torch, ctx, s, (TD, TM, TF), (D, M, F))
+        subs["skew"] = skew_sub(pq, torch, s, hbm)
 
     line = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "query": QUERY_TEXT,
-                   "l2": f"inputs ({plan_bytes / 1e9:.2f} GB) larger than L2 (129 MB); "
-                         "no flush between steps",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": bench_config(args.workload, world),
+        "parity": parity,
         "gb_per_s": round(world * plan_bytes * args.steps / (t_ms / 1e3) / 1e9, 1),
         "plan_frac_of_hbm": round(plan_bytes * args.steps / (t_ms / 1e3) / 1e9 / hbm, 4),
+        "plan_frac_moved_bytes": round(moved * args.steps / (t_ms / 1e3) / 1e9 / hbm, 4),
+        "moved_bytes_per_plan": moved,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "stage_ms": per_stage,
@@ -453,6 +713,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "result": {"ngroups": check["ngroups"], "top_key": check["keys"][:1]},
+        "sub_results": subs or None,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -1066,13 +1327,15 @@ def main(argv=None):
     ap.add_argument("--workload", default="x100", choices=["small", "x100", "x2000", "skew"])
     ap.add_argument("--arena-gb", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--ref-f-rows", type=int, default=20_000_000)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--queries", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=500.0)
     ap.add_argument("--host-queries", type=int, default=256)
     ap.add_argument("--having", type=int, default=4_000_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-subs", action="store_true",
+                    help="leave out the skew and serving sub-results of the default line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -420,19 +420,27 @@ double pq_last_latency_us(pq_ctx* ctx);
 /* ---- tuning ------------------------------------------------------------------ */
 
 typedef struct pq_tuning {
-  int32_t block_threads;
-  int32_t blocks_per_sm;
-  int32_t log2P;
-  int32_t partitioned;   /* 1 if the partitioned plan was fastest */
-  float load_factor;
-  float best_ms;         /* median time of the chosen setting     */
-  int32_t tried;         /* settings measured                     */
+  int32_t block_threads;  /* threads per block of the plan kernels (always
+                             256: they are written for 8 warps)           */
+  int32_t blocks_per_sm;  /* resident blocks per SM of the persistent grids */
+  int32_t log2P;          /* fan-out exponent of the partitioned plan      */
+  int32_t partitioned;    /* 1 if the partitioned plan was fastest         */
+  float load_factor;      /* hash-table load factor                        */
+  float best_ms;          /* median time of the chosen setting             */
+  int32_t tried;          /* settings measured                             */
   int32_t reserved[5];
 } pq_tuning;
 
-/* Time `sample` (resident tables) under a grid of settings (block size,
- * resident blocks per SM, load factor, partitioned or not and its fan-out),
- * keep the fastest in *out and make it the context's default. */
+/* Time `sample` (a join-first plan over resident tables; the tuning of
+ * Sec. 3.1 applied to this engine's launch and partition parameters) by
+ * coordinate descent: resident blocks per SM of the persistent kernels
+ * (1, 2, 3, 4, 6, 8), then the hash-table load factor (0.25, 0.4, 0.5, 0.7),
+ * then the partitioned plan with 2^4, 2^6, 2^8 and 2^10 buckets -- 14
+ * settings, each the median of 5 timed runs.  The fastest goes to *out; its
+ * blocks per SM and load factor become the context's defaults, and when
+ * the partitioned plan won, its fan-out becomes the default log2P of plans
+ * that set PQ_PLAN_PARTITIONED (the caller sets that flag: results are the
+ * same either way).  The sample's result is not returned. */
 pq_status pq_autotune(pq_ctx* ctx, const pq_plan* sample, pq_tuning* out);
 
 #ifdef __cplusplus

@@ -413,7 +413,7 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseFscatter:
       e = launch_chained(k_plan_fscatter, plan_grid(ctx, 19, 1), 256, s, b);
       break;
-    case kPhaseFagg: e = launch_chained(k_plan_fagg, plan_grid(ctx, 20), 256, s, b); break;
+    case kPhaseFagg: e = launch_chained(k_plan_fagg, plan_grid(ctx, 20, 1), 256, s, b); break;
     case kPhaseF: e = launch_chained(k_plan_fprobe, plan_grid(ctx, 13), 256, s, b); break;
     case kPhaseTopk: e = launch_chained(k_plan_topk, plan_grid(ctx, 7, 1), kTKW * 32, s, b); break;
     case kPhaseTopk2:
@@ -781,7 +781,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       clears.push_back({(void*)d.part, (size_t)((1 << d.part_log2) + 1) * 8});
       tmax[kPhaseFpart] += (r.n_f + kPT - 1) / kPT;
       tmax[kPhaseFscatter] += (r.n_f + kPT - 1) / kPT;
-      tmax[kPhaseFagg] += (r.n_f + kAT - 1) / kAT;
+      tmax[kPhaseFagg] += (r.n_f + 8 * kAT - 1) / (8 * kAT);
     }
     list_d = list_d || (r.builds && !d.d_static);
     list_m = list_m || !d.m_static;

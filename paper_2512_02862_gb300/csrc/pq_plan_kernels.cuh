@@ -1610,9 +1610,10 @@ __device__ __forceinline__ i64 topk_words(const PlanDev& q) {
 
 // End of an F-probe kernel: flush the block's aggregated sums to the plans'
 // tables; the block that finishes last sizes the top-k phase.
-// Flush a block's shared aggregation table into the plans' groups.
-__device__ __forceinline__ void agg_flush(const Batch& b, const u64* s_akey, const i64* s_asum,
-                                          i64* sc) {
+// Flush a block's shared aggregation table into the plans' groups; with
+// `reset` the table is emptied for further use.
+__device__ __forceinline__ void agg_flush(const Batch& b, u64* s_akey, i64* s_asum, i64* sc,
+                                          bool reset = false) {
   __syncthreads();
   int used = 0;
   for (int i = threadIdx.x; i < kAgg; i += blockDim.x) used |= s_akey[i] != 0;
@@ -1621,11 +1622,13 @@ __device__ __forceinline__ void agg_flush(const Batch& b, const u64* s_akey, con
     const u64 ak = i < kAgg ? s_akey[i] : 0;
     commit_hits(b, sc, nullptr, nullptr, ak != 0, ak ? (int)((ak - 1) >> 40) : 0,
                 (ak - 1) & ((1ULL << 40) - 1), ak ? s_asum[i] : 0);
+    if (reset && ak) s_akey[i] = 0, s_asum[i] = 0;
   }
+  __syncthreads();
 }
 
-__device__ __forceinline__ void fprobe_epilogue(const Batch& b, const u64* s_akey,
-                                                const i64* s_asum, i64* sc) {
+__device__ __forceinline__ void fprobe_epilogue(const Batch& b, u64* s_akey, i64* s_asum,
+                                                i64* sc) {
   agg_flush(b, s_akey, s_asum, sc);
   if (finish(b.work, kPhFprobe)) {
     block_prefix(b.dyn + 4 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
@@ -1673,7 +1676,8 @@ __device__ __forceinline__ void part_sizes(const Batch& b) {
   });
   block_prefix(b.dyn + 10 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
     const PlanDev& q = b.q[qi];
-    return q.part_log2 ? (i64)(__ldcg(q.part + (1 << q.part_log2)) + kAT - 1) / kAT : 0;
+    return q.part_log2 ? (i64)(__ldcg(q.part + (1 << q.part_log2)) + 8 * kAT - 1) / (8 * kAT)
+                       : 0;
   });
 }
 
@@ -2135,17 +2139,21 @@ __global__ void __launch_bounds__(256) k_plan_fscatter(Batch b) {
   finish(b.work, kPhFscatter);
 }
 
-// Aggregation pass of a partitioned plan: warp tiles of kAT partitioned
-// records, claimed in order, so that the GPU sweeps the buckets one after
-// another and the group sums of the buckets in work stay in L2 (a bucket's
-// groups are one range of the group arrays).  Records of
-// the same group in a batch of 32 combine first; hit-heavy plans go through
-// the block's shared aggregation table, as in the F probe.
+// Aggregation pass of a partitioned plan: block tiles of 8 * kAT
+// partitioned records (each warp takes kAT of them), claimed in order, so
+// that the GPU sweeps the buckets one after another and the group sums of
+// the buckets in work stay in L2 (a bucket's groups are one range of the
+// group arrays).  Records of the same group in a batch of 32 combine first;
+// for hit-heavy plans the block's shared aggregation table takes the
+// repeated groups of the tile (skewed data: the hot keys of the bucket in
+// work), and is flushed and emptied at the end of every tile, so that each
+// region of the sweep has the table to itself.
 __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
   chain_begin();
   __shared__ u64 s_akey[kAgg];
   __shared__ i64 s_asum[kAgg];
   __shared__ i64 s_sc[8][32];
+  __shared__ i64 s_t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   i64* sc = s_sc[warp];
   for (int i = threadIdx.x; i < kAgg; i += blockDim.x) s_akey[i] = 0, s_asum[i] = 0;
@@ -2153,14 +2161,14 @@ __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
   const u64 agg_min = (u64)gridDim.x * 2048;
   const i64* pre = b.dyn + 10 * (b.nq + 1);
   const i64 total = pre[b.nq];
-  WarpClaim wc;
+  BlockClaim bc;
   while (true) {
-    const i64 t = wc.next(b.work, kPhFagg);
+    const i64 t = bc.next(b.work, kPhFagg, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
     const i64 h = (i64)q.part[1 << q.part_log2];  // matched hits (part_sizes)
-    const i64 i0 = (t - pre[qi]) * kAT, i1 = min(h, i0 + kAT);
+    const i64 i0 = (t - pre[qi]) * (8 * kAT) + warp * kAT, i1 = min(h, i0 + kAT);
     const bool agg = (u64)h >= agg_min;
     // Slots of the plan's group arrays: a record outside them (which the
     // partition pass never writes) is reported, not added.
@@ -2175,6 +2183,7 @@ __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
       if (sl != ~0u && !ok) q_latch(q.ctr, b.st, PQ_ERR_CAPACITY, (i64)sl);
       commit_hits_g(b, sc, agg ? s_akey : nullptr, s_asum, ok, qi, sl, v, &g, exact);
     }
+    if (agg) agg_flush(b, s_akey, s_asum, sc, true);  // block-uniform: one plan per tile
   }
   agg_flush(b, s_akey, s_asum, sc);
   finish(b.work, kPhFagg);

@@ -322,6 +322,8 @@ double pq_last_latency_us(pq_ctx* ctx) { return ctx ? ctx->last_latency_us : 0.0
 
 pq_status pq_autotune(pq_ctx* ctx, const pq_plan* sample, pq_tuning* out) {
   if (!ctx || !sample || !out) return PQ_ERR_INVALID_ARG;
+  if (sample->flags & PQ_PLAN_AGG_FIRST)
+    return fail(ctx, PQ_ERR_INVALID_ARG, "autotune: the join-first plan only");
   ResolvedPlan r;
   pq_status st = resolve_plan(ctx, *sample, r, true);
   if (st != PQ_OK) return st;
@@ -335,53 +337,85 @@ pq_status pq_autotune(pq_ctx* ctx, const pq_plan* sample, pq_tuning* out) {
     return fail(ctx, PQ_ERR_CUDA, "autotune setup");
   }
   const int saved_bps = ctx->tune_bps;
-  const float saved_lf = ctx->opt.load_factor;
   memset(out, 0, sizeof *out);
   out->best_ms = 1e30f;
-  const int bps_set[] = {1, 2, 3, 4, 6};
-  const float lf_set[] = {0.25f, 0.4f, 0.5f, 0.7f};
-  pq_plan p = *sample;
-  p.flags |= PQ_PLAN_NO_GRAPH;
-  for (int bps : bps_set) {
-    for (float lf : lf_set) {
-      ctx->tune_bps = bps;
-      p.load_factor = lf;
-      float t[5];
-      int ok = 0;
-      for (int rep = 0; rep < 6 && st == PQ_OK; ++rep) {
-        cudaEventRecord(a, s);
-        st = run_batch_internal(ctx, &p, 1, res, s, false);
-        cudaEventRecord(b, s);
-        if (cudaEventSynchronize(b) != cudaSuccess) st = PQ_ERR_CUDA;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0) t[ok++] = ms;  // first run warms caches and code
-      }
-      if (st != PQ_OK) break;
-      std::sort(t, t + ok);
-      out->tried++;
-      if (t[ok / 2] < out->best_ms) {
-        out->best_ms = t[ok / 2];
-        out->blocks_per_sm = bps;
-        out->load_factor = lf;
-      }
+  // Median time of plan p under blocks-per-SM `bps` (first run untimed).
+  auto measure = [&](const pq_plan& p, int bps, float* ms_out) -> pq_status {
+    ctx->tune_bps = bps;
+    float t[5];
+    int ok = 0;
+    for (int rep = 0; rep < 6; ++rep) {
+      cudaEventRecord(a, s);
+      pq_status e = run_batch_internal(ctx, &p, 1, res, s, false);
+      cudaEventRecord(b, s);
+      if (e != PQ_OK) return e;
+      if (cudaEventSynchronize(b) != cudaSuccess) return PQ_ERR_CUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0) t[ok++] = ms;  // the first run warms caches and code
     }
+    std::sort(t, t + ok);
+    *ms_out = t[ok / 2];
+    return PQ_OK;
+  };
+  pq_plan p = *sample;
+  p.flags = (p.flags | PQ_PLAN_NO_GRAPH) & ~PQ_PLAN_PARTITIONED;
+  p.log2P = 0;
+  p.load_factor = sample->load_factor > 0 ? sample->load_factor : ctx->opt.load_factor;
+  int best_bps = std::max(1, saved_bps), best_lp = 0;
+  float best_lf = p.load_factor, best = 1e30f;
+  auto consider = [&](float ms, int bps, float lf, int lp) {
+    out->tried++;
+    if (ms < best) best = ms, best_bps = bps, best_lf = lf, best_lp = lp;
+  };
+  // Coordinate descent: resident blocks per SM of the persistent kernels,
+  // then the hash-table load factor, then the partition fan-out (2^0 = not
+  // partitioned), each swept with the best settings found so far.
+  const int bps_set[] = {1, 2, 3, 4, 6, 8};
+  const float lf_set[] = {0.25f, 0.4f, 0.5f, 0.7f};
+  const int lp_set[] = {4, 6, 8, 10};
+  for (int bps : bps_set) {
+    float ms;
+    if ((st = measure(p, bps, &ms)) != PQ_OK) break;
+    consider(ms, bps, p.load_factor, 0);
+  }
+  for (float lf : lf_set) {
+    if (st != PQ_OK) break;
+    pq_plan q = p;
+    q.load_factor = lf;
+    float ms;
+    if ((st = measure(q, best_bps, &ms)) != PQ_OK) break;
+    consider(ms, best_bps, lf, 0);
+  }
+  for (int lp : lp_set) {
+    if (st != PQ_OK) break;
+    pq_plan q = p;
+    q.load_factor = best_lf;
+    q.flags |= PQ_PLAN_PARTITIONED;
+    q.log2P = lp;
+    float ms;
+    if ((st = measure(q, best_bps, &ms)) != PQ_OK) break;
+    consider(ms, best_bps, best_lf, lp);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFreeHost(res);
+  cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
   if (st != PQ_OK) {
     ctx->tune_bps = saved_bps;
-    ctx->opt.load_factor = saved_lf;
     return st;
   }
-  out->block_threads = 256;
-  out->log2P = ctx->opt.log2P;
-  out->partitioned = 0;
-  ctx->tune_bps = out->blocks_per_sm;
-  ctx->opt.blocks_per_sm = out->blocks_per_sm;
-  ctx->opt.load_factor = out->load_factor;
+  out->block_threads = 256;  // fixed: the plan kernels are written for 8 warps
+  out->blocks_per_sm = best_bps;
+  out->load_factor = best_lf;
+  out->partitioned = best_lp > 0 ? 1 : 0;
+  out->log2P = best_lp > 0 ? best_lp : ctx->opt.log2P;
+  out->best_ms = best;
+  ctx->tune_bps = best_bps;
+  ctx->opt.blocks_per_sm = best_bps;
+  ctx->opt.load_factor = best_lf;
+  if (best_lp > 0) ctx->opt.log2P = best_lp;
   return PQ_OK;
 }
 

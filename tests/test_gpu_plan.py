@@ -527,11 +527,19 @@ def test_close_with_requests_in_flight(stream, small):
 
 
 def test_autotune_keeps_results(ctx, stream, small, small_tables):
+    """The tuner measures its 14 settings (blocks per SM, load factor,
+    partition fan-out), reports a choice inside the grid, and plans run with
+    the tuned defaults, partitioned or not, give the oracle's result."""
     TD, TM, TF, _ = small_tables
     plan = pq.make_plan(TD, TM, TF)
     t = pq.pq_autotune(ctx, plan)
-    assert t["tried"] >= 4 and t["best_ms"] > 0
-    assert_same(run(ctx, stream, plan), oracle_plan(*small))
+    assert t["tried"] == 14 and t["best_ms"] > 0 and t["block_threads"] == 256
+    assert t["blocks_per_sm"] in (1, 2, 3, 4, 6, 8)
+    assert t["load_factor"] in (0.25, pytest.approx(0.4), 0.5, pytest.approx(0.7))
+    assert t["partitioned"] in (0, 1) and t["log2P"] in range(1, 11)
+    want = oracle_plan(*small)
+    assert_same(run(ctx, stream, plan), want)
+    assert_same(run(ctx, stream, pq.make_plan(TD, TM, TF, flags=pq.PQ_PLAN_PARTITIONED)), want)
 
 
 @pytest.mark.parametrize("flags,log2P", [(0, 0), (pq.PQ_PLAN_PARTITIONED, 5)],
