@@ -205,6 +205,33 @@ __device__ __forceinline__ void chain_begin() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Block-wide exclusive sum of one value per thread (every thread calls; the
+// caller synchronises before calling it again).
+__device__ __forceinline__ u32 block_exclusive_sum(u32 v) {
+  __shared__ u32 s_w[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u32 x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 c = lane < nw ? s_w[lane] : 0u;
+    u32 y = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 z = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < nw) s_w[lane] = y - c;
+  }
+  __syncthreads();
+  return s_w[warp] + x - v;
+}
+
 __device__ __forceinline__ u32 lanemask_lt() {
   u32 m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -238,6 +265,54 @@ struct Spin {
     return true;
   }
 };
+
+// ---- 1D bulk copies (TMA) into shared memory, completing on an mbarrier ----
+__device__ __forceinline__ u32 smem_u32(const void* p) {
+  return (u32)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+// Makes initialised mbarriers visible to the async proxy (the copy engine).
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later async-
+// proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Arrive on `bar` and add `bytes` to the bytes its current phase waits for.
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait until the phase of `bar` with parity `par` completes; false after
+// `limit` polls (each poll itself waits up to a hardware time limit).
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 par, i64 limit) {
+  for (i64 it = 0;; ++it) {
+    u32 done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(par)
+        : "memory");
+    if (done) return true;
+    if (it >= limit) return false;
+  }
+}
 
 __device__ __forceinline__ u64 ld_volatile_u64(const u64* p) {
   return *(const volatile u64*)p;

@@ -276,6 +276,439 @@ __global__ void __launch_bounds__(256) k_part_scatter(const T* __restrict__ key,
   }
 }
 
+// ------------------------------------------------- staged partition ----
+// For fan-outs up to 2^kStagedMaxLog2: persistent blocks, block k taking the
+// contiguous rows [k * n / G, (k + 1) * n / G).  The histogram is then one
+// count per (bucket, block), so the scan and the per-bucket cursor reads are
+// small.  Each block walks its rows in sub-tiles of kSub: warp w takes rows
+// w * kSubWarpRows .. of the sub-tile in steps of 32, which fixes every
+// row's place in the sub-tile sorted by (bucket, input order); each
+// column is then staged in shared memory in that order and every bucket's
+// run is written with consecutive threads on consecutive rows.  Within a
+// bucket the order is input order: blocks in block order, sub-tiles in
+// order, warps in order, steps in order, lanes in order.
+constexpr int kStagedMaxLog2 = 10;
+constexpr int kSub = 2048;
+constexpr int kSubWarpRows = kSub / 8;     // rows of a warp in a sub-tile
+constexpr int kSubSteps = kSubWarpRows / 32;
+
+// Lanes of the warp whose bucket equals this lane's (b < 2^log2P, all lanes
+// taking part; an invalid lane passes a bucket of its own, 2^log2P), from one
+// ballot per bucket bit: cheaper than a general match for small bucket ids.
+__device__ __forceinline__ u32 bucket_peers(u32 b, int log2P) {
+  u32 peers = kFull;
+  for (int k = 0; k <= log2P; ++k) {
+    const u32 m = __ballot_sync(kFull, (b >> k) & 1u);
+    peers &= (b >> k) & 1u ? m : ~m;
+  }
+  return peers;
+}
+
+// First row of block k's chunk: a multiple of 16 rows (so that every column's
+// slice starts on a 16-byte boundary for the bulk copies), n for k = g.
+__host__ __device__ inline i64 chunk_begin(i64 n, i64 g, i64 k) {
+  if (k >= g) return n;
+  const i64 r = (i64)((__int128)n * k / g + 15) & ~(i64)15;
+  return r < n ? r : n;
+}
+
+// Histogram of the scatter's chunks: hsplit blocks per chunk (chunk k =
+// blockIdx.x / hsplit), each counting a share of the chunk's rows and adding
+// its counts into hist[b * g + k] (zeroed before).
+template <typename T>
+__global__ void __launch_bounds__(256, 8) k_part_hist_blk(const T* __restrict__ key, i64 n,
+                                                          int log2P, u32* __restrict__ hist,
+                                                          i64 g, int hsplit) {
+  extern __shared__ u32 sh[];
+  const int P = 1 << log2P;
+  for (int b = threadIdx.x; b < P; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+  const i64 k = blockIdx.x / hsplit, h = blockIdx.x % hsplit;
+  const i64 c0 = chunk_begin(n, g, k), c1 = chunk_begin(n, g, k + 1);
+  auto cut = [&](i64 x) { return x >= hsplit ? c1 : min(c1, c0 + (((c1 - c0) * x / hsplit + 15) & ~15LL)); };
+  const i64 r0 = cut(h), r1 = cut(h + 1);  // 16-row aligned shares
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kPerVec = 16 / sizeof(T);    // keys per 16-byte load
+  constexpr int kLd = 4;                     // 16-byte loads per lane per step
+  constexpr int kRows = kLd * 32 * kPerVec;  // rows of a warp step
+  const bool vec = ((uintptr_t)(key + r0) & 15) == 0;
+  // Warp w takes kRows consecutive rows per step: kLd loads of 16 bytes per
+  // lane, issued together, then counted (small enough for 8 blocks per SM).
+  for (i64 r = r0 + warp * kRows; r < r1; r += 8 * (i64)kRows) {  // warp-uniform
+    T v[kLd][kPerVec];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const i64 row = r + ((i64)j * 32 + lane) * kPerVec;
+      if (vec && row + kPerVec <= r1) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(key + row));
+        memcpy(v[j], &x, 16);
+      } else {
+#pragma unroll
+        for (int e = 0; e < kPerVec; ++e) v[j][e] = row + e < r1 ? __ldg(key + row + e) : T(0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) {
+      const i64 row = r + ((i64)j * 32 + lane) * kPerVec;
+#pragma unroll
+      for (int e = 0; e < kPerVec; ++e)
+        if (row + e < r1) atomicAdd(&sh[fib_bucket((i64)v[j][e], log2P)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < P; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[(i64)b * g + k], sh[b]);
+}
+
+// Shared memory of the staged scatter for P buckets (bytes).
+__host__ __device__ inline size_t staged_smem(int P) {
+  return (size_t)P * 8        // s_gb: global cursor per bucket
+         + (size_t)8 * P * 4  // s_cnt: per-warp counts, then per-warp offsets
+         + (size_t)P * 4      // s_run: run start of each bucket in the sub-tile
+         + (size_t)P * 4      // s_tot: the sub-tile's rows per bucket
+         + (size_t)kSub * 8   // s_stage: one column of the sub-tile, sorted
+         + (size_t)kSub * 2   // s_lpos: sorted place of each row
+         + (size_t)kSub * 2;  // s_sbk: bucket of each sorted place
+}
+
+// One column of a sub-tile: each thread issues its 16 loads before it uses
+// any of them, places the values in sorted order in shared memory, then
+// writes sorted places i = thread, thread + 256, ... to their runs.
+template <typename V>
+__device__ __forceinline__ void stage_column(const V* __restrict__ src, V* __restrict__ dst,
+                                             i64 r, int cnt, const unsigned short* s_lpos,
+                                             const unsigned short* s_sbk, const u32* s_run,
+                                             const i64* s_gb, V* s_stage) {
+  constexpr int kPer = kSub / 256;
+  V v[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = j * 256 + (int)threadIdx.x;
+    v[j] = i < cnt ? __ldcs(src + r + i) : V(0);
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = j * 256 + (int)threadIdx.x;
+    if (i < cnt) s_stage[s_lpos[i]] = v[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = j * 256 + (int)threadIdx.x;
+    if (i < cnt) {
+      const u32 b = s_sbk[i];
+      __stcs(dst + s_gb[b] + (i - (i64)s_run[b]), s_stage[i]);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_part_scatter_blk(const T* __restrict__ key, i64 n,
+                                                          int log2P, const i64* __restrict__ gofs,
+                                                          PayArgs pa, T* __restrict__ out_key,
+                                                          i64* d_offsets) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int P = 1 << log2P;
+  i64* s_gb = reinterpret_cast<i64*>(smem);
+  u32* s_cnt = reinterpret_cast<u32*>(s_gb + P);
+  u32* s_run = s_cnt + 8 * P;
+  u32* s_tot = s_run + P;
+  u64* s_stage = reinterpret_cast<u64*>(s_tot + P);
+  unsigned short* s_lpos = reinterpret_cast<unsigned short*>(s_stage + kSub);
+  unsigned short* s_sbk = s_lpos + kSub;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const i64 g = gridDim.x, k = blockIdx.x;
+  const i64 r0 = chunk_begin(n, g, k), r1 = chunk_begin(n, g, k + 1);
+  for (int b = threadIdx.x; b < P; b += blockDim.x) {
+    s_gb[b] = gofs[(i64)b * g + k];
+    if (k == 0) d_offsets[b] = s_gb[b];
+  }
+  if (k == 0 && threadIdx.x == 0) d_offsets[P] = n;
+  for (i64 r = r0; r < r1; r += kSub) {
+    const int cnt = (int)min((i64)kSub, r1 - r);
+    for (int b = threadIdx.x; b < 8 * P; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    // Bucket and place within the warp's rows of each of the lane's rows
+    // (the keys loaded first, so that their loads are in flight together).
+    u32 bp[kSubSteps];  // bucket << 9 | place among the warp's rows of that bucket
+#pragma unroll
+    for (int st = 0; st < kSubSteps; ++st) {
+      const int i = warp * kSubWarpRows + st * 32 + lane;
+      bp[st] = i < cnt ? fib_bucket((i64)__ldg(key + r + i), log2P) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int st = 0; st < kSubSteps; ++st) {
+      const bool valid = bp[st] != 0xFFFFFFFFu;
+      const u32 b = bp[st];
+      const u32 peers = bucket_peers(valid ? b : (1u << log2P), log2P);
+      u32 place = 0;
+      if (valid) place = s_cnt[warp * P + b] + __popc(peers & lanemask_lt());
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) s_cnt[warp * P + b] += (u32)__popc(peers);
+      __syncwarp();
+      bp[st] = valid ? b << 9 | place : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    static_assert(kSubWarpRows <= 512, "place takes 9 bits");
+    // Per bucket: offsets of the warps' rows, the sub-tile's total.
+    for (int b = threadIdx.x; b < P; b += blockDim.x) {
+      u32 run = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const u32 c = s_cnt[w * P + b];
+        s_cnt[w * P + b] = run;
+        run += c;
+      }
+      s_tot[b] = run;
+    }
+    __syncthreads();
+    {  // run starts: exclusive scan of the totals (P <= 4 * 256)
+      static_assert((1 << kStagedMaxLog2) <= 4 * 256, "four buckets per thread");
+      u32 v[4], sum = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b = (int)threadIdx.x * 4 + j;
+        v[j] = b < P ? s_tot[b] : 0u;
+        sum += v[j];
+      }
+      u32 run = block_exclusive_sum(sum);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b = (int)threadIdx.x * 4 + j;
+        if (b < P) s_run[b] = run;
+        run += v[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int st = 0; st < kSubSteps; ++st) {
+      if (bp[st] == 0xFFFFFFFFu) continue;
+      const u32 b = bp[st] >> 9;
+      const int i = warp * kSubWarpRows + st * 32 + lane;
+      const u32 at = s_run[b] + s_cnt[warp * P + b] + (bp[st] & 511u);
+      s_lpos[i] = (unsigned short)at;
+      s_sbk[at] = (unsigned short)b;
+    }
+    __syncthreads();
+    stage_column<T>(key, out_key, r, cnt, s_lpos, s_sbk, s_run, s_gb,
+                    reinterpret_cast<T*>(s_stage));
+    for (int j = 0; j < pa.n; ++j) {
+      if (pa.type[j] == PQ_INT64)
+        stage_column<i64>((const i64*)pa.src[j], (i64*)pa.dst[j], r, cnt, s_lpos, s_sbk, s_run,
+                          s_gb, reinterpret_cast<i64*>(s_stage));
+      else if (pa.type[j] == PQ_INT32)
+        stage_column<int>((const int*)pa.src[j], (int*)pa.dst[j], r, cnt, s_lpos, s_sbk, s_run,
+                          s_gb, reinterpret_cast<int*>(s_stage));
+      else
+        stage_column<signed char>((const signed char*)pa.src[j], (signed char*)pa.dst[j], r, cnt,
+                                  s_lpos, s_sbk, s_run, s_gb,
+                                  reinterpret_cast<signed char*>(s_stage));
+    }
+    for (int b = threadIdx.x; b < P; b += blockDim.x) s_gb[b] += s_tot[b];
+    __syncthreads();
+  }
+}
+
+// The staged scatter with its sub-tiles brought into shared memory by bulk
+// copies (TMA), double-buffered: while the block orders and writes sub-tile
+// j, the copies of sub-tile j + 1 are in flight.  The columns of a sub-tile
+// sit one after another in its buffer (kSub elements each, raw row order);
+// after the places are fixed, s_inv[i] holds the row of sorted place i, and
+// each column is written by gathering through it.  Used when every column
+// is 16-byte aligned and the buffers fit in shared memory.
+struct TmaCols {
+  const void* src[1 + PQ_MAX_PAYLOAD];
+  void* dst[1 + PQ_MAX_PAYLOAD];
+  int es[1 + PQ_MAX_PAYLOAD];   // element bytes
+  int off[1 + PQ_MAX_PAYLOAD];  // byte offset of the column in a buffer
+  int n;                        // columns, the key first
+  int buf_bytes;                // bytes of one buffer
+};
+
+__host__ __device__ inline size_t tma_smem(int P, int buf_bytes) {
+  return 16                          // two mbarriers
+         + 2 * (size_t)buf_bytes     // double-buffered sub-tile
+         + (size_t)P * 8             // s_gb
+         + (size_t)8 * P * 2         // s_cnt (u16: at most kSubWarpRows per warp)
+         + (size_t)P * 2 * 2         // s_run, s_tot (u16)
+         + (size_t)kSub * 2 * 2;     // s_inv, s_sbk
+}
+
+template <typename V>
+__device__ __forceinline__ void gather_column(const char* buf, int off, V* __restrict__ dst,
+                                              int cnt, const unsigned short* s_inv,
+                                              const unsigned short* s_sbk,
+                                              const unsigned short* s_run, const i64* s_gb) {
+  const V* col = reinterpret_cast<const V*>(buf + off);
+  constexpr int kPer = kSub / 256;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = j * 256 + (int)threadIdx.x;
+    if (i < cnt) {
+      const u32 b = s_sbk[i];
+      __stcs(dst + s_gb[b] + (i - (i64)s_run[b]), col[s_inv[i]]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
+                                                          const i64* __restrict__ gofs,
+                                                          TmaCols tc, i64* d_offsets,
+                                                          i64 spin_limit, DevStatus* st) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int P = 1 << log2P;
+  u64* bar = reinterpret_cast<u64*>(smem);
+  char* bufs = reinterpret_cast<char*>(smem + 16);
+  i64* s_gb = reinterpret_cast<i64*>(bufs + 2 * (size_t)tc.buf_bytes);
+  unsigned short* s_cnt = reinterpret_cast<unsigned short*>(s_gb + P);
+  unsigned short* s_run = s_cnt + 8 * P;
+  unsigned short* s_tot = s_run + P;
+  unsigned short* s_inv = s_tot + P;
+  unsigned short* s_sbk = s_inv + kSub;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const i64 g = gridDim.x, k = blockIdx.x;
+  const i64 r0 = chunk_begin(n, g, k), r1 = chunk_begin(n, g, k + 1);
+  const i64 nsub = (r1 - r0 + kSub - 1) / kSub;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  for (int b = threadIdx.x; b < P; b += blockDim.x) {
+    s_gb[b] = gofs[(i64)b * g + k];
+    if (k == 0) d_offsets[b] = s_gb[b];
+  }
+  if (k == 0 && threadIdx.x == 0) d_offsets[P] = n;
+  __syncthreads();
+  // Thread 0 starts the copies of sub-tile j into buffer j & 1: the part of
+  // each column slice that is a whole number of 16-byte units (all of it but
+  // possibly the last sub-tile's tail, which the block loads itself).
+  auto issue = [&](i64 j) {
+    if (threadIdx.x != 0 || j >= nsub) return;
+    const i64 r = r0 + j * kSub;
+    const i64 cnt = min((i64)kSub, r1 - r);
+    char* buf = bufs + (j & 1) * (size_t)tc.buf_bytes;
+    u32 total = 0;
+    for (int c = 0; c < tc.n; ++c) total += (u32)((cnt * tc.es[c]) & ~15LL);
+    mbar_expect_tx(&bar[j & 1], total);
+    for (int c = 0; c < tc.n; ++c) {
+      const u32 bytes = (u32)((cnt * tc.es[c]) & ~15LL);
+      if (bytes)
+        bulk_g2s(buf + tc.off[c], static_cast<const char*>(tc.src[c]) + r * tc.es[c], bytes,
+                 &bar[j & 1]);
+    }
+  };
+  issue(0);
+  issue(1);
+  for (i64 j = 0; j < nsub; ++j) {
+    const i64 r = r0 + j * kSub;
+    const int cnt = (int)min((i64)kSub, r1 - r);
+    char* buf = bufs + (j & 1) * (size_t)tc.buf_bytes;
+    const bool arrived = mbar_wait(&bar[j & 1], (u32)((j >> 1) & 1), spin_limit);
+    if (__syncthreads_or(!arrived)) {  // block-uniform
+      // The copies did not complete: report, give them a second bounded wait
+      // (they write this block's shared memory) and stop.
+      if (threadIdx.x == 0) latch(st, PQ_ERR_TIMEOUT, r);
+      mbar_wait(&bar[j & 1], (u32)((j >> 1) & 1), spin_limit);
+      if (j + 1 < nsub) mbar_wait(&bar[(j + 1) & 1], (u32)(((j + 1) >> 1) & 1), spin_limit);
+      return;
+    }
+    // The tail that is not a whole 16-byte unit (last sub-tile only).
+    for (int c = 0; c < tc.n; ++c) {
+      const int es = tc.es[c];
+      const int done = (int)(((i64)cnt * es) & ~15LL) / es;
+      for (int i = done + (int)threadIdx.x; i < cnt; i += blockDim.x) {
+        const char* src = static_cast<const char*>(tc.src[c]) + (r + i) * es;
+        char* d = buf + tc.off[c] + (size_t)i * es;
+        if (es == 8) *reinterpret_cast<i64*>(d) = *reinterpret_cast<const i64*>(src);
+        else if (es == 4) *reinterpret_cast<int*>(d) = *reinterpret_cast<const int*>(src);
+        else *d = *src;
+      }
+    }
+    for (int b = threadIdx.x; b < 8 * P; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    const T* s_key = reinterpret_cast<const T*>(buf + tc.off[0]);
+    u32 bp[kSubSteps];  // bucket << 9 | place among the warp's rows of that bucket
+#pragma unroll
+    for (int q = 0; q < kSubSteps; ++q) {
+      const int i = warp * kSubWarpRows + q * 32 + lane;
+      bp[q] = i < cnt ? fib_bucket((i64)s_key[i], log2P) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int q = 0; q < kSubSteps; ++q) {
+      const bool valid = bp[q] != 0xFFFFFFFFu;
+      const u32 b = bp[q];
+      const u32 peers = bucket_peers(valid ? b : (1u << log2P), log2P);
+      u32 place = 0;
+      if (valid) place = s_cnt[warp * P + b] + __popc(peers & lanemask_lt());
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1)
+        s_cnt[warp * P + b] = (unsigned short)(s_cnt[warp * P + b] + __popc(peers));
+      __syncwarp();
+      bp[q] = valid ? b << 9 | place : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < P; b += blockDim.x) {
+      u32 run = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const u32 c = s_cnt[w * P + b];
+        s_cnt[w * P + b] = (unsigned short)run;
+        run += c;
+      }
+      s_tot[b] = (unsigned short)run;
+    }
+    __syncthreads();
+    {
+      u32 v[4], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = (int)threadIdx.x * 4 + q;
+        v[q] = b < P ? s_tot[b] : 0u;
+        sum += v[q];
+      }
+      u32 run = block_exclusive_sum(sum);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = (int)threadIdx.x * 4 + q;
+        if (b < P) s_run[b] = (unsigned short)run;
+        run += v[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSubSteps; ++q) {
+      if (bp[q] == 0xFFFFFFFFu) continue;
+      const u32 b = bp[q] >> 9;
+      const int i = warp * kSubWarpRows + q * 32 + lane;
+      const u32 at = s_run[b] + s_cnt[warp * P + b] + (bp[q] & 511u);
+      s_inv[at] = (unsigned short)i;
+      s_sbk[at] = (unsigned short)b;
+    }
+    __syncthreads();
+    for (int c = 0; c < tc.n; ++c) {
+      if (tc.es[c] == 8)
+        gather_column<i64>(buf, tc.off[c], static_cast<i64*>(tc.dst[c]), cnt, s_inv, s_sbk,
+                           s_run, s_gb);
+      else if (tc.es[c] == 4)
+        gather_column<int>(buf, tc.off[c], static_cast<int*>(tc.dst[c]), cnt, s_inv, s_sbk,
+                           s_run, s_gb);
+      else
+        gather_column<signed char>(buf, tc.off[c], static_cast<signed char*>(tc.dst[c]), cnt,
+                                   s_inv, s_sbk, s_run, s_gb);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < P; b += blockDim.x) s_gb[b] += s_tot[b];
+    // Every thread's reads of this buffer are done: the next copies into it
+    // may start (ordered after the reads for the copy engine).
+    fence_proxy_async_smem();
+    __syncthreads();
+    issue(j + 2);
+  }
+}
+
 // ========================================================== hash join ====
 template <typename TK, typename TV>
 __global__ void k_ht_build(const TK* __restrict__ key, const TV* __restrict__ val, i64 n,
@@ -621,6 +1054,69 @@ pq_status pq_partition(pq_ctx* ctx, pq_col key, const pq_col* payload, int npay,
     return PQ_OK;
   }
   if (!key.data || !out_key) return pqh::fail(ctx, PQ_ERR_INVALID_ARG, "pq_partition: null key");
+  if (log2P <= kStagedMaxLog2) {
+    // Staged scatter: G persistent blocks, one chunk of rows each; with bulk
+    // copies into double-buffered sub-tiles when every column is 16-byte
+    // aligned and the buffers fit.
+    TmaCols tc{};
+    tc.n = 1 + npay;
+    tc.src[0] = key.data;
+    tc.dst[0] = out_key;
+    tc.es[0] = (int)pqh::dtype_size(key.type);
+    bool aligned = ((uintptr_t)key.data & 15) == 0 && ((uintptr_t)out_key & 15) == 0;
+    for (int j = 0; j < npay; ++j) {
+      tc.src[1 + j] = payload[j].data;
+      tc.dst[1 + j] = out_payload[j];
+      tc.es[1 + j] = (int)pqh::dtype_size(payload[j].type);
+      aligned = aligned && ((uintptr_t)payload[j].data & 15) == 0;
+    }
+    int off = 0;
+    for (int c = 0; c < tc.n; ++c) tc.off[c] = off, off += kSub * tc.es[c];
+    tc.buf_bytes = off;
+    const size_t smem_tma = tma_smem(P, tc.buf_bytes);
+    const bool use_tma = aligned && smem_tma <= 200 * 1024;
+    const size_t smem = use_tma ? smem_tma : staged_smem(P);
+    int occ = 1;
+    PQ_DISPATCH_T(key.type, T, {
+      const void* fn = use_tma ? (const void*)k_part_scatter_tma<T>
+                               : (const void*)k_part_scatter_blk<T>;
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem) != cudaSuccess)
+        occ = 1;
+    });
+    cudaGetLastError();
+    const i64 g = std::max<i64>(1, std::min<i64>((n + kSub - 1) / kSub,
+                                                 (i64)ctx->num_sms * std::max(occ, 1)));
+    const i64 m = g * P;
+    const i64 stiles = (m + 4095) / 4096;
+    pqh::Scratch scr(ctx, s);
+    u32* hist = (u32*)scr.get(m * 4);
+    i64* gofs = (i64*)scr.get(m * 8);
+    char* w = (char*)scr.get(stiles * 8 + 256);
+    if (!hist || !gofs || !w) return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_partition: no scratch");
+    PQ_CUDA(ctx, cudaMemsetAsync(w, 0, stiles * 8 + 256, s));
+    PQ_CUDA(ctx, cudaMemsetAsync(hist, 0, m * 4, s));
+    // Histogram blocks: at least two waves of eight per SM, each with at
+    // least 4096 rows.
+    const int hsplit = (int)std::max<i64>(
+        1, std::min<i64>(((i64)ctx->num_sms * 16 + g - 1) / g, (n / g) / 4096));
+    PQ_DISPATCH_T(key.type, T, {
+      k_part_hist_blk<T><<<(unsigned)(g * hsplit), 256, (size_t)P * 4, s>>>(
+          (const T*)key.data, n, log2P, hist, g, hsplit);
+      PQ_LAUNCHED(ctx);
+      k_scan_u32<<<(unsigned)std::min<i64>(stiles, (i64)ctx->num_sms * 4), 256, 0, s>>>(
+          hist, m, gofs, (u64*)(w + 256), (u32*)w, ctx->opt.spin_limit, ctx->d_status);
+      PQ_LAUNCHED(ctx);
+      if (use_tma)
+        k_part_scatter_tma<T><<<(unsigned)g, 256, smem, s>>>(
+            n, log2P, gofs, tc, (i64*)d_offsets, ctx->opt.spin_limit, ctx->d_status);
+      else
+        k_part_scatter_blk<T><<<(unsigned)g, 256, smem, s>>>((const T*)key.data, n, log2P, gofs,
+                                                             pa, (T*)out_key, (i64*)d_offsets);
+    });
+    PQ_LAUNCHED(ctx);
+    return PQ_OK;
+  }
   const i64 ntiles = (n + kPartTile - 1) / kPartTile;
   const i64 m = ntiles * P;
   const i64 stiles = (m + 4095) / 4096;

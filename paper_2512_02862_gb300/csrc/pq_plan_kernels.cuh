@@ -445,33 +445,6 @@ __device__ __forceinline__ bool finish(u32* work, int ph) {
   return s_last;
 }
 
-// Block-wide exclusive sum of one value per thread (every thread calls; the
-// caller synchronises before calling it again).
-__device__ __forceinline__ u32 block_exclusive_sum(u32 v) {
-  __shared__ u32 s_w[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  u32 x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    const u32 c = lane < nw ? s_w[lane] : 0u;
-    u32 y = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 z = __shfl_up_sync(kFull, y, o);
-      if (lane >= o) y += z;
-    }
-    if (lane < nw) s_w[lane] = y - c;
-  }
-  __syncthreads();
-  return s_w[warp] + x - v;
-}
-
 // Block-wide exclusive scan over nq values produced by `f(q)`; writes
 // pre[0..nq] (pre[nq] = total).  Run by one whole block.
 template <typename F>

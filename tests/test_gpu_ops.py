@@ -107,6 +107,44 @@ def test_partition_matches_oracle(ctx, stream, kt, log2P, n):
     assert np.array_equal(ow.cpu().numpy()[:n], ww)
 
 
+@pytest.mark.parametrize("log2P", [3, 10])
+@pytest.mark.parametrize("dist", ["uniform", "one-hot"])
+def test_partition_large_and_skewed(ctx, stream, log2P, dist):
+    """Several sub-tiles per block and a ragged tail; with one-hot keys most
+    rows fall in one bucket (a run spanning whole sub-tiles)."""
+    n = 3_000_017
+    rng = np.random.default_rng(log2P)
+    keys = rng.integers(-2**62, 2**62, size=n).astype(np.int64)
+    if dist == "one-hot":
+        keys[rng.random(n) < 0.9] = 12345
+    rows = np.arange(n, dtype=np.int64)
+    with torch.cuda.stream(stream):
+        ok, (orow,), off = pq.pq_partition(ctx, dev(keys), [dev(rows)], log2P=log2P,
+                                           stream=stream)
+        ctx.sync(stream)
+    wk, (wrow,), woff = oracle.partition(keys, log2P, [rows])
+    assert np.array_equal(off.cpu().numpy(), woff)
+    assert np.array_equal(ok.cpu().numpy()[:n], wk)
+    assert np.array_equal(orow.cpu().numpy()[:n], wrow)
+
+
+def test_partition_unaligned_columns(ctx, stream):
+    """Columns that start off a 16-byte boundary take the scatter without
+    bulk copies; the result is the same."""
+    n = 1_000_003
+    rng = np.random.default_rng(99)
+    keys = rng.integers(-2**40, 2**40, size=n + 1).astype(np.int64)
+    pay = rng.integers(-100, 100, size=n + 1).astype(np.int32)
+    with torch.cuda.stream(stream):
+        dk, dp = dev(keys), dev(pay)
+        ok, (op,), off = pq.pq_partition(ctx, dk[1:], [dp[1:]], log2P=7, stream=stream)
+        ctx.sync(stream)
+    wk, (wp,), woff = oracle.partition(keys[1:].copy(), 7, [pay[1:].copy()])
+    assert np.array_equal(off.cpu().numpy(), woff)
+    assert np.array_equal(ok.cpu().numpy()[:n], wk)
+    assert np.array_equal(op.cpu().numpy()[:n], wp)
+
+
 def join_pairs(rows, vals, cnt):
     k = int(cnt.item())
     r, v = rows[:k].cpu().numpy(), vals[:k].cpu().numpy()
