@@ -922,6 +922,60 @@ def run_serve(args):
     return 0
 
 
+def run_skew(args):
+    """The skewed workload at `--scale` of its size (F 200M rows at 1):
+    the plain and the partitioned (2^8 buckets) plan, `--steps` timed runs
+    each after `--warmup`, and their per-kernel times from a profiled pass."""
+    import torch
+
+    import __graft_entry__
+    import datagen
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+    torch.cuda.set_device(0)
+    w = datagen.WORKLOADS["skew"]
+    n_d, n_m, n_f = (int(w[k] * args.scale) for k in ("n_d", "n_m", "n_f"))
+    D, M, F = datagen.make(n_d, n_m, n_f, seed=w["seed"], fk="zipf", zipf_s=w["zipf_s"])
+    s = torch.cuda.Stream()
+    ctx = pq.Context(arena_bytes=args.arena_gb << 30)
+    with torch.cuda.stream(s):
+        TD, TM, TF, keep = resident_tables(pq, ctx, {"D": D, "M": M, "F": F}, s)
+    q = query("skew")
+    res = pq.pinned_results(1)
+    legs = {}
+    for name, flags, lp in (("plain", 0, 0), ("partitioned_2^8", pq.PQ_PLAN_PARTITIONED, 8)):
+        plan = pq.make_plan(TD, TM, TF, flags=flags | pq.PQ_PLAN_NO_GRAPH, log2P=lp, **q)
+        with torch.cuda.stream(s):
+            for _ in range(args.warmup):
+                pq.pq_run_plan(ctx, plan, res[0], stream=s)
+            ctx.sync(s)
+        ms = _events_ms(torch, s, lambda: pq.pq_run_plan(ctx, plan, res[0], stream=s),
+                        args.steps)
+        ctx.sync(s)
+        ctx.profile_enable(True)
+        ctx.profile_reset()
+        with torch.cuda.stream(s):
+            pq.pq_run_plan(ctx, plan, res[0], stream=s)
+            ctx.sync(s)
+        ctx.profile_enable(False)
+        stages = {}
+        for nm in ("plan_dscan", "plan_mscan", "plan_mrank", "plan_mdup", "plan_fscan",
+                   "plan_fpart", "plan_fscatter", "plan_fagg", "plan_fprobe", "plan_topk",
+                   "plan_topk2"):
+            try:
+                t, nl = ctx.profile(nm)
+                stages[nm] = round(t / max(nl, 1), 4)
+            except pq.PQError:
+                pass
+        legs[name] = {"ms_per_plan": round(ms, 4), "stage_ms": stages,
+                      "result": res[0].as_dict()["ngroups"]}
+    print(json.dumps({"metric": METRIC, "mode": "skew", "scale": args.scale,
+                      "config": {"workload": f"skew at {args.scale} of F 200M rows",
+                                 "rows": {"D": n_d, "M": n_m, "F": n_f}}, "legs": legs}))
+    ctx.close()
+    return 0
+
+
 def run_ops(args):
     """Each standalone operator on x100-sized columns, timed with CUDA events
     on its stream (median of args.steps launches after args.warmup), against
@@ -934,11 +988,16 @@ def run_ops(args):
     __graft_entry__.build()
     import paper_2512_02862_gb300 as pq
     torch.cuda.set_device(0)
-    D, M, F = datagen.workload("x100")
+    if args.rows:
+        w = datagen.WORKLOADS["x100"]
+        D, M, F = datagen.make(w["n_d"], max(1, args.rows // 4), args.rows, seed=w["seed"])
+    else:
+        D, M, F = datagen.workload("x100")
     s = torch.cuda.Stream()
     ctx = pq.Context(arena_bytes=16 << 30)
     dev = lambda a: torch.from_numpy(a).cuda()
     date2, mkey, price = dev(F["date2"]), dev(F["mkey"]), dev(F["price"])
+    want = lambda name: not args.ops or name in args.ops.split(",")
     m_key = dev(M["key"])
     peaks, _ = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -967,13 +1026,22 @@ def run_ops(args):
                      "bytes": nbytes, "note": note})
 
     n_f, n_m = len(F["mkey"]), len(M["key"])
-    ms, (sel, cnt) = timed(lambda: pq.pq_filter(ctx, date2, ">", 1200, stream=s))
-    k = int(cnt.item())
-    add("pq_filter", ms, 4 * n_f + 8 * k, n_f, f"F.date2 > 1200 over {n_f} int32 rows, {k} ids out")
-    for lp in (6, 10):
+    if want("filter"):
+        ms, (sel, cnt) = timed(lambda: pq.pq_filter(ctx, date2, ">", 1200, stream=s))
+        k = int(cnt.item())
+        add("pq_filter", ms, 4 * n_f + 8 * k, n_f,
+            f"F.date2 > 1200 over {n_f} int32 rows, {k} ids out")
+    for lp in (6, 10) if want("partition") else ():
         ms, _ = timed(lambda: pq.pq_partition(ctx, mkey, [price], log2P=lp, stream=s))
         add(f"pq_partition P={1 << lp}", ms, 2 * 16 * n_f, n_f,
-            f"F.mkey + price ({n_f} rows), read twice-free definition: 16 B in + 16 B out per row")
+            f"F.mkey + price ({n_f} rows): 16 B in + 16 B out per row")
+    if not (want("join") or want("groupby") or want("topk")):
+        print(json.dumps({"metric": METRIC, "mode": "ops", "unit": "GB/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "dtype": "int64",
+                          "data": "synthetic", "config": {"rows": n_f, "peak_hbm_gbs": hbm},
+                          "ops": rows}))
+        ctx.close()
+        return 0
     ht_holder = {}
 
     def build():
@@ -1102,6 +1170,34 @@ def run_stream(args):
     mt = float(np.median(mtimes))
     ctx.close()
 
+    # Out of core: the same mapped tables under a device budget too small
+    # for the plan's build side; the M side is radix-partitioned by key range
+    # and the plan runs in passes (F read over the link once per pass).
+    ctx = pq.Context(arena_bytes=int(args.ooc_arena_gb * (1 << 30)))
+    OD = pq.pq_load_columns(ctx, [host["D"]["key"], host["D"]["seg"]], mode=pq.PQ_MAPPED)
+    OM = pq.pq_load_columns(ctx, [host["M"][c] for c in ("key", "dref", "date")],
+                            mode=pq.PQ_MAPPED)
+    OF = pq.pq_load_columns(ctx, [host["F"][c] for c in ("mkey", "price", "disc", "date2")],
+                            mode=pq.PQ_MAPPED)
+    oplan = pq.make_plan(OD, OM, OF, **q)
+    ores = pq.pinned_results(1)
+    with torch.cuda.stream(s):
+        pq.pq_run_plan(ctx, oplan, ores[0], stream=s)
+        ctx.sync(s)
+        p0 = ctx.stats()["out_of_core_passes"]
+        otimes = []
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            pq.pq_run_plan(ctx, oplan, ores[0], stream=s)
+            ctx.sync(s)
+            otimes.append(time.perf_counter() - t0)
+        passes = (ctx.stats()["out_of_core_passes"] - p0) // max(1, args.steps)
+    ot = float(np.median(otimes))
+    out_of_core = {"value": n_f / ot, "unit": "rows/s", "ms_per_step": 1e3 * ot,
+                   "arena_gb": args.ooc_arena_gb, "passes": int(passes),
+                   "result_matches_streaming": ores[0].as_dict() == res[0].as_dict()}
+    ctx.close()
+
     # The same tables packed (frame of reference + bit packing, made once
     # ahead like files on storage): the ingest ring copies the packed bytes
     # and the device decodes each chunk before its scan.
@@ -1168,10 +1264,12 @@ def run_stream(args):
         "result": {"ngroups": got["ngroups"], "top_keys": got["keys"][:3]},
         "sampled_check": {"groups_checked": len(keys), "sums_match": checked},
         "mapped": mapped,
+        "out_of_core": out_of_core,
         "packed": packed_line,
     }
     print(json.dumps(line))
-    ok = checked and mapped["result_matches_streaming"] and packed_line["result_matches_streaming"]
+    ok = (checked and mapped["result_matches_streaming"] and
+          packed_line["result_matches_streaming"] and out_of_core["result_matches_streaming"])
     return 0 if ok else 1
 
 
@@ -1323,7 +1421,13 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream", "ops", "packed",
-                                                        "aggfirst"])
+                                                        "aggfirst", "skew"])
+    ap.add_argument("--ops", default="", help="ops mode: comma list of filter, partition, "
+                                              "join, groupby, topk (default all)")
+    ap.add_argument("--rows", type=int, default=0, help="ops mode: F rows (default x100's)")
+    ap.add_argument("--scale", type=float, default=1.0, help="skew mode: fraction of the size")
+    ap.add_argument("--ooc-arena-gb", type=float, default=6.0,
+                    help="stream mode: device budget of the out-of-core leg")
     ap.add_argument("--workload", default="x100", choices=["small", "x100", "x2000", "skew"])
     ap.add_argument("--arena-gb", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -1354,6 +1458,8 @@ def main(argv=None):
         return run_packed(args)
     if args.mode == "aggfirst":
         return run_aggfirst(args)
+    if args.mode == "skew":
+        return run_skew(args)
     return run_ours(args)
 
 

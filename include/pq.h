@@ -149,7 +149,8 @@ typedef struct pq_stats {
   int64_t chunks_ingested;   /* streaming chunks moved to the device          */
   int64_t plans_run;         /* plans completed (all paths)                   */
   int64_t graph_replays;     /* plan launches served by a captured CUDA graph */
-  int64_t reserved[7];
+  int64_t out_of_core_passes; /* passes of plans run out of core (pq_run_plan) */
+  int64_t reserved[6];
 } pq_stats;
 pq_status pq_get_stats(pq_ctx* ctx, pq_stats* out);
 
@@ -382,7 +383,18 @@ typedef struct pq_result {
  * identical plans replay a captured CUDA graph.  Streaming tables are fed
  * through the ingest ring with copies on side streams overlapped with compute.
  * If `result` is pinned host memory the call returns at once and the result
- * is valid after pq_sync(ctx, stream); otherwise the call waits. */
+ * is valid after pq_sync(ctx, stream); otherwise the call waits.
+ *
+ * Out of core: when a join-first plan over resident or mapped tables does
+ * not fit the arena and its M keys are dense (a key-range bitmap), the build
+ * side is radix-partitioned by key range (1024 buckets of the M key
+ * column, counted once per table) and the plan runs in passes over groups of
+ * consecutive buckets whose dictionary fits (Sec. 3.4, chunks bound the
+ * memory; Sec. 3.1, build and probe per partition); F is scanned once per
+ * pass.  The passes' groups are disjoint and their results are merged on
+ * the host, so such a call returns when the plan is done;
+ * pq_stats.out_of_core_passes counts the passes.  PQ_ERR_BUDGET when not
+ * even one bucket fits. */
 pq_status pq_run_plan(pq_ctx* ctx, const pq_plan* plan, pq_result* result, void* stream);
 
 /* Run `n` plans in one batch: each kernel of the chain is launched once for

@@ -55,7 +55,8 @@ class pq_stats(Structure):
     _fields_ = [("kernel_launches", c_int64), ("h2d_bytes", c_int64), ("d2h_bytes", c_int64),
                 ("arena_bytes", c_int64), ("arena_in_use", c_int64),
                 ("arena_high_water", c_int64), ("chunks_ingested", c_int64),
-                ("plans_run", c_int64), ("graph_replays", c_int64), ("reserved", c_int64 * 7)]
+                ("plans_run", c_int64), ("graph_replays", c_int64),
+                ("out_of_core_passes", c_int64), ("reserved", c_int64 * 6)]
 
 
 class pq_source(Structure):

@@ -451,6 +451,7 @@ pq_status pq_get_stats(pq_ctx* ctx, pq_stats* s) {
   s->chunks_ingested = ctx->chunks.load();
   s->plans_run = ctx->plans.load();
   s->graph_replays = ctx->replays.load();
+  s->out_of_core_passes = ctx->passes.load();
   return PQ_OK;
 }
 

@@ -121,6 +121,26 @@ struct KeyRange {
   bool known() const { return ready.load(std::memory_order_acquire); }
 };
 
+// Rows per key-range bucket of an integer key column: kHistBuckets buckets
+// of 2^shift keys from the column's smallest key (ukey order), measured on
+// the first out-of-core plan over the table and kept.  Published like
+// KeyRange: counts and shift are written before `ready` (release).
+constexpr int kHistBuckets = 1024;
+struct KeyHist {
+  std::atomic<bool> ready{false};
+  int shift = 0;
+  std::vector<uint32_t> counts;
+  KeyHist() = default;
+  KeyHist(const KeyHist& o) { *this = o; }
+  KeyHist& operator=(const KeyHist& o) {
+    shift = o.shift;
+    counts = o.counts;
+    ready.store(o.ready.load(std::memory_order_acquire), std::memory_order_release);
+    return *this;
+  }
+  bool known() const { return ready.load(std::memory_order_acquire); }
+};
+
 struct Column {
   int type = 0;           // pq_dtype
   bool packed = false;    // source is a packed column (PQ_SRC_PACKED)
@@ -133,6 +153,7 @@ struct Column {
   // Range and key order of an integer key column of a resident table,
   // measured on first use by a plan and kept (see KeyRange).
   mutable KeyRange range;
+  mutable KeyHist hist;
 };
 
 }  // namespace pqh
@@ -201,7 +222,7 @@ struct pq_ctx {
   std::mutex range_mu;                   // serialises writers of KeyRange
   std::mutex mu;                         // serialises API calls that touch state
   std::string last_error;
-  std::atomic<int64_t> launches{0}, h2d{0}, d2h{0}, chunks{0}, plans{0}, replays{0};
+  std::atomic<int64_t> launches{0}, h2d{0}, d2h{0}, chunks{0}, plans{0}, replays{0}, passes{0};
   std::atomic<uint64_t> next_table_id{1};
   std::map<std::string, pqh::Profile> prof;
   std::vector<cudaStream_t> copy_streams;
@@ -292,8 +313,14 @@ cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, i
                         cudaStream_t s);
 
 // Plan internals (pq_plan.cu) used by pq_serve.cu and pq_tune.cu.
+// The M key window of one pass of an out-of-core plan: M' restricted to the
+// keys with ukey in [lo, lo + bits), at most `cap` members.
+struct MWindow {
+  uint64_t lo, bits;
+  int64_t cap;
+};
 pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
-                             cudaStream_t s, bool allow_graph);
+                             cudaStream_t s, bool allow_graph, const MWindow* win = nullptr);
 // Upper bound of the arena bytes a batch of these plans needs (0 if invalid).
 size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n);
 pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result,

@@ -107,6 +107,59 @@ bool ensure_range(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
   return true;
 }
 
+// Rows per key-range bucket (kHistBuckets buckets of 2^shift keys from umin).
+__global__ void k_key_hist(const i64* key, i64 n, u64 umin, int shift, u32* out) {
+  __shared__ u32 h[kHistBuckets];
+  for (int i = threadIdx.x; i < kHistBuckets; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n;
+       i += (i64)gridDim.x * blockDim.x)
+    atomicAdd(&h[(ukey(__ldg(key + i)) - umin) >> shift], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHistBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(out + i, h[i]);
+}
+
+// The key histogram of int64 key column c (its range known), measured once
+// like the range (utility stream, no lock held across the wait).
+static bool ensure_key_hist(pq_ctx* ctx, const pq_table* t, int c, cudaStream_t s) {
+  const Column& col = t->cols[c];
+  if (col.hist.known()) return true;
+  if (!col.range.known() || !col.dev || t->nrows <= 0 || col.type != PQ_INT64) return false;
+  const u64 span = col.range.umax - col.range.umin;  // keys - 1
+  const int shift = part_shift(span + 1, 10);
+  static_assert(kHistBuckets == 1 << 10, "buckets");
+  cudaStream_t u = ctx->util_stream;
+  std::vector<u32> host(kHistBuckets);
+  u32* d = (u32*)ctx->arena.alloc(kHistBuckets * 4);
+  cudaEvent_t after = nullptr;
+  bool ok = d && cudaEventCreateWithFlags(&after, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventRecord(after, s ? s : cudaStreamLegacy) == cudaSuccess &&
+            cudaStreamWaitEvent(u, after, 0) == cudaSuccess &&
+            cudaMemsetAsync(d, 0, kHistBuckets * 4, u) == cudaSuccess;
+  if (ok) {
+    const int grid = (int)std::min<i64>((t->nrows + 255) / 256, (i64)ctx->num_sms * 8);
+    k_key_hist<<<grid, 256, 0, u>>>((const i64*)col.dev, t->nrows, col.range.umin, shift, d);
+    ok = cudaGetLastError() == cudaSuccess &&
+         cudaMemcpyAsync(host.data(), d, kHistBuckets * 4, cudaMemcpyDeviceToHost, u) ==
+             cudaSuccess &&
+         cudaStreamSynchronize(u) == cudaSuccess;
+    ctx->launches++;
+  }
+  if (after) cudaEventDestroy(after);
+  if (d) ctx->arena.release(d, u);
+  if (!ok) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> g(ctx->range_mu);
+  if (col.hist.known()) return true;
+  col.hist.shift = shift;
+  col.hist.counts = host;
+  col.hist.ready.store(true, std::memory_order_release);
+  return true;
+}
+
 // Static key bitmaps (see PlanDev): a side whose table is resident and whose
 // key range fits in 32 bits per slot of its table (sized for the table's
 // rows) gets a bitmap over that whole range, known before the plan runs.
@@ -219,7 +272,8 @@ pq_status resolve_plan(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, bool need
 // M side of a plan: a static bitmap means a dense dictionary of at most
 // n_m members over the table's key range, else a hash table of 2^e_m slots.
 static size_t mside_bytes(const ResolvedPlan& r) {
-  return r.dev.m_static ? al256(dense_layout(r.n_m, r.dev.m_sb).total) : mtable_bytes(r.e_m);
+  const i64 c = r.m_cap >= 0 ? r.m_cap : r.n_m;
+  return r.dev.m_static ? al256(dense_layout(c, r.dev.m_sb).total) : mtable_bytes(r.e_m);
 }
 
 size_t plan_bytes(const ResolvedPlan& r) {
@@ -557,7 +611,7 @@ size_t batch_workspace_bytes(pq_ctx* ctx, const pq_plan* plans, int n) {
 }
 
 pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
-                             cudaStream_t s, bool allow_graph) {
+                             cudaStream_t s, bool allow_graph, const MWindow* win) {
   if (n <= 0 || !plans || !results) return fail(ctx, PQ_ERR_INVALID_ARG, "batch: bad arguments");
   for (int i = 0; i < n; ++i)
     if (plans[i].flags & PQ_PLAN_AGG_FIRST) {  // aggregate-first plans run one by one
@@ -578,6 +632,13 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     if (!R[i].resident[0] || !R[i].resident[1] || !R[i].resident[2])
       return run_batch_streaming(ctx, plans, n, results, s);  // some table is streamed
     plan_static(ctx, plans[i], R[i], s, cap != cudaStreamCaptureStatusNone);
+  }
+  if (win) {  // one pass of an out-of-core plan: its M key window
+    if (n != 1 || !R[0].dev.m_static) return fail(ctx, PQ_ERR_INVALID_ARG, "plan pass");
+    R[0].dev.m_su = win->lo;
+    R[0].dev.m_sb = win->bits;
+    R[0].m_cap = win->cap;
+    allow_graph = false;
   }
   // Graph replay for a repeated single plan.
   const bool graphable = allow_graph && n == 1 && s != nullptr && !ctx->opt.profile &&
@@ -925,6 +986,93 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   return st;
 }
 
+// The results of the passes of an out-of-core plan (disjoint groups): top-k
+// of their top-k lists, summed group and hit counts, the first error.
+static void merge_passes(const std::vector<pq_result>& parts, int k, pq_result* out) {
+  std::vector<std::pair<int64_t, int64_t>> all;  // (sum, key)
+  pq_result r{};
+  for (const pq_result& p : parts) {
+    for (int64_t i = 0; i < p.n; ++i) all.push_back({p.sums[i], p.keys[i]});
+    r.ngroups += p.ngroups;
+    r.hits += p.hits;
+    if (!r.status) r.status = p.status;
+  }
+  std::sort(all.begin(), all.end(), [](const std::pair<int64_t, int64_t>& a,
+                                       const std::pair<int64_t, int64_t>& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  });
+  r.n = std::min<int64_t>(k, (int64_t)all.size());
+  for (int64_t i = 0; i < r.n; ++i) r.sums[i] = all[i].first, r.keys[i] = all[i].second;
+  *out = r;
+}
+
+// A join-first plan over resident (or mapped) tables.  When its workspace
+// does not fit the arena and its M side is a static dense dictionary, the
+// build side is radix-partitioned by key range (the M key column's
+// histogram of kHistBuckets buckets) and the plan runs in passes, each over
+// the consecutive buckets whose dictionary fits: the M scan keeps the
+// members of the pass's key window and the F scan hits only their keys
+// (Sec. 3.4: chunks keep memory bounded; Sec. 3.1: partition, then build
+// and probe per partition).  The passes' groups are disjoint; their results
+// are merged on the host, so such a call returns when the plan is done.
+pq_status run_plan_resident(pq_ctx* ctx, const pq_plan& p, pq_result* result, cudaStream_t s) {
+  pq_status st = run_batch_internal(ctx, &p, 1, result, s, true);
+  if (st != PQ_ERR_BUDGET) return st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (s) cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return st;
+  ResolvedPlan r;
+  if (resolve_plan(ctx, p, r, false) != PQ_OK) return st;
+  plan_static(ctx, p, r, s, false);
+  if (!r.dev.m_static || !ensure_key_hist(ctx, p.M, 0, s)) return st;
+  const std::string why = ctx->last_error;
+  const size_t head = batch_layout(1).end;
+  const size_t budget = ctx->arena.largest_free();
+  const KeyHist& h = p.M->cols[0].hist;
+  const u64 umin = p.M->cols[0].range.umin, umax = p.M->cols[0].range.umax;
+  auto window = [&](int b0, int b1) {  // buckets [b0, b1)
+    MWindow w;
+    w.lo = umin + ((u64)b0 << h.shift);
+    const u64 hi = std::min<u64>(umax, umin + ((u64)b1 << h.shift) - 1);  // last key
+    w.bits = hi - w.lo + 1;
+    w.cap = 0;
+    for (int b = b0; b < b1; ++b) w.cap += h.counts[b];
+    return w;
+  };
+  auto fits = [&](const MWindow& w) {
+    ResolvedPlan q = r;
+    q.dev.m_sb = w.bits;
+    q.m_cap = w.cap;
+    return head + plan_bytes(q) <= budget;
+  };
+  const int nb = (int)std::min<u64>(kHistBuckets, ((umax - umin) >> h.shift) + 1);
+  std::vector<MWindow> wins;
+  for (int b0 = 0; b0 < nb;) {
+    int b1 = b0 + 1;
+    if (!fits(window(b0, b1)))
+      return fail(ctx, PQ_ERR_BUDGET,
+                  "%s; out of core, one key bucket of M (%lld rows) does not fit either",
+                  why.c_str(), (long long)window(b0, b1).cap);
+    while (b1 < nb && fits(window(b0, b1 + 1))) ++b1;
+    wins.push_back(window(b0, b1));
+    b0 = b1;
+  }
+  pq_result* parts = nullptr;
+  PQ_CUDA(ctx, cudaHostAlloc((void**)&parts, sizeof(pq_result) * wins.size(), 0));
+  st = PQ_OK;
+  for (size_t i = 0; i < wins.size() && st == PQ_OK; ++i)
+    st = run_batch_internal(ctx, &p, 1, &parts[i], s, false, &wins[i]);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == PQ_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "out-of-core plan");
+  if (st == PQ_OK) {
+    merge_passes(std::vector<pq_result>(parts, parts + wins.size()), p.k, result);
+    ctx->plans -= (int64_t)wins.size() - 1;
+    ctx->passes += (int64_t)wins.size();
+  }
+  cudaFreeHost(parts);
+  return st;
+}
+
 }  // namespace pqh
 
 extern "C" {
@@ -938,7 +1086,7 @@ pq_status pq_run_plan(pq_ctx* ctx, const pq_plan* plan, pq_result* result, void*
   if (st != PQ_OK) return st;
   if (!r.resident[0] || !r.resident[1] || !r.resident[2])
     return pqh::run_plan_streaming(ctx, plan, result, pqh::S(stream));
-  return pqh::run_batch_internal(ctx, plan, 1, result, pqh::S(stream), true);
+  return pqh::run_plan_resident(ctx, *plan, result, pqh::S(stream));
 }
 
 pq_status pq_run_batch(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,

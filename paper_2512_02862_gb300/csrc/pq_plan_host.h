@@ -18,6 +18,7 @@ struct ResolvedPlan {
   DsetEntry* cache = nullptr;
   bool cache_new = false;
   bool resident[3] = {false, false, false};
+  i64 m_cap = -1;         // members the dense dictionary is sized for (-1: n_m)
 };
 
 // Validate `p`; fill predicates, sizes and (for resident tables) the column

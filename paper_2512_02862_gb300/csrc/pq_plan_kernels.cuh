@@ -915,6 +915,9 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
           }
         }
       }
+      // A static bitmap covers the plan's M key window (the whole key range,
+      // or one pass of an out-of-core plan): keys outside it are no members.
+      if (stat && mem && ukey(key) - q.m_su >= q.m_sb) mem = false;
       const u32 m = __ballot_sync(kFull, mem);
       if (!LIST || stat) {
         if (mem) bit_set(sbm, ukey(key) - q.m_su);
@@ -1011,7 +1014,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
     const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
     const u32* dt_keybm = dt.keybm;
     u32* sbm = reinterpret_cast<u32*>(q.ht_tag);  // dense layout: bm at 0
-    const u64 m_su = q.m_su;
+    const u64 m_su = q.m_su, m_sb = q.m_sb;  // the plan's M key window
     const Pred32 pm = to32(q.pm);
     const i64 base = (t - b.tM[qi]) * q.m_tile;
     const int lim = (int)min(q.n_m - base, (i64)q.m_tile);
@@ -1022,9 +1025,10 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
     u32 members = 0;  // this lane's
     auto set_bits = [&](u32 m, const i64 k[4]) {
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if ((m >> s) & 1u) bit_set(sbm, ukey(k[s]) - m_su);
-      members += __popc(m);
+      for (int s = 0; s < 4; ++s) {
+        const u64 idx = ukey(k[s]) - m_su;
+        if (((m >> s) & 1u) && idx < m_sb) bit_set(sbm, idx), ++members;
+      }
     };
     if (d_bits == 0) {
       // A D-set that is a hash table (the host does not choose this kernel
@@ -1032,8 +1036,8 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
       for (int r = lane; r < lim; r += 32) {
         if (!pass32(pm, ld_stream(pdate + r))) continue;
         if (!set_contains(dt, (i64)__ldg(pdref + r), keep)) continue;
-        bit_set(sbm, ukey(__ldg(pkey + r)) - m_su);
-        ++members;
+        const u64 idx = ukey(__ldg(pkey + r)) - m_su;
+        if (idx < m_sb) bit_set(sbm, idx), ++members;
       }
     } else {
       // Slot p = it % 2 holds date and dref of step it (read two steps
@@ -1366,7 +1370,8 @@ __global__ void __launch_bounds__(256) k_plan_mdup(Batch b) {
         const u64 di = ukey(dr) - d_umin;
         const bool mem = d_bits ? di < d_bits && bit_test(dt.keybm, di, keep)
                                 : set_contains(dt, dr, keep);
-        if (mem) atomicAdd(cnt + dense_rank(dv, ukey(__ldg(q.m_key + r)) - umin, keep), 1u);
+        const u64 idx = mem ? ukey(__ldg(q.m_key + r)) - umin : ~0ULL;
+        if (idx < q.m_sb) atomicAdd(cnt + dense_rank(dv, idx, keep), 1u);
       }
       continue;
     }
