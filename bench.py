@@ -976,6 +976,57 @@ def run_skew(args):
     return 0
 
 
+def run_buffering(args):
+    """Dynamic buffering of a streamed plan's F hits: the x100 tables in
+    pinned host memory streamed in small chunks (--chunk-mb), the query of
+    the benchmark (about 0.5 % of F rows join), the probe run after every
+    chunk (hit_buffer -1) against hits buffered on the device and probed
+    once the buffer could not take another chunk (hit_buffer 16).  CUDA
+    events around each plan on its stream; identical results required."""
+    import torch
+
+    import __graft_entry__
+    import datagen
+    __graft_entry__.build()
+    import paper_2512_02862_gb300 as pq
+    torch.cuda.set_device(0)
+    D, M, F = datagen.workload("x100")
+    pin = lambda t, names: [torch.from_numpy(np.ascontiguousarray(t[c])).pin_memory()
+                            for c in names]
+    host = (pin(D, ("key", "seg")), pin(M, ("key", "dref", "date")),
+            pin(F, ("mkey", "price", "disc", "date2")))
+    q = query("x100")
+    s = torch.cuda.Stream()
+    legs, results = {}, []
+    for chunk_mb in [int(x) for x in args.chunk_mb.split(",")]:
+        for hb in (-1, 16):
+            ctx = pq.Context(arena_bytes=16 << 30, chunk_bytes=chunk_mb << 20, ring_slots=6,
+                             copy_streams=2, hit_buffer=hb)
+            T = [pq.pq_load_columns(ctx, cols, mode=pq.PQ_STREAMING) for cols in host]
+            plan = pq.make_plan(*T, **q)
+            res = pq.pinned_results(1)
+            with torch.cuda.stream(s):
+                for _ in range(args.warmup):
+                    pq.pq_run_plan(ctx, plan, res[0], stream=s)
+                    ctx.sync(s)
+                l0 = ctx.stats()["kernel_launches"]
+                ms = _events_ms(torch, s, lambda: pq.pq_run_plan(ctx, plan, res[0], stream=s),
+                                args.steps)
+                ctx.sync(s)
+                launches = (ctx.stats()["kernel_launches"] - l0) // args.steps
+            results.append(res[0].as_dict())
+            legs[f"chunk_{chunk_mb}MB_{'per_chunk' if hb < 0 else 'buffered'}"] = {
+                "ms_per_plan": round(ms, 3), "rows_per_s": len(F["mkey"]) / (ms / 1e3),
+                "kernel_launches_per_plan": int(launches)}
+            ctx.close()
+    print(json.dumps({"metric": METRIC, "mode": "buffering", "steps": args.steps,
+                      "config": {"workload": "x100 in pinned host memory, streamed",
+                                 "query": QUERY_TEXT},
+                      "legs": legs,
+                      "results_identical": all(r == results[0] for r in results)}))
+    return 0
+
+
 def run_ops(args):
     """Each standalone operator on x100-sized columns, timed with CUDA events
     on its stream (median of args.steps launches after args.warmup), against
@@ -1421,7 +1472,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plan", choices=["plan", "serve", "stream", "ops", "packed",
-                                                        "aggfirst", "skew"])
+                                                        "aggfirst", "skew", "buffering"])
+    ap.add_argument("--chunk-mb", default="4,16", help="buffering mode: chunk sizes in MB")
     ap.add_argument("--ops", default="", help="ops mode: comma list of filter, partition, "
                                               "join, groupby, topk (default all)")
     ap.add_argument("--rows", type=int, default=0, help="ops mode: F rows (default x100's)")
@@ -1460,6 +1512,8 @@ def main(argv=None):
         return run_aggfirst(args)
     if args.mode == "skew":
         return run_skew(args)
+    if args.mode == "buffering":
+        return run_buffering(args)
     return run_ours(args)
 
 

@@ -101,7 +101,10 @@ typedef struct pq_options {
   int64_t spin_limit;      /* iteration limit of every device-side wait (1<<22)   */
   int32_t serve_queue;     /* pending requests before pq_submit says BUSY (4096)  */
   int32_t profile;         /* 1: record CUDA events around every plan kernel      */
-  int32_t reserved[6];
+  int32_t hit_buffer;      /* dynamic buffering of a streamed plan's F hits: the
+                              device buffer holds the hits of this many chunks of
+                              F rows (16); -1: probe every chunk (Sec. 5.3)       */
+  int32_t reserved[5];
 } pq_options;
 
 typedef struct pq_ctx pq_ctx;

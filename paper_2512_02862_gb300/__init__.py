@@ -48,7 +48,7 @@ class pq_options(Structure):
                 ("log2P", c_int32), ("chunk_bytes", c_int64), ("ingest_threads", c_int32),
                 ("copy_streams", c_int32), ("ring_slots", c_int32), ("serve_slots", c_int32),
                 ("spin_limit", c_int64), ("serve_queue", c_int32), ("profile", c_int32),
-                ("reserved", c_int32 * 6)]
+                ("hit_buffer", c_int32), ("reserved", c_int32 * 5)]
 
 
 class pq_stats(Structure):

@@ -335,6 +335,7 @@ pq_status pq_default_options(pq_options* o) {
   o->spin_limit = 1ll << 22;
   o->serve_queue = 4096;
   o->profile = 0;
+  o->hit_buffer = 16;
   return PQ_OK;
 }
 
@@ -359,6 +360,7 @@ pq_status pq_create(const pq_options* opt, void* arena, size_t arena_bytes, pq_c
     PQ_OPT(serve_slots) PQ_OPT(spin_limit) PQ_OPT(serve_queue)
 #undef PQ_OPT
     d.profile = o.profile;
+    if (o.hit_buffer > 0 || o.hit_buffer == -1) d.hit_buffer = o.hit_buffer;
     ctx->opt = d;
   }
   pq_options& o = ctx->opt;

@@ -180,6 +180,14 @@ static void plan_static(pq_ctx* ctx, const pq_plan& p, ResolvedPlan& r, cudaStre
   };
   d.d_static = r.resident[0] && fits(p.D, r.e_d, &d.d_su, &d.d_sb) ? 1 : 0;
   d.m_static = r.resident[1] && fits(p.M, r.e_m, &d.m_su, &d.m_sb) ? 1 : 0;
+  if (d.d_static) {
+    // A bitmap D-set uses only the key bitmap of its block: the smallest
+    // table whose 32 bits per slot cover the key range, not a hash table
+    // sized for the rows.
+    int e = 6;
+    while ((32ULL << e) < d.d_sb) ++e;
+    r.e_d = d.d_e = e;
+  }
   // Bound of one row's revenue |price * (100 - disc)|: the price column's
   // measured range times the largest |100 - disc| of an int8 (228).
   d.rev_max = 0;

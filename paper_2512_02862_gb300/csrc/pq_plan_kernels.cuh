@@ -316,6 +316,15 @@ struct PlanDev {
   // partitioned by group slot into 2^part_log2 buckets (part_shift) before
   // they are aggregated, so that each bucket's slice of the group arrays is
   // small enough to stay in L2 while its hits are added.  0: not partitioned.
+  // Dynamic buffering of a streamed plan's F hits (hb_cap > 0): the F scan
+  // gathers every hit's key, price and discount into these arrays (so the
+  // chunk's ring slot is free at once); the host launches the probe only
+  // after every few chunks (as many as the buffer holds rows of) and after
+  // the last one.
+  i64* hb_key;
+  i64* hb_price;
+  signed char* hb_disc;
+  u64 hb_cap;
   // Upper bound of |price * (100 - disc)| over the F table's rows (from the
   // measured range of its price column), or 0 when unknown.  When the hits
   // times this bound times the largest multiplicity stay below 2^63, no
@@ -1613,9 +1622,10 @@ __device__ __forceinline__ void fprobe_epilogue(const Batch& b, u64* s_akey, i64
       const PlanDev& q = b.q[qi];
       q.out->status = q.ctr->status;
       q.out->reserved = 0;
+      // A streamed F table probes chunk by chunk (or buffer by buffer).
       q.ctr->hits_total += (u64)ld_count(&q.ctr->hcount);
+      q.ctr->hcount = 0;
       q.out->hits = (i64)q.ctr->hits_total;
-      q.ctr->hcount = 0;  // a streamed F table probes chunk by chunk
       const i64 w = topk_words(q);
       return max((i64)1, (w + topk_tile_words_w(w) - 1) / topk_tile_words_w(w));
     });
@@ -1685,7 +1695,21 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
     u64 at = 0;
     if (lane == 0) at = atomicAdd(&q.ctr->hcount, (u64)cnt);
     at = __shfl_sync(kFull, at, 0);
-    for (u32 j = lane; j < cnt; j += 32) q.hlist[at + j] = hr[(hh + j) & (kHF - 1)];
+    if (q.hb_cap) {  // buffered: the hit's columns, not its row
+      const i64* mk = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
+      const i64* pr = ov ? (const i64*)b.ov.p[1] : q.f_price;
+      const signed char* ds = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+      for (u32 j = lane; j < cnt; j += 32) {
+        const u32 row = hr[(hh + j) & (kHF - 1)];
+        if (at + j < q.hb_cap) {  // the host sizes the buffer for a whole chunk
+          q.hb_key[at + j] = __ldg(mk + row);
+          q.hb_price[at + j] = __ldg(pr + row);
+          q.hb_disc[at + j] = __ldg(ds + row);
+        }
+      }
+    } else {
+      for (u32 j = lane; j < cnt; j += 32) q.hlist[at + j] = hr[(hh + j) & (kHF - 1)];
+    }
     hh += cnt;
     __syncwarp();
   };
@@ -1803,14 +1827,16 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   if (finish(b.work, kPhFscan)) {
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
     block_prefix(b.dyn + 7 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
-      QCtr* c = b.q[qi].ctr;
+      const PlanDev& q = b.q[qi];
+      QCtr* c = q.ctr;
       const i64 h = ld_count(&c->hcount);
+      if (q.hb_cap && h > (i64)q.hb_cap) q_latch(c, b.st, PQ_ERR_CAPACITY, h);
       // Hits per probe tile: about two tiles per warp of this grid, in
       // multiples of 32, between 64 and 4096.
       i64 tl = (h / (2 * warps) + 31) / 32 * 32;
       tl = tl < 64 ? 64 : tl > 4096 ? 4096 : tl;
       c->hp_tile = tl;
-      return b.q[qi].part_log2 ? 0 : (h + tl - 1) / tl;  // partitioned: fpart .. fagg
+      return q.part_log2 ? 0 : (h + tl - 1) / tl;  // partitioned: fpart .. fagg
     });
     block_prefix(b.dyn + 8 * (b.nq + 1), b.nq, [&](int qi) -> i64 {
       const PlanDev& q = b.q[qi];
@@ -1847,9 +1873,10 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
     ProbeCtx pc;
-    pc.mkey = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
-    pc.price = ov ? (const i64*)b.ov.p[1] : q.f_price;
-    pc.disc = ov ? (const signed char*)b.ov.p[2] : q.f_disc;
+    const bool buffered = q.hb_cap != 0;  // hits are buffer entries, not rows
+    pc.mkey = buffered ? q.hb_key : ov ? (const i64*)b.ov.p[0] : q.f_mkey;
+    pc.price = buffered ? q.hb_price : ov ? (const i64*)b.ov.p[1] : q.f_price;
+    pc.disc = buffered ? q.hb_disc : ov ? (const signed char*)b.ov.p[2] : q.f_disc;
     pc.base = 0;
     pc.keep = keep;
     pc.qi = qi;
@@ -1878,7 +1905,7 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
         u64 slot = 0;
         i64 v = 0;
         if (act) {
-          const i64 row = __ldg(q.hlist + i + lane);
+          const i64 row = buffered ? i + lane : (i64)__ldg(q.hlist + i + lane);
           const i64 k = __ldg(pc.mkey + row);
           const i64 price = __ldg(pc.price + row);
           const i64 disc = __ldg(pc.disc + row);
@@ -1900,7 +1927,7 @@ __global__ void __launch_bounds__(256) k_plan_fprobe(Batch b) {
     for (i64 i = i0; i < i1; i += 32) {
       const bool act = i + lane < i1;
       Hit x = {false, 0, 0};
-      if (act) x = probe_row(b, pc, __ldg(q.hlist + i + lane));
+      if (act) x = probe_row(b, pc, buffered ? (u32)(i + lane) : __ldg(q.hlist + i + lane));
       commit_hits_g(b, sc, akey, s_asum, x.act, qi, x.slot, x.v, nullptr, exact);
     }
   }

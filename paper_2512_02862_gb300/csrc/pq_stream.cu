@@ -258,6 +258,20 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   d.dlist = (i64*)(ws + L.end);
   d.mlist = (i64*)(ws + L.end + al(r.n_d * 8));
   d.hlist = (u32*)(ws + L.end + al(r.n_d * 8) + al(r.n_m * 8));
+  // Dynamic buffering (Sec. 5.3): a streamed F table's hits are gathered
+  // into a buffer that holds `hit_buffer` chunks of rows (so it cannot
+  // overflow), and the probe runs after every `hit_buffer` chunks and after
+  // the last one instead of after every chunk.
+  if (!r.resident[2] && !plog && ctx->opt.hit_buffer > 0 && f_hits > 0) {
+    const u64 cap = (u64)f_hits * (u64)ctx->opt.hit_buffer;
+    char* hb = (char*)scr.get(al(cap * 8) * 2 + al(cap));
+    if (hb) {  // else the probe runs chunk by chunk
+      d.hb_key = (i64*)hb;
+      d.hb_price = (i64*)(hb + al(cap * 8));
+      d.hb_disc = (signed char*)(hb + 2 * al(cap * 8));
+      d.hb_cap = cap;
+    }
+  }
   if (plog) {
     char* q = pws;
     d.part = (u64*)q;
@@ -387,15 +401,18 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     return PQ_OK;
   };
   // The F table's phase is the scan and the probe of its hits (for a
-  // partitioned plan: the scan counting buckets, the partition pass, the
-  // aggregation pass, then the probe kernel's epilogue), chunk by chunk.
+  // partitioned plan: the scan, the partition, scatter and aggregation
+  // passes, then the probe kernel's epilogue), chunk by chunk; with buffered
+  // hits the probe only after every hit_buffer chunks and the last.
+  bool probe_now = true;
+  i64 f_seen = 0;
   auto launch_table = [&](int t, const Batch& bt, bool v) -> pq_status {
     if (t < 2) return launch_phase(ctx, t == 0 ? kPhaseD : kPhaseM, bt, v, s);
     if (plog) PQ_CUDA(ctx, cudaMemsetAsync(d.part, 0, ((1 << plog) + 1) * 8, s));
     pq_status e = launch_phase(ctx, kPhaseFscan, bt, v, s);
     for (int ph : {kPhaseFpart, kPhaseFscatter, kPhaseFagg})
       if (e == PQ_OK && plog) e = launch_phase(ctx, ph, bt, v, s);
-    if (e == PQ_OK) e = launch_phase(ctx, kPhaseF, bt, v, s);
+    if (e == PQ_OK && probe_now) e = launch_phase(ctx, kPhaseF, bt, v, s);
     return e;
   };
   size_t c = 0;
@@ -424,6 +441,9 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
         Batch bc = b;
         bc.ov.table = t + 1;
         bc.ov.n = ch.rows;
+        const bool last = c + 1 == chunks.size() || chunks[c + 1].table != t;
+        if (t == 2) ++f_seen;
+        probe_now = t != 2 || !d.hb_cap || last || f_seen % ctx->opt.hit_buffer == 0;
         const int tile = t == 0   ? scan_tile(ch.rows, 512, kTD, resident_warps(ctx, 0))
                          : t == 1 ? scan_tile(ch.rows, 128, kTM, resident_warps(ctx, 3))
                                   : scan_tile(ch.rows, 128, kTF, resident_warps(ctx, 8));

@@ -346,6 +346,36 @@ def test_streaming_plan_matches_oracle(stream_ctx, stream, small, tmp_path, sour
         assert ctx.stats()["chunks_ingested"] > 20
 
 
+@pytest.mark.parametrize("hit_buffer", [-1, 1, 2, 16])
+def test_streaming_hit_buffer(stream, small, hit_buffer):
+    """Dynamic buffering of a streamed F table's hits: probe every chunk
+    (-1), or keep the hits of up to 1, 2, 16 chunks of rows on the device
+    and probe when the buffer could not take another chunk or after the
+    last; with every row a hit the small buffers force probes mid-stream."""
+    D, M, F = small
+    c = pq.Context(arena_bytes=2 << 30, chunk_bytes=1 << 20, ring_slots=3,
+                   hit_buffer=hit_buffer)
+    pin = lambda t, names: [torch.from_numpy(np.ascontiguousarray(t[x])).pin_memory()
+                            for x in names]
+    with torch.cuda.stream(stream):
+        TD = pq.pq_load_columns(c, pin(D, ("key", "seg")), mode=pq.PQ_STREAMING)
+        TM = pq.pq_load_columns(c, pin(M, ("key", "dref", "date")), mode=pq.PQ_STREAMING)
+        TF = pq.pq_load_columns(c, pin(F, ("mkey", "price", "disc", "date2")),
+                                mode=pq.PQ_STREAMING)
+        for p in (dict(seg=1, mc=1200, fc=1200, k=10),
+                  dict(seg=0, mc=0, fc=0, k=64, d_op="all", m_op="all", f_op="all")):
+            kw = dict(seg=p["seg"], m_date_lt=p["mc"], f_date_gt=p["fc"], k=p["k"],
+                      d_op=p.get("d_op", "=="), m_op=p.get("m_op", "<"),
+                      f_op=p.get("f_op", ">"))
+            got = pq.pq_run_plan(c, pq.make_plan(TD, TM, TF, **kw), stream=stream)
+            c.sync(stream)
+            want = oracle_plan(D, M, F, seg=p["seg"], mc=p["mc"], fc=p["fc"], k=p["k"],
+                               d_op=kw["d_op"], m_op=kw["m_op"], f_op=kw["f_op"])
+            assert_same(got.as_dict(), want, f"hit_buffer {hit_buffer} {p}")
+            assert got.hits == (len(F["mkey"]) if "f_op" in p else got.hits)
+    c.close()
+
+
 class _DevView:
     """A device array seen through __cuda_array_interface__ (the test only reads it)."""
 
