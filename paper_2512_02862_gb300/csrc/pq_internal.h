@@ -236,7 +236,7 @@ struct pq_ctx {
   int tune_threads = 256;
   int tune_bps = 2;
   // resident blocks per SM of each plan kernel (filled by plan_kernels_init)
-  int plan_occ[24] = {0};
+  int plan_occ[28] = {0};
 };
 
 namespace pqh {

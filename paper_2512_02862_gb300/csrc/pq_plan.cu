@@ -372,21 +372,25 @@ static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "
 static_assert(sizeof(kPhaseName) / sizeof(kPhaseName[0]) == kPhaseTopk2 + 1, "phase names");
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
-  const void* fn[21] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
+  const void* fn[25] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
                         (const void*)k_plan_dbuild,      (const void*)k_plan_mscan<true, true>,
                         (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
-                        (const void*)k_plan_fscan<false>, (const void*)k_plan_topk,
-                        (const void*)k_plan_fscan<true>,  (const void*)k_plan_mscan<false, true>,
+                        (const void*)k_plan_fscan<false, false>, (const void*)k_plan_topk,
+                        (const void*)k_plan_fscan<true, false>,  (const void*)k_plan_mscan<false, true>,
                         (const void*)k_plan_topk2,       (const void*)k_plan_mrank,
                         (const void*)k_plan_mdup,        (const void*)k_plan_fprobe,
                         (const void*)k_plan_mscan<true, false>,
                         (const void*)k_plan_mscan<false, false>,
-                        (const void*)k_plan_mscan_bm<true>,
-                        (const void*)k_plan_mscan_bm<false>,
+                        (const void*)k_plan_mscan_bm<true, false>,
+                        (const void*)k_plan_mscan_bm<false, false>,
                         (const void*)k_plan_fpart,
                         (const void*)k_plan_fscatter,
-                        (const void*)k_plan_fagg};
-  for (int i = 0; i < 21; ++i) {
+                        (const void*)k_plan_fagg,
+                        (const void*)k_plan_fscan<false, true>,
+                        (const void*)k_plan_fscan<true, true>,
+                        (const void*)k_plan_mscan_bm<true, true>,
+                        (const void*)k_plan_mscan_bm<false, true>};
+  for (int i = 0; i < 25; ++i) {
     int n = 0;
     const int threads = i == 7 || i == 10 ? kTKW * 32 : 256;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn[i], threads, 0) != cudaSuccess)
@@ -402,6 +406,8 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
 static thread_local i64 t_tiles_max = -1;
 static thread_local bool t_list_m = true;  // some plan of the batch keeps an M key list
 static thread_local bool t_bm_dm = false;  // every plan: static M bitmap, D-set bitmap
+static thread_local bool t_buf = false;    // some plan buffers its F hits
+static thread_local bool t_win = false;    // some plan is an out-of-core pass (M key window)
 static int plan_grid(pq_ctx* ctx, int occ_index, int tiles_per_block = 8) {
   const i64 g = (i64)ctx->num_sms * std::max(1, std::min(ctx->tune_bps, ctx->plan_occ[occ_index]));
   if (t_tiles_max < 0) return (int)g;
@@ -434,6 +440,11 @@ static cudaError_t launch_chained(void (*k)(P...), int grid, int block, cudaStre
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+void set_kernel_variants(bool buffered_hits, bool key_window) {
+  t_buf = buffered_hits;
+  t_win = key_window;
+}
+
 pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStream_t s,
                        i64 tiles_max, bool list_m, bool bm_dm) {
   t_list_m = list_m;
@@ -453,9 +464,12 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseDfill: e = launch_chained(k_plan_fill, plan_grid(ctx, 1, 1), 256, s, b, 0); break;
     case kPhaseDbuild: e = launch_chained(k_plan_dbuild, plan_grid(ctx, 2), 256, s, b); break;
     case kPhaseM:
-      if (t_bm_dm)
-        e = vec ? launch_chained(k_plan_mscan_bm<true>, plan_grid(ctx, 16), 256, s, b)
-                : launch_chained(k_plan_mscan_bm<false>, plan_grid(ctx, 17), 256, s, b);
+      if (t_bm_dm && t_win)
+        e = vec ? launch_chained(k_plan_mscan_bm<true, true>, plan_grid(ctx, 23), 256, s, b)
+                : launch_chained(k_plan_mscan_bm<false, true>, plan_grid(ctx, 24), 256, s, b);
+      else if (t_bm_dm)
+        e = vec ? launch_chained(k_plan_mscan_bm<true, false>, plan_grid(ctx, 16), 256, s, b)
+                : launch_chained(k_plan_mscan_bm<false, false>, plan_grid(ctx, 17), 256, s, b);
       else if (t_list_m)
         e = vec ? launch_chained(k_plan_mscan<true, true>, plan_grid(ctx, 3), 256, s, b)
                 : launch_chained(k_plan_mscan<false, true>, plan_grid(ctx, 9), 256, s, b);
@@ -468,8 +482,12 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseMrank: e = launch_chained(k_plan_mrank, plan_grid(ctx, 11), 256, s, b); break;
     case kPhaseMdup: e = launch_chained(k_plan_mdup, plan_grid(ctx, 12), 256, s, b); break;
     case kPhaseFscan:
-      e = vec ? launch_chained(k_plan_fscan<true>, plan_grid(ctx, 8), 256, s, b)
-              : launch_chained(k_plan_fscan<false>, plan_grid(ctx, 6), 256, s, b);
+      if (t_buf)
+        e = vec ? launch_chained(k_plan_fscan<true, true>, plan_grid(ctx, 22), 256, s, b)
+                : launch_chained(k_plan_fscan<false, true>, plan_grid(ctx, 21), 256, s, b);
+      else
+        e = vec ? launch_chained(k_plan_fscan<true, false>, plan_grid(ctx, 8), 256, s, b)
+                : launch_chained(k_plan_fscan<false, false>, plan_grid(ctx, 6), 256, s, b);
       break;
     case kPhaseFpart: e = launch_chained(k_plan_fpart, plan_grid(ctx, 18, 1), 256, s, b); break;
     case kPhaseFscatter:
@@ -641,6 +659,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
       return run_batch_streaming(ctx, plans, n, results, s);  // some table is streamed
     plan_static(ctx, plans[i], R[i], s, cap != cudaStreamCaptureStatusNone);
   }
+  set_kernel_variants(false, win != nullptr);
   if (win) {  // one pass of an out-of-core plan: its M key window
     if (n != 1 || !R[0].dev.m_static) return fail(ctx, PQ_ERR_INVALID_ARG, "plan pass");
     R[0].dev.m_su = win->lo;

@@ -92,6 +92,9 @@ pqk::Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L);
 // static M bitmap and a D-set bitmap (the ring-free M scan runs).
 pq_status launch_phase(pq_ctx* ctx, int phase, const pqk::Batch& b, bool vec, cudaStream_t s,
                        i64 tiles_max = -1, bool list_m = true, bool bm_dm = false);
+// Kernel variants for the launches that follow on this thread: the F scan
+// that buffers hits, the M scan of an out-of-core pass's key window.
+void set_kernel_variants(bool buffered_hits, bool key_window);
 
 // Phases in chain order.  Fpart, Fscatter and Fagg run only for batches
 // with a partitioned plan; the F probe (kPhaseF) always runs, for the plans

@@ -1003,7 +1003,10 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan(Batch b) {
 // are read two steps ahead, the D bitmap words are loaded when they arrive
 // and tested one step later; then the members' keys are loaded, and two
 // steps after that their bits are set (reductions nobody waits for).
-template <bool VEC>
+// WIN: some plan of the batch is one pass of an out-of-core plan, whose M
+// bitmap covers a key window: members outside it are dropped (compiled
+// separately, so that the whole-range scan keeps its registers).
+template <bool VEC, bool WIN>
 __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
   chain_begin();
   const int lane = threadIdx.x & 31;
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
     const TableView dt = table_view(q.dset_tag, *q.dset_log2, false);
     const u32* dt_keybm = dt.keybm;
     u32* sbm = reinterpret_cast<u32*>(q.ht_tag);  // dense layout: bm at 0
-    const u64 m_su = q.m_su, m_sb = q.m_sb;  // the plan's M key window
+    const u64 m_su = q.m_su, m_sb = WIN ? q.m_sb : 0;  // the plan's M key window
     const Pred32 pm = to32(q.pm);
     const i64 base = (t - b.tM[qi]) * q.m_tile;
     const int lim = (int)min(q.n_m - base, (i64)q.m_tile);
@@ -1036,7 +1039,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const u64 idx = ukey(k[s]) - m_su;
-        if (((m >> s) & 1u) && idx < m_sb) bit_set(sbm, idx), ++members;
+        if (((m >> s) & 1u) && (!WIN || idx < m_sb)) bit_set(sbm, idx), ++members;
       }
     };
     if (d_bits == 0) {
@@ -1046,7 +1049,7 @@ __global__ void __launch_bounds__(256, 3) k_plan_mscan_bm(Batch b) {
         if (!pass32(pm, ld_stream(pdate + r))) continue;
         if (!set_contains(dt, (i64)__ldg(pdref + r), keep)) continue;
         const u64 idx = ukey(__ldg(pkey + r)) - m_su;
-        if (idx < m_sb) bit_set(sbm, idx), ++members;
+        if (!WIN || idx < m_sb) bit_set(sbm, idx), ++members;
       }
     } else {
       // Slot p = it % 2 holds date and dref of step it (read two steps
@@ -1679,7 +1682,10 @@ __device__ __forceinline__ void part_sizes(const Batch& b) {
 // hit candidate and the probe decides.  The ring carries over from tile to
 // tile of the same plan.  The kernel does nothing else, so that it stays
 // small enough for four blocks per SM.
-template <bool VEC>
+// BUF: some plan of the batch buffers its hits (dynamic buffering of a
+// streamed F table): compiled separately, so that the resident scan keeps
+// its registers.
+template <bool VEC, bool BUF>
 __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
   chain_begin();
   __shared__ u32 s_hr[8][kHF];
@@ -1695,7 +1701,7 @@ __global__ void __launch_bounds__(256, 4) k_plan_fscan(Batch b) {
     u64 at = 0;
     if (lane == 0) at = atomicAdd(&q.ctr->hcount, (u64)cnt);
     at = __shfl_sync(kFull, at, 0);
-    if (q.hb_cap) {  // buffered: the hit's columns, not its row
+    if (BUF && q.hb_cap) {  // buffered: the hit's columns, not its row
       const i64* mk = ov ? (const i64*)b.ov.p[0] : q.f_mkey;
       const i64* pr = ov ? (const i64*)b.ov.p[1] : q.f_price;
       const signed char* ds = ov ? (const signed char*)b.ov.p[2] : q.f_disc;

@@ -258,6 +258,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
   d.dlist = (i64*)(ws + L.end);
   d.mlist = (i64*)(ws + L.end + al(r.n_d * 8));
   d.hlist = (u32*)(ws + L.end + al(r.n_d * 8) + al(r.n_m * 8));
+  set_kernel_variants(false, false);
   // Dynamic buffering (Sec. 5.3): a streamed F table's hits are gathered
   // into a buffer that holds `hit_buffer` chunks of rows (so it cannot
   // overflow), and the probe runs after every `hit_buffer` chunks and after
@@ -270,6 +271,7 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       d.hb_price = (i64*)(hb + al(cap * 8));
       d.hb_disc = (signed char*)(hb + 2 * al(cap * 8));
       d.hb_cap = cap;
+      set_kernel_variants(true, false);
     }
   }
   if (plog) {
@@ -540,6 +542,7 @@ namespace pqh {
 // place.  Plans whose streamed tables differ run one after another.
 pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_result* results,
                               cudaStream_t s) {
+  set_kernel_variants(false, false);
   std::vector<ResolvedPlan> R(n);
   for (int i = 0; i < n; ++i) {
     pq_status st = resolve_plan(ctx, plans[i], R[i], false);
