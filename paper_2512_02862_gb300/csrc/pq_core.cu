@@ -584,7 +584,10 @@ pq_status pq_table_free(pq_ctx* ctx, pq_table* t, void* stream) {
   if (!ctx || !t) return PQ_ERR_INVALID_ARG;
   cudaStream_t s = S(stream);
   forget_table(ctx, t->id, s);
-  for (auto& c : t->cols) ctx->arena.release(c.owned, s);
+  for (auto& c : t->cols) {
+    ctx->arena.release(c.owned, s);
+    ctx->arena.release(c.pres.block, s);
+  }
   delete t;
   return PQ_OK;
 }

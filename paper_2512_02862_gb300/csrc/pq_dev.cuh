@@ -172,6 +172,12 @@ __device__ __forceinline__ int2 ld_stream_v2i(const void* ptr, u64 pol) {
                : "l"(ptr), "l"(pol));
   return v;
 }
+// Four 64-bit values in one 256-bit load (32-byte aligned).
+__device__ __forceinline__ void ld_stream_v4l(const void* ptr, u64 pol, i64 v[4]) {
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s64 {%0, %1, %2, %3}, [%4], %5;"
+      : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3])
+      : "l"(ptr), "l"(pol));
+}
 __device__ __forceinline__ longlong2 ld_stream_v2(const void* ptr, u64 pol) {
   longlong2 v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s64 {%0, %1}, [%2], %3;"

@@ -141,6 +141,30 @@ struct KeyHist {
   bool known() const { return ready.load(std::memory_order_acquire); }
 };
 
+// Which keys of an integer key column's range occur in the column: a
+// bitmap over [umin, umax] with a rank directory (the dense dictionary's
+// layout: dense_layout(0, bits)), so that a key's rank among the column's
+// distinct keys is three loads.  Measured on the first aggregate-first plan
+// over the table, kept in an arena block the table owns.  Published like
+// KeyRange.
+struct KeyPresence {
+  std::atomic<bool> ready{false};
+  void* block = nullptr;
+  uint64_t bits = 0, distinct = 0;
+  // Bit j: the column's key-ordered segment j (rows from the j-th segment
+  // start of its KeyRange) is gapless: its distinct keys are consecutive
+  // among the column's distinct keys.
+  uint32_t gapless = 0;
+  KeyPresence() = default;
+  KeyPresence(const KeyPresence& o) { *this = o; }
+  KeyPresence& operator=(const KeyPresence& o) {
+    block = o.block, bits = o.bits, distinct = o.distinct, gapless = o.gapless;
+    ready.store(o.ready.load(std::memory_order_acquire), std::memory_order_release);
+    return *this;
+  }
+  bool known() const { return ready.load(std::memory_order_acquire); }
+};
+
 struct Column {
   int type = 0;           // pq_dtype
   bool packed = false;    // source is a packed column (PQ_SRC_PACKED)
@@ -154,6 +178,7 @@ struct Column {
   // measured on first use by a plan and kept (see KeyRange).
   mutable KeyRange range;
   mutable KeyHist hist;
+  mutable KeyPresence pres;
 };
 
 }  // namespace pqh

@@ -183,6 +183,68 @@ def test_key_ordered_segments(ctx, stream, nseg, narrow):
         t.free(stream)
 
 
+def gapless_chunks(seed, big_price=False, R=3000):
+    """F as key-ordered segments whose distinct keys are consecutive among
+    F's keys (gapless: every key once, with 1..7 rows, plus runs of 2047,
+    2048, 2049 and 6000 rows, so that runs cut 2048-row units and cover whole
+    ones; then a prefix of the keys; then a range that starts below the
+    prefix's end), followed by one segment with gaps (every third key of a
+    range).  big_price: prices up to
+    2^40, beyond the 32-bit revenue bound.  Every segment but the last is
+    padded with its last key to a multiple of 16 rows, so that each starts
+    16-byte aligned in every column (the staged scan); R keys."""
+    rng = np.random.default_rng(seed)
+    D = dict(key=np.arange(1, 101, dtype=np.int32), seg=rng.integers(0, 5, 100).astype(np.int8))
+    M = dict(key=np.arange(R, dtype=np.int64) * 4, dref=rng.integers(1, 101, R).astype(np.int32),
+             date=rng.integers(0, 2406, R).astype(np.int32))
+    rep = rng.integers(1, 8, R)
+    rep[[10, 500, 1200, R - 1]] = [2047, 2048, 6000, 2049]
+    a, b, c = R * 2 // 15, R // 10, R * 17 // 30
+    segs = [np.repeat(M["key"], rep),
+            np.repeat(M["key"][:a], rng.integers(1, 8, a)),
+            np.repeat(M["key"][b:c], rng.integers(1, 5, c - b)),
+            np.repeat(M["key"][R // 30:R * 2 // 3:3], rng.integers(1, 4, len(range(R // 30, R * 2 // 3, 3))))]
+    for i in range(3):
+        segs[i] = np.concatenate([segs[i], np.full(-len(segs[i]) % 16, segs[i][-1])])
+    mk = np.concatenate(segs).astype(np.int64)
+    n = len(mk)
+    hi = 1 << 40 if big_price else 10_500_000
+    F = dict(mkey=mk, price=rng.integers(-hi // 50, hi, n).astype(np.int64),
+             disc=rng.integers(0, 11, n).astype(np.int8),
+             date2=rng.integers(0, 2406, n).astype(np.int32))
+    return D, M, F
+
+
+@pytest.mark.parametrize("big_price,R", [(False, 3000), (True, 3000), (False, 600_000)],
+                         ids=["bounded", "tracked", "bounded-large"])
+def test_gapless_segments(ctx, stream, big_price, R):
+    """Gapless key-ordered segments (staged scan: a unit of rows per warp,
+    runs carried between its 128-row steps; R = 600,000 gives units of
+    several steps) beside a segment with gaps, whole and cut by row ranges
+    at aligned, odd and step-edge rows."""
+    D, M, F = gapless_chunks(11, big_price, R)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    cut = lambda t, r0, n: {c: v[r0:r0 + n] for c, v in t.items()}
+    n_f = len(F["mkey"])
+    for having in (I64_MIN, 0, 3_000_000_000):
+        for p in PREDS[:2]:
+            got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=p["seg"], m_date_lt=p["mc"],
+                                                f_date_gt=p["fc"], k=64, having=having))
+            same(got, oracle.run_plan_aggfirst(D, M, F, seg=p["seg"], m_date_lt=p["mc"],
+                                               f_date_gt=p["fc"], having=having, k=64),
+                 f"gapless {p} {having}")
+        for r0, n in ((0, 12_000), (16, n_f - 16), (2048, 4096), (1, n_f - 1), (2047, 6002),
+                      (n_f - 3000, 3000), (5, 1)):
+            got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=1, m_date_lt=2000, f_date_gt=300,
+                                                k=64, having=having, rows=dict(f=(r0, n))))
+            same(got, oracle.run_plan_aggfirst(D, M, cut(F, r0, n), seg=1, m_date_lt=2000,
+                                               f_date_gt=300, having=having, k=64),
+                 f"gapless rows {r0} {n} {having}")
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
 def mixed_plans(tables):
     """Aggregate-first and join-first plans over the same tables, with the
     oracle call that gives each one's result."""
