@@ -558,7 +558,7 @@ def run_ours(args):
     per_stage = {}
     for nm in ("plan_dscan", "plan_dfill", "plan_dbuild", "plan_mscan", "plan_mfill",
                "plan_mbuild", "plan_mrank", "plan_mdup", "plan_fscan", "plan_fprobe",
-               "plan_topk", "plan_topk2"):
+               "plan_topk"):
         try:
             ms, n = ctx.profile(nm)
             per_stage[nm] = round(ms / max(n, 1), 5)
@@ -960,8 +960,7 @@ def run_skew(args):
         ctx.profile_enable(False)
         stages = {}
         for nm in ("plan_dscan", "plan_mscan", "plan_mrank", "plan_mdup", "plan_fscan",
-                   "plan_fpart", "plan_fscatter", "plan_fagg", "plan_fprobe", "plan_topk",
-                   "plan_topk2"):
+                   "plan_fpart", "plan_fscatter", "plan_fagg", "plan_fprobe", "plan_topk"):
             try:
                 t, nl = ctx.profile(nm)
                 stages[nm] = round(t / max(nl, 1), 4)

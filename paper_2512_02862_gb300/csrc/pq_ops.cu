@@ -855,12 +855,12 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   __shared__ i64 sk[8 * kMaxK], ss[8 * kMaxK];
   __shared__ int sc[8];
   __shared__ bool s_last;
-  __shared__ i64 s_scr[8][64];
+  __shared__ i64 s_scr[8][kTopScr];
   chain_begin();
   const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
-  // Only the first nb blocks take pairs (at least 2048 each), so that a
-  // small count read on the device leaves few lists to merge.
-  const int nb = (int)max((i64)1, min((i64)gridDim.x, (n + 2047) / 2048));
+  // Only the first nb blocks take pairs (at least 256 each: one per thread),
+  // so that a small count read on the device leaves few lists to merge.
+  const int nb = (int)max((i64)1, min((i64)gridDim.x, (n + 255) / 256));
   const i64 per = (n + nb - 1) / nb;
   const i64 lo = min(n, per * blockIdx.x), hi = min(n, lo + per);
   TopList L;

@@ -290,8 +290,8 @@ size_t plan_bytes(const ResolvedPlan& r) {
   if (r.builds && r.dset_from == -1) b += dset_block_bytes(r.e_d);  // own D-set
   if (!r.dev.m_static) b += al(r.n_m * 8);                          // M list
   b += mside_bytes(r);                   // M dictionary or table
-  b += al(r.parts * 8) * 2 + al(r.parts * 4);                  // top-k tile maxima
-  b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k candidates
+  b += al(r.parts * 4);                                        // top-k list lengths
+  b += al(topk_cand_cap(r.e_m, r.dev.k) * 8) * 2;              // top-k tile lists
   b += al(r.n_f * 4);                                           // F hit list
   if (r.dev.part_log2)                                          // partitioned hits
     b += al(((1 << r.dev.part_log2) + 1) * 8) + al(r.n_f * 8) + al(r.n_f * 4) + al(r.n_f * 8);
@@ -311,8 +311,6 @@ void plan_assign(ResolvedPlan& r, char* base) {
   if (r.builds && r.dset_from == -1) dset_block_assign(take(dset_block_bytes(r.e_d)), r.e_d, d);
   d.mlist = d.m_static ? nullptr : (i64*)take(r.n_m * 8);
   d.ht_tag = (unsigned short*)take(mside_bytes(r));
-  d.tk_k = (i64*)take(r.parts * 8);
-  d.tk_s = (i64*)take(r.parts * 8);
   d.tk_c = (int*)take(r.parts * 4);
   d.cand_k = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
   d.cand_s = (i64*)take(topk_cand_cap(r.e_m, d.k) * 8);
@@ -368,8 +366,8 @@ Batch make_batch(pq_ctx* ctx, char* ws, int nq, const BatchLayout& L) {
 static const char* kPhaseName[] = {"plan_dscan", "plan_dfill",  "plan_dbuild", "plan_mscan",
                                    "plan_mfill", "plan_mbuild", "plan_mrank",  "plan_mdup",
                                    "plan_fscan", "plan_fpart",  "plan_fscatter", "plan_fagg",
-                                   "plan_fprobe", "plan_topk",  "plan_topk2"};
-static_assert(sizeof(kPhaseName) / sizeof(kPhaseName[0]) == kPhaseTopk2 + 1, "phase names");
+                                   "plan_fprobe", "plan_topk"};
+static_assert(sizeof(kPhaseName) / sizeof(kPhaseName[0]) == kPhaseTopk + 1, "phase names");
 
 pq_status plan_kernels_init(pq_ctx* ctx) {
   const void* fn[25] = {(const void*)k_plan_dscan<true>, (const void*)k_plan_fill,
@@ -377,7 +375,7 @@ pq_status plan_kernels_init(pq_ctx* ctx) {
                         (const void*)k_plan_fill,        (const void*)k_plan_mbuild,
                         (const void*)k_plan_fscan<false, false>, (const void*)k_plan_topk,
                         (const void*)k_plan_fscan<true, false>,  (const void*)k_plan_mscan<false, true>,
-                        (const void*)k_plan_topk2,       (const void*)k_plan_mrank,
+                        (const void*)k_plan_topk,        (const void*)k_plan_mrank,
                         (const void*)k_plan_mdup,        (const void*)k_plan_fprobe,
                         (const void*)k_plan_mscan<true, false>,
                         (const void*)k_plan_mscan<false, false>,
@@ -496,9 +494,6 @@ pq_status launch_phase(pq_ctx* ctx, int phase, const Batch& b, bool vec, cudaStr
     case kPhaseFagg: e = launch_chained(k_plan_fagg, plan_grid(ctx, 20, 1), 256, s, b); break;
     case kPhaseF: e = launch_chained(k_plan_fprobe, plan_grid(ctx, 13), 256, s, b); break;
     case kPhaseTopk: e = launch_chained(k_plan_topk, plan_grid(ctx, 7, 1), kTKW * 32, s, b); break;
-    case kPhaseTopk2:
-      e = launch_chained(k_plan_topk2, plan_grid(ctx, 10, 1), kTKW * 32, s, b);
-      break;
   }
   prof_end(stop, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "plan kernel launch");
@@ -836,7 +831,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   bool any_part = false;
   std::vector<std::pair<void*, size_t>> clears;  // static D bitmaps to zero first
   std::vector<std::pair<void*, size_t>> m_clears;  // static M bitmaps: the D scan clears them
-  i64 tmax[kPhaseTopk2 + 1] = {0};  // largest tile count of each phase
+  i64 tmax[kPhaseTopk + 1] = {0};  // largest tile count of each phase
   std::vector<char> host(L.upload_bytes());
   PlanDev* descs = (PlanDev*)host.data();
   i64* tD = (i64*)(host.data() + (L.tD - L.desc));
@@ -900,7 +895,6 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
   tmax[kPhaseFscan] = tF[n];
   tmax[kPhaseF] = 0;
   for (int i = 0; i < n; ++i) tmax[kPhaseF] += (R[i].n_f + 63) / 64;
-  tmax[kPhaseTopk2] = tmax[kPhaseTopk];
 
   cudaError_t ue = cudaSuccess;
   for (auto ev : waits)
@@ -923,7 +917,7 @@ pq_status run_batch_internal(pq_ctx* ctx, const pq_plan* plans, int n, pq_result
     for (auto& c : clears) PQ_CUDA(ctx, cudaMemsetAsync(c.first, 0, c.second, s));
     // The first phase that reads the M dictionary's directories.
     const int first_probe = any_part ? kPhaseFpart : kPhaseF;
-    for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk2; ++ph) {
+    for (int ph = any_build ? kPhaseD : kPhaseM; ph <= kPhaseTopk; ++ph) {
       // Phases only plans with key lists need.
       if (!list_d && (ph == kPhaseDfill || ph == kPhaseDbuild)) continue;
       if (!list_m && (ph == kPhaseMfill || ph == kPhaseMbuild)) continue;

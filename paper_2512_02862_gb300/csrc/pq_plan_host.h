@@ -100,8 +100,7 @@ void set_kernel_variants(bool buffered_hits, bool key_window);
 // with a partitioned plan; the F probe (kPhaseF) always runs, for the plans
 // that are not partitioned, and its last block sizes the top-k for all.
 enum { kPhaseD = 0, kPhaseDfill, kPhaseDbuild, kPhaseM, kPhaseMfill, kPhaseMbuild, kPhaseMrank,
-       kPhaseMdup, kPhaseFscan, kPhaseFpart, kPhaseFscatter, kPhaseFagg, kPhaseF, kPhaseTopk,
-       kPhaseTopk2 };
+       kPhaseMdup, kPhaseFscan, kPhaseFpart, kPhaseFscatter, kPhaseFagg, kPhaseF, kPhaseTopk };
 inline bool part_phase(int ph) {
   return ph == kPhaseFpart || ph == kPhaseFscatter || ph == kPhaseFagg;
 }

@@ -55,13 +55,6 @@ struct QCtr {
   u64 m_umin;  // M bitmap: ukey of bit 0
   u64 m_bits;  // M bitmap: bit count (0 = no bitmap)
   u64 pad[2];
-  // Top-k: admission threshold (a record qualifies when it is not after
-  // (thr_s, thr_k) in the output order; thr_all: every record qualifies),
-  // candidate count, ticket of the selection pass.
-  i64 thr_k, thr_s;
-  int thr_all;
-  u32 tk_ticket2;
-  u64 ccount;
   // Regions the D and M fills clear: byte offset from the table's start and
   // 16-byte units (set by the scans' last blocks).
   u64 d_fill_off, d_fill_units, m_fill_off, m_fill_units;
@@ -127,12 +120,13 @@ __host__ __device__ __forceinline__ i64 fill_tiles(int e, bool with_sums, u64 bi
 }
 
 // Top-k tiles of an M table of 2^e slots: ranges of its first-hit bitmap,
-// at least 32 words each and at most 128 tiles per table (so that the
-// threshold is taken over at most 128 tile maxima).
+// at least 32 words each and at most kTKP tiles per table (so that the
+// last tile's threshold is taken over at most kTKP tile maxima).
+constexpr int kTKP = 256;  // most top-k tiles of a plan
 __host__ __device__ __forceinline__ i64 topk_tile_words(int e) {
   const i64 words = ((1LL << e) + 31) >> 5;
   i64 tw = 32;
-  while ((words + tw - 1) / tw > 128) tw <<= 1;
+  while ((words + tw - 1) / tw > kTKP) tw <<= 1;
   return tw;
 }
 __host__ __device__ __forceinline__ i64 topk_parts(int e) {
@@ -140,9 +134,9 @@ __host__ __device__ __forceinline__ i64 topk_parts(int e) {
   const i64 tw = topk_tile_words(e);
   return (words + tw - 1) / tw;
 }
-// Candidates of the selection pass: records not after the K-th best tile
-// maximum.  Only the K tiles with the best maxima can hold such records, so
-// K tiles' worth of slots (or the whole table) always suffices.
+// Entries of the tiles' top-K lists: at most kTKP (256) tiles of at least
+// 1024 slots each, so K lists fit in K tiles' worth of slots (or the whole
+// table).
 __host__ __device__ __forceinline__ i64 topk_cand_cap(int e, int K) {
   const i64 slots = 1LL << e, tile_slots = topk_tile_words(e) * 32;
   return slots < (i64)K * tile_slots ? slots : (i64)K * tile_slots;
@@ -188,7 +182,7 @@ __host__ __device__ __forceinline__ DenseLayout dense_layout(i64 c, u64 bits) {
 // slots, or the dense dictionary's slots).
 __host__ __device__ __forceinline__ i64 topk_tile_words_w(i64 words) {
   i64 tw = 32;
-  while ((words + tw - 1) / tw > 128) tw <<= 1;  // at most 128 tiles
+  while ((words + tw - 1) / tw > kTKP) tw <<= 1;  // at most kTKP tiles
   return tw;
 }
 
@@ -306,11 +300,9 @@ struct PlanDev {
   unsigned short* dset_tag;  // D-set table (keys only), laid out by table_layout
   i64* mlist;
   unsigned short* ht_tag;    // M table ({key, sum} records), laid out by table_layout
-  i64* tk_k;    // top-k: per tile, the best record (key, sum) and
-  i64* tk_s;    // whether the tile has any group
-  int* tk_c;
-  i64* cand_k;  // top-k candidates (topk_cand_cap entries)
-  i64* cand_s;
+  int* tk_c;    // top-k: per tile, the length of its list
+  i64* cand_k;  // top-k: per tile, its sorted list of K (key, sum) records
+  i64* cand_s;  // (topk_cand_cap entries hold every tile's)
   u32* hlist;   // F rows that hit (n_f entries, rows of the plan)
   // Partitioned F phase (PQ_PLAN_PARTITIONED): the hits are radix-
   // partitioned by group slot into 2^part_log2 buckets (part_shift) before
@@ -369,7 +361,7 @@ struct Batch {
 };
 
 enum { kPhDscan = 0, kPhDfill, kPhDbuild, kPhMscan, kPhMfill, kPhMbuild, kPhFprobe, kPhTopk,
-       kPhTopk2, kPhMrank, kPhMdup, kPhFscan, kPhFpart, kPhFagg, kPhFscatter };
+       kPhMrank, kPhMdup, kPhFscan, kPhFpart, kPhFagg, kPhFscatter };
 
 // Largest fan-out of a partitioned plan (buckets 2^kMaxPartLog2), hits per
 // block tile of its partition and scatter passes, records per warp tile of
@@ -1210,26 +1202,57 @@ __device__ __forceinline__ u64 dense_rank(const DenseView& d, u64 idx, u64 keep)
   return (u64)t + wp + __popc(w & ((1u << (idx & 31)) - 1u));
 }
 
-// Key of dense slot `rank` (< distinct keys): the rank-th set bit.
-__device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank) {
-  const u64 tiles = (d.blocks + kRankTile - 1) / kRankTile;
-  u64 lo = 0, hi = tiles;  // tdir[tiles] = total > rank
+// Last index i in [lo, hi) with a[i] <= x, for a non-decreasing a with
+// a[lo] <= x: a 16-ary search (15 independent loads per round, so that a
+// round costs one memory latency).
+template <typename T>
+__device__ __forceinline__ u64 last_le(const T* a, u64 lo, u64 hi, u64 x) {
   while (hi - lo > 1) {
-    const u64 mid = (lo + hi) >> 1;
-    if (d.tdir[mid] <= rank) lo = mid;
-    else hi = mid;
+    const u64 step = (hi - lo + 15) / 16;
+    u32 c = 0;
+#pragma unroll
+    for (int j = 1; j < 16; ++j) {
+      const u64 p = lo + j * step;
+      c += p < hi && (u64)a[p] <= x;
+    }
+    hi = min(hi, lo + (c + 1) * step);
+    lo += c * step;
   }
-  u32 r = (u32)(rank - d.tdir[lo]);
-  const u64 words = d.blocks * 16;
-  u64 w0 = lo * kRankTile * 16, w1 = min(words, w0 + kRankTile * 16);
-  while (w1 - w0 > 1) {  // last word of the tile with wdir <= r
-    const u64 mid = (w0 + w1) >> 1;
-    if (d.wdir[mid] <= r) w0 = mid;
-    else w1 = mid;
-  }
-  r -= d.wdir[w0];
+  return lo;
+}
+
+// last_le with a first guess g: a window of 16 entries around g is read at
+// once (one memory latency when the answer lies in it, as it does for keys
+// spread evenly); otherwise the search goes on on the side the window shows.
+template <typename T>
+__device__ __forceinline__ u64 last_le_near(const T* a, u64 lo, u64 hi, u64 x, u64 g) {
+  if (hi - lo <= 16) return last_le(a, lo, hi, x);
+  g = min(max(g, lo), hi - 1);
+  const u64 w0 = min(g > lo + 7 ? g - 7 : lo, hi - 16);
+  u32 le = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) le += (u64)a[w0 + j] <= x;  // a prefix of the window
+  if (le == 0) return last_le(a, lo, w0, x);
+  if (le == 16 && w0 + 16 < hi) return last_le(a, w0 + 15, hi, x);
+  return w0 + le - 1;
+}
+
+// Key of dense slot `rank` (< total, the distinct keys): the rank-th set
+// bit.  The tile and the word are first looked for where an even spread of
+// the keys puts them.
+__device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank, u64 total) {
+  const u64 tiles = (d.blocks + kRankTile - 1) / kRankTile;
+  const u64 tg = total ? (u64)((unsigned __int128)rank * tiles / total) : 0;
+  const u64 t = last_le_near(d.tdir, 0, tiles, rank, tg);  // tdir[tiles] = total > rank
+  const u32 r = (u32)(rank - d.tdir[t]);
+  const u64 words = d.blocks * 16, w_lo = t * kRankTile * 16,
+            w_hi = min(words, (t + 1) * kRankTile * 16);
+  const u32 tbits = (u32)(d.tdir[t + 1] - d.tdir[t]);
+  const u64 wg = w_lo + (tbits ? (u64)r * (w_hi - w_lo) / tbits : 0);
+  const u64 w0 = last_le_near(d.wdir, w_lo, w_hi, r, wg);
+  u32 rr = r - d.wdir[w0];
   u32 x = d.bm[w0];
-  for (; r; --r) x &= x - 1;
+  for (; rr; --rr) x &= x - 1;
   const u64 u = umin + w0 * 32 + (u64)(__ffs(x) - 1);
   return (i64)(u ^ (1ULL << 63));
 }
@@ -2201,20 +2224,14 @@ __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
 }
 
 // ------------------------------------------------------------------- topk ----
-// Two passes over the M table's first-hit bitmap, tiled in block tiles
+// One pass over the M table's first-hit bitmap, tiled in block tiles
 // (topk_tile_words; each of a block's 4 warps takes a quarter).  A warp reads
 // 8 steps of 32 words (one per lane and step) at a time, writes the slots of
 // their set bits into its shared-memory ring, and reads the ring's records
-// 256 at a time (8 in flight per lane).
-//  A: every tile keeps its best record and counts its groups; the block that
-//     finishes a plan's last tile ranks the tile maxima in parallel and takes
-//     the K-th best as the threshold (no threshold with fewer than K
-//     non-empty tiles).  At least K records are not after it, so the top K
-//     are among the records that are not after it.
-//  B: the records not after the threshold are appended to the candidate
-//     list; the block that finishes the plan's last tile selects the top K
-//     of the candidates (four warp lists merged in shared memory) and writes
-//     the result with the group count.
+// 256 at a time (8 in flight per lane) into its top-K list.  A block merges
+// its warps' lists in shared memory and stores the tile's sorted list; the
+// block that finishes a plan's last tile merges the tiles' lists and writes
+// the result with the group count.
 constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
 constexpr int kTKW = 4;     // warps per top-k block
 
@@ -2262,7 +2279,7 @@ __device__ __forceinline__ TopkSrc topk_src(const PlanDev& q) {
 __device__ __forceinline__ i64 topk_out_key(const PlanDev& q, bool dense, i64 k) {
   if (!dense) return k;
   return dense_key(dense_view(q.ht_tag, (i64)q.ctr->mcount, q.ctr->m_bits), q.ctr->m_umin,
-                   (u64)k);
+                   (u64)k, q.ctr->m_distinct);
 }
 
 template <typename On>
@@ -2324,96 +2341,160 @@ __device__ __forceinline__ u64 tk_scan(const TopkSrc& src, i64 tw, i64 lt, u32* 
   return groups;
 }
 
+// Branch-free record order (a before b) for the rank counts below.
+__device__ __forceinline__ int ks_bef(i64 ak, i64 as, i64 bk, i64 bs) {
+  return (int)(as > bs) | ((int)(as == bs) & (int)(ak < bk));
+}
+// Rank of (xk, xs) among n records in shared memory (keys k, sums s): the
+// records before it, counted with four independent sums per step so that
+// the reads overlap.
+__device__ __forceinline__ int rank_among(const i64* k, const i64* s, int n, i64 xk, i64 xs) {
+  int r0 = 0, r1 = 0, r2 = 0, r3 = 0, j = 0;
+  for (; j + 4 <= n; j += 4) {
+    r0 += ks_bef(k[j], s[j], xk, xs);
+    r1 += ks_bef(k[j + 1], s[j + 1], xk, xs);
+    r2 += ks_bef(k[j + 2], s[j + 2], xk, xs);
+    r3 += ks_bef(k[j + 3], s[j + 3], xk, xs);
+  }
+  for (; j < n; ++j) r0 += ks_bef(k[j], s[j], xk, xs);
+  return r0 + r1 + r2 + r3;
+}
+
+// A lane's best kLL records of a tile, sorted (registers), and the best
+// record it dropped.
+constexpr int kLL = 4;
+struct LaneTop {
+  i64 k[kLL], s[kLL];
+  int n;
+  i64 dk, ds;
+  bool dv;
+  __device__ __forceinline__ void clear() { n = 0, dv = false, dk = ds = 0; }
+  __device__ __forceinline__ void drop(i64 xk, i64 xs) {
+    if (!dv || ks_bef(xk, xs, dk, ds)) dk = xk, ds = xs, dv = true;
+  }
+  __device__ __forceinline__ void insert(i64 xk, i64 xs) {
+    if (n == kLL) {
+      if (!ks_bef(xk, xs, k[kLL - 1], s[kLL - 1])) {
+        drop(xk, xs);
+        return;
+      }
+      drop(k[kLL - 1], s[kLL - 1]);
+    } else {
+      ++n;
+    }
+    // The new record at position n - 1, then one bubble pass upwards.
+#pragma unroll
+    for (int i = 0; i < kLL; ++i)
+      if (i == n - 1) k[i] = xk, s[i] = xs;
+#pragma unroll
+    for (int i = kLL - 1; i > 0; --i)
+      if (i < n && ks_bef(k[i], s[i], k[i - 1], s[i - 1])) {
+        const i64 tk = k[i], ts = s[i];
+        k[i] = k[i - 1], s[i] = s[i - 1];
+        k[i - 1] = tk, s[i - 1] = ts;
+      }
+  }
+};
+
+// The plan's last tile: the top K of the tiles' sorted lists, merged by one
+// warp in K rounds (dense slots follow key order; the K results become keys
+// at the end).  Lane l owns tiles l, l + 32, ...
+// and offers the best head among them; a round takes the best offer (warp
+// max reductions over the record's 128-bit order value, most significant
+// word first, until one lane is left) and advances that tile.  The lists are
+// first copied to shared memory when they fit.
+__device__ __forceinline__ void topk_final(const PlanDev& q, int K, int parts, bool dense,
+                                           u32* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // The dense dictionary's constants (for slot -> key), read beside the lists.
+  const u64 m_n = dense ? q.ctr->mcount : 0, m_bits = dense ? q.ctr->m_bits : 0;
+  const u64 m_umin = dense ? q.ctr->m_umin : 0, m_tot = dense ? q.ctr->m_distinct : 0;
+  int* lc = reinterpret_cast<int*>(scratch);  // list lengths
+  int* lp = lc + kTKP;                         // heads
+  i64* sk = reinterpret_cast<i64*>(lp + kTKP);
+  const int all = parts * K;
+  const bool fit = (size_t)all * 16 + kTKP * 8 <= (size_t)kTKW * kTKR * 4;
+  i64* ss = sk + (fit ? all : 0);
+  for (int i = threadIdx.x; i < parts; i += blockDim.x) lc[i] = __ldcg(q.tk_c + i), lp[i] = 0;
+  if (fit) {  // 8 entries per thread in flight
+    for (int e0 = threadIdx.x; e0 < all; e0 += 8 * blockDim.x) {
+      i64 xk[8], xs[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        xk[u] = e < all ? __ldcg(q.cand_k + e) : 0;
+        xs[u] = e < all ? __ldcg(q.cand_s + e) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < all) sk[e] = xk[u], ss[e] = xs[u];
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  const i64* lk = fit ? sk : q.cand_k;
+  const i64* ls = fit ? ss : q.cand_s;
+  // The best head among this lane's tiles (t = -1: none).
+  auto best_of = [&](int& t, i64& bk, i64& bs) {
+    t = -1;
+    for (int i = lane; i < parts; i += 32) {
+      if (lp[i] >= lc[i]) continue;
+      const i64 e = (i64)i * K + lp[i];
+      const i64 xk = fit ? lk[e] : __ldcg(lk + e), xs = fit ? ls[e] : __ldcg(ls + e);
+      if (t < 0 || ks_bef(xk, xs, bk, bs)) t = i, bk = xk, bs = xs;
+    }
+  };
+  int t;
+  i64 bk = 0, bs = 0;
+  best_of(t, bk, bs);
+  __shared__ i64 f_k[kMaxK], f_s[kMaxK];  // the merged entries (slots when dense)
+  int n = 0;
+  for (; n < K; ++n) {
+    u32 act = __ballot_sync(kFull, t >= 0);
+    if (!act) break;
+    // Order value: sum (signed order) then key (smaller first), as 4 words.
+    const u64 hi = (u64)bs ^ (1ULL << 63), lo = ~((u64)bk ^ (1ULL << 63));
+    const u32 w[4] = {(u32)(hi >> 32), (u32)hi, (u32)(lo >> 32), (u32)lo};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (__popc(act) == 1) break;
+      const bool in = (act >> lane) & 1u;
+      const u32 m = __reduce_max_sync(kFull, in ? w[j] : 0u);
+      act &= __ballot_sync(kFull, in && w[j] == m);
+    }
+    const int win = __ffs(act) - 1;
+    if (lane == win) {
+      f_k[n] = bk, f_s[n] = bs;
+      ++lp[t];
+      best_of(t, bk, bs);
+    }
+    __syncwarp();
+  }
+  // Each lane converts and writes the entries at its rank.
+  for (int i = lane; i < n; i += 32) {
+    i64 k = f_k[i];
+    if (dense)
+      k = dense_key(dense_view(q.ht_tag, (i64)m_n, m_bits), m_umin, (u64)k, m_tot);
+    q.out->keys[i] = k, q.out->sums[i] = f_s[i];
+  }
+  if (lane == 0) {
+    q.out->n = n;
+    q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
+  }
+}
+
 __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
   chain_begin();
   __shared__ __align__(16) u32 s_ring[kTKW][kTKR];
-  __shared__ KS s_best[kTKW];
-  __shared__ int s_thr_found;
-  __shared__ i64 s_t;
-  __shared__ bool s_last;
-  const i64* pre = b.dyn + 4 * (b.nq + 1);
-  const i64 total = pre[b.nq];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  BlockClaim bc;
-  while (true) {
-    const i64 t = bc.next(b.work, kPhTopk, &s_t);
-    if (t >= total) break;
-    const int qi = find_q(pre, b.nq, t);
-    const PlanDev& q = b.q[qi];
-    const TopkSrc src = topk_src(q);
-    const i64 tw = topk_tile_words_w(src.words);
-    const i64 lt = t - pre[qi];
-    KS best = {0, 0, false};
-    u64 groups = tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ks_before(r[u], best)) best = r[u];
-    });
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      KS x;
-      x.k = __shfl_xor_sync(kFull, best.k, o);
-      x.s = __shfl_xor_sync(kFull, best.s, o);
-      x.v = __shfl_xor_sync(kFull, best.v, o);
-      if (ks_before(x, best)) best = x;
-      groups += __shfl_xor_sync(kFull, groups, o);
-    }
-    if (lane == 0) {
-      s_best[warp] = best;
-      if (groups) atomicAdd(&q.ctr->gcount, groups);
-    }
-    __syncthreads();
-    const int parts = (int)(pre[qi + 1] - pre[qi]);
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < kTKW; ++w)
-        if (ks_before(s_best[w], best)) best = s_best[w];
-      q.tk_k[lt] = best.k;
-      q.tk_s[lt] = best.s;
-      q.tk_c[lt] = best.v ? 1 : 0;
-      __threadfence();
-      s_last = (int)atomicAdd(&q.ctr->tk_ticket, 1u) == parts - 1;
-    }
-    __syncthreads();
-    if (!s_last) continue;
-    // Last tile of the plan: rank the tile maxima (all pairs, in shared
-    // memory; the maxima are distinct records, so the ranks are distinct)
-    // and take the K-th best as the threshold.
-    __threadfence();
-    KS* sm = reinterpret_cast<KS*>(&s_ring[0][0]);  // parts <= 128 entries
-    if (threadIdx.x == 0) s_thr_found = 0;
-    for (int i = threadIdx.x; i < parts; i += blockDim.x) {
-      KS x;
-      x.v = __ldcg(q.tk_c + i) != 0;
-      x.k = x.v ? __ldcg(q.tk_k + i) : 0;
-      x.s = x.v ? __ldcg(q.tk_s + i) : 0;
-      sm[i] = x;
-    }
-    __syncthreads();
-    const int K = q.k;
-    for (int i = threadIdx.x; i < parts; i += blockDim.x) {
-      const KS x = sm[i];
-      if (!x.v) continue;
-      int r = 0;
-      for (int j = 0; j < parts; ++j) r += ks_before(sm[j], x);
-      if (r == K - 1) {
-        q.ctr->thr_k = x.k;
-        q.ctr->thr_s = x.s;
-        s_thr_found = 1;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) q.ctr->thr_all = s_thr_found ? 0 : 1;
-  }
-  finish(b.work, kPhTopk);
-}
-
-__global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
-  chain_begin();
-  __shared__ u32 s_ring[kTKW][kTKR];
-  __shared__ i64 s_scr[kTKW][64];
+  __shared__ i64 s_scr[kTKW][kTopScr];
   __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
   __shared__ int s_mc[kTKW];
-  __shared__ i64 s_t;
+  __shared__ i64 s_hk[kTKW * 32], s_hs[kTKW * 32];      // lane heads
+  __shared__ i64 s_ck[kLL * 32], s_cs[kLL * 32];        // a tile's candidates
+  __shared__ i64 s_t, s_thk, s_ths, s_kk, s_ks;
+  __shared__ int s_nh, s_nc, s_found, s_cnt;
   __shared__ bool s_last;
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
@@ -2422,7 +2503,7 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
   L.bind(s_scr[warp]);
   BlockClaim bc;
   while (true) {
-    const i64 t = bc.next(b.work, kPhTopk2, &s_t);
+    const i64 t = bc.next(b.work, kPhTopk, &s_t);
     if (t >= total) break;
     const int qi = find_q(pre, b.nq, t);
     const PlanDev& q = b.q[qi];
@@ -2430,76 +2511,90 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk2(Batch b) {
     const TopkSrc src = topk_src(q);
     const i64 tw = topk_tile_words_w(src.words);
     const i64 lt = t - pre[qi];
-    const KS thr = {q.ctr->thr_k, q.ctr->thr_s, true};
-    const bool all = q.ctr->thr_all != 0;
-    const u64 cap = (u64)min((i64)topk_cand_cap(q.ctr->mlog2, K), (i64)K * tw * 32);
-    tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const bool keep = r[u].v && (all || !ks_before(thr, r[u]));
-        const u32 m = __ballot_sync(kFull, keep);
-        if (!m) continue;
-        u64 at = 0;
-        if (lane == __ffs(m) - 1) at = atomicAdd(&q.ctr->ccount, (u64)__popc(m));
-        at = __shfl_sync(kFull, at, __ffs(m) - 1) + __popc(m & lanemask_lt());
-        if (keep && at < cap) q.cand_k[at] = r[u].k, q.cand_s[at] = r[u].s;
-        if (keep && at >= cap) q_latch(q.ctr, b.st, PQ_ERR_CAPACITY, (i64)at);  // not reached
-      }
-    });
-    __syncthreads();
     const int parts = (int)(pre[qi + 1] - pre[qi]);
+    i64* tk = q.cand_k + lt * K;
+    i64* ts = q.cand_s + lt * K;
+    // The tile's top K.  K <= 32: each lane keeps its best kLL records;
+    // thr = the K-th best of the lanes' best; the entries not after thr (at
+    // most kLL from each of K lanes) are ranked.  Exact unless a lane dropped
+    // a record that is not after the K-th result; then (and for K > 32) the
+    // tile is scanned again into per-warp lists merged in shared memory.
+    bool done = false;
+    u64 groups = 0;
+    if (K <= 32) {
+      LaneTop T;
+      T.clear();
+      groups = tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (r[u].v) T.insert(r[u].k, r[u].s);
+      });
+      if (threadIdx.x == 0) s_nh = 0, s_nc = 0, s_found = 0;
+      __syncthreads();
+      if (T.n) {
+        const int h = atomicAdd(&s_nh, 1);
+        s_hk[h] = T.k[0], s_hs[h] = T.s[0];
+      }
+      __syncthreads();
+      if (T.n && rank_among(s_hk, s_hs, s_nh, T.k[0], T.s[0]) == K - 1)
+        s_thk = T.k[0], s_ths = T.s[0], s_found = 1;
+      __syncthreads();
+      const bool every = s_found == 0;
+      const i64 thk = s_thk, ths = s_ths;
+#pragma unroll
+      for (int i = 0; i < kLL; ++i)
+        if (i < T.n && (every || !ks_bef(thk, ths, T.k[i], T.s[i]))) {
+          const int c = atomicAdd(&s_nc, 1);
+          s_ck[c] = T.k[i], s_cs[c] = T.s[i];
+        }
+      __syncthreads();
+      const int nc = s_nc, nres = min(K, nc);
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const i64 xk = s_ck[c], xs = s_cs[c];
+        const int r = rank_among(s_ck, s_cs, nc, xk, xs);
+        if (r < K) tk[r] = xk, ts[r] = xs;
+        if (r == K - 1) s_kk = xk, s_ks = xs;
+      }
+      __syncthreads();
+      const bool bad = T.dv && !(nres == K && ks_bef(s_kk, s_ks, T.dk, T.ds));
+      done = !__syncthreads_or(bad);
+      if (done && threadIdx.x == 0) s_cnt = nres;
+    }
+    if (!done) {
+      L.clear();
+      const u64 g = tk_scan(src, tw, lt, s_ring[warp], [&](const KS* r) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) L.offer(K, r[u].v, r[u].k, r[u].s);
+      });
+      if (K > 32) groups = g;
+      tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
+      if (warp == 0) {
+        L.store(tk, ts);
+        if (lane == 0) s_cnt = L.cnt;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) groups += __shfl_xor_sync(kFull, groups, o);
+    if (lane == 0 && groups) atomicAdd(&q.ctr->gcount, groups);
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) {
+      q.tk_c[lt] = s_cnt;
       __threadfence();
-      s_last = (int)atomicAdd(&q.ctr->tk_ticket2, 1u) == parts - 1;
+      s_last = (int)atomicAdd(&q.ctr->tk_ticket, 1u) == parts - 1;
     }
     __syncthreads();
-    if (!s_last) continue;
-    // Last tile: the top K of the candidates, a quarter per warp, then the
-    // warps' lists merged in shared memory.
-    __threadfence();
-    const i64 c = min((i64)ld_volatile_u64(&q.ctr->ccount), (i64)cap);
-    if (c <= 32 && K <= 32) {  // usual case: one warp sorts the candidates
-      if (warp == 0) {
-        bool v = lane < c;
-        i64 ck = v ? __ldcg(q.cand_k + lane) : 0, cs = v ? __ldcg(q.cand_s + lane) : 0;
-        tk_sort32(ck, cs, v);
-        if (lane < K && v) q.out->keys[lane] = topk_out_key(q, src.dense, ck), q.out->sums[lane] = cs;
-        if (lane == 0) {
-          q.out->n = (int)min((i64)K, c);
-          q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
-        }
-      }
+    if (!s_last) {
+      if (gridDim.x >= total) break;
       continue;
     }
-    const i64 per = (c + kTKW - 1) / kTKW;
-    const i64 c0 = min(c, warp * per), c1 = min(c, c0 + per);
-    L.clear();
-    for (i64 j = c0; j < c1; j += 256) {
-      bool v[8];
-      i64 ck[8], cs[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const i64 x = j + u * 32 + lane;
-        v[u] = x < c1;
-        ck[u] = v[u] ? __ldcg(q.cand_k + x) : 0;
-        cs[u] = v[u] ? __ldcg(q.cand_s + x) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) L.offer(K, v[u], ck[u], cs[u]);
-    }
-    tk_block_merge_all(L, K, s_mk, s_ms, s_mc);
-    if (warp == 0) {
-      L.store((i64*)q.out->keys, (i64*)q.out->sums);
-      for (int i = lane; i < L.cnt; i += 32)  // each lane converts what it stored
-        q.out->keys[i] = topk_out_key(q, src.dense, q.out->keys[i]);
-      if (lane == 0) {
-        q.out->n = L.cnt;
-        q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
-      }
-    }
+    __threadfence();
+    topk_final(q, K, parts, src.dense, &s_ring[0][0]);
+    if (gridDim.x >= total) break;  // one tile per block: no ticket needed to stop
   }
-  finish(b.work, kPhTopk2);
+  finish(b.work, kPhTopk);
 }
+
 
 #endif  // PQ_DEFINE_PLAN_KERNELS
 

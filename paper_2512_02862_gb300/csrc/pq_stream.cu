@@ -489,14 +489,10 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
       }
     } else {
       const i64 parts = topk_parts(e), cap = topk_cand_cap(e, d.k);
-      char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 8) * 2 + al(parts * 4) +
+      char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 4) +
                                  al(cap * 8) * 2);
       if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming plan: M table of 2^%d slots", e);
       char* p = mtable_assign(blk, e, d);
-      d.tk_k = (i64*)p;
-      p += al(parts * 8);
-      d.tk_s = (i64*)p;
-      p += al(parts * 8);
       d.tk_c = (int*)p;
       p += al(parts * 4);
       d.cand_k = (i64*)p;
@@ -510,7 +506,6 @@ pq_status run_plan_streaming(pq_ctx* ctx, const pq_plan* plan, pq_result* result
     }
   }
   st = launch_phase(ctx, kPhaseTopk, b, true, s);
-  if (st == PQ_OK) st = launch_phase(ctx, kPhaseTopk2, b, true, s);
   if (st != PQ_OK) return st;
   ctx->plans++;
   const size_t bytes = sizeof(pq_result);
@@ -845,14 +840,10 @@ pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_resul
         PQ_CUDA(ctx, cudaMemcpyAsync(d.dset_log2, dset_ph[i], 24, cudaMemcpyDeviceToDevice, s));
       } else {
         const i64 parts = topk_parts(e), cap = topk_cand_cap(e, d.k);
-        char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 8) * 2 + al(parts * 4) +
+        char* blk = (char*)scr.get(mtable_bytes(e) + al(parts * 4) +
                                    al(cap * 8) * 2);
         if (!blk) return fail(ctx, PQ_ERR_BUDGET, "streaming batch: M table of 2^%d slots", e);
         char* p = mtable_assign(blk, e, d);
-        d.tk_k = (i64*)p;
-        p += al(parts * 8);
-        d.tk_s = (i64*)p;
-        p += al(parts * 8);
         d.tk_c = (int*)p;
         p += al(parts * 4);
         d.cand_k = (i64*)p;
@@ -871,7 +862,6 @@ pq_status run_batch_streaming(pq_ctx* ctx, const pq_plan* plans, int n, pq_resul
     }
   }
   st = launch_phase(ctx, kPhaseTopk, b, true, s);
-  if (st == PQ_OK) st = launch_phase(ctx, kPhaseTopk2, b, true, s);
   if (st != PQ_OK) return st;
   ctx->plans += n;
   return read_back(ctx, results, out, n, s);

@@ -4,16 +4,17 @@
 // A warp keeps its best K <= 64 entries sorted in registers: lane j holds
 // entries j and 32 + j.  Candidates are tested 32 at a time against the
 // current K-th entry, so after the list fills most candidates cost one
-// comparison.  For K <= 32 the candidates that beat it enter together: a few
-// of them by rank (each list entry and candidate counts what precedes it in
-// the merged order, one broadcast per candidate; the first K land in place
-// through a 32-entry shared-memory scratch per warp), more of them by a
-// bitonic sort of the 32 lanes followed by a bitonic merge with the list.
-// For larger K they enter one by one with a warp-wide shift.
+// comparison.  For K <= 32 the candidates that beat it enter together, by
+// rank: the list and the candidates are written to a per-warp shared-memory
+// scratch, each entry counts what precedes it in the merged order, and the
+// first K land in place (no chain of shuffles).  For larger K they enter one
+// by one with a warp-wide shift.
 #pragma once
 #include "pq_dev.cuh"
 
 namespace pqk {
+
+constexpr int kTopScr = 128;  // i64 entries of a warp's TopList scratch
 
 __device__ __forceinline__ bool tk_before(i64 ka, i64 sa, i64 kb, i64 sb) {
   return sa > sb || (sa == sb && ka < kb);
@@ -49,7 +50,8 @@ __device__ __forceinline__ void tk_sort32(i64& k, i64& s, bool& v) {
 struct TopList {
   i64 k0, s0, k1, s1;  // entries lane and 32 + lane
   int cnt;             // warp-uniform number of valid entries
-  i64* scr;            // the warp's scratch: 32 keys, then 32 sums (K <= 32)
+  i64* scr;            // the warp's scratch (kTopScr entries): keys at [0, 64), sums at
+                       // [64, 128); list entries at [0, 32), candidates at [32, 64)
 
   __device__ void clear() {
     k0 = k1 = 0;
@@ -94,49 +96,45 @@ struct TopList {
     cnt = cnt + 1 < K ? cnt + 1 : K;
   }
 
-  // Merge the candidates of the lanes in m (K <= 32).  The merged order is
-  // (sum desc, key asc), then list entries before equal candidates, then
-  // candidates by lane, so every rank is distinct.
-  __device__ __forceinline__ void merge32(int K, u32 m, bool want, i64 ck, i64 cs) {
+  // Merge the candidates of the lanes in m (K <= 32) by rank: the list and
+  // the candidates go to shared memory, every list entry and candidate
+  // counts the entries that precede it in the merged order (broadcast reads,
+  // independent of one another), and the first K land in place.  The merged
+  // order is (sum desc, key asc), then list entries before equal
+  // candidates, then candidates by lane, so every rank is distinct.
+  __device__ __forceinline__ void merge_rank(int K, u32 m, bool want, i64 ck, i64 cs) {
     const int lane = threadIdx.x & 31;
+    i64* sk = scr;
+    i64* ss = scr + 64;
+    sk[lane] = k0, ss[lane] = s0;
+    sk[32 + lane] = ck, ss[32 + lane] = cs;
+    __syncwarp();
     const bool has = lane < cnt;
     int re = lane;  // rank of this lane's list entry
     int rc = 0;     // rank of this lane's candidate
-    for (u32 mm = m; mm; mm &= mm - 1) {
-      const int j = __ffs(mm) - 1;
-      const i64 bk = __shfl_sync(kFull, ck, j), bs = __shfl_sync(kFull, cs, j);
-      const bool cand_first = has && tk_before(bk, bs, k0, s0);
-      re += cand_first;
-      const int before_j = __popc(__ballot_sync(kFull, has && !cand_first));
-      if (lane == j) rc += before_j;
-      if (want && j != lane && (tk_before(bk, bs, ck, cs) || (!tk_before(ck, cs, bk, bs) && j < lane)))
-        ++rc;
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      if (!((m >> j) & 1u)) continue;  // m is warp-uniform
+      const i64 bk = sk[32 + j], bs = ss[32 + j];
+      re += has && tk_before(bk, bs, k0, s0);
+      rc += want && j != lane && (tk_before(bk, bs, ck, cs) || (!tk_before(ck, cs, bk, bs) && j < lane));
     }
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) rc += want && !tk_before(ck, cs, sk[j], ss[j]);
     __syncwarp();
-    if (has && re < K) scr[re] = k0, scr[32 + re] = s0;
-    if (want && rc < K) scr[rc] = ck, scr[32 + rc] = cs;
+    if (has && re < K) sk[re] = k0, ss[re] = s0;
+    if (want && rc < K) sk[rc] = ck, ss[rc] = cs;
     __syncwarp();
     const int nc = min(K, cnt + __popc(m));
-    if (lane < nc) k0 = scr[lane], s0 = scr[32 + lane];
+    if (lane < nc) k0 = sk[lane], s0 = ss[lane];
     __syncwarp();
     cnt = nc;
   }
 
-  // Merge many candidates (K <= 32): sort the lanes' candidates, pair the
-  // list (earliest first) with the reversed candidates and keep the earlier
-  // of each pair (the 32 earliest of both, as a bitonic sequence), then
-  // finish with a bitonic merge.
-  __device__ __forceinline__ void merge_sorted(int K, u32 m, bool want, i64 ck, i64 cs) {
+  // Merge a list of c <= 32 entries (lane j holds entry j; K <= 32).
+  __device__ __forceinline__ void merge_list(int K, int c, i64 ck, i64 cs) {
     const int lane = threadIdx.x & 31;
-    bool cv = want;
-    tk_sort32(ck, cs, cv);
-    const i64 rk = __shfl_sync(kFull, ck, 31 - lane), rs = __shfl_sync(kFull, cs, 31 - lane);
-    const bool rv = __shfl_sync(kFull, cv ? 1 : 0, 31 - lane) != 0;
-    bool v = lane < cnt;
-    if (tk_before_v(rk, rs, rv, k0, s0, v)) k0 = rk, s0 = rs, v = rv;
-#pragma unroll
-    for (int stride = 16; stride > 0; stride >>= 1) tk_cmpx(k0, s0, v, stride, true);
-    cnt = min(K, cnt + __popc(m));
+    merge_rank(K, c >= 32 ? kFull : (1u << c) - 1u, lane < c, ck, cs);
   }
 
   // Offer one candidate per lane (valid lanes only); warp-uniform call.
@@ -150,10 +148,7 @@ struct TopList {
     u32 m = __ballot_sync(kFull, want);
     if (!m) return;
     if (K <= 32) {
-      if (__popc(m) <= 3)
-        merge32(K, m, want, ck, cs);
-      else
-        merge_sorted(K, m, want, ck, cs);
+      merge_rank(K, m, want, ck, cs);
       return;
     }
     while (m) {
@@ -173,9 +168,29 @@ struct TopList {
 };
 
 // Merge the per-warp lists of one block into warp 0's list through shared
-// memory (`sk`, `ss`: nwarps * K entries, `sc`: nwarps counts).
+// memory (`sk`, `ss`: nwarps * K entries, `sc`: nwarps counts).  K <= 32: a
+// tree (warp w takes the list of warp w + d at distance d = 1, 2, 4, ...,
+// one bitonic merge of sorted lists per level); larger K: warp 0 offers the
+// other lists' entries.
 __device__ __forceinline__ void tk_block_merge(TopList& L, int K, i64* sk, i64* ss, int* sc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (K <= 32) {
+    for (int d = 1; d < nw; d <<= 1) {
+      const bool give = warp % (2 * d) == d, take = warp % (2 * d) == 0 && warp + d < nw;
+      if (give) {
+        L.store(sk + warp * K, ss + warp * K);
+        if (lane == 0) sc[warp] = L.cnt;
+      }
+      __syncthreads();
+      if (take) {
+        const int w = warp + d, c = sc[w];
+        const bool v = lane < c;
+        L.merge_list(K, c, v ? sk[w * K + lane] : 0, v ? ss[w * K + lane] : 0);
+      }
+      __syncthreads();
+    }
+    return;
+  }
   if (warp > 0) {
     L.store(sk + warp * K, ss + warp * K);
     if (lane == 0) sc[warp] = L.cnt;
@@ -200,6 +215,10 @@ __device__ __forceinline__ void tk_block_merge(TopList& L, int K, i64* sk, i64* 
 // counts), then warp 0 offers all stored entries, 32 per call.
 __device__ __forceinline__ void tk_block_merge_all(TopList& L, int K, i64* sk, i64* ss, int* sc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (K <= 32) {
+    tk_block_merge(L, K, sk, ss, sc);
+    return;
+  }
   L.store(sk + warp * K, ss + warp * K);
   if (lane == 0) sc[warp] = L.cnt;
   __syncthreads();

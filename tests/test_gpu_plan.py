@@ -127,10 +127,11 @@ def test_duplicate_build_keys(ctx, stream):
     assert_same(got, want)
 
 
-@pytest.mark.parametrize("n_m", [131_072, 131_073, 131_104])
+@pytest.mark.parametrize("n_m", [131_072, 131_073, 262_144, 262_145, 262_176])
 def test_topk_tiles_at_the_bound(ctx, stream, n_m):
-    """Distinct member counts just above 128 top-k tiles of 32 bitmap words:
-    the tiling must stay within 128 tiles (the tile arrays' size)."""
+    """Distinct member counts around 128 and 256 top-k tiles of 32 bitmap
+    words: the tiling must stay within 256 tiles (the tile lists' and the
+    last tile's scratch size)."""
     D, M, F = datagen.make(2000, n_m, 300_000, seed=11)
     ops = dict(d_op="all", m_op="all", f_op="all")
     want = oracle_plan(D, M, F, seg=0, mc=0, fc=0, k=10, **ops)
@@ -139,6 +140,29 @@ def test_topk_tiles_at_the_bound(ctx, stream, n_m):
     got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=0, m_date_lt=0, f_date_gt=0, k=10,
                                         flags=pq.PQ_PLAN_NO_GRAPH, **ops))
     assert_same(got, want, str(n_m))
+    for t in (TD, TM, TF):
+        t.free(stream)
+
+
+@pytest.mark.parametrize("k", [1, 10, 32, 33, 64])
+def test_topk_lane_lists_overflow(ctx, stream, k):
+    """Every M key a group, one F row each, the largest sums on slots 32
+    apart: in the top-k scan those records land on one lane of each warp,
+    more of them than a lane keeps, so the tiles fall back to the exact
+    per-warp lists (k <= 32); k > 32 takes them always."""
+    n = 40_000
+    D = dict(key=np.arange(1, 11, dtype=np.int32), seg=np.ones(10, np.int8))
+    M = dict(key=np.arange(n, dtype=np.int64), dref=np.ones(n, np.int32),
+             date=np.zeros(n, np.int32))
+    key = np.arange(n, dtype=np.int64)
+    F = dict(mkey=key, price=1000 + key + np.where(key % 32 == 0, 10**7, 0),
+             disc=np.zeros(n, np.int8), date2=np.full(n, 2000, np.int32))
+    ops = dict(d_op="all", m_op="all", f_op="all")
+    want = oracle_plan(D, M, F, seg=0, mc=0, fc=0, k=k, **ops)
+    with torch.cuda.stream(stream):
+        TD, TM, TF, keep = load_tables(pq, ctx, D, M, F, stream=stream)
+    got = run(ctx, stream, pq.make_plan(TD, TM, TF, seg=0, m_date_lt=0, f_date_gt=0, k=k, **ops))
+    assert_same(got, want, str(k))
     for t in (TD, TM, TF):
         t.free(stream)
 
