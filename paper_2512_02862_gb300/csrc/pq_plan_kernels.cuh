@@ -2233,6 +2233,7 @@ __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
 // block that finishes a plan's last tile merges the tiles' lists and writes
 // the result with the group count.
 constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
+constexpr i64 kTopkSpin = 1 << 24;  // polls of the last tile's converting warp (never reached)
 constexpr int kTKW = 4;     // warps per top-k block
 
 struct KS {
@@ -2396,26 +2397,100 @@ struct LaneTop {
   }
 };
 
+// K rounds of the last tile's merge (one warp): lane l owns tiles l + 32 j
+// (j < kTKP / 32) and keeps their heads in registers; a round takes the best
+// head of the warp (warp max reductions over the record's order value, 32
+// bits at a time, until one lane is left), records it, and the winner moves
+// that tile's head on.  lk / ls: the lists (K entries per tile, shared or
+// global memory), lc: their lengths.  Returns the number of entries taken.
+template <typename LoadK, typename LoadS>
+__device__ __forceinline__ int topk_merge_rounds(int K, int parts, const int* lc, LoadK lk,
+                                                 LoadS ls, i64* f_k, i64* f_s,
+                                                 volatile int* f_n) {
+  constexpr int J = kTKP / 32;
+  const int lane = threadIdx.x & 31;
+  i64 hk[J], hs[J];
+  int pos[J], len[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int i = lane + 32 * j;
+    len[j] = i < parts ? lc[i] : 0;
+    pos[j] = 0;
+    hk[j] = len[j] ? lk((i64)i * K) : 0;
+    hs[j] = len[j] ? ls((i64)i * K) : 0;
+  }
+  auto best = [&](int& jb) {
+    jb = -1;
+    i64 ck = 0, cs = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (pos[j] < len[j] && (jb < 0 || ks_bef(hk[j], hs[j], ck, cs))) jb = j, ck = hk[j], cs = hs[j];
+  };
+  int jb;
+  best(jb);
+  int n = 0;
+  for (; n < K; ++n) {
+    u32 act = __ballot_sync(kFull, jb >= 0);
+    if (!act) break;
+    i64 bk = 0, bs = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (j == jb) bk = hk[j], bs = hs[j];
+    // Order value: sum (signed order) then key (smaller first), as 4 words.
+    const u64 hi = (u64)bs ^ (1ULL << 63), lo = ~((u64)bk ^ (1ULL << 63));
+    const u32 w[4] = {(u32)(hi >> 32), (u32)hi, (u32)(lo >> 32), (u32)lo};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (__popc(act) == 1) break;
+      const bool in = (act >> lane) & 1u;
+      const u32 m = __reduce_max_sync(kFull, in ? w[j] : 0u);
+      act &= __ballot_sync(kFull, in && w[j] == m);
+    }
+    if (lane == __ffs(act) - 1) {
+      f_k[n] = bk, f_s[n] = bs;
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (j == jb) {
+          ++pos[j];
+          if (pos[j] < len[j]) {
+            const i64 e = (i64)(lane + 32 * j) * K + pos[j];
+            hk[j] = lk(e), hs[j] = ls(e);
+          }
+        }
+      best(jb);
+    }
+    __syncwarp();
+    if (lane == 0) {  // entry n is out: the converting warp may take it
+      __threadfence_block();
+      *f_n = n + 1;
+    }
+  }
+  return n;
+}
+
 // The plan's last tile: the top K of the tiles' sorted lists, merged by one
 // warp in K rounds (dense slots follow key order; the K results become keys
-// at the end).  Lane l owns tiles l, l + 32, ...
-// and offers the best head among them; a round takes the best offer (warp
-// max reductions over the record's 128-bit order value, most significant
-// word first, until one lane is left) and advances that tile.  The lists are
-// first copied to shared memory when they fit.
+// at the end).  The lists are first copied to shared memory when they fit.
 __device__ __forceinline__ void topk_final(const PlanDev& q, int K, int parts, bool dense,
-                                           u32* scratch) {
+                                           u32* scratch, DevStatus* st) {
+  __shared__ i64 f_k[kMaxK], f_s[kMaxK];  // the merged entries (slots when dense)
+  __shared__ volatile int f_n, f_end;      // entries published, merge done
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // The dense dictionary's constants (for slot -> key), read beside the lists.
-  const u64 m_n = dense ? q.ctr->mcount : 0, m_bits = dense ? q.ctr->m_bits : 0;
-  const u64 m_umin = dense ? q.ctr->m_umin : 0, m_tot = dense ? q.ctr->m_distinct : 0;
+  // The dense dictionary (slot -> key of the results), read before the lists.
+  DenseView dv{};
+  u64 m_umin = 0, m_tot = 0;
+  if (threadIdx.x == 0) f_n = 0, f_end = 0;
+  if (dense && warp == 1) {
+    const u64 m_n = q.ctr->mcount, m_bits = q.ctr->m_bits;
+    m_umin = q.ctr->m_umin, m_tot = q.ctr->m_distinct;
+    dv = dense_view(q.ht_tag, (i64)m_n, m_bits);
+  }
   int* lc = reinterpret_cast<int*>(scratch);  // list lengths
-  int* lp = lc + kTKP;                         // heads
-  i64* sk = reinterpret_cast<i64*>(lp + kTKP);
+  i64* sk = reinterpret_cast<i64*>(lc + kTKP);
   const int all = parts * K;
-  const bool fit = (size_t)all * 16 + kTKP * 8 <= (size_t)kTKW * kTKR * 4;
-  i64* ss = sk + (fit ? all : 0);
-  for (int i = threadIdx.x; i < parts; i += blockDim.x) lc[i] = __ldcg(q.tk_c + i), lp[i] = 0;
+  const bool fit = (size_t)all * 16 + kTKP * 4 <= (size_t)kTKW * kTKR * 4;
+  i64* ss = sk + all;
+  for (int i = threadIdx.x; i < parts; i += blockDim.x) lc[i] = __ldcg(q.tk_c + i);
   if (fit) {  // 8 entries per thread in flight
     for (int e0 = threadIdx.x; e0 < all; e0 += 8 * blockDim.x) {
       i64 xk[8], xs[8];
@@ -2433,52 +2508,35 @@ __device__ __forceinline__ void topk_final(const PlanDev& q, int K, int parts, b
     }
   }
   __syncthreads();
+  // Warp 0 merges; with dense slots warp 1 turns each published entry into
+  // its key meanwhile (lane i takes entries i and 32 + i), so that the
+  // dictionary reads overlap the merge rounds.
+  if (dense && warp == 1) {
+    for (int i = lane; i < K; i += 32) {
+      i64 spins = 0;
+      while (f_n <= i && !f_end && ++spins < kTopkSpin) __nanosleep(64);
+      __threadfence_block();
+      if (f_n <= i) {  // fewer entries, or the wait ran out (reported)
+        if (!f_end) q_latch(q.ctr, st, PQ_ERR_TIMEOUT, i);
+        break;
+      }
+      q.out->keys[i] = dense_key(dv, m_umin, (u64)f_k[i], m_tot), q.out->sums[i] = f_s[i];
+    }
+    return;
+  }
   if (warp != 0) return;
-  const i64* lk = fit ? sk : q.cand_k;
-  const i64* ls = fit ? ss : q.cand_s;
-  // The best head among this lane's tiles (t = -1: none).
-  auto best_of = [&](int& t, i64& bk, i64& bs) {
-    t = -1;
-    for (int i = lane; i < parts; i += 32) {
-      if (lp[i] >= lc[i]) continue;
-      const i64 e = (i64)i * K + lp[i];
-      const i64 xk = fit ? lk[e] : __ldcg(lk + e), xs = fit ? ls[e] : __ldcg(ls + e);
-      if (t < 0 || ks_bef(xk, xs, bk, bs)) t = i, bk = xk, bs = xs;
-    }
-  };
-  int t;
-  i64 bk = 0, bs = 0;
-  best_of(t, bk, bs);
-  __shared__ i64 f_k[kMaxK], f_s[kMaxK];  // the merged entries (slots when dense)
-  int n = 0;
-  for (; n < K; ++n) {
-    u32 act = __ballot_sync(kFull, t >= 0);
-    if (!act) break;
-    // Order value: sum (signed order) then key (smaller first), as 4 words.
-    const u64 hi = (u64)bs ^ (1ULL << 63), lo = ~((u64)bk ^ (1ULL << 63));
-    const u32 w[4] = {(u32)(hi >> 32), (u32)hi, (u32)(lo >> 32), (u32)lo};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (__popc(act) == 1) break;
-      const bool in = (act >> lane) & 1u;
-      const u32 m = __reduce_max_sync(kFull, in ? w[j] : 0u);
-      act &= __ballot_sync(kFull, in && w[j] == m);
-    }
-    const int win = __ffs(act) - 1;
-    if (lane == win) {
-      f_k[n] = bk, f_s[n] = bs;
-      ++lp[t];
-      best_of(t, bk, bs);
-    }
-    __syncwarp();
+  const int n =
+      fit ? topk_merge_rounds(K, parts, lc, [&](i64 e) { return sk[e]; },
+                              [&](i64 e) { return ss[e]; }, f_k, f_s, &f_n)
+          : topk_merge_rounds(K, parts, lc, [&](i64 e) { return __ldcg(q.cand_k + e); },
+                              [&](i64 e) { return __ldcg(q.cand_s + e); }, f_k, f_s, &f_n);
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    f_end = 1;
   }
-  // Each lane converts and writes the entries at its rank.
-  for (int i = lane; i < n; i += 32) {
-    i64 k = f_k[i];
-    if (dense)
-      k = dense_key(dense_view(q.ht_tag, (i64)m_n, m_bits), m_umin, (u64)k, m_tot);
-    q.out->keys[i] = k, q.out->sums[i] = f_s[i];
-  }
+  if (!dense)
+    for (int i = lane; i < n; i += 32) q.out->keys[i] = f_k[i], q.out->sums[i] = f_s[i];
   if (lane == 0) {
     q.out->n = n;
     q.out->ngroups = (i64)ld_volatile_u64(&q.ctr->gcount);
@@ -2589,7 +2647,7 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
       continue;
     }
     __threadfence();
-    topk_final(q, K, parts, src.dense, &s_ring[0][0]);
+    topk_final(q, K, parts, src.dense, &s_ring[0][0], b.st);
     if (gridDim.x >= total) break;  // one tile per block: no ticket needed to stop
   }
   finish(b.work, kPhTopk);
