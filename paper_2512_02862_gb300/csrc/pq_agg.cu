@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
 constexpr int kAS = 3;                    // stages per warp
 constexpr int kStageBytes = 128 * 21;     // mkey 1024 B, price 1024 B, date2 512 B, disc 128 B
 constexpr int kAggWarps = 8;              // warps per block
-constexpr size_t kAggSmem = (size_t)kAggWarps * kAS * (8 + kStageBytes);
+constexpr int kAggRuns = 136;             // a step's stored runs: at most 128 + the carried one
+constexpr int kStageOut = kAggRuns * 9 + 8;  // per warp: their sums, then their flags (16-byte multiple)
+constexpr size_t kAggSmem = (size_t)kAggWarps * (kAS * (8 + kStageBytes) + kStageOut);
 
 // Sorted F, a gapless segment (its distinct keys hold consecutive slots).
 // A step's runs are summed by the segmented warp scan of k_agg_fscan; a
@@ -367,6 +369,12 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64* bar = reinterpret_cast<u64*>(smem) + warp * kAS;
   unsigned char* ring = smem + kAggWarps * kAS * 8 + (size_t)warp * kAS * kStageBytes;
+  // The step's run totals, gathered here and stored as one contiguous range
+  // of slots (whole sectors, not 8-byte pieces), unless the segment adds to
+  // groups of earlier ones (accum: stored one by one).
+  i64* ost = reinterpret_cast<i64*>(smem + kAggWarps * kAS * (8 + kStageBytes) +
+                                     (size_t)warp * kStageOut);
+  unsigned char* ohit = reinterpret_cast<unsigned char*>(ost + kAggRuns);
   const u32 fb = (u32)a.f_base, lt = lanemask_lt();
   const i64 u = (i64)blockIdx.x * kAggWarps + warp, u0 = u * a.unit;
   u64 mag = 0, rows = 0;
@@ -509,14 +517,18 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       // The carried run: it ends before this step (committed by lane 0) or
       // goes on into row 0 (its sum and pass flag join that row's).
       u32 pmc = pm;
+      bool cc = false;  // the carried run is committed with this step's runs
       if (s > 0) {
         if (h0) {
           if (lane == 0) {
             if (first_open)
               a.edge[u].psum = carry_s, a.edge[u].pcnt = carry_c;
-            else
+            else if (a.accum)
               store_slot(a, cur_slot, carry_s, carry_c);
+            else
+              ost[0] = (i64)carry_s, ohit[0] = carry_c ? 1 : 0;
           }
+          cc = !first_open && !a.accum;
           first_open = false, whole = false;
         } else if (lane == 0) {
           v[0] += carry_s, pmc |= carry_c ? 1u : 0u;
@@ -555,6 +567,9 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       const u32 R = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
       const u32 sbase = s == 0 ? __shfl_sync(kFull, ubase, 0) : cur_slot + (h0 ? 1u : 0u);
       u32 ri = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+      // Slots stored by this step: [lo, sbase + R): the carried run first
+      // (cc), without the unit's first run when it began in an earlier unit.
+      const u32 lo = cc ? sbase - 1 : sbase + (first_open && R ? 1u : 0u);
       u64 acc = (sh & 1u) ? 0 : in_s;
       u32 cnt = (sh & 1u) ? 0 : in_p;
 #pragma unroll
@@ -565,10 +580,20 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
         cnt |= (pmc >> j) & 1u;
         const bool end = j < 3 ? (hb >> (j + 1)) & 1u : (lane < 31 && next_head);
         if (!end) continue;
-        if (first_open && ri == 0)  // the unit's first run, begun in an earlier unit
+        if (first_open && ri == 0) {  // the unit's first run, begun in an earlier unit
           a.edge[u].psum = acc, a.edge[u].pcnt = cnt;
-        else
+        } else if (a.accum) {
           store_slot(a, sbase + ri, acc, cnt);
+        } else {
+          const u32 o = sbase + ri - lo;
+          ost[o] = (i64)acc, ohit[o] = cnt ? 1 : 0;
+        }
+      }
+      if (!a.accum) {  // the range, stored by the warp
+        __syncwarp();
+        const int n = (int)(sbase + R - lo);
+        for (int i = lane; i < n; i += 32) a.sums[lo + i] = ost[i], a.hit[lo + i] = ohit[i];
+        __syncwarp();
       }
       // The step's last run is carried on.
       carry_s = __shfl_sync(kFull, acc, 31);
