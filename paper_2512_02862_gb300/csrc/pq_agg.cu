@@ -340,30 +340,35 @@ __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
 }
 
 // Gapless-segment scan: each warp owns one contiguous unit of rows (a
-// multiple of 128) and streams it through a ring of kAS stages of 128 rows
-// in shared memory, filled by bulk copies (lane 0 issues them, an mbarrier
-// per stage counts their bytes), so that the copies of the next stages are
-// in flight while a step is reduced.
-constexpr int kAS = 3;                    // stages per warp
-constexpr int kStageBytes = 128 * 21;     // mkey 1024 B, price 1024 B, date2 512 B, disc 128 B
+// multiple of kStep) and streams it through a ring of kAS stages of kStep
+// rows in shared memory, filled by bulk copies (lane 0 issues them, an
+// mbarrier per stage counts their bytes), so that the copies of the next
+// stage are in flight while a step is reduced.  A lane takes kRPL
+// consecutive rows of a step, so that the warp-wide work of a step (the
+// scan over lanes, the ballots, the carry) is shared by 8 rows per lane.
+constexpr int kRPL = 8;                   // rows per lane and step
+constexpr int kStep = 32 * kRPL;          // rows per step (and stage)
+constexpr int kAS = 2;                    // stages per warp
+constexpr int kStageBytes = kStep * 21;   // mkey 8 B, price 8 B, date2 4 B, disc 1 B per row
+constexpr int kOffP = kStep * 8, kOffD = kStep * 16, kOffC = kStep * 20;
 constexpr int kAggWarps = 8;              // warps per block
-constexpr int kAggRuns = 136;             // a step's stored runs: at most 128 + the carried one
+constexpr int kAggRuns = kStep + 8;       // a step's stored runs: at most kStep + the carried one
 constexpr int kStageOut = kAggRuns * 9 + 8;  // per warp: their sums, then their flags (16-byte multiple)
 constexpr size_t kAggSmem = (size_t)kAggWarps * (kAS * (8 + kStageBytes) + kStageOut);
 
 // Sorted F, a gapless segment (its distinct keys hold consecutive slots).
-// A step's runs are summed by the segmented warp scan of k_agg_fscan; a
-// run's slot is the slot of the unit's first key (one rank lookup per unit)
-// plus the key changes before it, counted with three ballots.  The step's
-// last run is carried into the next step in registers, so only the units'
-// edges cut runs (edge records per unit, finished by k_agg_fixup with slots
-// in place of keys).  BOUNDED: the price column's range bounds every
-// revenue by 2^39 and all of them together by 2^62, so no magnitude is
-// tracked.  A stage whose copies do not complete within the spin limit
-// latches PQ_ERR_TIMEOUT; the warp then waits (bounded) for its copies in
-// flight and stops.
+// A step's runs are summed by a segmented scan over lanes; a run's slot is
+// the slot of the unit's first key (one rank lookup per unit) plus the key
+// changes before it, counted with four ballots.  The step's last run is
+// carried into the next step in registers, so only the units' edges cut
+// runs (edge records per unit, finished by k_agg_fixup with slots in place
+// of keys).  BOUNDED: the price column's range bounds every revenue by 2^39
+// and all of them together by 2^62, so no magnitude is tracked.  A stage
+// whose copies do not complete within the spin limit latches
+// PQ_ERR_TIMEOUT; the warp then waits (bounded) for its copies in flight
+// and stops.
 template <bool BOUNDED>
-__global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
+__global__ void __launch_bounds__(256, 2) k_agg_fscan_t(AggPlan a) {
   extern __shared__ __align__(128) unsigned char smem[];
   chain_begin();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
   bool ovf = false;
   if (u0 < a.n_f) {
     const i64 lim = min(a.unit, a.n_f - u0);
-    const int steps = (int)((lim + 127) >> 7);
+    const int steps = (int)((lim + kStep - 1) / kStep);
     if (lane == 0) {
       for (int s = 0; s < kAS; ++s) mbar_init(&bar[s], 1);
       fence_mbar_init();
@@ -391,16 +396,16 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
     // groups; a segment's last < 16 rows are read from global memory).
     auto issue = [&](int s) {
       if (lane != 0 || s >= steps) return;
-      const i64 r = u0 + (i64)s * 128;
-      const u32 n = (u32)min((i64)128, a.n_f - r) & ~15u;
+      const i64 r = u0 + (i64)s * kStep;
+      const u32 n = (u32)min((i64)kStep, a.n_f - r) & ~15u;
       unsigned char* st = ring + (s % kAS) * kStageBytes;
       u64* b = &bar[s % kAS];
       mbar_expect_tx(b, n * 21);
       if (n) {
         bulk_g2s(st, a.f_mkey + r, n * 8, b);
-        bulk_g2s(st + 1024, a.f_price + r, n * 8, b);
-        bulk_g2s(st + 2048, a.f_date + r, n * 4, b);
-        bulk_g2s(st + 2560, a.f_disc + r, n, b);
+        bulk_g2s(st + kOffP, a.f_price + r, n * 8, b);
+        bulk_g2s(st + kOffD, a.f_date + r, n * 4, b);
+        bulk_g2s(st + kOffC, a.f_disc + r, n, b);
       }
     };
     for (int s = 0; s < kAS; ++s) issue(s);
@@ -411,47 +416,52 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
     u32 cur_key = 0, cur_slot = 0, carry_c = 0, ubase = 0;
     u64 carry_s = 0;
     bool first_open = false, whole = true, cin = false, failed = false;
-    i64 k3 = 0;  // lane 31: the unit's last key
+    i64 k_last = 0;  // lane 31: the unit's last key
     for (int s = 0; s < steps; ++s) {
       const unsigned char* st = ring + (s % kAS) * kStageBytes;
       const bool ok = mbar_wait(&bar[s % kAS], (u32)((s / kAS) & 1), a.spin);
       if (!__all_sync(kFull, ok)) {
-        if (lane == 0) latch(a.st, PQ_ERR_TIMEOUT, u0 + (i64)s * 128);
+        if (lane == 0) latch(a.st, PQ_ERR_TIMEOUT, u0 + (i64)s * kStep);
         for (int t = s; t < steps && t < s + kAS; ++t)
           mbar_wait(&bar[t % kAS], (u32)((t / kAS) & 1), a.spin);
         failed = true;
         break;
       }
-      const i64 s0 = u0 + (i64)s * 128;
-      const int nr = (int)min((i64)128, a.n_f - s0);
-      i64 k[4], p[4];
-      int dt[4];
-      u32 dc = 0;
-      if (nr == 128) {
-        const longlong2 k01 = reinterpret_cast<const longlong2*>(st)[2 * lane];
-        const longlong2 k23 = reinterpret_cast<const longlong2*>(st)[2 * lane + 1];
-        const longlong2 p01 = reinterpret_cast<const longlong2*>(st + 1024)[2 * lane];
-        const longlong2 p23 = reinterpret_cast<const longlong2*>(st + 1024)[2 * lane + 1];
-        const int4 d4 = reinterpret_cast<const int4*>(st + 2048)[lane];
-        dc = reinterpret_cast<const u32*>(st + 2560)[lane];
-        k[0] = k01.x, k[1] = k01.y, k[2] = k23.x, k[3] = k23.y;
-        p[0] = p01.x, p[1] = p01.y, p[2] = p23.x, p[3] = p23.y;
-        dt[0] = d4.x, dt[1] = d4.y, dt[2] = d4.z, dt[3] = d4.w;
+      const i64 s0 = u0 + (i64)s * kStep;
+      const int nr = (int)min((i64)kStep, a.n_f - s0);
+      i64 k[kRPL], p[kRPL];
+      int dt[kRPL];
+      u64 dc = 0;
+      if (nr == kStep) {
+        const longlong2* sk = reinterpret_cast<const longlong2*>(st) + 4 * lane;
+        const longlong2* sp = reinterpret_cast<const longlong2*>(st + kOffP) + 4 * lane;
+        const int4* sd = reinterpret_cast<const int4*>(st + kOffD) + 2 * lane;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const longlong2 x = sk[h], y = sp[h];
+          k[2 * h] = x.x, k[2 * h + 1] = x.y, p[2 * h] = y.x, p[2 * h + 1] = y.y;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int4 d = sd[h];
+          dt[4 * h] = d.x, dt[4 * h + 1] = d.y, dt[4 * h + 2] = d.z, dt[4 * h + 3] = d.w;
+        }
+        dc = reinterpret_cast<const u64*>(st + kOffC)[lane];
       } else {  // the segment's last step: rows past its end repeat the last row
         const int nc = nr & ~15;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = min(4 * lane + j, nr - 1);
+        for (int j = 0; j < kRPL; ++j) {
+          const int q = min(kRPL * lane + j, nr - 1);
           if (q < nc) {
             k[j] = reinterpret_cast<const i64*>(st)[q];
-            p[j] = reinterpret_cast<const i64*>(st + 1024)[q];
-            dt[j] = reinterpret_cast<const int*>(st + 2048)[q];
-            dc |= (u32)st[2560 + q] << (8 * j);
+            p[j] = reinterpret_cast<const i64*>(st + kOffP)[q];
+            dt[j] = reinterpret_cast<const int*>(st + kOffD)[q];
+            dc |= (u64)st[kOffC + q] << (8 * j);
           } else {
             k[j] = a.f_mkey[s0 + q];
             p[j] = a.f_price[s0 + q];
             dt[j] = a.f_date[s0 + q];
-            dc |= (u32)(unsigned char)a.f_disc[s0 + q] << (8 * j);
+            dc |= (u64)(unsigned char)a.f_disc[s0 + q] << (8 * j);
           }
         }
       }
@@ -459,65 +469,52 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       __syncwarp();
       if (lane == 0 && s + kAS < steps) fence_proxy_async_smem();
       issue(s + kAS);
-      u32 ix[4];
+      u32 ix[kRPL];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) ix[j] = (u32)k[j] - fb;
+      for (int j = 0; j < kRPL; ++j) ix[j] = (u32)k[j] - fb;
       if (s == 0) {  // the unit's first key: its slot, and whether its run began earlier
         if (lane == 0) ubase = (u32)fslot(a, ix[0]);
         cin = __shfl_sync(kFull, lane == 0 && u0 > 0 && ek == k[0], 0);
         first_open = cin;
       }
-      if (lane == 31) k3 = k[3];
-      const int nv = nr - 4 * lane;  // the lane's rows inside the segment
+      if (lane == 31) k_last = k[kRPL - 1];
+      const int nv = nr - kRPL * lane;  // the lane's rows inside the segment
       u32 pm = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) pm |= (j < nv && pass32(a.pf, dt[j]) ? 1u : 0u) << j;
-      u64 v[4];
+      for (int j = 0; j < kRPL; ++j) pm |= (j < nv && pass32(a.pf, dt[j]) ? 1u : 0u) << j;
+      u64 v[kRPL];
       if (BOUNDED) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kRPL; ++j) {
           const i64 r = (i64)(int)p[j] * (i64)(100 - (int)(signed char)(dc >> (8 * j)));
           v[j] = (pm >> j) & 1u ? (u64)r : 0;
         }
       } else {
-        bool small = true;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) small = small && p[j] == (i64)(int)p[j];
-        if (small) {
-          u64 tm = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const i64 r = (i64)(int)p[j] * (i64)(100 - (int)(signed char)(dc >> (8 * j)));
-            const bool in = (pm >> j) & 1u;
-            v[j] = in ? (u64)r : 0;
-            tm += in ? (r < 0 ? (u64)0 - (u64)r : (u64)r) : 0;
-          }
-          mag = mag >= kMag ? kMag : min(kMag, mag + tm);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const bool in = (pm >> j) & 1u;
-            const __int128 rev = (__int128)p[j] * (100 - (int)(signed char)(dc >> (8 * j)));
-            const i64 r64 = (i64)rev;
-            ovf = ovf || (in && rev != (__int128)r64);
-            v[j] = in ? (u64)r64 : 0;
-            const u64 m = r64 < 0 ? (u64)0 - (u64)r64 : (u64)r64;
-            if (in) mag = mag >= kMag || m >= kMag ? kMag : min(kMag, mag + m);
-          }
+        for (int j = 0; j < kRPL; ++j) {
+          const bool in = (pm >> j) & 1u;
+          const __int128 rev = (__int128)p[j] * (100 - (int)(signed char)(dc >> (8 * j)));
+          const i64 r64 = (i64)rev;
+          ovf = ovf || (in && rev != (__int128)r64);
+          v[j] = in ? (u64)r64 : 0;
+          const u64 m = r64 < 0 ? (u64)0 - (u64)r64 : (u64)r64;
+          if (in) mag = mag >= kMag || m >= kMag ? kMag : min(kMag, mag + m);
         }
       }
       rows += __popc(pm);
       // Key changes (bit j: row j holds another key than the row before it;
       // lane 0's row 0 compares with the previous step's last key, and
       // counts as a change at the unit's first step).
-      const u32 prev = __shfl_up_sync(kFull, ix[3], 1);
-      u32 hb = (ix[1] != ix[0] ? 2u : 0u) | (ix[2] != ix[1] ? 4u : 0u) | (ix[3] != ix[2] ? 8u : 0u);
+      const u32 prev = __shfl_up_sync(kFull, ix[kRPL - 1], 1);
+      u32 hb = 0;
+#pragma unroll
+      for (int j = 1; j < kRPL; ++j) hb |= (ix[j] != ix[j - 1] ? 1u : 0u) << j;
       hb |= (lane ? ix[0] != prev : (s == 0 || ix[0] != cur_key)) ? 1u : 0u;
       const bool h0 = __shfl_sync(kFull, hb & 1u, 0);
-      // The carried run: it ends before this step (committed by lane 0) or
-      // goes on into row 0 (its sum and pass flag join that row's).
+      // The carried run: it ends before this step (committed with this
+      // step's runs) or goes on into row 0 (its sum and pass flag join it).
       u32 pmc = pm;
-      bool cc = false;  // the carried run is committed with this step's runs
+      bool cc = false;
       if (s > 0) {
         if (h0) {
           if (lane == 0) {
@@ -540,7 +537,7 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       u64 ls = 0;
       u32 fl = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kRPL; ++j) {
         if ((sh >> j) & 1u) ls = 0, fl = 1;
         ls += v[j];
         fl |= ((pmc >> j) & 1u) << 1;
@@ -558,27 +555,27 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       const u64 in_s = __shfl_up_sync(kFull, ls, 1);
       const u32 in_p = __shfl_up_sync(kFull, fl, 1) >> 1;
       const bool next_head = __shfl_down_sync(kFull, sh & 1u, 1);
-      // Slots: key changes after row 0 of the step, before each lane (three
-      // ballots of the lanes' counts, 0..4) and in all.
-      const u32 hx = lane ? hb : hb & 0xEu;
+      // Slots: key changes after row 0 of the step, before each lane (four
+      // ballots of the lanes' counts, 0..8) and in all.
+      const u32 hx = lane ? hb : hb & ~1u;
       const u32 hc = __popc(hx);
       const u32 b0 = __ballot_sync(kFull, hc & 1u), b1 = __ballot_sync(kFull, hc & 2u),
-                b2 = __ballot_sync(kFull, hc & 4u);
-      const u32 R = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+                b2 = __ballot_sync(kFull, hc & 4u), b3 = __ballot_sync(kFull, hc & 8u);
+      const u32 R = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
       const u32 sbase = s == 0 ? __shfl_sync(kFull, ubase, 0) : cur_slot + (h0 ? 1u : 0u);
-      u32 ri = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+      u32 ri = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
       // Slots stored by this step: [lo, sbase + R): the carried run first
       // (cc), without the unit's first run when it began in an earlier unit.
       const u32 lo = cc ? sbase - 1 : sbase + (first_open && R ? 1u : 0u);
       u64 acc = (sh & 1u) ? 0 : in_s;
       u32 cnt = (sh & 1u) ? 0 : in_p;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kRPL; ++j) {
         if (j > 0 && ((hb >> j) & 1u)) acc = 0, cnt = 0;
         ri += (hx >> j) & 1u;
         acc += v[j];
         cnt |= (pmc >> j) & 1u;
-        const bool end = j < 3 ? (hb >> (j + 1)) & 1u : (lane < 31 && next_head);
+        const bool end = j < kRPL - 1 ? (hb >> (j + 1)) & 1u : (lane < 31 && next_head);
         if (!end) continue;
         if (first_open && ri == 0) {  // the unit's first run, begun in an earlier unit
           a.edge[u].psum = acc, a.edge[u].pcnt = cnt;
@@ -599,12 +596,12 @@ __global__ void __launch_bounds__(256, 3) k_agg_fscan_t(AggPlan a) {
       carry_s = __shfl_sync(kFull, acc, 31);
       carry_c = __shfl_sync(kFull, cnt, 31);
       cur_slot = sbase + R;
-      cur_key = __shfl_sync(kFull, ix[3], 31);
+      cur_key = __shfl_sync(kFull, ix[kRPL - 1], 31);
       if (R) first_open = false, whole = false;
     }
     // The unit's end: its last run is cut if the next row holds its key.
     if (!failed) {
-      const bool cout = __shfl_sync(kFull, lane == 31 && u0 + lim < a.n_f && ek == k3, 31);
+      const bool cout = __shfl_sync(kFull, lane == 31 && u0 + lim < a.n_f && ek == k_last, 31);
       if (lane == 0) {
         if (cout) a.edge[u].lsum = carry_s, a.edge[u].lcnt = carry_c, a.edge[u].lkey = cur_slot;
         if (first_open)
@@ -1186,9 +1183,9 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
       const bool tma = (uintptr_t)b.f_mkey % 16 == 0 && (uintptr_t)b.f_price % 16 == 0 &&
                        (uintptr_t)b.f_date % 16 == 0 && (uintptr_t)b.f_disc % 16 == 0;
       if (sorted && g.gap[j] && tma) {
-        // One unit per warp of one resident wave, in whole 128-row steps.
+        // One unit per warp of one resident wave, in whole steps.
         const i64 warps = (i64)sms * occ_t[bounded] * kAggWarps;
-        b.unit = std::max<i64>(1, (b.n_f + warps * 128 - 1) / (warps * 128)) * 128;
+        b.unit = std::max<i64>(1, (b.n_f + warps * kStep - 1) / (warps * kStep)) * kStep;
         const i64 nu = (b.n_f + b.unit - 1) / b.unit;
         b.gapless = 1;
         b.spin = ctx->opt.spin_limit;
