@@ -4,24 +4,31 @@
 //
 //   D' bitmap  <- D rows with seg op_d c_d                  (k_agg_dbits)
 //   M' bitmap  <- M rows with date op_m c_m, dref in D'      (k_agg_mbits)
-//   G          <- F rows with date2 op_f c_f: sums[mkey] += price*(100-disc),
-//                 a group per set flag of the F key range    (k_agg_fscan,
-//                                                             k_agg_fixup)
+//   G          <- F rows with date2 op_f c_f: sums[slot(mkey)] +=
+//                 price*(100-disc), a flag per group     (k_agg_fscan_t,
+//                                                         k_agg_fscan,
+//                                                         k_agg_fixup)
 //   candidates <- keys of M' whose group exists and has sum > having
 //                                                            (k_agg_select)
-//   result     <- top-k of the candidates (the top-k operator's kernel) and
-//                 their number                               (k_agg_result)
+//   result     <- top-k of the candidates (the top-k operator's kernel,
+//                 which also writes the result record)
 //
-// The group sums live in a dense array over the F key range (8 bytes per key
-// of the range), so the plan needs keys whose range is at most a few times
-// the F row count.  Consecutive rows of the same group are added up inside
-// the warp first.  When F's keys come in a few non-decreasing segments
-// (measured once per key column), each segment is scanned by its own launch
-// and every group's total is stored once (k_agg_fixup finishes the runs that
-// tile edges cut); otherwise each run's total is one reduction into a zeroed
-// array.  int64 overflow: a group sum can only leave int64 if the magnitudes
-// of all summed revenues reach 2^62, which the plan tracks (one atomic per
-// warp) and reports as PQ_ERR_OVERFLOW; a single revenue is formed exactly.
+// A group's slot is its key's rank among the F table's distinct keys (a
+// presence bitmap of the F key column with a rank directory, measured once
+// per table), so the sums and flags are dense; the key range must still be
+// at most a few times the F row count (the presence bitmap spans it).
+// Consecutive rows of the same group are added up inside the warp first.
+// When F's keys come in a few non-decreasing segments (measured once per
+// key column), each segment is scanned by its own launch and every group's
+// total is stored once (k_agg_fixup finishes the runs that tile or unit
+// edges cut); a gapless segment (its distinct keys consecutive among the
+// table's) is streamed through shared memory by k_agg_fscan_t, with slots
+// counted from one rank lookup per unit.  Otherwise each run's total is one
+// reduction into a zeroed array.  int64 overflow: a group sum can only
+// leave int64 if the magnitudes of all summed revenues reach 2^62, which
+// the plan tracks (one atomic per warp) unless the price column's range
+// bounds them, and reports as PQ_ERR_OVERFLOW; a single revenue is formed
+// exactly.
 #include <algorithm>
 #include <vector>
 
@@ -351,10 +358,10 @@ constexpr int kStep = 32 * kRPL;          // rows per step (and stage)
 constexpr int kAS = 2;                    // stages per warp
 constexpr int kStageBytes = kStep * 21;   // mkey 8 B, price 8 B, date2 4 B, disc 1 B per row
 constexpr int kOffP = kStep * 8, kOffD = kStep * 16, kOffC = kStep * 20;
-constexpr int kAggWarps = 8;              // warps per block
+constexpr int kAggWarps = 4;              // warps per block (small blocks: 5 fit an SM)
 constexpr int kAggRuns = kStep + 8;       // a step's stored runs: at most kStep + the carried one
-constexpr int kStageOut = kAggRuns * 9 + 8;  // per warp: their sums, then their flags (16-byte multiple)
-constexpr size_t kAggSmem = (size_t)kAggWarps * (kAS * (8 + kStageBytes) + kStageOut);
+static_assert(kAggRuns * 9 <= kStageBytes, "a step's runs are staged in its own stage");
+constexpr size_t kAggSmem = (size_t)kAggWarps * kAS * (8 + kStageBytes);
 
 // Sorted F, a gapless segment (its distinct keys hold consecutive slots).
 // A step's runs are summed by a segmented scan over lanes; a run's slot is
@@ -368,18 +375,12 @@ constexpr size_t kAggSmem = (size_t)kAggWarps * (kAS * (8 + kStageBytes) + kStag
 // PQ_ERR_TIMEOUT; the warp then waits (bounded) for its copies in flight
 // and stops.
 template <bool BOUNDED>
-__global__ void __launch_bounds__(256, 2) k_agg_fscan_t(AggPlan a) {
+__global__ void __launch_bounds__(kAggWarps * 32, 5) k_agg_fscan_t(AggPlan a) {
   extern __shared__ __align__(128) unsigned char smem[];
   chain_begin();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64* bar = reinterpret_cast<u64*>(smem) + warp * kAS;
   unsigned char* ring = smem + kAggWarps * kAS * 8 + (size_t)warp * kAS * kStageBytes;
-  // The step's run totals, gathered here and stored as one contiguous range
-  // of slots (whole sectors, not 8-byte pieces), unless the segment adds to
-  // groups of earlier ones (accum: stored one by one).
-  i64* ost = reinterpret_cast<i64*>(smem + kAggWarps * kAS * (8 + kStageBytes) +
-                                     (size_t)warp * kStageOut);
-  unsigned char* ohit = reinterpret_cast<unsigned char*>(ost + kAggRuns);
   const u32 fb = (u32)a.f_base, lt = lanemask_lt();
   const i64 u = (i64)blockIdx.x * kAggWarps + warp, u0 = u * a.unit;
   u64 mag = 0, rows = 0;
@@ -418,7 +419,13 @@ __global__ void __launch_bounds__(256, 2) k_agg_fscan_t(AggPlan a) {
     bool first_open = false, whole = true, cin = false, failed = false;
     i64 k_last = 0;  // lane 31: the unit's last key
     for (int s = 0; s < steps; ++s) {
-      const unsigned char* st = ring + (s % kAS) * kStageBytes;
+      unsigned char* st = ring + (s % kAS) * kStageBytes;
+      // The step's run totals, gathered in its own stage once its rows are
+      // in registers, and stored as one contiguous range of slots (whole
+      // sectors, not 8-byte pieces), unless the segment adds to groups of
+      // earlier ones (accum: stored one by one).
+      i64* ost = reinterpret_cast<i64*>(st);
+      unsigned char* ohit = st + kAggRuns * 8;
       const bool ok = mbar_wait(&bar[s % kAS], (u32)((s / kAS) & 1), a.spin);
       if (!__all_sync(kFull, ok)) {
         if (lane == 0) latch(a.st, PQ_ERR_TIMEOUT, u0 + (i64)s * kStep);
@@ -465,10 +472,7 @@ __global__ void __launch_bounds__(256, 2) k_agg_fscan_t(AggPlan a) {
           }
         }
       }
-      // The stage is read: lane 0 refills it with step s + kAS.
-      __syncwarp();
-      if (lane == 0 && s + kAS < steps) fence_proxy_async_smem();
-      issue(s + kAS);
+      __syncwarp();  // the stage is read: it holds the run totals from here on
       u32 ix[kRPL];
 #pragma unroll
       for (int j = 0; j < kRPL; ++j) ix[j] = (u32)k[j] - fb;
@@ -590,8 +594,11 @@ __global__ void __launch_bounds__(256, 2) k_agg_fscan_t(AggPlan a) {
         __syncwarp();
         const int n = (int)(sbase + R - lo);
         for (int i = lane; i < n; i += 32) a.sums[lo + i] = ost[i], a.hit[lo + i] = ohit[i];
-        __syncwarp();
       }
+      // Lane 0 refills the stage with step s + kAS.
+      __syncwarp();
+      if (lane == 0 && s + kAS < steps) fence_proxy_async_smem();
+      issue(s + kAS);
       // The step's last run is carried on.
       carry_s = __shfl_sync(kFull, acc, 31);
       carry_c = __shfl_sync(kFull, cnt, 31);
@@ -810,21 +817,6 @@ __global__ void k_pres_gapless(const i64* key, i64 n, u64 umin, SegStarts sb, co
   if (j == 0) *mask = b;
 }
 
-__global__ void k_agg_result(const u64* ctr, const i64* keys, const i64* sums,
-                             const i64* nout, int k, pq_result* out) {
-  chain_begin();
-  const int t = threadIdx.x;
-  const i64 n = *nout;
-  if (t < k && t < n) out->keys[t] = keys[t], out->sums[t] = sums[t];
-  if (t == 0) {
-    out->n = n;
-    out->ngroups = (i64)ctr[0];
-    out->status = (int)ctr[3];
-    out->reserved = 0;
-    out->hits = (i64)ctr[2];
-  }
-}
-
 // Launch of a plan kernel; `chained`: programmatic dependent launch (the
 // kernel waits for its predecessor at entry, so only the launch overlaps).
 template <typename... P, typename... A>
@@ -861,12 +853,12 @@ cudaError_t launch_smem(void (*k)(P...), int grid, int block, size_t smem, cudaS
 // Blocks of 256 threads of kernel k resident per SM (at least 1), with
 // `smem` bytes of dynamic shared memory (allowed for k first).
 template <typename K>
-int resident_blocks(K k, size_t smem = 0) {
+int resident_blocks(K k, size_t smem = 0, int threads = 256) {
   int n = 0;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     cudaGetLastError();
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     n = 1;
   }
@@ -1123,10 +1115,7 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
   }
   a.cand_k = (i64*)c;
   a.cand_s = a.cand_k + cap;
-  i64* ok = (i64*)(c + al256(16 * cap));
-  i64* os = ok + PQ_MAX_K;
-  i64* nout = (i64*)(c + al256(16 * cap) + al256(16 * PQ_MAX_K));
-  pq_result* dres = (pq_result*)((char*)nout + 256);
+  pq_result* dres = (pq_result*)(c + al256(16 * cap) + al256(16 * PQ_MAX_K) + 256);
   void* lists = (char*)dres + al256(sizeof(pq_result));
   a.d_key = d.d_key, a.d_seg = d.d_seg, a.n_d = r.n_d, a.pd = d.pd;
   a.d_base = T[0]->cols[0].range.umin, a.d_bits = d_bits;
@@ -1145,8 +1134,8 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
   };
   // The F scans are persistent: one wave of as many blocks as fit.
   static const int occ[2] = {resident_blocks(k_agg_fscan<false>), resident_blocks(k_agg_fscan<true>)};
-  static const int occ_t[2] = {resident_blocks(k_agg_fscan_t<false>, kAggSmem),
-                               resident_blocks(k_agg_fscan_t<true>, kAggSmem)};
+  static const int occ_t[2] = {resident_blocks(k_agg_fscan_t<false>, kAggSmem, kAggWarps * 32),
+                               resident_blocks(k_agg_fscan_t<true>, kAggSmem, kAggWarps * 32)};
   // Bounded revenues: |price| < 2^31 and n_f * max|revenue| < 2^62, from the
   // price column's measured range (max |price| * 228).
   const bool bounded = g.rev_max > 0 && g.rev_max <= 228ULL * 0x7fffffffULL &&
@@ -1191,9 +1180,11 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
         b.spin = ctx->opt.spin_limit;
         const int tg = (int)((nu + kAggWarps - 1) / kAggWarps);
         if (bounded)
-          PQ_CUDA(ctx, go(launch_smem(k_agg_fscan_t<true>, tg, 256, kAggSmem, s, chained, b)));
+          PQ_CUDA(ctx, go(launch_smem(k_agg_fscan_t<true>, tg, kAggWarps * 32, kAggSmem, s, chained,
+                                      b)));
         else
-          PQ_CUDA(ctx, go(launch_smem(k_agg_fscan_t<false>, tg, 256, kAggSmem, s, chained, b)));
+          PQ_CUDA(ctx, go(launch_smem(k_agg_fscan_t<false>, tg, kAggWarps * 32, kAggSmem, s,
+                                      chained, b)));
         PQ_CUDA(ctx, go(launch(k_agg_fixup, grid(nu, 256), 256, s, chained, b, nu)));
       } else if (sorted) {
         const i64 nt = (b.n_f + 127) / 128;
@@ -1207,13 +1198,11 @@ pq_status run_plan_aggfirst(pq_ctx* ctx, const pq_plan& plan, pq_result* result,
       PQ_CUDA(ctx, go(launch(k_agg_select, grid((i64)(m_bits + 31) / 32, 256), 256, s, chained, a)));
   }
   ctx->launches += launches;
-  // Top-k of the candidates (ticket zeroed with the counters), then the record.
+  // Top-k of the candidates (ticket zeroed with the counters), written into
+  // the result record with the plan's counters.
   PQ_CUDA(ctx, topk_launch(ctx, (const int64_t*)a.cand_k, (const int64_t*)a.cand_s, (int64_t)cap,
-                           (const int64_t*)a.ctr, d.k, (int64_t*)ok, (int64_t*)os, (int64_t*)nout,
-                           (unsigned*)(z + 128), lists, chained, s));
-  PQ_CUDA(ctx, launch(k_agg_result, 1, 64, s, true, (const u64*)a.ctr, (const i64*)ok,
-                      (const i64*)os, (const i64*)nout, d.k, dres));
-  ctx->launches += 1;
+                           (const int64_t*)a.ctr, d.k, dres->keys, dres->sums, &dres->n,
+                           (unsigned*)(z + 128), lists, chained, s, (const uint64_t*)a.ctr, dres));
   ctx->plans++;
   return read_back(ctx, result, dres, 1, s);
 }

@@ -335,7 +335,8 @@ size_t topk_scratch_bytes(pq_ctx* ctx, int64_t n, int k);
 cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t n,
                         const int64_t* d_n, int k, int64_t* out_keys, int64_t* out_sums,
                         int64_t* d_nout, unsigned* ticket, void* lists, bool chained,
-                        cudaStream_t s);
+                        cudaStream_t s, const uint64_t* rec_ctr = nullptr,
+                        pq_result* rec = nullptr);
 
 // Plan internals (pq_plan.cu) used by pq_serve.cu and pq_tune.cu.
 // The M key window of one pass of an out-of-core plan: M' restricted to the

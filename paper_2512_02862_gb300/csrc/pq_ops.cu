@@ -851,7 +851,8 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
                                               const i64* __restrict__ sums, i64 n_cap,
                                               const i64* d_n, int K, i64* part_k, i64* part_s,
                                               int* part_c, u32* ticket, i64* out_keys,
-                                              i64* out_sums, i64* d_nout) {
+                                              i64* out_sums, i64* d_nout, const u64* rec_ctr,
+                                              pq_result* rec) {
   __shared__ i64 sk[8 * kMaxK], ss[8 * kMaxK];
   __shared__ int sc[8];
   __shared__ bool s_last;
@@ -861,6 +862,7 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   // Only the first nb blocks take pairs (at least 256 each: one per thread),
   // so that a small count read on the device leaves few lists to merge.
   const int nb = (int)max((i64)1, min((i64)gridDim.x, (n + 255) / 256));
+  if ((int)blockIdx.x >= nb) return;  // no pairs: the nb blocks take the ticket
   const i64 per = (n + nb - 1) / nb;
   const i64 lo = min(n, per * blockIdx.x), hi = min(n, lo + per);
   TopList L;
@@ -880,7 +882,7 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
     u32 t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
     t = __shfl_sync(kFull, t, 0);
-    if (lane == 0) s_last = (t == gridDim.x - 1);
+    if (lane == 0) s_last = (t == (u32)nb - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -909,6 +911,14 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   if (threadIdx.x < 32) {
     L.store(out_keys, out_sums);
     if (lane == 0) *d_nout = L.cnt;
+    // A plan's result record (out_keys, out_sums, d_nout point into it):
+    // the rest of it from the plan's counters (groups, status, F rows).
+    if (lane == 0 && rec) {
+      rec->ngroups = (i64)rec_ctr[0];
+      rec->status = (int)rec_ctr[3];
+      rec->reserved = 0;
+      rec->hits = (i64)rec_ctr[2];
+    }
   }
 }
 
@@ -953,7 +963,7 @@ size_t topk_scratch_bytes(pq_ctx* ctx, int64_t n, int k) {
 cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, int64_t n,
                         const int64_t* d_n, int k, int64_t* out_keys, int64_t* out_sums,
                         int64_t* d_nout, unsigned* ticket, void* lists, bool chained,
-                        cudaStream_t s) {
+                        cudaStream_t s, const uint64_t* rec_ctr, pq_result* rec) {
   const int grid = topk_grid(ctx, n);
   i64* pk = (i64*)lists;
   i64* ps = pk + (i64)grid * k;
@@ -970,7 +980,7 @@ cudaError_t topk_launch(pq_ctx* ctx, const int64_t* keys, const int64_t* sums, i
   ctx->launches++;
   return cudaLaunchKernelEx(&cfg, k_topk, (const i64*)keys, (const i64*)sums, (i64)n,
                             (const i64*)d_n, k, pk, ps, pc, (u32*)ticket, (i64*)out_keys,
-                            (i64*)out_sums, (i64*)d_nout);
+                            (i64*)out_sums, (i64*)d_nout, (const u64*)rec_ctr, rec);
 }
 
 pq_status fill_i64(pq_ctx* ctx, i64* p, int64_t n, i64 v, cudaStream_t s) {
