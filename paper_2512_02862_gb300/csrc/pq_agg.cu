@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(256) k_agg_fscan(AggPlan a) {
 // stage are in flight while a step is reduced.  A lane takes kRPL
 // consecutive rows of a step, so that the warp-wide work of a step (the
 // scan over lanes, the ballots, the carry) is shared by 8 rows per lane.
-constexpr int kRPL = 8;                   // rows per lane and step
+constexpr int kRPL = 6;                   // rows per lane and step (even)
 constexpr int kStep = 32 * kRPL;          // rows per step (and stage)
 constexpr int kAS = 2;                    // stages per warp
 constexpr int kStageBytes = kStep * 21;   // mkey 8 B, price 8 B, date2 4 B, disc 1 B per row
@@ -375,7 +375,7 @@ constexpr size_t kAggSmem = (size_t)kAggWarps * kAS * (8 + kStageBytes);
 // PQ_ERR_TIMEOUT; the warp then waits (bounded) for its copies in flight
 // and stops.
 template <bool BOUNDED>
-__global__ void __launch_bounds__(kAggWarps * 32, 5) k_agg_fscan_t(AggPlan a) {
+__global__ void __launch_bounds__(kAggWarps * 32, 6) k_agg_fscan_t(AggPlan a) {
   extern __shared__ __align__(128) unsigned char smem[];
   chain_begin();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -439,21 +439,19 @@ __global__ void __launch_bounds__(kAggWarps * 32, 5) k_agg_fscan_t(AggPlan a) {
       i64 k[kRPL], p[kRPL];
       int dt[kRPL];
       u64 dc = 0;
-      if (nr == kStep) {
-        const longlong2* sk = reinterpret_cast<const longlong2*>(st) + 4 * lane;
-        const longlong2* sp = reinterpret_cast<const longlong2*>(st + kOffP) + 4 * lane;
-        const int4* sd = reinterpret_cast<const int4*>(st + kOffD) + 2 * lane;
+      if (nr == kStep) {  // the lane's kRPL rows: 16-byte reads of keys and prices
+        const longlong2* sk = reinterpret_cast<const longlong2*>(st) + (kRPL / 2) * lane;
+        const longlong2* sp = reinterpret_cast<const longlong2*>(st + kOffP) + (kRPL / 2) * lane;
+        const int2* sd = reinterpret_cast<const int2*>(st + kOffD) + (kRPL / 2) * lane;
+        const unsigned short* sc = reinterpret_cast<const unsigned short*>(st + kOffC) + (kRPL / 2) * lane;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 0; h < kRPL / 2; ++h) {
           const longlong2 x = sk[h], y = sp[h];
+          const int2 d = sd[h];
           k[2 * h] = x.x, k[2 * h + 1] = x.y, p[2 * h] = y.x, p[2 * h + 1] = y.y;
+          dt[2 * h] = d.x, dt[2 * h + 1] = d.y;
+          dc |= (u64)sc[h] << (16 * h);
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int4 d = sd[h];
-          dt[4 * h] = d.x, dt[4 * h + 1] = d.y, dt[4 * h + 2] = d.z, dt[4 * h + 3] = d.w;
-        }
-        dc = reinterpret_cast<const u64*>(st + kOffC)[lane];
       } else {  // the segment's last step: rows past its end repeat the last row
         const int nc = nr & ~15;
 #pragma unroll
