@@ -127,6 +127,116 @@ __global__ void __launch_bounds__(256) k_filter(const T* __restrict__ col,
   }
 }
 
+// Large inputs: two passes with no chain between tiles.  Pass 1 counts the
+// passing rows of every kFilterTile tile (tiles spread over the grid, all
+// loads independent); a scan of the counts gives each tile's offset; pass 2
+// reads the column again and writes each tile's rows at its offset.  The
+// column is read twice, but no tile waits for another.
+template <typename T, bool SEL, bool VEC>
+__device__ __forceinline__ u32 filter_tile_bits(const T* __restrict__ col,
+                                                const i64* __restrict__ sel_in, i64 n, Pred p,
+                                                i64 tile, i64 (&rows)[16]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const i64 wbase = tile * kFilterTile + warp * 512;
+  i64 v[16];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const i64 e0 = wbase + g * 128 + lane * 4;
+    if (SEL) {
+      i64 r[4];
+      load4<i64, VEC>(sel_in, e0, n, r);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        rows[g * 4 + s] = r[s];
+        v[g * 4 + s] = e0 + s < n ? (i64)__ldg(col + r[s]) : 0;
+      }
+    } else {
+      i64 x[4];
+      load4<T, VEC>(col, e0, n, x);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[g * 4 + s] = x[s], rows[g * 4 + s] = e0 + s;
+    }
+  }
+  u32 bits = 0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (wbase + g * 128 + lane * 4 + s < n && pass(p, v[g * 4 + s])) bits |= 1u << (g * 4 + s);
+  return bits;
+}
+
+template <typename T, bool SEL, bool VEC>
+__global__ void __launch_bounds__(256) k_filter_count(const T* __restrict__ col,
+                                                      const i64* __restrict__ sel_in, i64 n_cap,
+                                                      const i64* d_n, Pred p, u32* counts) {
+  __shared__ u32 s_w[8];
+  const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
+  const i64 ntiles = (n + kFilterTile - 1) / kFilterTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (i64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    i64 rows[16];
+    const u32 bits = filter_tile_bits<T, SEL, VEC>(col, sel_in, n, p, tile, rows);
+    const u32 c = __reduce_add_sync(kFull, (u32)__popc(bits));
+    if (lane == 0) s_w[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u32 t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+      counts[tile] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, bool SEL, bool VEC>
+__global__ void __launch_bounds__(256) k_filter_write(const T* __restrict__ col,
+                                                      const i64* __restrict__ sel_in, i64 n_cap,
+                                                      const i64* d_n, Pred p,
+                                                      const i64* __restrict__ offs,
+                                                      const u32* __restrict__ counts,
+                                                      i64* __restrict__ out, i64* d_count) {
+  __shared__ u32 s_w[8];
+  const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
+  const i64 ntiles = (n + kFilterTile - 1) / kFilterTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (i64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    i64 rows[16];
+    const i64 toff = __ldg(offs + tile);
+    const u32 bits = filter_tile_bits<T, SEL, VEC>(col, sel_in, n, p, tile, rows);
+    u64 packed = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) packed |= (u64)__popc((bits >> (4 * g)) & 0xFu) << (16 * g);
+    u64 incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const u64 wt = __shfl_sync(kFull, incl, 31);
+    const u64 excl = incl - packed;
+    if (lane == 0)
+      s_w[warp] = (u32)((wt & 0xFFFF) + ((wt >> 16) & 0xFFFF) + ((wt >> 32) & 0xFFFF) + (wt >> 48));
+    __syncthreads();
+    i64 pos = toff;
+    for (int w = 0; w < warp; ++w) pos += s_w[w];
+    if (tile == ntiles - 1 && threadIdx.x == 0) *d_count = toff + __ldg(counts + tile);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const u32 bg = (bits >> (4 * g)) & 0xFu;
+      i64 at = pos + (i64)((excl >> (16 * g)) & 0xFFFF);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (bg & (1u << s)) {
+          if (at < n_cap) out[at] = rows[g * 4 + s];
+          ++at;
+        }
+      pos += (i64)((wt >> (16 * g)) & 0xFFFF);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_fill(i64* __restrict__ p, i64 n, i64 v) {
   const i64 stride = (i64)gridDim.x * blockDim.x;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
@@ -1019,6 +1129,44 @@ pq_status pq_filter(pq_ctx* ctx, pq_col col, int op, int64_t c, const int64_t* s
   if (n_cap == 0) return PQ_OK;
   const i64 ntiles = (n_cap + kFilterTile - 1) / kFilterTile;
   pqh::Scratch scr(ctx, s);
+  const bool vec2 = sel ? aligned16(sel_in) : aligned16(col.data);
+  if (ntiles >= (i64)ctx->num_sms * 8) {
+    // Large input: count, scan the tile counts, write (no chain between tiles).
+    const i64 stiles = (ntiles + 4095) / 4096;
+    const size_t cnt_b = (size_t)((ntiles * 4 + 255) / 256 * 256), off_b = (size_t)((ntiles * 8 + 255) / 256 * 256);
+    char* w2 = (char*)scr.get(cnt_b + off_b + stiles * 8 + 256);
+    if (!w2) return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_filter: no scratch");
+    u32* counts = (u32*)w2;
+    i64* offs = (i64*)(w2 + cnt_b);
+    u32* sctr = (u32*)(w2 + cnt_b + off_b);
+    PQ_CUDA(ctx, cudaMemsetAsync(counts, 0, cnt_b, s));
+    PQ_CUDA(ctx, cudaMemsetAsync(sctr, 0, stiles * 8 + 256, s));
+    const int g2 = (int)std::max<i64>(1, std::min<i64>(ntiles, (i64)ctx->num_sms * 8));
+    PQ_DISPATCH_T(col.type, T, {
+      if (sel) {
+        if (vec2) k_filter_count<T, true, true><<<g2, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in, n_cap, (const i64*)d_n_in, p, counts);
+        else k_filter_count<T, true, false><<<g2, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in, n_cap, (const i64*)d_n_in, p, counts);
+      } else {
+        if (vec2) k_filter_count<T, false, true><<<g2, 256, 0, s>>>((const T*)col.data, nullptr, n_cap, nullptr, p, counts);
+        else k_filter_count<T, false, false><<<g2, 256, 0, s>>>((const T*)col.data, nullptr, n_cap, nullptr, p, counts);
+      }
+    });
+    PQ_LAUNCHED(ctx);
+    k_scan_u32<<<(unsigned)std::min<i64>(stiles, (i64)ctx->num_sms * 4), 256, 0, s>>>(
+        counts, ntiles, offs, (u64*)(sctr + 64), sctr, ctx->opt.spin_limit, ctx->d_status);
+    PQ_LAUNCHED(ctx);
+    PQ_DISPATCH_T(col.type, T, {
+      if (sel) {
+        if (vec2) k_filter_write<T, true, true><<<g2, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in, n_cap, (const i64*)d_n_in, p, offs, counts, (i64*)sel_out, (i64*)d_count);
+        else k_filter_write<T, true, false><<<g2, 256, 0, s>>>((const T*)col.data, (const i64*)sel_in, n_cap, (const i64*)d_n_in, p, offs, counts, (i64*)sel_out, (i64*)d_count);
+      } else {
+        if (vec2) k_filter_write<T, false, true><<<g2, 256, 0, s>>>((const T*)col.data, nullptr, n_cap, nullptr, p, offs, counts, (i64*)sel_out, (i64*)d_count);
+        else k_filter_write<T, false, false><<<g2, 256, 0, s>>>((const T*)col.data, nullptr, n_cap, nullptr, p, offs, counts, (i64*)sel_out, (i64*)d_count);
+      }
+    });
+    PQ_LAUNCHED(ctx);
+    return PQ_OK;
+  }
   char* w = (char*)scr.get(ntiles * 8 + 256);
   if (!w) return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_filter: no scratch");
   u64* state = (u64*)(w + 256);

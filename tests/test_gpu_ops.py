@@ -37,7 +37,8 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-SIZES = [0, 1, 15, 16, 17, 4095, 4096, 4097, 100_003, 1_000_001]
+# 6,000,007 rows: more tiles than 8 per SM, the two-pass (count, scan, write) path
+SIZES = [0, 1, 15, 16, 17, 4095, 4096, 4097, 100_003, 1_000_001, 6_000_007]
 
 
 @pytest.mark.parametrize("dt", [np.int8, np.int32, np.int64])
@@ -57,7 +58,7 @@ def test_filter_matches_oracle(ctx, stream, dt, n):
         assert np.array_equal(out[:k].cpu().numpy(), want), (op, c)
 
 
-@pytest.mark.parametrize("n", [5, 4097, 300_001])
+@pytest.mark.parametrize("n", [5, 4097, 300_001, 12_000_001])
 def test_filter_with_selection_vector(ctx, stream, n):
     rng = np.random.default_rng(n)
     a = rng.integers(0, 100, size=n).astype(np.int32)
@@ -75,9 +76,10 @@ def test_filter_with_selection_vector(ctx, stream, n):
     assert np.array_equal(s3[:int(c3.item())].cpu().numpy(), want)
 
 
-def test_filter_unaligned_column_takes_scalar_path(ctx, stream):
+@pytest.mark.parametrize("n", [50_001, 6_000_001])
+def test_filter_unaligned_column_takes_scalar_path(ctx, stream, n):
     rng = np.random.default_rng(3)
-    a = rng.integers(0, 1000, size=50_001).astype(np.int32)
+    a = rng.integers(0, 1000, size=n).astype(np.int32)
     x = dev(a)[1:]                      # 4-byte offset: not 16-byte aligned
     with torch.cuda.stream(stream):
         out, cnt = pq.pq_filter(ctx, x, "<", 500, stream=stream)
