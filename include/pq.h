@@ -288,7 +288,10 @@ pq_status pq_join_probe(pq_ctx* ctx, const pq_ht* ht, pq_col probe_key, int64_t*
 /* Group-by SUM (Sec. 3.2): one (key, exact int64 sum) per distinct key, in no
  * defined order; *d_ngroups receives the number of groups.  `val` is int8,
  * int32 or int64 (summed in int64).  At most `cap` groups are written; the
- * hash table is sized for min(key.n, cap) groups. */
+ * hash table is sized for min(key.n, cap) groups.  Inputs of 2^20 rows or
+ * more (outside stream capture) first measure the key range, which waits
+ * for the stream once; when the range is at most 4 keys per row the groups
+ * are summed in a slot array over the range instead of the hash table. */
 pq_status pq_groupby_sum(pq_ctx* ctx, pq_col key, pq_col val, int64_t* out_keys,
                          int64_t* out_sums, int64_t cap, int64_t* d_ngroups, void* stream);
 

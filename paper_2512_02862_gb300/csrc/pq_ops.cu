@@ -938,6 +938,133 @@ __global__ void k_gb_insert(const TK* __restrict__ key, const TV* __restrict__ v
   }
 }
 
+// Dense keys (a key range of at most 4 rows per key): the group of key k is
+// slot k - min, its sum in a zeroed array and its existence in a bitmap, so
+// a group costs one reduction and one bit, at addresses that follow the key
+// order.  The key range is measured first (k_gb_range).
+__device__ __forceinline__ u64 gb_ukey(i64 k) { return (u64)k ^ 0x8000000000000000ULL; }
+
+template <typename TK>
+__global__ void __launch_bounds__(256) k_gb_range(const TK* __restrict__ key, i64 n, u64* rng) {
+  u64 lo = ~0ULL, hi = 0;
+  const i64 stride = (i64)gridDim.x * blockDim.x * 4;
+  for (i64 i0 = ((i64)blockIdx.x * blockDim.x + threadIdx.x) * 4; i0 < n; i0 += stride) {
+    i64 k[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? (i64)__ldg(key + i0 + j) : (i64)__ldg(key + i0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lo = min(lo, gb_ukey(k[j])), hi = max(hi, gb_ukey(k[j]));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    lo = min(lo, (u64)__shfl_xor_sync(kFull, lo, o));
+    hi = max(hi, (u64)__shfl_xor_sync(kFull, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(reinterpret_cast<unsigned long long*>(rng), (unsigned long long)lo);
+    atomicMax(reinterpret_cast<unsigned long long*>(rng + 1), (unsigned long long)hi);
+  }
+}
+
+// Each lane takes 4 consecutive rows of a 128-row warp step; runs of equal
+// keys are summed by a segmented scan over the lanes and each run adds its
+// total to its slot once (sorted or clustered keys: one reduction per group
+// and step).  The reserved key is reported as for the hash table.
+template <typename TK, typename TV>
+__global__ void __launch_bounds__(256) k_gb_dense(const TK* __restrict__ key,
+                                                  const TV* __restrict__ val, i64 n, u64 umin,
+                                                  i64* __restrict__ sums, u32* __restrict__ bm,
+                                                  DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const i64 gw = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const i64 nw = ((i64)gridDim.x * blockDim.x) >> 5;
+  for (i64 wb = gw * 128; wb < n; wb += nw * 128) {
+    const i64 r0 = wb + 4 * lane;
+    u64 idx[4];
+    i64 v[4];
+    u32 ok = 0;  // bit j: row j exists and its key is not the reserved one
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool in = r0 + j < n;
+      const i64 k = in ? (i64)__ldg(key + r0 + j) : kEmpty;
+      v[j] = in ? (i64)__ldg(val + r0 + j) : 0;
+      if (in && k == kEmpty) latch(st, PQ_ERR_RESERVED_KEY, r0 + j);
+      ok |= (in && k != kEmpty ? 1u : 0u) << j;
+      idx[j] = gb_ukey(k) - umin;
+    }
+    // Runs: a row starts one when its key differs from the row before it
+    // (or it is not a group row); lane 0's first row always does.
+    const u64 prev = __shfl_up_sync(kFull, idx[3], 1);
+    const u32 okp = __shfl_up_sync(kFull, ok, 1);
+    u32 head = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool pj = j ? ((ok >> (j - 1)) & 1u) : (lane ? (okp >> 3) & 1u : 0u);
+      const u64 pk = j ? idx[j - 1] : prev;
+      const bool oj = (ok >> j) & 1u;
+      head |= (!oj || !pj || idx[j] != pk || (j == 0 && lane == 0) ? 1u : 0u) << j;
+    }
+    // The lane's last run, summed back to the lane where it starts.
+    i64 ls = 0;
+    u32 fl = 0;  // bit 0: the run starts in this lane
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((head >> j) & 1u) ls = 0, fl = 1;
+      ls += v[j];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      if (__all_sync(kFull, fl & 1u)) break;
+      const i64 us = __shfl_up_sync(kFull, ls, o);
+      const u32 uf = __shfl_up_sync(kFull, fl, o);
+      if (lane >= o) {
+        if (!(fl & 1u)) ls += us;
+        fl |= uf & 1u;
+      }
+    }
+    const i64 in_s = __shfl_up_sync(kFull, ls, 1);
+    const bool next_head = __shfl_down_sync(kFull, head & 1u, 1);
+    i64 acc = (head & 1u) ? 0 : in_s;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j > 0 && ((head >> j) & 1u)) acc = 0;
+      acc += v[j];
+      const bool end = j < 3 ? (head >> (j + 1)) & 1u : (lane == 31 || next_head);
+      if (end && ((ok >> j) & 1u)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(sums + idx[j]), (unsigned long long)acc);
+        atomicOr(bm + (idx[j] >> 5), 1u << (idx[j] & 31));
+      }
+    }
+  }
+}
+
+// The groups of the dense path in slot order: each set bit of the bitmap.
+__global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ bm,
+                                                       const i64* __restrict__ sums, u64 span,
+                                                       u64 umin, i64* __restrict__ out_keys,
+                                                       i64* __restrict__ out_sums, i64 cap,
+                                                       u64* d_ngroups) {
+  const i64 words = (i64)((span + 31) / 32);
+  const i64 stride = (i64)gridDim.x * blockDim.x;
+  for (i64 w0 = (i64)blockIdx.x * blockDim.x; w0 < words; w0 += stride) {
+    const i64 w = w0 + threadIdx.x;
+    u32 bits = w < words ? __ldg(bm + w) : 0u;
+    while (__any_sync(kFull, bits)) {
+      const bool has = bits != 0;
+      u64 idx = 0;
+      if (has) {
+        idx = (u64)w * 32 + (u64)(__ffs(bits) - 1);
+        bits &= bits - 1;
+      }
+      const u64 pos = warp_reserve(d_ngroups, has ? 1u : 0u);
+      if (has && pos < (u64)cap) {
+        out_keys[pos] = (i64)((umin + idx) ^ 0x8000000000000000ULL);
+        out_sums[pos] = __ldg(sums + idx);
+      }
+    }
+  }
+}
+
 __global__ void k_gb_emit(const i64* __restrict__ keys, const i64* __restrict__ sums, i64 slots,
                           i64* __restrict__ out_keys, i64* __restrict__ out_sums, i64 cap,
                           u64* d_ngroups) {
@@ -1385,6 +1512,55 @@ pq_status pq_groupby_sum(pq_ctx* ctx, pq_col key, pq_col val, int64_t* out_keys,
   cudaStream_t s = S(stream);
   PQ_CUDA(ctx, cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), s));
   if (key.n == 0) return PQ_OK;
+  // Large inputs outside stream capture: measure the key range (one read of
+  // the keys and one small read-back); dense keys take the slot array.
+  cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &capst);
+  if (capst == cudaStreamCaptureStatusNone && key.n >= (1 << 20)) {
+    pqh::Scratch rs(ctx, s);
+    u64* rng = (u64*)rs.get(256);
+    if (rng) {
+      PQ_CUDA(ctx, cudaMemsetAsync(rng, 0xFF, 8, s));
+      PQ_CUDA(ctx, cudaMemsetAsync(rng + 1, 0, 8, s));
+      const int gr = (int)std::min<i64>((key.n + 1023) / 1024, (i64)ctx->num_sms * 8);
+      PQ_DISPATCH_T(key.type, TK, {
+        k_gb_range<TK><<<gr, 256, 0, s>>>((const TK*)key.data, key.n, rng);
+      });
+      PQ_LAUNCHED(ctx);
+      pqh::SmallPinned hp(ctx);
+      PQ_CUDA(ctx, cudaMemcpyAsync(hp.p, rng, 16, cudaMemcpyDeviceToHost, s));
+      PQ_CUDA(ctx, cudaStreamSynchronize(s));
+      const u64 lo = (u64)hp.p[0], hi = (u64)hp.p[1];
+      const u64 span = hi >= lo ? hi - lo + 1 : 0;
+      if (span && span <= 4 * (u64)key.n && span <= (1ULL << 34)) {
+        pqh::Scratch scr(ctx, s);
+        const size_t sb = (size_t)((span * 8 + 255) / 256 * 256);
+        const size_t bb = (size_t)(((span + 31) / 32 * 4 + 255) / 256 * 256);
+        char* blk = (char*)scr.get(sb + bb);
+        if (blk) {
+          i64* sums = (i64*)blk;
+          u32* bm = (u32*)(blk + sb);
+          PQ_CUDA(ctx, cudaMemsetAsync(blk, 0, sb + bb, s));
+          const int gd = (int)std::min<i64>((key.n + 1023) / 1024, (i64)ctx->num_sms * 8);
+          PQ_DISPATCH_T(key.type, TK, {
+            PQ_DISPATCH_T(val.type, TV, {
+              k_gb_dense<TK, TV><<<gd, 256, 0, s>>>((const TK*)key.data, (const TV*)val.data,
+                                                    key.n, lo, sums, bm, ctx->d_status);
+            });
+          });
+          PQ_LAUNCHED(ctx);
+          const i64 words = (i64)((span + 31) / 32);
+          const int ge = (int)std::max<i64>(1, std::min<i64>((words + 255) / 256, (i64)ctx->num_sms * 8));
+          k_gb_dense_emit<<<ge, 256, 0, s>>>(bm, sums, span, lo, (i64*)out_keys, (i64*)out_sums,
+                                             cap, (u64*)d_ngroups);
+          PQ_LAUNCHED(ctx);
+          k_check_cap<<<1, 1, 0, s>>>((const i64*)d_ngroups, cap, ctx->d_status);
+          PQ_LAUNCHED(ctx);
+          return PQ_OK;
+        }
+      }
+    }
+  }
   const int lf = (int)(ctx->opt.load_factor * 1024 + 0.5f);
   const int log2cap = cap_log2(std::min<i64>(key.n, std::max<i64>(cap, 1)), lf);
   const i64 slots = (i64)1 << log2cap;

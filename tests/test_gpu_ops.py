@@ -233,6 +233,36 @@ def test_groupby_matches_oracle(ctx, stream, kt, vt, n, distinct):
     assert np.array_equal(gk, wk) and np.array_equal(gs, ws)
 
 
+@pytest.mark.parametrize("layout", ["clustered", "sparse", "capacity"])
+def test_groupby_large_inputs(ctx, stream, layout):
+    """Inputs of a million rows and more: dense keys take the slot array
+    (clustered runs of one key, as F is by mkey: runs cut by the 128-row
+    steps), keys spread over 2^40 values take the hash table, and a cap
+    below the group count is reported on the dense path too."""
+    rng = np.random.default_rng(17)
+    n = 3_000_001
+    if layout == "sparse":
+        k = rng.integers(-(1 << 40), 1 << 40, size=n // 4).astype(np.int64)
+        k = np.repeat(k, 4)[:n]
+    else:
+        k = (np.repeat(np.arange(n // 3 + 1, dtype=np.int64) * 4 - 1_000_000,
+                       rng.integers(1, 6, size=n // 3 + 1)))[:n]
+    v = rng.integers(-10**9, 10**9, size=len(k)).astype(np.int64)
+    wk, ws, ovf = oracle.groupby_sum(k, v)
+    assert not ovf
+    cap = 1000 if layout == "capacity" else len(wk)
+    with torch.cuda.stream(stream):
+        ok, os_, cnt = pq.pq_groupby_sum(ctx, dev(k), dev(v), cap=cap, stream=stream)
+        if layout == "capacity":
+            with pytest.raises(pq.PQError) as e:
+                ctx.sync(stream)
+            assert e.value.status == pq.PQ_ERR_CAPACITY and int(cnt.item()) == len(wk)
+            return
+        ctx.sync(stream)
+    gk, gs = groups_sorted(ok, os_, cnt)
+    assert np.array_equal(gk, wk) and np.array_equal(gs, ws)
+
+
 def test_groupby_capacity_overflow(ctx, stream):
     k = np.arange(10_000, dtype=np.int64)
     v = np.ones(10_000, dtype=np.int64)
