@@ -1084,7 +1084,7 @@ __global__ void k_gb_emit(const i64* __restrict__ keys, const i64* __restrict__ 
 }
 
 // ================================================================ top-k ====
-__global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
+__global__ void __launch_bounds__(256, 2) k_topk(const i64* __restrict__ keys,
                                               const i64* __restrict__ sums, i64 n_cap,
                                               const i64* d_n, int K, i64* part_k, i64* part_s,
                                               int* part_c, u32* ticket, i64* out_keys,
@@ -1094,6 +1094,7 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   __shared__ int sc[8];
   __shared__ bool s_last;
   __shared__ i64 s_scr[8][kTopScr];
+  __shared__ LaneRankSmem<256> s_lr;
   chain_begin();
   const i64 n = d_n ? min(*d_n, n_cap) : n_cap;
   // Only the first nb blocks take pairs (at least 256 each: one per thread),
@@ -1102,60 +1103,102 @@ __global__ void __launch_bounds__(256) k_topk(const i64* __restrict__ keys,
   if ((int)blockIdx.x >= nb) return;  // no pairs: the nb blocks take the ticket
   const i64 per = (n + nb - 1) / nb;
   const i64 lo = min(n, per * blockIdx.x), hi = min(n, lo + per);
+  const int lane = threadIdx.x & 31;
+  // A single block writes the result itself; otherwise its list.
+  i64* bk = nb == 1 ? out_keys : part_k + (i64)blockIdx.x * K;
+  i64* bs = nb == 1 ? out_sums : part_s + (i64)blockIdx.x * K;
+  // K <= 32: each thread keeps its best kLL pairs in registers and the
+  // block ranks the few that can be in its top K (tk_lane_rank); when that
+  // cannot vouch for its result, and for K > 32, the warps' register lists
+  // are merged in shared memory (TopList).
+  int cnt = -1;
+  if (K <= 32) {
+    LaneTop T;
+    T.clear();
+    i64 i = lo + threadIdx.x;
+    for (; i + 3 * 256 < hi; i += 4 * 256) {  // four pairs' loads in flight
+      i64 k[4], s[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = __ldcs(keys + i + u * 256), s[u] = __ldcs(sums + i + u * 256);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) T.insert(k[u], s[u]);
+    }
+    for (; i < hi; i += blockDim.x) T.insert(keys[i], sums[i]);
+    cnt = tk_lane_rank(T, K, s_lr, bk, bs);
+  }
   TopList L;
   L.bind(s_scr[threadIdx.x >> 5]);
-  L.clear();
-  for (i64 b = lo; b < hi; b += blockDim.x) {
-    const i64 i = b + threadIdx.x;
-    const bool v = i < hi;
-    L.offer(K, v, v ? keys[i] : 0, v ? sums[i] : 0);
+  if (cnt < 0) {
+    L.clear();
+    for (i64 b = lo; b < hi; b += blockDim.x) {
+      const i64 i = b + threadIdx.x;
+      const bool v = i < hi;
+      L.offer(K, v, v ? keys[i] : 0, v ? sums[i] : 0);
+    }
+    tk_block_merge(L, K, sk, ss, sc);
+    if (threadIdx.x < 32) {
+      L.store(bk, bs);
+      cnt = L.cnt;
+    }
   }
-  tk_block_merge(L, K, sk, ss, sc);
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    L.store(part_k + (i64)blockIdx.x * K, part_s + (i64)blockIdx.x * K);
-    if (lane == 0) part_c[blockIdx.x] = L.cnt;
+  // Thread 0 holds the count on either path.
+  if (nb == 1) {
+    if (threadIdx.x == 0) *d_nout = cnt;
+  } else {
+    if (threadIdx.x == 0) part_c[blockIdx.x] = cnt;
+    __threadfence();  // every thread's list writes, before the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (u32)nb - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // The last block merges the blocks' lists, read from L2 (other blocks
+    // wrote them): entry e of the nb * K list slots is valid when its slot
+    // is below its list's count.
     __threadfence();
-    u32 t = 0;
-    if (lane == 0) t = atomicAdd(ticket, 1u);
-    t = __shfl_sync(kFull, t, 0);
-    if (lane == 0) s_last = (t == (u32)nb - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  // The last block merges the blocks' lists: each warp offers 32 entries
-  // of the grid * K list slots per round; an entry, its slot's list count
-  // and its value are independent loads (L2, not L1: other blocks wrote
-  // them), so a round costs one memory latency.  Slots past a list's count
-  // are in the buffer but unused.
-  __threadfence();
-  L.clear();
-  const int total = nb * K;
-  for (int base = (threadIdx.x >> 5) * 32; base < total; base += blockDim.x) {
-    const int e = base + lane;
-    bool v = false;
-    i64 k = 0, s = 0;
-    if (e < total) {
-      const int b = e / K;
-      const int c = __ldcg(part_c + b);
-      k = __ldcg(part_k + e);
-      s = __ldcg(part_s + e);
-      v = e - b * K < c;
+    const int total = nb * K;
+    cnt = -1;
+    if (K <= 32) {
+      LaneTop T;
+      T.clear();
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int b = e / K;
+        const int c = __ldcg(part_c + b);
+        const i64 k = __ldcg(part_k + e), s = __ldcg(part_s + e);
+        if (e - b * K < c) T.insert(k, s);
+      }
+      cnt = tk_lane_rank(T, K, s_lr, out_keys, out_sums);
     }
-    L.offer(K, v, k, s);
-  }
-  tk_block_merge(L, K, sk, ss, sc);
-  if (threadIdx.x < 32) {
-    L.store(out_keys, out_sums);
-    if (lane == 0) *d_nout = L.cnt;
-    // A plan's result record (out_keys, out_sums, d_nout point into it):
-    // the rest of it from the plan's counters (groups, status, F rows).
-    if (lane == 0 && rec) {
-      rec->ngroups = (i64)rec_ctr[0];
-      rec->status = (int)rec_ctr[3];
-      rec->reserved = 0;
-      rec->hits = (i64)rec_ctr[2];
+    if (cnt < 0) {
+      // Each warp offers 32 of the list slots per round.
+      L.clear();
+      for (int base = (threadIdx.x >> 5) * 32; base < total; base += blockDim.x) {
+        const int e = base + lane;
+        bool v = false;
+        i64 k = 0, s = 0;
+        if (e < total) {
+          const int b = e / K;
+          const int c = __ldcg(part_c + b);
+          k = __ldcg(part_k + e);
+          s = __ldcg(part_s + e);
+          v = e - b * K < c;
+        }
+        L.offer(K, v, k, s);
+      }
+      tk_block_merge(L, K, sk, ss, sc);
+      if (threadIdx.x < 32) {
+        L.store(out_keys, out_sums);
+        cnt = L.cnt;
+      }
     }
+    if (threadIdx.x == 0) *d_nout = cnt;
+  }
+  // A plan's result record (out_keys, out_sums, d_nout point into it): the
+  // rest of it from the plan's counters (groups, status, F rows).
+  if (threadIdx.x == 0 && rec) {
+    rec->ngroups = (i64)rec_ctr[0];
+    rec->status = (int)rec_ctr[3];
+    rec->reserved = 0;
+    rec->hits = (i64)rec_ctr[2];
   }
 }
 

@@ -2342,61 +2342,6 @@ __device__ __forceinline__ u64 tk_scan(const TopkSrc& src, i64 tw, i64 lt, u32* 
   return groups;
 }
 
-// Branch-free record order (a before b) for the rank counts below.
-__device__ __forceinline__ int ks_bef(i64 ak, i64 as, i64 bk, i64 bs) {
-  return (int)(as > bs) | ((int)(as == bs) & (int)(ak < bk));
-}
-// Rank of (xk, xs) among n records in shared memory (keys k, sums s): the
-// records before it, counted with four independent sums per step so that
-// the reads overlap.
-__device__ __forceinline__ int rank_among(const i64* k, const i64* s, int n, i64 xk, i64 xs) {
-  int r0 = 0, r1 = 0, r2 = 0, r3 = 0, j = 0;
-  for (; j + 4 <= n; j += 4) {
-    r0 += ks_bef(k[j], s[j], xk, xs);
-    r1 += ks_bef(k[j + 1], s[j + 1], xk, xs);
-    r2 += ks_bef(k[j + 2], s[j + 2], xk, xs);
-    r3 += ks_bef(k[j + 3], s[j + 3], xk, xs);
-  }
-  for (; j < n; ++j) r0 += ks_bef(k[j], s[j], xk, xs);
-  return r0 + r1 + r2 + r3;
-}
-
-// A lane's best kLL records of a tile, sorted (registers), and the best
-// record it dropped.
-constexpr int kLL = 4;
-struct LaneTop {
-  i64 k[kLL], s[kLL];
-  int n;
-  i64 dk, ds;
-  bool dv;
-  __device__ __forceinline__ void clear() { n = 0, dv = false, dk = ds = 0; }
-  __device__ __forceinline__ void drop(i64 xk, i64 xs) {
-    if (!dv || ks_bef(xk, xs, dk, ds)) dk = xk, ds = xs, dv = true;
-  }
-  __device__ __forceinline__ void insert(i64 xk, i64 xs) {
-    if (n == kLL) {
-      if (!ks_bef(xk, xs, k[kLL - 1], s[kLL - 1])) {
-        drop(xk, xs);
-        return;
-      }
-      drop(k[kLL - 1], s[kLL - 1]);
-    } else {
-      ++n;
-    }
-    // The new record at position n - 1, then one bubble pass upwards.
-#pragma unroll
-    for (int i = 0; i < kLL; ++i)
-      if (i == n - 1) k[i] = xk, s[i] = xs;
-#pragma unroll
-    for (int i = kLL - 1; i > 0; --i)
-      if (i < n && ks_bef(k[i], s[i], k[i - 1], s[i - 1])) {
-        const i64 tk = k[i], ts = s[i];
-        k[i] = k[i - 1], s[i] = s[i - 1];
-        k[i - 1] = tk, s[i - 1] = ts;
-      }
-  }
-};
-
 // K rounds of the last tile's merge (one warp): lane l owns tiles l + 32 j
 // (j < kTKP / 32) and keeps their heads in registers; a round takes the best
 // head of the warp (warp max reductions over the record's order value, 32
@@ -2549,10 +2494,9 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
   __shared__ i64 s_scr[kTKW][kTopScr];
   __shared__ i64 s_mk[kTKW * kMaxK], s_ms[kTKW * kMaxK];
   __shared__ int s_mc[kTKW];
-  __shared__ i64 s_hk[kTKW * 32], s_hs[kTKW * 32];      // lane heads
-  __shared__ i64 s_ck[kLL * 32], s_cs[kLL * 32];        // a tile's candidates
-  __shared__ i64 s_t, s_thk, s_ths, s_kk, s_ks;
-  __shared__ int s_nh, s_nc, s_found, s_cnt;
+  __shared__ LaneRankSmem<kTKW * 32> s_lr;
+  __shared__ i64 s_t;
+  __shared__ int s_cnt;
   __shared__ bool s_last;
   const i64* pre = b.dyn + 4 * (b.nq + 1);
   const i64 total = pre[b.nq];
@@ -2587,35 +2531,8 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
         for (int u = 0; u < 8; ++u)
           if (r[u].v) T.insert(r[u].k, r[u].s);
       });
-      if (threadIdx.x == 0) s_nh = 0, s_nc = 0, s_found = 0;
-      __syncthreads();
-      if (T.n) {
-        const int h = atomicAdd(&s_nh, 1);
-        s_hk[h] = T.k[0], s_hs[h] = T.s[0];
-      }
-      __syncthreads();
-      if (T.n && rank_among(s_hk, s_hs, s_nh, T.k[0], T.s[0]) == K - 1)
-        s_thk = T.k[0], s_ths = T.s[0], s_found = 1;
-      __syncthreads();
-      const bool every = s_found == 0;
-      const i64 thk = s_thk, ths = s_ths;
-#pragma unroll
-      for (int i = 0; i < kLL; ++i)
-        if (i < T.n && (every || !ks_bef(thk, ths, T.k[i], T.s[i]))) {
-          const int c = atomicAdd(&s_nc, 1);
-          s_ck[c] = T.k[i], s_cs[c] = T.s[i];
-        }
-      __syncthreads();
-      const int nc = s_nc, nres = min(K, nc);
-      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const i64 xk = s_ck[c], xs = s_cs[c];
-        const int r = rank_among(s_ck, s_cs, nc, xk, xs);
-        if (r < K) tk[r] = xk, ts[r] = xs;
-        if (r == K - 1) s_kk = xk, s_ks = xs;
-      }
-      __syncthreads();
-      const bool bad = T.dv && !(nres == K && ks_bef(s_kk, s_ks, T.dk, T.ds));
-      done = !__syncthreads_or(bad);
+      const int nres = tk_lane_rank(T, K, s_lr, tk, ts);
+      done = nres >= 0;
       if (done && threadIdx.x == 0) s_cnt = nres;
     }
     if (!done) {

@@ -167,6 +167,117 @@ struct TopList {
   }
 };
 
+// Branch-free record order (a before b) for the rank counts below.
+__device__ __forceinline__ int ks_bef(i64 ak, i64 as, i64 bk, i64 bs) {
+  return (int)(as > bs) | ((int)(as == bs) & (int)(ak < bk));
+}
+// Rank of record x (at index xi) among n records in shared memory (keys k,
+// sums s): the records before it, and the equal ones at a lower index, so
+// that the ranks of n records are distinct even with repeated records.
+// Four independent sums per step, so that the reads overlap.
+__device__ __forceinline__ int rank_among(const i64* k, const i64* s, int n, i64 xk, i64 xs,
+                                          int xi) {
+  int r0 = 0, r1 = 0, r2 = 0, r3 = 0, j = 0;
+  auto at = [&](int i) {
+    return ks_bef(k[i], s[i], xk, xs) | ((int)(i < xi) & (int)(k[i] == xk) & (int)(s[i] == xs));
+  };
+  for (; j + 4 <= n; j += 4) r0 += at(j), r1 += at(j + 1), r2 += at(j + 2), r3 += at(j + 3);
+  for (; j < n; ++j) r0 += at(j);
+  return r0 + r1 + r2 + r3;
+}
+
+// A thread's best kLL records, sorted (registers), and the best record it
+// dropped.
+constexpr int kLL = 4;
+struct LaneTop {
+  i64 k[kLL], s[kLL];
+  int n;
+  i64 dk, ds;
+  bool dv;
+  __device__ __forceinline__ void clear() { n = 0, dv = false, dk = ds = 0; }
+  __device__ __forceinline__ void drop(i64 xk, i64 xs) {
+    if (!dv || ks_bef(xk, xs, dk, ds)) dk = xk, ds = xs, dv = true;
+  }
+  __device__ __forceinline__ void insert(i64 xk, i64 xs) {
+    if (n == kLL) {
+      if (!ks_bef(xk, xs, k[kLL - 1], s[kLL - 1])) {
+        drop(xk, xs);
+        return;
+      }
+      drop(k[kLL - 1], s[kLL - 1]);
+    } else {
+      ++n;
+    }
+    // The new record at position n - 1, then one bubble pass upwards.
+#pragma unroll
+    for (int i = 0; i < kLL; ++i)
+      if (i == n - 1) k[i] = xk, s[i] = xs;
+#pragma unroll
+    for (int i = kLL - 1; i > 0; --i)
+      if (i < n && ks_bef(k[i], s[i], k[i - 1], s[i - 1])) {
+        const i64 tk = k[i], ts = s[i];
+        k[i] = k[i - 1], s[i] = s[i - 1];
+        k[i - 1] = tk, s[i - 1] = ts;
+      }
+  }
+};
+
+// Shared memory of tk_lane_rank for blocks of up to NT threads.
+template <int NT>
+struct LaneRankSmem {
+  i64 hk[NT], hs[NT];              // the threads' list heads
+  i64 ck[kLL * 32], cs[kLL * 32];  // the records not after the threshold
+  i64 thk, ths, kk, ks;            // the threshold, the K-th result
+  int nh, nc, found;
+};
+
+// The block's top K (K <= 32) from its threads' lists T: thr = the K-th best
+// of the lists' heads.  At least K records are then not after thr, so every
+// record of the result is not after it: only those (at most kLL from each of
+// the K lists whose head is not after thr) are ranked, among themselves.
+// Writes the first min(K, their number) to out_k / out_s in order and
+// returns that number, or -1 (block-uniform) when the result may be
+// incomplete: a thread dropped a record that is not after the K-th result,
+// or repeated records left more than kLL * 32 candidates.  Every thread of
+// the block calls it.
+template <int NT>
+__device__ __forceinline__ int tk_lane_rank(const LaneTop& T, int K, LaneRankSmem<NT>& m,
+                                            i64* out_k, i64* out_s) {
+  constexpr int kCap = kLL * 32;
+  if (threadIdx.x == 0) m.nh = 0, m.nc = 0, m.found = 0;
+  __syncthreads();
+  int h = -1;
+  if (T.n) {
+    h = atomicAdd(&m.nh, 1);
+    m.hk[h] = T.k[0], m.hs[h] = T.s[0];
+  }
+  __syncthreads();
+  if (T.n && rank_among(m.hk, m.hs, m.nh, T.k[0], T.s[0], h) == K - 1)
+    m.thk = T.k[0], m.ths = T.s[0], m.found = 1;
+  __syncthreads();
+  const bool every = m.found == 0;
+  const i64 thk = m.thk, ths = m.ths;
+#pragma unroll
+  for (int i = 0; i < kLL; ++i)
+    if (i < T.n && (every || !ks_bef(thk, ths, T.k[i], T.s[i]))) {
+      const int c = atomicAdd(&m.nc, 1);
+      if (c < kCap) m.ck[c] = T.k[i], m.cs[c] = T.s[i];
+    }
+  __syncthreads();
+  const int nc = m.nc;
+  if (nc > kCap) return -1;  // block-uniform
+  const int nres = min(K, nc);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const i64 xk = m.ck[c], xs = m.cs[c];
+    const int r = rank_among(m.ck, m.cs, nc, xk, xs, c);
+    if (r < K) out_k[r] = xk, out_s[r] = xs;
+    if (r == K - 1) m.kk = xk, m.ks = xs;
+  }
+  __syncthreads();
+  const bool bad = T.dv && !(nres == K && ks_bef(m.kk, m.ks, T.dk, T.ds));
+  return __syncthreads_or(bad) ? -1 : nres;
+}
+
 // Merge the per-warp lists of one block into warp 0's list through shared
 // memory (`sk`, `ss`: nwarps * K entries, `sc`: nwarps counts).  K <= 32: a
 // tree (warp w takes the list of warp w + d at distance d = 1, 2, 4, ...,

@@ -304,6 +304,32 @@ def test_topk_identical_entries(ctx, stream, k):
     assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
 
 
+@pytest.mark.parametrize("k,where", [(5, "block"), (10, "block"), (32, "block"), (32, "final")])
+def test_topk_lane_lists_overflow(ctx, stream, k, where):
+    # Blocks of 256 threads take 2048 consecutive pairs each (40 blocks for
+    # 81,920 pairs); a thread takes every 256th pair of its block's range and
+    # keeps its best 4.  "block": the 8 best pairs all fall to thread 0 of
+    # block 0; "final": the best pair of blocks 0, 8, 16, 24 and 32 (each its
+    # list's first entry, list entry e = 32 * block) fall to thread 0 of the
+    # merge of the 40 lists, which takes entries 0, 256, 512, ...
+    n = 40 * 2048
+    rng = np.random.default_rng(k)
+    keys = rng.permutation(n).astype(np.int64)
+    sums = rng.integers(0, 10**6, size=n).astype(np.int64)
+    if where == "block":
+        rows = np.arange(8) * 256
+    else:
+        rows = np.array([0, 8, 16, 24, 32]) * 2048
+    sums[rows] = 10**9 + np.arange(len(rows))
+    wk, ws = oracle.topk(keys, sums, k)
+    with torch.cuda.stream(stream):
+        ok, os_, cnt = pq.pq_topk(ctx, dev(keys), dev(sums), k, stream=stream)
+        ctx.sync(stream)
+    m = int(cnt.item())
+    assert m == len(wk) == k
+    assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
+
+
 def test_topk_count_from_device(ctx, stream):
     rng = np.random.default_rng(5)
     keys = np.arange(100_000, dtype=np.int64)
