@@ -402,12 +402,15 @@ constexpr int kSub = 2048;
 constexpr int kSubWarpRows = kSub / 8;     // rows of a warp in a sub-tile
 constexpr int kSubSteps = kSubWarpRows / 32;
 
-// Lanes of the warp whose bucket equals this lane's (b < 2^log2P, all lanes
-// taking part; an invalid lane passes a bucket of its own, 2^log2P), from one
-// ballot per bucket bit: cheaper than a general match for small bucket ids.
-__device__ __forceinline__ u32 bucket_peers(u32 b, int log2P) {
+// Lanes of the warp whose bucket equals this lane's, from one ballot per
+// bucket bit (all lanes taking part): cheaper than a general match for small
+// bucket ids.  nbits = log2P when every lane holds a row; otherwise
+// log2P + 1, an invalid lane passing a bucket of its own, 2^log2P.
+__device__ __forceinline__ u32 bucket_peers(u32 b, int nbits) {
   u32 peers = kFull;
-  for (int k = 0; k <= log2P; ++k) {
+#pragma unroll
+  for (int k = 0; k <= kStagedMaxLog2; ++k) {
+    if (k >= nbits) break;  // warp-uniform
     const u32 m = __ballot_sync(kFull, (b >> k) & 1u);
     peers &= (b >> k) & 1u ? m : ~m;
   }
@@ -441,30 +444,26 @@ __global__ void __launch_bounds__(256, 8) k_part_hist_blk(const T* __restrict__ 
   constexpr int kPerVec = 16 / sizeof(T);    // keys per 16-byte load
   constexpr int kLd = 4;                     // 16-byte loads per lane per step
   constexpr int kRows = kLd * 32 * kPerVec;  // rows of a warp step
+  // Whole warp steps (kRows consecutive rows: kLd loads of 16 bytes per
+  // lane, issued together, then counted with no bounds tests) while the
+  // share's start is 16-byte aligned; the rest row by row.
   const bool vec = ((uintptr_t)(key + r0) & 15) == 0;
-  // Warp w takes kRows consecutive rows per step: kLd loads of 16 bytes per
-  // lane, issued together, then counted (small enough for 8 blocks per SM).
-  for (i64 r = r0 + warp * kRows; r < r1; r += 8 * (i64)kRows) {  // warp-uniform
-    T v[kLd][kPerVec];
+  const i64 steps = vec ? (r1 - r0) / kRows : 0;
+  for (i64 st = warp; st < steps; st += 8) {  // warp-uniform
+    const uint4* p = reinterpret_cast<const uint4*>(key + r0 + st * kRows);
+    uint4 x[kLd];
+#pragma unroll
+    for (int j = 0; j < kLd; ++j) x[j] = __ldcs(p + j * 32 + lane);
 #pragma unroll
     for (int j = 0; j < kLd; ++j) {
-      const i64 row = r + ((i64)j * 32 + lane) * kPerVec;
-      if (vec && row + kPerVec <= r1) {
-        const uint4 x = __ldg(reinterpret_cast<const uint4*>(key + row));
-        memcpy(v[j], &x, 16);
-      } else {
+      T v[kPerVec];
+      memcpy(v, &x[j], 16);
 #pragma unroll
-        for (int e = 0; e < kPerVec; ++e) v[j][e] = row + e < r1 ? __ldg(key + row + e) : T(0);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kLd; ++j) {
-      const i64 row = r + ((i64)j * 32 + lane) * kPerVec;
-#pragma unroll
-      for (int e = 0; e < kPerVec; ++e)
-        if (row + e < r1) atomicAdd(&sh[fib_bucket((i64)v[j][e], log2P)], 1u);
+      for (int e = 0; e < kPerVec; ++e) atomicAdd(&sh[fib_bucket((i64)v[e], log2P)], 1u);
     }
   }
+  for (i64 i = r0 + steps * kRows + threadIdx.x; i < r1; i += blockDim.x)
+    atomicAdd(&sh[fib_bucket((i64)__ldg(key + i), log2P)], 1u);
   __syncthreads();
   for (int b = threadIdx.x; b < P; b += blockDim.x)
     if (sh[b]) atomicAdd(&hist[(i64)b * g + k], sh[b]);
@@ -541,6 +540,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_blk(const T* __restrict__ 
     __syncthreads();
     // Bucket and place within the warp's rows of each of the lane's rows
     // (the keys loaded first, so that their loads are in flight together).
+    const int nbits = cnt == kSub ? log2P : log2P + 1;  // every lane holds a row?
     u32 bp[kSubSteps];  // bucket << 9 | place among the warp's rows of that bucket
 #pragma unroll
     for (int st = 0; st < kSubSteps; ++st) {
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_blk(const T* __restrict__ 
     for (int st = 0; st < kSubSteps; ++st) {
       const bool valid = bp[st] != 0xFFFFFFFFu;
       const u32 b = bp[st];
-      const u32 peers = bucket_peers(valid ? b : (1u << log2P), log2P);
+      const u32 peers = bucket_peers(valid ? b : (1u << log2P), nbits);
       u32 place = 0;
       if (valid) place = s_cnt[warp * P + b] + __popc(peers & lanemask_lt());
       __syncwarp();
@@ -645,21 +645,18 @@ __host__ __device__ inline size_t tma_smem(int P, int buf_bytes) {
          + (size_t)kSub * 2 * 2;     // s_inv, s_sbk
 }
 
+// One column of a sub-tile, written in sorted order: sorted place
+// i = j * 256 + thread takes the buffered row src[j] to output row drow[j]
+// (both worked out once for all columns).
 template <typename V>
 __device__ __forceinline__ void gather_column(const char* buf, int off, V* __restrict__ dst,
-                                              int cnt, const unsigned short* s_inv,
-                                              const unsigned short* s_sbk,
-                                              const unsigned short* s_run, const i64* s_gb) {
+                                              int cnt, const unsigned short* src,
+                                              const i64* drow) {
   const V* col = reinterpret_cast<const V*>(buf + off);
   constexpr int kPer = kSub / 256;
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int i = j * 256 + (int)threadIdx.x;
-    if (i < cnt) {
-      const u32 b = s_sbk[i];
-      __stcs(dst + s_gb[b] + (i - (i64)s_run[b]), col[s_inv[i]]);
-    }
-  }
+  for (int j = 0; j < kPer; ++j)
+    if (j * 256 + (int)threadIdx.x < cnt) __stcs(dst + drow[j], col[src[j]]);
 }
 
 template <typename T>
@@ -726,7 +723,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
       return;
     }
     // The tail that is not a whole 16-byte unit (last sub-tile only).
-    for (int c = 0; c < tc.n; ++c) {
+    for (int c = 0; cnt < kSub && c < tc.n; ++c) {
       const int es = tc.es[c];
       const int done = (int)(((i64)cnt * es) & ~15LL) / es;
       for (int i = done + (int)threadIdx.x; i < cnt; i += blockDim.x) {
@@ -740,6 +737,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
     for (int b = threadIdx.x; b < 8 * P; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
     const T* s_key = reinterpret_cast<const T*>(buf + tc.off[0]);
+    const int nbits = cnt == kSub ? log2P : log2P + 1;  // every lane holds a row?
     u32 bp[kSubSteps];  // bucket << 9 | place among the warp's rows of that bucket
 #pragma unroll
     for (int q = 0; q < kSubSteps; ++q) {
@@ -750,7 +748,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
     for (int q = 0; q < kSubSteps; ++q) {
       const bool valid = bp[q] != 0xFFFFFFFFu;
       const u32 b = bp[q];
-      const u32 peers = bucket_peers(valid ? b : (1u << log2P), log2P);
+      const u32 peers = bucket_peers(valid ? b : (1u << log2P), nbits);
       u32 place = 0;
       if (valid) place = s_cnt[warp * P + b] + __popc(peers & lanemask_lt());
       __syncwarp();
@@ -798,16 +796,28 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
       s_sbk[at] = (unsigned short)b;
     }
     __syncthreads();
+    // This thread's sorted places: their rows in the buffer and output rows.
+    constexpr int kPer = kSub / 256;
+    unsigned short src[kPer];
+    i64 drow[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = q * 256 + (int)threadIdx.x;
+      src[q] = 0, drow[q] = 0;
+      if (i < cnt) {
+        const u32 b = s_sbk[i];
+        src[q] = s_inv[i];
+        drow[q] = s_gb[b] + (i - (i64)s_run[b]);
+      }
+    }
     for (int c = 0; c < tc.n; ++c) {
       if (tc.es[c] == 8)
-        gather_column<i64>(buf, tc.off[c], static_cast<i64*>(tc.dst[c]), cnt, s_inv, s_sbk,
-                           s_run, s_gb);
+        gather_column<i64>(buf, tc.off[c], static_cast<i64*>(tc.dst[c]), cnt, src, drow);
       else if (tc.es[c] == 4)
-        gather_column<int>(buf, tc.off[c], static_cast<int*>(tc.dst[c]), cnt, s_inv, s_sbk,
-                           s_run, s_gb);
+        gather_column<int>(buf, tc.off[c], static_cast<int*>(tc.dst[c]), cnt, src, drow);
       else
         gather_column<signed char>(buf, tc.off[c], static_cast<signed char*>(tc.dst[c]), cnt,
-                                   s_inv, s_sbk, s_run, s_gb);
+                                   src, drow);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < P; b += blockDim.x) s_gb[b] += s_tot[b];
@@ -1424,10 +1434,10 @@ pq_status pq_partition(pq_ctx* ctx, pq_col key, const pq_col* payload, int npay,
     if (!hist || !gofs || !w) return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_partition: no scratch");
     PQ_CUDA(ctx, cudaMemsetAsync(w, 0, stiles * 8 + 256, s));
     PQ_CUDA(ctx, cudaMemsetAsync(hist, 0, m * 4, s));
-    // Histogram blocks: at least two waves of eight per SM, each with at
-    // least 4096 rows.
+    // Histogram blocks: at most one wave of eight per SM (hsplit blocks per
+    // chunk), each with at least 4096 rows.
     const int hsplit = (int)std::max<i64>(
-        1, std::min<i64>(((i64)ctx->num_sms * 16 + g - 1) / g, (n / g) / 4096));
+        1, std::min<i64>(((i64)ctx->num_sms * 8) / g, (n / g) / 4096));
     PQ_DISPATCH_T(key.type, T, {
       k_part_hist_blk<T><<<(unsigned)(g * hsplit), 256, (size_t)P * 4, s>>>(
           (const T*)key.data, n, log2P, hist, g, hsplit);
