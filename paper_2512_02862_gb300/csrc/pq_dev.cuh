@@ -284,6 +284,23 @@ __device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Acquire-release fence at GPU scope: after a ticket shows that other blocks
+// published their results (each behind a fence), their writes are visible to
+// this thread's later reads.  Lighter than __threadfence (sequentially
+// consistent).
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+// Release store / acquire load of a shared-memory int at CTA scope: a warp
+// that sees the stored value also sees the writes ordered before the store.
+__device__ __forceinline__ void st_release_cta_s32(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
 // Orders this thread's earlier shared-memory accesses before later async-
 // proxy (bulk copy) writes to the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -1242,13 +1242,15 @@ __device__ __forceinline__ u64 last_le_near(const T* a, u64 lo, u64 hi, u64 x, u
 // the keys puts them.
 __device__ __forceinline__ i64 dense_key(const DenseView& d, u64 umin, u64 rank, u64 total) {
   const u64 tiles = (d.blocks + kRankTile - 1) / kRankTile;
-  const u64 tg = total ? (u64)((unsigned __int128)rank * tiles / total) : 0;
+  // First guesses in single precision (only where to look first: the
+  // searches are exact from any guess).
+  const u64 tg = total ? (u64)((float)rank / (float)total * (float)tiles) : 0;
   const u64 t = last_le_near(d.tdir, 0, tiles, rank, tg);  // tdir[tiles] = total > rank
   const u32 r = (u32)(rank - d.tdir[t]);
   const u64 words = d.blocks * 16, w_lo = t * kRankTile * 16,
             w_hi = min(words, (t + 1) * kRankTile * 16);
   const u32 tbits = (u32)(d.tdir[t + 1] - d.tdir[t]);
-  const u64 wg = w_lo + (tbits ? (u64)r * (w_hi - w_lo) / tbits : 0);
+  const u64 wg = w_lo + (tbits ? (u64)((float)r / (float)tbits * (float)(w_hi - w_lo)) : 0);
   const u64 w0 = last_le_near(d.wdir, w_lo, w_hi, r, wg);
   u32 rr = r - d.wdir[w0];
   u32 x = d.bm[w0];
@@ -2233,7 +2235,6 @@ __global__ void __launch_bounds__(256) k_plan_fagg(Batch b) {
 // block that finishes a plan's last tile merges the tiles' lists and writes
 // the result with the group count.
 constexpr int kTKR = 2048;  // entries of a top-k warp's slot ring
-constexpr i64 kTopkSpin = 1 << 24;  // polls of the last tile's converting warp (never reached)
 constexpr int kTKW = 4;     // warps per top-k block
 
 struct KS {
@@ -2347,11 +2348,12 @@ __device__ __forceinline__ u64 tk_scan(const TopkSrc& src, i64 tw, i64 lt, u32* 
 // head of the warp (warp max reductions over the record's order value, 32
 // bits at a time, until one lane is left), records it, and the winner moves
 // that tile's head on.  lk / ls: the lists (K entries per tile, shared or
-// global memory), lc: their lengths.  Returns the number of entries taken.
+// global memory), lc: their lengths.  Entry n goes to f_k / f_s[n], and
+// f_n (shared) then counts the entries out, by a release store that the
+// converting warp's acquire loads pair with.  Returns the number of entries.
 template <typename LoadK, typename LoadS>
 __device__ __forceinline__ int topk_merge_rounds(int K, int parts, const int* lc, LoadK lk,
-                                                 LoadS ls, i64* f_k, i64* f_s,
-                                                 volatile int* f_n) {
+                                                 LoadS ls, i64* f_k, i64* f_s, int* f_n) {
   constexpr int J = kTKP / 32;
   const int lane = threadIdx.x & 31;
   i64 hk[J], hs[J];
@@ -2405,10 +2407,7 @@ __device__ __forceinline__ int topk_merge_rounds(int K, int parts, const int* lc
       best(jb);
     }
     __syncwarp();
-    if (lane == 0) {  // entry n is out: the converting warp may take it
-      __threadfence_block();
-      *f_n = n + 1;
-    }
+    if (lane == 0) st_release_cta_s32(f_n, n + 1);  // entry n is out
   }
   return n;
 }
@@ -2416,53 +2415,69 @@ __device__ __forceinline__ int topk_merge_rounds(int K, int parts, const int* lc
 // The plan's last tile: the top K of the tiles' sorted lists, merged by one
 // warp in K rounds (dense slots follow key order; the K results become keys
 // at the end).  The lists are first copied to shared memory when they fit.
+// With dense slots, warp 1 turns each merged entry into its key as soon as
+// the merge puts it out (lane i takes entries i and 32 + i), so that those
+// dictionary searches overlap the remaining rounds; its waits are bounded
+// (kTopkSpin polls, then PQ_ERR_TIMEOUT).
+constexpr i64 kTopkSpin = 1 << 24;
 __device__ __forceinline__ void topk_final(const PlanDev& q, int K, int parts, bool dense,
                                            u32* scratch, DevStatus* st) {
   __shared__ i64 f_k[kMaxK], f_s[kMaxK];  // the merged entries (slots when dense)
-  __shared__ volatile int f_n, f_end;      // entries published, merge done
+  __shared__ int f_n, f_end;               // entries out; 1 once the merge is done
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // The dense dictionary (slot -> key of the results), read before the lists.
-  DenseView dv{};
-  u64 m_umin = 0, m_tot = 0;
+  // The dense dictionary's counters, loaded while the lists are copied.
+  u64 m_n = 0, m_bits = 0, m_umin = 0, m_tot = 0;
+  if (dense && warp == 1)
+    m_n = q.ctr->mcount, m_bits = q.ctr->m_bits, m_umin = q.ctr->m_umin, m_tot = q.ctr->m_distinct;
   if (threadIdx.x == 0) f_n = 0, f_end = 0;
-  if (dense && warp == 1) {
-    const u64 m_n = q.ctr->mcount, m_bits = q.ctr->m_bits;
-    m_umin = q.ctr->m_umin, m_tot = q.ctr->m_distinct;
-    dv = dense_view(q.ht_tag, (i64)m_n, m_bits);
-  }
   int* lc = reinterpret_cast<int*>(scratch);  // list lengths
   i64* sk = reinterpret_cast<i64*>(lc + kTKP);
   const int all = parts * K;
   const bool fit = (size_t)all * 16 + kTKP * 4 <= (size_t)kTKW * kTKR * 4;
   i64* ss = sk + all;
-  for (int i = threadIdx.x; i < parts; i += blockDim.x) lc[i] = __ldcg(q.tk_c + i);
-  if (fit) {  // 8 entries per thread in flight
-    for (int e0 = threadIdx.x; e0 < all; e0 += 8 * blockDim.x) {
-      i64 xk[8], xs[8];
+  // The list lengths and (when they fit) the lists: every load issued
+  // before any is used, so that the copy costs about one memory latency.
+  constexpr int kLcPer = kTKP / (kTKW * 32);
+  int lcv[kLcPer];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < kLcPer; ++u) {
+    const int i = (int)threadIdx.x + u * kTKW * 32;
+    lcv[u] = i < parts ? __ldcg(q.tk_c + i) : 0;
+  }
+  if (fit) {  // 16 entries per thread in flight
+    for (int e0 = threadIdx.x; e0 < all; e0 += 16 * blockDim.x) {
+      i64 xk[16], xs[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
         const int e = e0 + u * blockDim.x;
         xk[u] = e < all ? __ldcg(q.cand_k + e) : 0;
         xs[u] = e < all ? __ldcg(q.cand_s + e) : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int e = e0 + u * blockDim.x;
         if (e < all) sk[e] = xk[u], ss[e] = xs[u];
       }
     }
   }
+#pragma unroll
+  for (int u = 0; u < kLcPer; ++u) {
+    const int i = (int)threadIdx.x + u * kTKW * 32;
+    if (i < parts) lc[i] = lcv[u];
+  }
   __syncthreads();
-  // Warp 0 merges; with dense slots warp 1 turns each published entry into
-  // its key meanwhile (lane i takes entries i and 32 + i), so that the
-  // dictionary reads overlap the merge rounds.
   if (dense && warp == 1) {
+    const DenseView dv = dense_view(q.ht_tag, (i64)m_n, m_bits);
     for (int i = lane; i < K; i += 32) {
       i64 spins = 0;
-      while (f_n <= i && !f_end && ++spins < kTopkSpin) __nanosleep(64);
-      __threadfence_block();
-      if (f_n <= i) {  // fewer entries, or the wait ran out (reported)
-        if (!f_end) q_latch(q.ctr, st, PQ_ERR_TIMEOUT, i);
+      int out = ld_acquire_cta_s32(&f_n);
+      while (out <= i && !ld_acquire_cta_s32(&f_end) && ++spins < kTopkSpin) {
+        __nanosleep(32);
+        out = ld_acquire_cta_s32(&f_n);
+      }
+      out = ld_acquire_cta_s32(&f_n);
+      if (out <= i) {  // fewer entries, or the wait ran out (reported)
+        if (!ld_acquire_cta_s32(&f_end)) q_latch(q.ctr, st, PQ_ERR_TIMEOUT, i);
         break;
       }
       q.out->keys[i] = dense_key(dv, m_umin, (u64)f_k[i], m_tot), q.out->sums[i] = f_s[i];
@@ -2476,10 +2491,7 @@ __device__ __forceinline__ void topk_final(const PlanDev& q, int K, int parts, b
           : topk_merge_rounds(K, parts, lc, [&](i64 e) { return __ldcg(q.cand_k + e); },
                               [&](i64 e) { return __ldcg(q.cand_s + e); }, f_k, f_s, &f_n);
   __syncwarp();
-  if (lane == 0) {
-    __threadfence_block();
-    f_end = 1;
-  }
+  if (lane == 0) st_release_cta_s32(&f_end, 1);
   if (!dense)
     for (int i = lane; i < n; i += 32) q.out->keys[i] = f_k[i], q.out->sums[i] = f_s[i];
   if (lane == 0) {
@@ -2557,13 +2569,14 @@ __global__ void __launch_bounds__(kTKW * 32) k_plan_topk(Batch b) {
       q.tk_c[lt] = s_cnt;
       __threadfence();
       s_last = (int)atomicAdd(&q.ctr->tk_ticket, 1u) == parts - 1;
+      if (s_last) fence_acq_rel_gpu();
     }
     __syncthreads();
     if (!s_last) {
       if (gridDim.x >= total) break;
       continue;
     }
-    __threadfence();
+    fence_acq_rel_gpu();  // the other tiles' lists, published before their tickets
     topk_final(q, K, parts, src.dense, &s_ring[0][0], b.st);
     if (gridDim.x >= total) break;  // one tile per block: no ticket needed to stop
   }
