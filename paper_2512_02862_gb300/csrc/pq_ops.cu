@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
                                                           const i64* __restrict__ gofs,
                                                           TmaCols tc, i64* d_offsets,
                                                           i64 spin_limit, DevStatus* st) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int P = 1 << log2P;
   u64* bar = reinterpret_cast<u64*>(smem);
   char* bufs = reinterpret_cast<char*>(smem + 16);
@@ -858,45 +858,86 @@ __global__ void k_ht_build(const TK* __restrict__ key, const TV* __restrict__ va
   }
 }
 
+// Hash-join probe: a warp probes 64 rows at a time, two per lane, whose
+// chains of loads (key, then slot after slot of linear probing, every
+// matching build row when the build keys repeat) run side by side.  The
+// warp stages its matches in shared memory and writes them out kPrbBuf at a
+// time, reserving each run with one atomic on the output counter: one
+// reservation per pair-producing round would make that counter the bound
+// (millions of atomics on one address).  Blocks of 8 warps, one resident
+// wave.
+constexpr int kPrbBuf = 256;
 template <typename TK>
-__global__ void k_ht_probe(const TK* __restrict__ pkey, i64 n, const i64* __restrict__ keys,
-                           const i64* __restrict__ vals, int log2cap, const i64* meta,
-                           i64* __restrict__ out_row, i64* __restrict__ out_val, i64 cap,
-                           u64* d_count) {
+__global__ void __launch_bounds__(256) k_ht_probe(const TK* __restrict__ pkey, i64 n,
+                                                  const i64* __restrict__ keys,
+                                                  const i64* __restrict__ vals, int log2cap,
+                                                  const i64* meta, i64* __restrict__ out_row,
+                                                  i64* __restrict__ out_val, i64 cap,
+                                                  u64* d_count) {
+  __shared__ i64 s_row[8][kPrbBuf], s_val[8][kPrbBuf];
   const u64 mask = (1ULL << log2cap) - 1;
   const bool dup = meta[0] != 0;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  i64* br = s_row[warp];
+  i64* bv = s_val[warp];
+  u32 nb = 0;  // staged pairs (warp-uniform)
+  auto flush = [&]() {
+    __syncwarp();
+    u64 base = 0;
+    if (lane == 0) base = atomicAdd(d_count, (u64)nb);
+    base = __shfl_sync(kFull, base, 0);
+    for (u32 e = lane; e < nb; e += 32) {
+      const u64 pos = base + e;
+      if (pos < (u64)cap) out_row[pos] = br[e], out_val[pos] = bv[e];
+    }
+    __syncwarp();
+    nb = 0;
+  };
   const i64 gw = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const i64 nwarps = ((i64)gridDim.x * blockDim.x) >> 5;
-  for (i64 wb = gw * 32; wb < n; wb += nwarps * 32) {
-    const i64 i = wb + lane;
-    bool active = i < n;
-    const i64 k = active ? (i64)__ldg(pkey + i) : 0;
-    if (k == kEmpty) active = false;
-    u64 s = slot_hash(k) & mask;
-    while (__any_sync(kFull, active)) {
-      bool emit = false;
-      i64 v = 0;
-      if (active) {
-        const i64 kk = __ldg(keys + s);
-        if (kk == kEmpty) {
-          active = false;
-        } else {
-          if (kk == k) {
-            emit = true;
-            v = __ldg(vals + s);
-            if (!dup) active = false;
+  for (i64 wb = gw * 64; wb < n; wb += nwarps * 64) {
+    i64 i[2], k[2];
+    bool active[2];
+    u64 s[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      i[h] = wb + h * 32 + lane;
+      active[h] = i[h] < n;
+      k[h] = active[h] ? (i64)__ldg(pkey + i[h]) : 0;
+      if (k[h] == kEmpty) active[h] = false;
+      s[h] = slot_hash(k[h]) & mask;
+    }
+    while (__any_sync(kFull, active[0] || active[1])) {
+      i64 kk[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) kk[h] = active[h] ? __ldg(keys + s[h]) : kEmpty;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        bool emit = false;
+        i64 v = 0;
+        if (active[h]) {
+          if (kk[h] == kEmpty) {
+            active[h] = false;
+          } else {
+            if (kk[h] == k[h]) {
+              emit = true;
+              v = __ldg(vals + s[h]);
+              if (!dup) active[h] = false;
+            }
+            s[h] = (s[h] + 1) & mask;
           }
-          s = (s + 1) & mask;
         }
+        const u32 m = __ballot_sync(kFull, emit);
+        if (emit) {
+          const u32 at = nb + __popc(m & lanemask_lt());
+          br[at] = i[h], bv[at] = v;
+        }
+        nb += __popc(m);
       }
-      const u64 pos = warp_reserve(d_count, emit ? 1u : 0u);
-      if (emit && pos < (u64)cap) {
-        out_row[pos] = i;
-        out_val[pos] = v;
-      }
+      if (nb > kPrbBuf - 64) flush();  // room for a full round stays
     }
   }
+  if (nb) flush();
 }
 
 __global__ void k_check_cap(const i64* d_count, i64 cap, DevStatus* st) {
@@ -1048,7 +1089,23 @@ __global__ void __launch_bounds__(256) k_gb_dense(const TK* __restrict__ key,
   }
 }
 
-// The groups of the dense path in slot order: each set bit of the bitmap.
+// Positions for a block's outputs, cnt per thread: one atomic on the
+// output counter per block step (a block-wide scan of the counts), so that
+// the counter is not a point of contention.  Every thread of the block
+// calls it; returns this thread's first position.
+__device__ __forceinline__ u64 block_reserve(u64* counter, u32 cnt) {
+  __shared__ u64 s_base;
+  const u32 before = block_exclusive_sum(cnt);
+  if (threadIdx.x == blockDim.x - 1) s_base = atomicAdd(counter, (u64)(before + cnt));
+  __syncthreads();
+  const u64 pos = s_base + before;
+  __syncthreads();  // s_base is read before the next call writes it
+  return pos;
+}
+
+// The groups of the dense slot array, from its existence bitmap: a thread
+// takes one bitmap word and writes its groups in key order at consecutive
+// positions reserved for the whole block at once.
 __global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ bm,
                                                        const i64* __restrict__ sums, u64 span,
                                                        u64 umin, i64* __restrict__ out_keys,
@@ -1056,18 +1113,13 @@ __global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ b
                                                        u64* d_ngroups) {
   const i64 words = (i64)((span + 31) / 32);
   const i64 stride = (i64)gridDim.x * blockDim.x;
-  for (i64 w0 = (i64)blockIdx.x * blockDim.x; w0 < words; w0 += stride) {
+  for (i64 w0 = (i64)blockIdx.x * blockDim.x; w0 < words; w0 += stride) {  // block-uniform
     const i64 w = w0 + threadIdx.x;
     u32 bits = w < words ? __ldg(bm + w) : 0u;
-    while (__any_sync(kFull, bits)) {
-      const bool has = bits != 0;
-      u64 idx = 0;
-      if (has) {
-        idx = (u64)w * 32 + (u64)(__ffs(bits) - 1);
-        bits &= bits - 1;
-      }
-      const u64 pos = warp_reserve(d_ngroups, has ? 1u : 0u);
-      if (has && pos < (u64)cap) {
+    u64 pos = block_reserve(d_ngroups, (u32)__popc(bits));
+    for (; bits; bits &= bits - 1, ++pos) {
+      const u64 idx = (u64)w * 32 + (u64)(__ffs(bits) - 1);
+      if (pos < (u64)cap) {
         out_keys[pos] = (i64)((umin + idx) ^ 0x8000000000000000ULL);
         out_sums[pos] = __ldg(sums + idx);
       }
@@ -1075,21 +1127,31 @@ __global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ b
   }
 }
 
-__global__ void k_gb_emit(const i64* __restrict__ keys, const i64* __restrict__ sums, i64 slots,
-                          i64* __restrict__ out_keys, i64* __restrict__ out_sums, i64 cap,
-                          u64* d_ngroups) {
-  const int lane = threadIdx.x & 31;
-  const i64 gw = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const i64 nwarps = ((i64)gridDim.x * blockDim.x) >> 5;
-  (void)lane;
-  for (i64 wb = gw * 32; wb < slots; wb += nwarps * 32) {
-    const i64 s = wb + (threadIdx.x & 31);
-    const bool has = s < slots && keys[s] != kEmpty;
-    const u64 pos = warp_reserve(d_ngroups, has ? 1u : 0u);
-    if (has && pos < (u64)cap) {
-      out_keys[pos] = keys[s];
-      out_sums[pos] = sums[s];
+// The groups of the hash table: a thread takes kGbEmitPer consecutive slots
+// and writes their groups at consecutive positions reserved per block step.
+constexpr int kGbEmitPer = 8;
+__global__ void __launch_bounds__(256) k_gb_emit(const i64* __restrict__ keys,
+                                                 const i64* __restrict__ sums, i64 slots,
+                                                 i64* __restrict__ out_keys,
+                                                 i64* __restrict__ out_sums, i64 cap,
+                                                 u64* d_ngroups) {
+  const i64 step = (i64)gridDim.x * blockDim.x * kGbEmitPer;
+  for (i64 b0 = (i64)blockIdx.x * blockDim.x * kGbEmitPer; b0 < slots; b0 += step) {  // block-uniform
+    const i64 b = b0 + (i64)threadIdx.x * kGbEmitPer;
+    i64 k[kGbEmitPer];
+    u32 m = 0;
+#pragma unroll
+    for (int j = 0; j < kGbEmitPer; ++j) {
+      k[j] = b + j < slots ? keys[b + j] : kEmpty;
+      m |= (u32)(k[j] != kEmpty) << j;
     }
+    u64 pos = block_reserve(d_ngroups, (u32)__popc(m));
+#pragma unroll
+    for (int j = 0; j < kGbEmitPer; ++j)
+      if ((m >> j) & 1u) {
+        if (pos < (u64)cap) out_keys[pos] = k[j], out_sums[pos] = sums[b + j];
+        ++pos;
+      }
   }
 }
 
@@ -1235,6 +1297,16 @@ void launch_filter_v(pq_ctx* ctx, bool vec, int grid, cudaStream_t s, const void
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Blocks of 256 threads (static shared memory only) resident per SM.
+int resident_blocks256(const void* k) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return occ;
+}
 
 }  // namespace
 
@@ -1544,8 +1616,9 @@ pq_status pq_join_probe(pq_ctx* ctx, const pq_ht* ht, pq_col probe_key, int64_t*
   cudaStream_t s = S(stream);
   PQ_CUDA(ctx, cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
   if (probe_key.n == 0) return PQ_OK;
-  const int grid = (int)std::min<i64>((probe_key.n + 255) / 256, (i64)ctx->num_sms * 8);
   PQ_DISPATCH_T(probe_key.type, TK, {
+    static const int occ = std::max(1, resident_blocks256((const void*)k_ht_probe<TK>));
+    const int grid = (int)std::min<i64>((probe_key.n + 511) / 512, (i64)ctx->num_sms * occ);
     k_ht_probe<TK><<<grid, 256, 0, s>>>((const TK*)probe_key.data, probe_key.n, ht->keys,
                                         ht->vals, ht->log2cap, ht->meta, (i64*)out_probe_row,
                                         (i64*)out_build_val, cap, (u64*)d_count);
