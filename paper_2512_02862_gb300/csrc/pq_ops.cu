@@ -1185,6 +1185,41 @@ __global__ void __launch_bounds__(256, 2) k_topk(const i64* __restrict__ keys,
   // are merged in shared memory (TopList).
   int cnt = -1;
   if (K <= 32) {
+    // A first threshold: each thread's best of 4 of its pairs spread over
+    // its share (a sorted input then gives a threshold near its end), and
+    // thr = the K-th best of those.  At least K pairs are not after thr, so
+    // a pair after it cannot be among the block's K best: only the others
+    // enter the lists, which keeps the lanes of a warp on the same path.
+    // Blocks with fewer than 8 pairs per thread skip it (block-uniform).
+    bool filt = false;
+    i64 thk = 0, ths = 0;
+    if (hi - lo >= 8 * 256) {
+      const i64 mine = hi - lo > (i64)threadIdx.x ? (hi - lo - threadIdx.x + 255) / 256 : 0;
+      i64 hk = 0, hs = 0;
+      bool hv = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const i64 j = mine * q / 4;
+        if (j < mine) {
+          const i64 xk = keys[lo + threadIdx.x + j * 256], xs = sums[lo + threadIdx.x + j * 256];
+          if (!hv || ks_bef(xk, xs, hk, hs)) hk = xk, hs = xs, hv = true;
+        }
+      }
+      if (threadIdx.x == 0) s_lr.nh = 0, s_lr.found = 0;
+      __syncthreads();
+      int h = -1;
+      if (hv) {
+        h = atomicAdd(&s_lr.nh, 1);
+        s_lr.hk[h] = hk, s_lr.hs[h] = hs;
+      }
+      __syncthreads();
+      if (hv && rank_among(s_lr.hk, s_lr.hs, s_lr.nh, hk, hs, h) == K - 1)
+        s_lr.thk = hk, s_lr.ths = hs, s_lr.found = 1;
+      __syncthreads();
+      filt = s_lr.found != 0;
+      thk = s_lr.thk, ths = s_lr.ths;
+      __syncthreads();  // tk_lane_rank reuses s_lr
+    }
     LaneTop T;
     T.clear();
     i64 i = lo + threadIdx.x;
@@ -1193,9 +1228,13 @@ __global__ void __launch_bounds__(256, 2) k_topk(const i64* __restrict__ keys,
 #pragma unroll
       for (int u = 0; u < 4; ++u) k[u] = __ldcs(keys + i + u * 256), s[u] = __ldcs(sums + i + u * 256);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) T.insert(k[u], s[u]);
+      for (int u = 0; u < 4; ++u)
+        if (!filt || !ks_bef(thk, ths, k[u], s[u])) T.insert(k[u], s[u]);
     }
-    for (; i < hi; i += blockDim.x) T.insert(keys[i], sums[i]);
+    for (; i < hi; i += blockDim.x) {
+      const i64 xk = keys[i], xs = sums[i];
+      if (!filt || !ks_bef(thk, ths, xk, xs)) T.insert(xk, xs);
+    }
     cnt = tk_lane_rank(T, K, s_lr, bk, bs);
   }
   TopList L;

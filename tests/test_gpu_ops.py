@@ -330,6 +330,29 @@ def test_topk_lane_lists_overflow(ctx, stream, k, where):
     assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
 
 
+@pytest.mark.parametrize("order", ["ascending", "descending", "equal"])
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_topk_sorted_inputs(ctx, stream, order, k):
+    # Pairs sorted by sum (either way) or all of one sum: the block
+    # threshold taken from a few spread pairs per thread must keep every
+    # pair that can be among the k best.
+    n = 2_000_000
+    rng = np.random.default_rng(k)
+    keys = rng.permutation(n).astype(np.int64)
+    sums = np.sort(rng.integers(-10**9, 10**9, size=n)).astype(np.int64)
+    if order == "descending":
+        sums = sums[::-1].copy()
+    elif order == "equal":
+        sums[:] = 7
+    wk, ws = oracle.topk(keys, sums, k)
+    with torch.cuda.stream(stream):
+        ok, os_, cnt = pq.pq_topk(ctx, dev(keys), dev(sums), k, stream=stream)
+        ctx.sync(stream)
+    m = int(cnt.item())
+    assert m == len(wk) == k
+    assert np.array_equal(ok[:m].cpu().numpy(), wk) and np.array_equal(os_[:m].cpu().numpy(), ws)
+
+
 def test_topk_count_from_device(ctx, stream):
     rng = np.random.default_rng(5)
     keys = np.arange(100_000, dtype=np.int64)
