@@ -1103,9 +1103,11 @@ __device__ __forceinline__ u64 block_reserve(u64* counter, u32 cnt) {
   return pos;
 }
 
-// The groups of the dense slot array, from its existence bitmap: a thread
-// takes one bitmap word and writes its groups in key order at consecutive
-// positions reserved for the whole block at once.
+// The groups of the dense slot array, from its existence bitmap, in key
+// order within each block step: a thread reserves the positions of one
+// bitmap word's groups (one atomic per block step), then the warp writes
+// its 32 words one after another, lane l taking bit l, so that the sums are
+// read and the groups written in contiguous runs.
 __global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ bm,
                                                        const i64* __restrict__ sums, u64 span,
                                                        u64 umin, i64* __restrict__ out_keys,
@@ -1115,13 +1117,19 @@ __global__ void __launch_bounds__(256) k_gb_dense_emit(const u32* __restrict__ b
   const i64 stride = (i64)gridDim.x * blockDim.x;
   for (i64 w0 = (i64)blockIdx.x * blockDim.x; w0 < words; w0 += stride) {  // block-uniform
     const i64 w = w0 + threadIdx.x;
-    u32 bits = w < words ? __ldg(bm + w) : 0u;
-    u64 pos = block_reserve(d_ngroups, (u32)__popc(bits));
-    for (; bits; bits &= bits - 1, ++pos) {
-      const u64 idx = (u64)w * 32 + (u64)(__ffs(bits) - 1);
-      if (pos < (u64)cap) {
-        out_keys[pos] = (i64)((umin + idx) ^ 0x8000000000000000ULL);
-        out_sums[pos] = __ldg(sums + idx);
+    const u32 bits = w < words ? __ldg(bm + w) : 0u;
+    const u64 pos = block_reserve(d_ngroups, (u32)__popc(bits));
+    const int lane = threadIdx.x & 31;
+    const i64 wfirst = w - lane;
+    for (int c = 0; c < 32; ++c) {
+      const u32 wc = __shfl_sync(kFull, bits, c);
+      const u64 pc = __shfl_sync(kFull, pos, c);
+      if (!((wc >> lane) & 1u)) continue;
+      const u64 p = pc + __popc(wc & lanemask_lt());
+      const u64 idx = (u64)(wfirst + c) * 32 + (u64)lane;
+      if (p < (u64)cap) {
+        out_keys[p] = (i64)((umin + idx) ^ 0x8000000000000000ULL);
+        out_sums[p] = __ldg(sums + idx);
       }
     }
   }
