@@ -192,7 +192,7 @@ struct pq_table {
 
 struct pq_ht {
   pqk::i64* keys = nullptr;
-  pqk::i64* vals = nullptr;
+  pqk::i64* vals = nullptr;  // keys + 1: slots are {key, value} pairs
   pqk::i64* meta = nullptr;   // [0] duplicate-key flag, [1] inserted count
   int log2cap = 0;
   int64_t n = 0;

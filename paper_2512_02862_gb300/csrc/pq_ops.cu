@@ -830,10 +830,11 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
 }
 
 // ========================================================== hash join ====
+// The join's hash table: 2^log2cap slots of 16 bytes, {key, value} side by
+// side, so that an insert and a match each touch one sector.
 template <typename TK, typename TV>
 __global__ void k_ht_build(const TK* __restrict__ key, const TV* __restrict__ val, i64 n,
-                           i64* __restrict__ keys, i64* __restrict__ vals, int log2cap, i64* meta,
-                           DevStatus* st) {
+                           i64* __restrict__ slots, int log2cap, i64* meta, DevStatus* st) {
   const u64 mask = (1ULL << log2cap) - 1;
   const i64 stride = (i64)gridDim.x * blockDim.x;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -846,9 +847,9 @@ __global__ void k_ht_build(const TK* __restrict__ key, const TV* __restrict__ va
     u64 s = slot_hash(k) & mask;
     u64 probes = 0;
     for (; probes <= mask; ++probes) {
-      const i64 old = (i64)atomicCAS((u64*)&keys[s], (u64)kEmpty, (u64)k);
+      const i64 old = (i64)atomicCAS((u64*)&slots[2 * s], (u64)kEmpty, (u64)k);
       if (old == kEmpty) {
-        vals[s] = v;
+        slots[2 * s + 1] = v;
         break;
       }
       if (old == k) meta[0] = 1;
@@ -869,8 +870,7 @@ __global__ void k_ht_build(const TK* __restrict__ key, const TV* __restrict__ va
 constexpr int kPrbBuf = 256;
 template <typename TK>
 __global__ void __launch_bounds__(256) k_ht_probe(const TK* __restrict__ pkey, i64 n,
-                                                  const i64* __restrict__ keys,
-                                                  const i64* __restrict__ vals, int log2cap,
+                                                  const longlong2* __restrict__ slots, int log2cap,
                                                   const i64* meta, i64* __restrict__ out_row,
                                                   i64* __restrict__ out_val, i64 cap,
                                                   u64* d_count) {
@@ -908,20 +908,20 @@ __global__ void __launch_bounds__(256) k_ht_probe(const TK* __restrict__ pkey, i
       s[h] = slot_hash(k[h]) & mask;
     }
     while (__any_sync(kFull, active[0] || active[1])) {
-      i64 kk[2];
+      longlong2 kv[2];  // {key, value} of each row's current slot
 #pragma unroll
-      for (int h = 0; h < 2; ++h) kk[h] = active[h] ? __ldg(keys + s[h]) : kEmpty;
+      for (int h = 0; h < 2; ++h) kv[h] = active[h] ? __ldg(slots + s[h]) : make_longlong2(kEmpty, 0);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         bool emit = false;
         i64 v = 0;
         if (active[h]) {
-          if (kk[h] == kEmpty) {
+          if (kv[h].x == kEmpty) {
             active[h] = false;
           } else {
-            if (kk[h] == k[h]) {
+            if (kv[h].x == k[h]) {
               emit = true;
-              v = __ldg(vals + s[h]);
+              v = kv[h].y;
               if (!dup) active[h] = false;
             }
             s[h] = (s[h] + 1) & mask;
@@ -1620,11 +1620,11 @@ pq_status pq_join_build(pq_ctx* ctx, pq_col key, pq_col val, float load_factor, 
     return pqh::fail(ctx, PQ_ERR_BUDGET, "pq_join_build: table of %lld slots", (long long)cap);
   }
   ht->meta = (i64*)ht->block;
-  ht->keys = (i64*)((char*)ht->block + 256);
-  ht->vals = ht->keys + cap;
+  ht->keys = (i64*)((char*)ht->block + 256);  // {key, value} per slot
+  ht->vals = ht->keys + 1;
   ht->log2cap = log2cap;
   ht->n = key.n;
-  pq_status st = pqh::fill_i64(ctx, ht->keys, cap, kEmpty, s);
+  pq_status st = pqh::fill_i64(ctx, ht->keys, 2 * cap, kEmpty, s);
   if (st == PQ_OK && cudaMemsetAsync(ht->meta, 0, 256, s) != cudaSuccess)
     st = pqh::fail(ctx, PQ_ERR_CUDA, "memset");
   if (st == PQ_OK && key.n > 0) {
@@ -1632,12 +1632,12 @@ pq_status pq_join_build(pq_ctx* ctx, pq_col key, pq_col val, float load_factor, 
     PQ_DISPATCH_T(key.type, TK, {
       if (!val.data) {
         k_ht_build<TK, long long><<<grid, 256, 0, s>>>((const TK*)key.data, nullptr, key.n,
-                                                       ht->keys, ht->vals, log2cap, ht->meta,
+                                                       ht->keys, log2cap, ht->meta,
                                                        ctx->d_status);
       } else {
         PQ_DISPATCH_T(val.type, TV, {
           k_ht_build<TK, TV><<<grid, 256, 0, s>>>((const TK*)key.data, (const TV*)val.data,
-                                                  key.n, ht->keys, ht->vals, log2cap, ht->meta,
+                                                  key.n, ht->keys, log2cap, ht->meta,
                                                   ctx->d_status);
         });
       }
@@ -1666,8 +1666,9 @@ pq_status pq_join_probe(pq_ctx* ctx, const pq_ht* ht, pq_col probe_key, int64_t*
   PQ_DISPATCH_T(probe_key.type, TK, {
     static const int occ = std::max(1, resident_blocks256((const void*)k_ht_probe<TK>));
     const int grid = (int)std::min<i64>((probe_key.n + 511) / 512, (i64)ctx->num_sms * occ);
-    k_ht_probe<TK><<<grid, 256, 0, s>>>((const TK*)probe_key.data, probe_key.n, ht->keys,
-                                        ht->vals, ht->log2cap, ht->meta, (i64*)out_probe_row,
+    k_ht_probe<TK><<<grid, 256, 0, s>>>((const TK*)probe_key.data, probe_key.n,
+                                        (const longlong2*)ht->keys, ht->log2cap, ht->meta,
+                                        (i64*)out_probe_row,
                                         (i64*)out_build_val, cap, (u64*)d_count);
   });
   PQ_LAUNCHED(ctx);
