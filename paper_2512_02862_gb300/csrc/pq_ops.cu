@@ -636,34 +636,39 @@ struct TmaCols {
   int buf_bytes;                // bytes of one buffer
 };
 
-__host__ __device__ inline size_t tma_smem(int P, int buf_bytes) {
+// SUB: rows of a sub-tile (2048, or 4096 where many buckets would leave
+// runs of about two rows per bucket and sub-tile).
+__host__ __device__ inline size_t tma_smem(int P, int buf_bytes, int sub) {
   return 16                          // two mbarriers
          + 2 * (size_t)buf_bytes     // double-buffered sub-tile
          + (size_t)P * 8             // s_gb
-         + (size_t)8 * P * 2         // s_cnt (u16: at most kSubWarpRows per warp)
+         + (size_t)8 * P * 2         // s_cnt (u16: at most sub / 8 per warp)
          + (size_t)P * 2 * 2         // s_run, s_tot (u16)
-         + (size_t)kSub * 2 * 2;     // s_inv, s_sbk
+         + (size_t)sub * 2 * 2;      // s_inv, s_sbk
 }
 
-// One column of a sub-tile, written in sorted order: sorted place
-// i = j * 256 + thread takes the buffered row src[j] to output row drow[j]
-// (both worked out once for all columns).
-template <typename V>
+// One column of a sub-tile of SUB rows, written in sorted order: sorted
+// place i = j * 256 + thread takes the buffered row src[j] to output row
+// drow[j] (both worked out once for all columns).
+template <typename V, int SUB>
 __device__ __forceinline__ void gather_column(const char* buf, int off, V* __restrict__ dst,
                                               int cnt, const unsigned short* src,
                                               const i64* drow) {
   const V* col = reinterpret_cast<const V*>(buf + off);
-  constexpr int kPer = kSub / 256;
+  constexpr int kPer = SUB / 256;
 #pragma unroll
   for (int j = 0; j < kPer; ++j)
     if (j * 256 + (int)threadIdx.x < cnt) __stcs(dst + drow[j], col[src[j]]);
 }
 
-template <typename T>
+template <typename T, int SUB>
 __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
                                                           const i64* __restrict__ gofs,
                                                           TmaCols tc, i64* d_offsets,
                                                           i64 spin_limit, DevStatus* st) {
+  constexpr int kWRows = SUB / 8;  // rows of a warp in a sub-tile
+  constexpr int kSteps = kWRows / 32;
+  static_assert(kWRows <= 512, "place takes 9 bits");
   extern __shared__ __align__(16) unsigned char smem[];
   const int P = 1 << log2P;
   u64* bar = reinterpret_cast<u64*>(smem);
@@ -673,11 +678,11 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
   unsigned short* s_run = s_cnt + 8 * P;
   unsigned short* s_tot = s_run + P;
   unsigned short* s_inv = s_tot + P;
-  unsigned short* s_sbk = s_inv + kSub;
+  unsigned short* s_sbk = s_inv + SUB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const i64 g = gridDim.x, k = blockIdx.x;
   const i64 r0 = chunk_begin(n, g, k), r1 = chunk_begin(n, g, k + 1);
-  const i64 nsub = (r1 - r0 + kSub - 1) / kSub;
+  const i64 nsub = (r1 - r0 + SUB - 1) / SUB;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -694,8 +699,8 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
   // possibly the last sub-tile's tail, which the block loads itself).
   auto issue = [&](i64 j) {
     if (threadIdx.x != 0 || j >= nsub) return;
-    const i64 r = r0 + j * kSub;
-    const i64 cnt = min((i64)kSub, r1 - r);
+    const i64 r = r0 + j * SUB;
+    const i64 cnt = min((i64)SUB, r1 - r);
     char* buf = bufs + (j & 1) * (size_t)tc.buf_bytes;
     u32 total = 0;
     for (int c = 0; c < tc.n; ++c) total += (u32)((cnt * tc.es[c]) & ~15LL);
@@ -710,8 +715,8 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
   issue(0);
   issue(1);
   for (i64 j = 0; j < nsub; ++j) {
-    const i64 r = r0 + j * kSub;
-    const int cnt = (int)min((i64)kSub, r1 - r);
+    const i64 r = r0 + j * SUB;
+    const int cnt = (int)min((i64)SUB, r1 - r);
     char* buf = bufs + (j & 1) * (size_t)tc.buf_bytes;
     const bool arrived = mbar_wait(&bar[j & 1], (u32)((j >> 1) & 1), spin_limit);
     if (__syncthreads_or(!arrived)) {  // block-uniform
@@ -723,7 +728,7 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
       return;
     }
     // The tail that is not a whole 16-byte unit (last sub-tile only).
-    for (int c = 0; cnt < kSub && c < tc.n; ++c) {
+    for (int c = 0; cnt < SUB && c < tc.n; ++c) {
       const int es = tc.es[c];
       const int done = (int)(((i64)cnt * es) & ~15LL) / es;
       for (int i = done + (int)threadIdx.x; i < cnt; i += blockDim.x) {
@@ -737,15 +742,15 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
     for (int b = threadIdx.x; b < 8 * P; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
     const T* s_key = reinterpret_cast<const T*>(buf + tc.off[0]);
-    const int nbits = cnt == kSub ? log2P : log2P + 1;  // every lane holds a row?
-    u32 bp[kSubSteps];  // bucket << 9 | place among the warp's rows of that bucket
+    const int nbits = cnt == SUB ? log2P : log2P + 1;  // every lane holds a row?
+    u32 bp[kSteps];  // bucket << 9 | place among the warp's rows of that bucket
 #pragma unroll
-    for (int q = 0; q < kSubSteps; ++q) {
-      const int i = warp * kSubWarpRows + q * 32 + lane;
+    for (int q = 0; q < kSteps; ++q) {
+      const int i = warp * kWRows + q * 32 + lane;
       bp[q] = i < cnt ? fib_bucket((i64)s_key[i], log2P) : 0xFFFFFFFFu;
     }
 #pragma unroll
-    for (int q = 0; q < kSubSteps; ++q) {
+    for (int q = 0; q < kSteps; ++q) {
       const bool valid = bp[q] != 0xFFFFFFFFu;
       const u32 b = bp[q];
       const u32 peers = bucket_peers(valid ? b : (1u << log2P), nbits);
@@ -787,17 +792,17 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kSubSteps; ++q) {
+    for (int q = 0; q < kSteps; ++q) {
       if (bp[q] == 0xFFFFFFFFu) continue;
       const u32 b = bp[q] >> 9;
-      const int i = warp * kSubWarpRows + q * 32 + lane;
+      const int i = warp * kWRows + q * 32 + lane;
       const u32 at = s_run[b] + s_cnt[warp * P + b] + (bp[q] & 511u);
       s_inv[at] = (unsigned short)i;
       s_sbk[at] = (unsigned short)b;
     }
     __syncthreads();
     // This thread's sorted places: their rows in the buffer and output rows.
-    constexpr int kPer = kSub / 256;
+    constexpr int kPer = SUB / 256;
     unsigned short src[kPer];
     i64 drow[kPer];
 #pragma unroll
@@ -812,11 +817,11 @@ __global__ void __launch_bounds__(256) k_part_scatter_tma(i64 n, int log2P,
     }
     for (int c = 0; c < tc.n; ++c) {
       if (tc.es[c] == 8)
-        gather_column<i64>(buf, tc.off[c], static_cast<i64*>(tc.dst[c]), cnt, src, drow);
+        gather_column<i64, SUB>(buf, tc.off[c], static_cast<i64*>(tc.dst[c]), cnt, src, drow);
       else if (tc.es[c] == 4)
-        gather_column<int>(buf, tc.off[c], static_cast<int*>(tc.dst[c]), cnt, src, drow);
+        gather_column<int, SUB>(buf, tc.off[c], static_cast<int*>(tc.dst[c]), cnt, src, drow);
       else
-        gather_column<signed char>(buf, tc.off[c], static_cast<signed char*>(tc.dst[c]), cnt,
+        gather_column<signed char, SUB>(buf, tc.off[c], static_cast<signed char*>(tc.dst[c]), cnt,
                                    src, drow);
     }
     __syncthreads();
@@ -1527,22 +1532,31 @@ pq_status pq_partition(pq_ctx* ctx, pq_col key, const pq_col* payload, int npay,
       tc.es[1 + j] = (int)pqh::dtype_size(payload[j].type);
       aligned = aligned && ((uintptr_t)payload[j].data & 15) == 0;
     }
-    int off = 0;
-    for (int c = 0; c < tc.n; ++c) tc.off[c] = off, off += kSub * tc.es[c];
-    tc.buf_bytes = off;
-    const size_t smem_tma = tma_smem(P, tc.buf_bytes);
+    // Sub-tiles of 4096 rows from 512 buckets on (when they fit), so that a
+    // bucket's run in a sub-tile fills its sectors; 2048 otherwise.
+    auto layout = [&](int sub) {
+      int off = 0;
+      for (int c = 0; c < tc.n; ++c) tc.off[c] = off, off += sub * tc.es[c];
+      tc.buf_bytes = off;
+      return tma_smem(P, tc.buf_bytes, sub);
+    };
+    int sub = log2P >= 9 ? 4096 : kSub;
+    size_t smem_tma = layout(sub);
+    if (smem_tma > 200 * 1024 && sub != kSub) smem_tma = layout(sub = kSub);
     const bool use_tma = aligned && smem_tma <= 200 * 1024;
     const size_t smem = use_tma ? smem_tma : staged_smem(P);
+    const i64 rows_sub = use_tma ? sub : kSub;
     int occ = 1;
     PQ_DISPATCH_T(key.type, T, {
-      const void* fn = use_tma ? (const void*)k_part_scatter_tma<T>
-                               : (const void*)k_part_scatter_blk<T>;
+      const void* fn = !use_tma      ? (const void*)k_part_scatter_blk<T>
+                       : sub == 4096 ? (const void*)k_part_scatter_tma<T, 4096>
+                                     : (const void*)k_part_scatter_tma<T, kSub>;
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem) != cudaSuccess)
         occ = 1;
     });
     cudaGetLastError();
-    const i64 g = std::max<i64>(1, std::min<i64>((n + kSub - 1) / kSub,
+    const i64 g = std::max<i64>(1, std::min<i64>((n + rows_sub - 1) / rows_sub,
                                                  (i64)ctx->num_sms * std::max(occ, 1)));
     const i64 m = g * P;
     const i64 stiles = (m + 4095) / 4096;
@@ -1564,8 +1578,11 @@ pq_status pq_partition(pq_ctx* ctx, pq_col key, const pq_col* payload, int npay,
       k_scan_u32<<<(unsigned)std::min<i64>(stiles, (i64)ctx->num_sms * 4), 256, 0, s>>>(
           hist, m, gofs, (u64*)(w + 256), (u32*)w, ctx->opt.spin_limit, ctx->d_status);
       PQ_LAUNCHED(ctx);
-      if (use_tma)
-        k_part_scatter_tma<T><<<(unsigned)g, 256, smem, s>>>(
+      if (use_tma && sub == 4096)
+        k_part_scatter_tma<T, 4096><<<(unsigned)g, 256, smem, s>>>(
+            n, log2P, gofs, tc, (i64*)d_offsets, ctx->opt.spin_limit, ctx->d_status);
+      else if (use_tma)
+        k_part_scatter_tma<T, kSub><<<(unsigned)g, 256, smem, s>>>(
             n, log2P, gofs, tc, (i64*)d_offsets, ctx->opt.spin_limit, ctx->d_status);
       else
         k_part_scatter_blk<T><<<(unsigned)g, 256, smem, s>>>((const T*)key.data, n, log2P, gofs,

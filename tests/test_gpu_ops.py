@@ -109,11 +109,12 @@ def test_partition_matches_oracle(ctx, stream, kt, log2P, n):
     assert np.array_equal(ow.cpu().numpy()[:n], ww)
 
 
-@pytest.mark.parametrize("log2P", [3, 10])
+@pytest.mark.parametrize("log2P", [3, 9, 10])
 @pytest.mark.parametrize("dist", ["uniform", "one-hot"])
 def test_partition_large_and_skewed(ctx, stream, log2P, dist):
-    """Several sub-tiles per block and a ragged tail; with one-hot keys most
-    rows fall in one bucket (a run spanning whole sub-tiles)."""
+    """Several sub-tiles per block and a ragged tail (sub-tiles of 4096 rows
+    from 512 buckets on, 2048 below); with one-hot keys most rows fall in
+    one bucket (a run spanning whole sub-tiles)."""
     n = 3_000_017
     rng = np.random.default_rng(log2P)
     keys = rng.integers(-2**62, 2**62, size=n).astype(np.int64)
